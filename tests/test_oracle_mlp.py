@@ -1,0 +1,96 @@
+"""Pins for the learned-guess oracle: central finite differences of the loss, the Adam
+first-step property (bias correction makes the first update lr*g/(|g|+eps)), block
+round trips and the validity checks on a converged density."""
+import numpy as np
+import pytest
+
+from oracle import mlp
+
+
+def small_problem(seed=0, n=24):
+    rng = np.random.default_rng(seed)
+    X = rng.standard_normal((n, mlp.NIN))
+    Y = 0.2 * rng.standard_normal((n, mlp.NOUT))
+    return X, Y
+
+
+def test_backward_matches_central_differences():
+    params = mlp.init_params(1)
+    X, Y = small_problem()
+    loss, grads = mlp.loss_and_grad(params, X, Y)
+    rng = np.random.default_rng(9)
+    h = 1e-6
+    for li, p in enumerate(params):
+        for _ in range(6):
+            idx = tuple(rng.integers(0, s) for s in p.shape)
+            old = p[idx]
+            p[idx] = old + h
+            lp, _ = mlp.loss_and_grad(params, X, Y)
+            p[idx] = old - h
+            lm, _ = mlp.loss_and_grad(params, X, Y)
+            p[idx] = old
+            fd = (lp - lm) / (2 * h)
+            assert grads[li][idx] == pytest.approx(fd, rel=1e-5, abs=1e-10), (li, idx)
+
+
+def test_adam_first_step_is_sign_step():
+    params = [np.array([1.0, -2.0, 0.5])]
+    g = [np.array([0.3, -4.0, 1e-3])]
+    opt = mlp.Adam(params, lr=1e-2)
+    before = params[0].copy()
+    opt.step(params, g)
+    expect = before - 1e-2 * g[0] / (np.abs(g[0]) + 1e-8)
+    assert np.allclose(params[0], expect, rtol=1e-12)
+
+
+def test_adam_minimises_quadratic():
+    p = [np.array([3.0, -1.0])]
+    opt = mlp.Adam(p, lr=0.05)
+    for _ in range(2000):
+        opt.step(p, [2 * p[0]])
+    assert np.max(np.abs(p[0])) < 1e-2
+
+
+def test_training_reduces_loss():
+    params = mlp.init_params(2)
+    X, Y = small_problem(3, 64)
+    opt = mlp.Adam(params, lr=1e-3)
+    l0, _ = mlp.loss_and_grad(params, X, Y)
+    for _ in range(200):
+        _, g = mlp.loss_and_grad(params, X, Y)
+        opt.step(params, g)
+    l1, _ = mlp.loss_and_grad(params, X, Y)
+    assert l1 < 0.2 * l0
+
+
+def test_features_symmetric_and_cutoff():
+    xyz = np.array([[0, 0, 0], [1.5, 0, 0], [0, 13.0, 0]], dtype=float)
+    pairs, f = mlp.pair_features(xyz)
+    got = {tuple(p) for p in pairs}
+    # centre 2 is more than 12 bohr from both others: only its diagonal block remains
+    assert got == {(0, 0), (1, 0), (1, 1), (2, 2)}
+    # distance 1.5 peaks in the bin nearest 1.5 bohr
+    k = list(map(tuple, pairs)).index((1, 0))
+    assert np.argmax(f[k, :mlp.NRBF]) == int(round(1.5 / (12 / 31)))
+    assert f[k, -1] == 0.0
+    d = list(map(tuple, pairs)).index((0, 0))
+    assert f[d, -1] == 1.0 and np.all(f[d, :mlp.NRBF] == 0)
+
+
+def test_block_round_trip(c0, c0_scf):
+    pairs, _ = mlp.pair_features(c0.xyz)
+    t = mlp.block_targets(c0_scf.D, pairs)
+    D = mlp.assemble_density(t, pairs, c0.natm)
+    # all pairs of the 6 bohr cube are within the cutoff, and converged blocks of a
+    # symmetric D need not be symmetric, so compare the symmetrised blocks
+    for (a, b) in pairs[:50]:
+        blk = c0_scf.D[5 * a:5 * a + 5, 5 * b:5 * b + 5]
+        assert np.allclose(D[5 * a:5 * a + 5, 5 * b:5 * b + 5], 0.5 * (blk + blk.T))
+
+
+def test_validity_checks(c0_system, c0_scf):
+    assert mlp.guess_is_valid(c0_scf.D, c0_system.S, c0_system.nelec)
+    assert not mlp.guess_is_valid(1.3 * c0_scf.D, c0_system.S, c0_system.nelec)
+    bad = c0_scf.D + 0.5 * np.random.default_rng(0).standard_normal(c0_scf.D.shape)
+    bad = 0.5 * (bad + bad.T)
+    assert not mlp.guess_is_valid(bad, c0_system.S, c0_system.nelec)
