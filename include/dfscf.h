@@ -1,0 +1,198 @@
+/*
+ * dfscf.h - C ABI of the GB300 (sm_103a) density-fitted Hartree-Fock library.
+ *
+ * Method: density fitting of the four-centre Coulomb integrals as stated in
+ * arXiv 2506.06661, Section "Density fitting":
+ *     (mn|kl) ~ sum_P T_{P,mn} T_{P,kl},   M_PQ = (chi_P|chi_Q) = L L^T,
+ *     T_{P,mn} = sum_Q (L^-1)_{PQ} (chi_Q|mn)                 (this library calls T "B"),
+ * used to build the Coulomb matrix J = sum_P B_P (B_P . D) and the exchange matrix
+ * K = sum_P (B_P C)(B_P C)^T inside a restricted Hartree-Fock SCF loop with DIIS.
+ * The get_jk call shape (J and K for a given density) follows the paper's description
+ * of get_jk in PySCF and GPU4PySCF (Sections "PySCF" and "GPU4PySCF").
+ *
+ * Basis: s-type primitives phi_a(r) = N_a exp(-a |r - A|^2), N_a = (2a/pi)^(3/4), for
+ * both the orbital and the auxiliary set.  Orbital pairs are packed m >= n with
+ * index mn = m(m+1)/2 + n; npair = nao(nao+1)/2.
+ *
+ * Conventions for every call:
+ *   - all matrices are row-major; all array arguments are DEVICE pointers unless the
+ *     parameter is documented as host memory;
+ *   - the caller owns every buffer.  Calls that need scratch take (work, work_bytes);
+ *     the matching *_work_bytes() query gives the size.  The library never allocates
+ *     device memory;
+ *   - every call is asynchronous on stream `s` unless documented otherwise; results are
+ *     valid once the stream has synchronised;
+ *   - every call returns DF_OK or one of the error codes below and, on error, records a
+ *     thread-local message readable with df_last_error().  Argument errors are detected
+ *     on the host before anything is launched.
+ *   - there is no CPU fallback: a missing or failing GPU yields DF_ERR_CUDA.
+ */
+#ifndef DFSCF_H
+#define DFSCF_H
+
+#include <stddef.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------------------- */
+#define DF_OK 0
+#define DF_ERR_ARG 1         /* null pointer, bad size, workspace too small, ...        */
+#define DF_ERR_CUDA 2        /* a CUDA runtime call or kernel launch failed             */
+#define DF_ERR_NOT_SPD 3     /* Cholesky pivot <= tol * max diagonal                    */
+#define DF_ERR_NOCONV 4      /* SCF did not converge within max_cycle                   */
+#define DF_ERR_TIMEOUT 5     /* a bounded device-side wait gave up                      */
+#define DF_ERR_NOMEM 6       /* the caller's buffer is smaller than the query says      */
+#define DF_ERR_NUMERIC 7     /* NaN/Inf detected in an SCF quantity                     */
+
+/* ---- precision modes -------------------------------------------------------------- */
+#define DF_FP64 0            /* every contraction in FP64                               */
+#define DF_MIXED 1           /* K contractions as split-BF16 x3 on tcgen05 tensor cores
+                                (hi = RN_bf16(x), lo = RN_bf16(x - hi); products
+                                hi*hi + hi*lo + lo*hi, FP32 accumulation), J in FP32
+                                with FP64 reduction                                       */
+
+/* Message describing the last error on the calling thread ("" if none). */
+const char* df_last_error(void);
+
+/* Library version, major*10000 + minor*100 + patch. */
+int df_version(void);
+
+/* ---- a1: Boys function -------------------------------------------------------------
+ * out[i] = F0(t[i]) = int_0^1 exp(-t u^2) du for n values (t >= 0).  The order-zero
+ * Boys function is the radial factor of every s-type Coulomb integral implied by the
+ * paper's DF integrals (chi_P|chi_Q) and (chi_Q|mn).  One GPU lane per value.        */
+int df_boys_f0(const double* t, long n, double* out, cudaStream_t s);
+
+/* ---- one-electron integrals ---------------------------------------------------------
+ * S, T, V (each [nao][nao]; any may be NULL) for s primitives at ao_xyz [nao][3] with
+ * exponents ao_exp [nao]; V sums the attraction of natm point nuclei nuc_xyz [natm][3]
+ * with charges nuc_z [natm].  Products of primitives use the Gaussian product theorem
+ * of the paper's overlap example (Section "Numba JIT compilation").                  */
+int df_int1e(const double* ao_xyz, const double* ao_exp, int nao, const double* nuc_xyz,
+             const double* nuc_z, int natm, double* S, double* T, double* V, cudaStream_t s);
+
+/* Nuclear repulsion sum_{A<B} Z_A Z_B / R_AB of natm nuclei, written to the device
+ * double *e_nuc.                                                                      */
+int df_nuclear_repulsion(const double* nuc_xyz, const double* nuc_z, int natm, double* e_nuc,
+                         cudaStream_t s);
+
+/* ---- a2: Coulomb metric and its Cholesky factor ------------------------------------
+ * M_PQ = (chi_P|chi_Q) for naux auxiliary s primitives, then M = L L^T
+ * (Section "Density fitting", metric equation).  L is [naux][naux], lower triangle
+ * filled, strict upper triangle set to zero.  Optionally M is also written to M_out
+ * ([naux][naux], may be NULL).
+ * Synchronises the stream once to read the pivot status.  If a pivot is <= 1e-14 times
+ * the largest diagonal element of M, returns DF_ERR_NOT_SPD and stores the 0-based
+ * pivot index in the HOST int *bad_pivot (otherwise *bad_pivot = -1).
+ * work: df_metric_chol_work_bytes(naux) bytes.                                         */
+size_t df_metric_chol_work_bytes(int naux);
+int df_metric_chol(const double* aux_xyz, const double* aux_exp, int naux, double* L, double* M_out,
+                   int* bad_pivot, void* work, size_t work_bytes, cudaStream_t s);
+
+/* ---- a3 + a4: three-centre integrals and whitening ---------------------------------
+ * B_{P,mn} = sum_Q (L^-1)_{PQ} (chi_Q|mn) for all packed pairs (Section "Density
+ * fitting", whitened three-index tensor), computed in FP64 by blocked forward
+ * substitution.  B is one caller-owned buffer of df_B_bytes(nao, naux, precision) bytes
+ * holding, in this order:
+ *   [0]  FP64 packed rows: naux rows of df_B_ld(nao) doubles, entry mn at m(m+1)/2+n,
+ *        padding zero;
+ *   [1]  (DF_MIXED only) FP32 copy of [0], same row layout;
+ *   [2]  (DF_MIXED only) BF16 hi and lo planes of the full symmetric B_P, each
+ *        naux x npad x npad with npad = df_nao_pad(nao), padding zero.
+ * L is the factor from df_metric_chol.  work: df_build_B_work_bytes(...) bytes.         */
+long df_B_ld(int nao);
+int df_nao_pad(int nao);
+size_t df_B_bytes(int nao, int naux, int precision);
+size_t df_build_B_work_bytes(int nao, int naux);
+int df_build_B(const double* ao_xyz, const double* ao_exp, int nao, const double* aux_xyz,
+               const double* aux_exp, int naux, const double* L, int precision, void* B,
+               size_t B_bytes, void* work, size_t work_bytes, cudaStream_t s);
+
+/* Copy the FP64 packed row P of B (npair doubles) to `row` (device).  For tests.      */
+int df_B_get_packed(const void* B, int nao, int naux, int P, double* row, cudaStream_t s);
+
+/* ---- a5..a8: Coulomb and exchange matrices ------------------------------------------
+ * J[D]_mn = sum_P d_P B_{P,mn}, d_P = sum_{kl} B_{P,kl} D_kl   (J = sum_P B_P (B_P . D))
+ * K_mn    = sum_P sum_i (B_P C)_{mi} (B_P C)_{ni}               (K = K[C C^T])
+ * D: [nao][nao] symmetric density; C: [nao][nocc] occupied coefficients.  For an RHF
+ * density D = 2 C C^T the Fock matrix is F = h + J - K.  J or K may be NULL to skip it
+ * (then D or C may be NULL too).  precision DF_MIXED requires B built with DF_MIXED.
+ * work: df_jk_work_bytes(nao, naux, nocc, precision) bytes.                           */
+size_t df_jk_work_bytes(int nao, int naux, int nocc, int precision);
+int df_jk(const void* B, int nao, int naux, int precision, const double* D, const double* C,
+          int nocc, double* J, double* K, void* work, size_t work_bytes, cudaStream_t s);
+
+/* ---- a11: symmetric eigensolver ----------------------------------------------------
+ * Eigenvalues w[0..n) ascending and eigenvectors (columns of Z, [n][n]) of the
+ * symmetric matrix A [n][n] (A is overwritten).  Householder tridiagonalisation and
+ * implicit QL.  work: df_eigh_work_bytes(n).                                           */
+size_t df_eigh_work_bytes(int n);
+int df_eigh(double* A, int n, double* w, double* Z, void* work, size_t work_bytes, cudaStream_t s);
+
+/* ---- a9..a12: restricted Hartree-Fock SCF --------------------------------------------
+ * Mean-field DF-RHF ("density_fit()" mean-field in the paper's DF section) with Pulay
+ * DIIS (named as PySCF's default accelerator in the paper's SOSCF section):
+ *   F = h + J[D] - 1/2 K[D],  E = 1/2 tr(D (h + F)) + E_nuc,
+ *   e = X^T (F D S - S D F) X with canonical orthogonalisation X = U s^-1/2 (s > lindep),
+ *   extrapolation over <= diis_space vectors, aufbau occupation of nocc = nelec/2.
+ * Converged when |dE| < conv_tol and max|e| < conv_err.  In DF_MIXED mode the loop runs
+ * with mixed-precision J/K until |dE| < switch_tol or max|e| < switch_err, then at least
+ * n_fp64_final FP64 iterations follow and the reported energy is the FP64 one.
+ * dm0 (device [nao][nao], may be NULL): initial density; it need not be idempotent nor
+ * have the right electron count (paper, Section "Initial Guess for Mean-field Methods").
+ * If dm0 fails the checks |tr(dm0 S) - nelec| / nelec < 0.05 and
+ * ||dm0 S dm0 - 2 dm0||_F / ||dm0||_F < 0.5 the core-Hamiltonian guess is used instead.
+ * Outputs (device, may be NULL): D_out [nao][nao], C_out [nao][nocc], mo_energy [nocc+1].
+ * res is HOST memory.  The host loop reads one small status block per iteration.       */
+typedef struct {
+  int natm;
+  const double* xyz;      /* [natm][3] */
+  const double* charges;  /* [natm]    */
+  int nao;
+  const double* ao_xyz;   /* [nao][3]  */
+  const double* ao_exp;   /* [nao]     */
+  int naux;
+  const double* aux_xyz;  /* [naux][3] */
+  const double* aux_exp;  /* [naux]    */
+  int nelec;              /* even */
+} df_molecule;
+
+typedef struct {
+  int precision;      /* DF_FP64 or DF_MIXED                  (default DF_FP64) */
+  int diis_space;     /* DIIS history length                   (8)              */
+  int max_cycle;      /* Fock builds before DF_ERR_NOCONV      (100)            */
+  int n_fp64_final;   /* FP64 iterations after the mixed phase (2)              */
+  double conv_tol;    /* |dE| threshold                         (1e-8)          */
+  double conv_err;    /* max|e| threshold                       (1e-5)          */
+  double lindep;      /* canonical orthogonalisation cut        (1e-8)          */
+  double switch_tol;  /* mixed -> FP64 switch on |dE|           (1e-7)          */
+  double switch_err;  /* mixed -> FP64 switch on max|e|         (1e-4)          */
+  int verbose;        /* print one line per iteration to stdout (0)             */
+} scf_opts;
+
+typedef struct {
+  double energy;        /* total energy (Hartree)                                 */
+  double e_nuc;         /* nuclear repulsion                                      */
+  double homo, lumo;    /* orbital energies of the last diagonalisation           */
+  double last_de;       /* |dE| of the final iteration                            */
+  double last_err;      /* max|e| of the final iteration                          */
+  int iterations;       /* Fock builds in total                                   */
+  int fp64_iterations;  /* Fock builds done in FP64                               */
+  int converged;        /* 1 if both thresholds were met                          */
+  int guess;            /* 0 core guess, 1 dm0 used, 2 dm0 rejected -> core guess */
+  int nmo;              /* orbitals kept by canonical orthogonalisation           */
+} scf_result;
+
+void scf_default_opts(scf_opts* opt);
+size_t scf_work_bytes(int nao, int naux, int nocc, int precision);
+int scf_run(const df_molecule* mol, const scf_opts* opt, const double* dm0, double* D_out,
+            double* C_out, double* mo_energy, scf_result* res, void* work, size_t work_bytes,
+            cudaStream_t s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DFSCF_H */

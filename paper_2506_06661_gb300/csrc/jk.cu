@@ -1,0 +1,448 @@
+// Whitened three-index tensor B and the DF Coulomb / exchange builds
+// (arXiv 2506.06661, Section "Density fitting"):
+//   B_{P,mn} = sum_Q (L^-1)_{PQ} (Q|mn)
+//   J_mn = sum_P d_P B_{P,mn},  d_P = sum_{kl} B_{P,kl} D_kl       (J = sum_P B_P (B_P . D))
+//   K_mn = sum_P sum_i X_{P,mi} X_{P,ni},  X_P = B_P C
+//
+// B layout (one caller-owned buffer):
+//   FP64 packed rows   naux x ld doubles,   ld = npair rounded up to 32 (256-byte rows)
+//   FP32 packed rows   naux x ld floats     (mixed mode)
+//   BF16 hi, lo planes naux x npad x npad   (mixed mode; full symmetric B_P, npad = nao
+//                                            rounded up to 128, zero padding)
+// J streams the packed rows (each symmetric pair stored once, weight 2 off the diagonal);
+// the mixed K reads the BF16 planes through TMA as plain K-major GEMM operands.
+#include <cuda_bf16.h>
+
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace dfscf {
+
+long B_ld(int nao) { return (long)align_up((size_t)npair_of(nao), 32); }
+int nao_pad(int nao) { return (int)align_up((size_t)nao, 128); }
+
+BLayout B_layout(int nao, int naux, int precision) {
+  BLayout L{};
+  L.ld = B_ld(nao);
+  L.npad = nao_pad(nao);
+  size_t off = 0;
+  L.off64 = off;
+  off += align_up(sizeof(double) * (size_t)naux * L.ld, 256);
+  if (precision == DF_MIXED) {
+    L.off32 = off;
+    off += align_up(sizeof(float) * (size_t)naux * L.ld, 256);
+    L.offhi = off;
+    off += align_up(sizeof(__nv_bfloat16) * (size_t)naux * L.npad * L.npad, 256);
+    L.offlo = off;
+    off += align_up(sizeof(__nv_bfloat16) * (size_t)naux * L.npad * L.npad, 256);
+  }
+  L.bytes = off;
+  return L;
+}
+
+// ---- mixed-precision copies of B ----------------------------------------------------
+__global__ void b_to_fp32_kernel(const double* __restrict__ B64, float* __restrict__ B32, size_t n) {
+  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) B32[i] = (float)B64[i];
+}
+
+// hi = RN_bf16(x), lo = RN_bf16(x - hi), written for both (m,n) and (n,m) of row P.
+__global__ void b_to_split_bf16_kernel(const double* __restrict__ B64, long ld, int nao, int npad,
+                                       __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo) {
+  int P = blockIdx.y;
+  long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long)npad * npad) return;
+  int m = (int)(e / npad), n = (int)(e % npad);
+  double x = 0.0;
+  if (m < nao && n < nao) {
+    int a = max(m, n), b = min(m, n);
+    x = B64[(size_t)P * ld + (size_t)a * (a + 1) / 2 + b];
+  }
+  __nv_bfloat16 h = __double2bfloat16(x);
+  __nv_bfloat16 l = __double2bfloat16(x - (double)__bfloat162float(h));
+  size_t o = (size_t)P * npad * npad + e;
+  hi[o] = h;
+  lo[o] = l;
+}
+
+// ---- J --------------------------------------------------------------------------------
+// Dw_mn = w_mn D_mn for packed m >= n (w = 2 off the diagonal, 1 on it); padding zero.
+template <typename T>
+__global__ void weighted_packed_density_kernel(const double* __restrict__ D, int nao, long npair, long ld,
+                                               T* __restrict__ Dw) {
+  long ij = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (ij >= ld) return;
+  if (ij >= npair) {
+    Dw[ij] = (T)0;
+    return;
+  }
+  int m, n;
+  unpack_pair(ij, m, n);
+  double w = (m == n) ? 1.0 : 2.0;
+  Dw[ij] = (T)(w * 0.5 * (D[(size_t)m * nao + n] + D[(size_t)n * nao + m]));
+}
+
+// d_P = sum_ij B[P][ij] Dw[ij]; one CTA per row, 128-bit loads.
+__global__ void __launch_bounds__(512) jpass1_fp64_kernel(const double* __restrict__ B, long ld,
+                                                          const double* __restrict__ Dw, double* __restrict__ d) {
+  __shared__ double sh[16];
+  const double2* row = reinterpret_cast<const double2*>(B + (size_t)blockIdx.x * ld);
+  const double2* dw = reinterpret_cast<const double2*>(Dw);
+  long n2 = ld / 2;
+  double acc0 = 0.0, acc1 = 0.0;
+  long i = threadIdx.x;
+  for (; i + 3 * 512 < n2; i += 4 * 512) {
+    double2 b0 = __ldcs(row + i), b1 = __ldcs(row + i + 512), b2 = __ldcs(row + i + 1024), b3 = __ldcs(row + i + 1536);
+    double2 w0 = dw[i], w1 = dw[i + 512], w2 = dw[i + 1024], w3 = dw[i + 1536];
+    acc0 = fma(b0.x, w0.x, acc0); acc1 = fma(b0.y, w0.y, acc1);
+    acc0 = fma(b1.x, w1.x, acc0); acc1 = fma(b1.y, w1.y, acc1);
+    acc0 = fma(b2.x, w2.x, acc0); acc1 = fma(b2.y, w2.y, acc1);
+    acc0 = fma(b3.x, w3.x, acc0); acc1 = fma(b3.y, w3.y, acc1);
+  }
+  for (; i < n2; i += 512) {
+    double2 b0 = __ldcs(row + i), w0 = dw[i];
+    acc0 = fma(b0.x, w0.x, acc0); acc1 = fma(b0.y, w0.y, acc1);
+  }
+  double t = block_sum(acc0 + acc1, sh);
+  if (threadIdx.x == 0) d[blockIdx.x] = t;
+}
+
+// Mixed: FP32 products and FP32 partial sums over 8 elements, FP64 accumulation.
+__global__ void __launch_bounds__(512) jpass1_fp32_kernel(const float* __restrict__ B, long ld,
+                                                          const float* __restrict__ Dw, double* __restrict__ d) {
+  __shared__ double sh[16];
+  const float4* row = reinterpret_cast<const float4*>(B + (size_t)blockIdx.x * ld);
+  const float4* dw = reinterpret_cast<const float4*>(Dw);
+  long n4 = ld / 4;
+  double acc = 0.0;
+  long i = threadIdx.x;
+  for (; i + 512 < n4; i += 2 * 512) {
+    float4 b0 = __ldcs(row + i), b1 = __ldcs(row + i + 512);
+    float4 w0 = dw[i], w1 = dw[i + 512];
+    float s = b0.x * w0.x;
+    s = fmaf(b0.y, w0.y, s); s = fmaf(b0.z, w0.z, s); s = fmaf(b0.w, w0.w, s);
+    s = fmaf(b1.x, w1.x, s); s = fmaf(b1.y, w1.y, s); s = fmaf(b1.z, w1.z, s); s = fmaf(b1.w, w1.w, s);
+    acc += (double)s;
+  }
+  for (; i < n4; i += 512) {
+    float4 b0 = __ldcs(row + i), w0 = dw[i];
+    float s = b0.x * w0.x;
+    s = fmaf(b0.y, w0.y, s); s = fmaf(b0.z, w0.z, s); s = fmaf(b0.w, w0.w, s);
+    acc += (double)s;
+  }
+  double t = block_sum(acc, sh);
+  if (threadIdx.x == 0) d[blockIdx.x] = t;
+}
+
+constexpr int JP2_ROWS = 256;  // P rows per split of pass 2
+
+// Jpart[split][ij] = sum_{P in split} d_P B[P][ij]; one lane per two packed columns.
+__global__ void __launch_bounds__(256) jpass2_fp64_kernel(const double* __restrict__ B, long ld, int naux,
+                                                          const double* __restrict__ d, double* __restrict__ Jpart) {
+  __shared__ double sd[JP2_ROWS];
+  int p0 = blockIdx.y * JP2_ROWS;
+  int np = min(JP2_ROWS, naux - p0);
+  for (int i = threadIdx.x; i < np; i += blockDim.x) sd[i] = d[p0 + i];
+  __syncthreads();
+  long c2 = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c2 * 2 >= ld) return;
+  const double2* col = reinterpret_cast<const double2*>(B + (size_t)p0 * ld) + c2;
+  long st = ld / 2;
+  double ax = 0.0, ay = 0.0, bx = 0.0, by = 0.0;
+  int p = 0;
+  for (; p + 1 < np; p += 2) {
+    double2 v0 = __ldcs(col + (size_t)p * st), v1 = __ldcs(col + (size_t)(p + 1) * st);
+    ax = fma(sd[p], v0.x, ax); ay = fma(sd[p], v0.y, ay);
+    bx = fma(sd[p + 1], v1.x, bx); by = fma(sd[p + 1], v1.y, by);
+  }
+  if (p < np) {
+    double2 v0 = __ldcs(col + (size_t)p * st);
+    ax = fma(sd[p], v0.x, ax); ay = fma(sd[p], v0.y, ay);
+  }
+  reinterpret_cast<double2*>(Jpart + (size_t)blockIdx.y * ld)[c2] = make_double2(ax + bx, ay + by);
+}
+
+__global__ void __launch_bounds__(256) jpass2_fp32_kernel(const float* __restrict__ B, long ld, int naux,
+                                                          const double* __restrict__ d, double* __restrict__ Jpart) {
+  __shared__ float sd[JP2_ROWS];
+  int p0 = blockIdx.y * JP2_ROWS;
+  int np = min(JP2_ROWS, naux - p0);
+  for (int i = threadIdx.x; i < np; i += blockDim.x) sd[i] = (float)d[p0 + i];
+  __syncthreads();
+  long c4 = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c4 * 4 >= ld) return;
+  const float4* col = reinterpret_cast<const float4*>(B + (size_t)p0 * ld) + c4;
+  long st = ld / 4;
+  double a[4] = {0, 0, 0, 0};
+  for (int p = 0; p < np; p += 8) {
+    float s[4] = {0.f, 0.f, 0.f, 0.f};
+    int pe = min(np, p + 8);
+    for (int q = p; q < pe; ++q) {
+      float4 v = __ldcs(col + (size_t)q * st);
+      s[0] = fmaf(sd[q], v.x, s[0]); s[1] = fmaf(sd[q], v.y, s[1]);
+      s[2] = fmaf(sd[q], v.z, s[2]); s[3] = fmaf(sd[q], v.w, s[3]);
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) a[k] += (double)s[k];
+  }
+  double* out = Jpart + (size_t)blockIdx.y * ld + c4 * 4;
+  out[0] = a[0]; out[1] = a[1]; out[2] = a[2]; out[3] = a[3];
+}
+
+// J[m][n] = J[n][m] = sum_split Jpart[split][mn].
+__global__ void jreduce_unpack_kernel(const double* __restrict__ Jpart, int nsplit, long ld, int nao,
+                                      double* __restrict__ J) {
+  long ij = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (ij >= (long)nao * (nao + 1) / 2) return;
+  double s = 0.0;
+  for (int k = 0; k < nsplit; ++k) s += Jpart[(size_t)k * ld + ij];
+  int m, n;
+  unpack_pair(ij, m, n);
+  J[(size_t)m * nao + n] = s;
+  J[(size_t)n * nao + m] = s;
+}
+
+// ---- FP64 K ---------------------------------------------------------------------------
+// X[m][P][i] = sum_n B_P[m][n] C[n][i]; B_P gathered from the packed row.
+// CTA tile 64 (m) x 32 (i), 256 lanes with 4 x 2 outputs each.
+__global__ void __launch_bounds__(256) k_halftransform_fp64_kernel(const double* __restrict__ B, long ld, int nao,
+                                                                   int naux, const double* __restrict__ C, int nocc,
+                                                                   double* __restrict__ X) {
+  __shared__ double As[16][65];
+  __shared__ double Cs[16][33];
+  int P = blockIdx.z;
+  int m0 = blockIdx.y * 64, i0 = blockIdx.x * 32;
+  const double* row = B + (size_t)P * ld;
+  int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;  // tx -> i (2 each, stride 16), ty -> m (4 each, stride 16)
+  double acc[4][2] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
+  for (int n0 = 0; n0 < nao; n0 += 16) {
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      int idx = threadIdx.x + 256 * r;
+      int mm = idx >> 4, nn = idx & 15;
+      int gm = m0 + mm, gn = n0 + nn;
+      double v = 0.0;
+      if (gm < nao && gn < nao) {
+        int a = max(gm, gn), b = min(gm, gn);
+        v = row[(size_t)a * (a + 1) / 2 + b];
+      }
+      As[nn][mm] = v;
+    }
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      int idx = threadIdx.x + 256 * r;
+      int nn = idx >> 5, ii = idx & 31;
+      int gn = n0 + nn, gi = i0 + ii;
+      Cs[nn][ii] = (gn < nao && gi < nocc) ? C[(size_t)gn * nocc + gi] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      double a[4], c[2];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) a[u] = As[k][ty + 16 * u];
+      c[0] = Cs[k][tx];
+      c[1] = Cs[k][tx + 16];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        acc[u][0] = fma(a[u], c[0], acc[u][0]);
+        acc[u][1] = fma(a[u], c[1], acc[u][1]);
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    int gm = m0 + ty + 16 * u;
+    if (gm >= nao) continue;
+#pragma unroll
+    for (int v = 0; v < 2; ++v) {
+      int gi = i0 + tx + 16 * v;
+      if (gi < nocc) X[((size_t)gm * naux + P) * nocc + gi] = acc[u][v];
+    }
+  }
+}
+
+// K[m][n] = K[n][m] = sum_split Kpart[split][m][n] over the lower triangle m >= n.
+__global__ void ksum_mirror_kernel(const double* __restrict__ Kpart, int nsplit, int nao, double* __restrict__ K) {
+  long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long)nao * nao) return;
+  int m = (int)(e / nao), n = (int)(e % nao);
+  if (n > m) return;
+  double s = 0.0;
+  for (int k = 0; k < nsplit; ++k) s += Kpart[(size_t)k * nao * nao + e];
+  K[(size_t)m * nao + n] = s;
+  K[(size_t)n * nao + m] = s;
+}
+
+int ksplit_count(int nao, long kdim) {
+  // enough CTAs for ~4 waves on 152 SMs over the lower-triangle tiles
+  long tiles = (long)((nao + 63) / 64) * ((nao + 63) / 64 + 1) / 2;
+  long want = (4L * 152 * 4 + tiles - 1) / tiles;
+  long maxs = max(1L, kdim / 512);
+  return (int)max(1L, min(want, min(maxs, 64L)));
+}
+
+JKWork jk_work_layout(int nao, int naux, int nocc, int precision, Arena* a, Sizer* z) {
+  JKWork w{};
+  long ld = B_ld(nao);
+  int nsplit_j = (naux + JP2_ROWS - 1) / JP2_ROWS;
+  int nsplit_k = ksplit_count(nao, (long)naux * max(nocc, 1));
+  w.nsplit_j = nsplit_j;
+  w.nsplit_k = nsplit_k;
+#define TAKE(T, ptr, count) \
+  if (a) ptr = a->take<T>(count); else z->take<T>(count);
+  TAKE(double, w.Dw, ld);
+  TAKE(float, w.Dw32, ld);
+  TAKE(double, w.d, naux);
+  TAKE(double, w.Jpart, (size_t)nsplit_j * ld);
+  if (precision == DF_FP64) {
+    TAKE(double, w.X, (size_t)nao * naux * max(nocc, 1));
+    TAKE(double, w.Kpart, (size_t)nsplit_k * nao * nao);
+  } else {
+    mixed_k_work_layout(nao, naux, nocc, a, z, &w.mk);
+  }
+#undef TAKE
+  return w;
+}
+
+int build_J(const void* Bbuf, const BLayout& L, int nao, int naux, int precision, const double* D, double* J,
+            const JKWork& w, cudaStream_t s) {
+  long npair = npair_of(nao), ld = L.ld;
+  const char* base = (const char*)Bbuf;
+  unsigned g = (unsigned)((ld + 255) / 256);
+  unsigned gp = (unsigned)((npair + 255) / 256);
+  if (precision == DF_FP64) {
+    weighted_packed_density_kernel<double><<<g, 256, 0, s>>>(D, nao, npair, ld, w.Dw);
+    DF_LAUNCHED("weighted_packed_density_kernel");
+    jpass1_fp64_kernel<<<naux, 512, 0, s>>>((const double*)(base + L.off64), ld, w.Dw, w.d);
+    DF_LAUNCHED("jpass1_fp64_kernel");
+    dim3 grid2((unsigned)((ld / 2 + 255) / 256), (unsigned)w.nsplit_j);
+    jpass2_fp64_kernel<<<grid2, 256, 0, s>>>((const double*)(base + L.off64), ld, naux, w.d, w.Jpart);
+    DF_LAUNCHED("jpass2_fp64_kernel");
+  } else {
+    weighted_packed_density_kernel<float><<<g, 256, 0, s>>>(D, nao, npair, ld, w.Dw32);
+    DF_LAUNCHED("weighted_packed_density_kernel");
+    jpass1_fp32_kernel<<<naux, 512, 0, s>>>((const float*)(base + L.off32), ld, w.Dw32, w.d);
+    DF_LAUNCHED("jpass1_fp32_kernel");
+    dim3 grid2((unsigned)((ld / 4 + 255) / 256), (unsigned)w.nsplit_j);
+    jpass2_fp32_kernel<<<grid2, 256, 0, s>>>((const float*)(base + L.off32), ld, naux, w.d, w.Jpart);
+    DF_LAUNCHED("jpass2_fp32_kernel");
+  }
+  jreduce_unpack_kernel<<<gp, 256, 0, s>>>(w.Jpart, w.nsplit_j, ld, nao, J);
+  DF_LAUNCHED("jreduce_unpack_kernel");
+  return DF_OK;
+}
+
+int build_K_fp64(const double* B64, long ld, int nao, int naux, const double* C, int nocc, double* K, const JKWork& w,
+                 cudaStream_t s) {
+  dim3 grid((nocc + 31) / 32, (nao + 63) / 64, naux);
+  k_halftransform_fp64_kernel<<<grid, 256, 0, s>>>(B64, ld, nao, naux, C, nocc, w.X);
+  DF_LAUNCHED("k_halftransform_fp64_kernel");
+  long kdim = (long)naux * nocc;
+  long kchunk = (kdim + w.nsplit_k - 1) / w.nsplit_k;
+  kchunk = (kchunk + 15) / 16 * 16;
+  int nsplit = (int)((kdim + kchunk - 1) / kchunk);
+  DF_TRY(dgemm(false, true, nao, nao, (int)kdim, 1.0, w.X, kdim, 0, w.X, kdim, 0, 0.0, w.Kpart, nao,
+               (long)nao * nao, nsplit, s, kchunk, 1));
+  long nn = (long)nao * nao;
+  ksum_mirror_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, s>>>(w.Kpart, nsplit, nao, K);
+  DF_LAUNCHED("ksum_mirror_kernel");
+  return DF_OK;
+}
+
+int run_jk(const void* B, int nao, int naux, int precision, const double* D, const double* C, int nocc, double* J,
+           double* K, const JKWork& w, cudaStream_t s) {
+  BLayout L = B_layout(nao, naux, precision);
+  if (J) DF_TRY(build_J(B, L, nao, naux, precision, D, J, w, s));
+  if (K) {
+    if (precision == DF_FP64)
+      DF_TRY(build_K_fp64((const double*)((const char*)B + L.off64), L.ld, nao, naux, C, nocc, K, w, s));
+    else
+      DF_TRY(build_K_mixed(B, L, nao, naux, C, nocc, K, w.mk, s));
+  }
+  return DF_OK;
+}
+
+int build_B(const double* ao_xyz, const double* ao_exp, int nao, const double* aux_xyz, const double* aux_exp,
+            int naux, const double* Lfac, int precision, void* Bbuf, double* pair_tab, cudaStream_t s) {
+  BLayout L = B_layout(nao, naux, precision);
+  double* B64 = (double*)((char*)Bbuf + L.off64);
+  DF_TRY(launch_int3c(ao_xyz, ao_exp, nao, aux_xyz, aux_exp, naux, B64, L.ld, pair_tab, s));
+  DF_TRY(forward_substitution(B64, L.ld, L.ld, Lfac, naux, s));
+  if (precision == DF_MIXED) {
+    size_t n = (size_t)naux * L.ld;
+    b_to_fp32_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(B64, (float*)((char*)Bbuf + L.off32), n);
+    DF_LAUNCHED("b_to_fp32_kernel");
+    dim3 grid((unsigned)(((long)L.npad * L.npad + 255) / 256), (unsigned)naux);
+    DF_REQUIRE(naux <= 65535, DF_ERR_ARG, "naux too large");
+    b_to_split_bf16_kernel<<<grid, 256, 0, s>>>(B64, L.ld, nao, L.npad, (__nv_bfloat16*)((char*)Bbuf + L.offhi),
+                                                (__nv_bfloat16*)((char*)Bbuf + L.offlo));
+    DF_LAUNCHED("b_to_split_bf16_kernel");
+  }
+  return DF_OK;
+}
+
+}  // namespace dfscf
+
+using namespace dfscf;
+
+extern "C" long df_B_ld(int nao) { return nao > 0 ? B_ld(nao) : 0; }
+extern "C" int df_nao_pad(int nao) { return nao > 0 ? nao_pad(nao) : 0; }
+
+extern "C" size_t df_B_bytes(int nao, int naux, int precision) {
+  if (nao <= 0 || naux <= 0 || (precision != DF_FP64 && precision != DF_MIXED)) return 0;
+  return B_layout(nao, naux, precision).bytes;
+}
+
+extern "C" size_t df_build_B_work_bytes(int nao, int naux) {
+  (void)naux;
+  return nao > 0 ? align_up(sizeof(double) * 5 * (size_t)npair_of(nao), 256) : 0;
+}
+
+extern "C" int df_build_B(const double* ao_xyz, const double* ao_exp, int nao, const double* aux_xyz,
+                          const double* aux_exp, int naux, const double* L, int precision, void* B, size_t B_bytes,
+                          void* work, size_t work_bytes, cudaStream_t s) {
+  clear_error();
+  DF_REQUIRE(nao > 0 && naux > 0, DF_ERR_ARG, "df_build_B: bad sizes nao=%d naux=%d", nao, naux);
+  DF_REQUIRE(precision == DF_FP64 || precision == DF_MIXED, DF_ERR_ARG, "df_build_B: bad precision %d", precision);
+  DF_REQUIRE(ao_xyz && ao_exp && aux_xyz && aux_exp && L && B, DF_ERR_ARG, "df_build_B: null pointer");
+  DF_REQUIRE(B_bytes >= df_B_bytes(nao, naux, precision), DF_ERR_NOMEM, "df_build_B: B buffer of %zu bytes < %zu",
+             B_bytes, df_B_bytes(nao, naux, precision));
+  DF_REQUIRE(work && work_bytes >= df_build_B_work_bytes(nao, naux), DF_ERR_NOMEM,
+             "df_build_B: workspace of %zu bytes < %zu", work_bytes, df_build_B_work_bytes(nao, naux));
+  DF_REQUIRE(precision == DF_FP64 || naux <= 65535, DF_ERR_ARG, "df_build_B: naux > 65535 in mixed mode");
+  return build_B(ao_xyz, ao_exp, nao, aux_xyz, aux_exp, naux, L, precision, B, (double*)work, s);
+}
+
+extern "C" int df_B_get_packed(const void* B, int nao, int naux, int P, double* row, cudaStream_t s) {
+  clear_error();
+  DF_REQUIRE(B && row && nao > 0 && P >= 0 && P < naux, DF_ERR_ARG, "df_B_get_packed: bad arguments");
+  long ld = B_ld(nao);
+  DF_CUDA(cudaMemcpyAsync(row, (const double*)B + (size_t)P * ld, sizeof(double) * npair_of(nao),
+                          cudaMemcpyDeviceToDevice, s));
+  return DF_OK;
+}
+
+extern "C" size_t df_jk_work_bytes(int nao, int naux, int nocc, int precision) {
+  if (nao <= 0 || naux <= 0 || nocc < 0) return 0;
+  Sizer z;
+  jk_work_layout(nao, naux, nocc, precision, nullptr, &z);
+  return z.used;
+}
+
+extern "C" int df_jk(const void* B, int nao, int naux, int precision, const double* D, const double* C, int nocc,
+                     double* J, double* K, void* work, size_t work_bytes, cudaStream_t s) {
+  clear_error();
+  DF_REQUIRE(B && nao > 0 && naux > 0, DF_ERR_ARG, "df_jk: bad B or sizes");
+  DF_REQUIRE(precision == DF_FP64 || precision == DF_MIXED, DF_ERR_ARG, "df_jk: bad precision %d", precision);
+  DF_REQUIRE(!J || D, DF_ERR_ARG, "df_jk: J requested without D");
+  DF_REQUIRE(!K || (C && nocc > 0), DF_ERR_ARG, "df_jk: K requested without C / nocc");
+  DF_REQUIRE(naux <= 65535, DF_ERR_ARG, "df_jk: naux > 65535");
+  size_t need = df_jk_work_bytes(nao, naux, nocc, precision);
+  DF_REQUIRE(work && work_bytes >= need, DF_ERR_NOMEM, "df_jk: workspace of %zu bytes < %zu", work_bytes, need);
+  Arena a(work, work_bytes);
+  JKWork w = jk_work_layout(nao, naux, nocc, precision, &a, nullptr);
+  DF_REQUIRE(!a.overflow, DF_ERR_NOMEM, "df_jk: workspace overflow");
+  return run_jk(B, nao, naux, precision, D, C, nocc, J, K, w, s);
+}

@@ -1,0 +1,72 @@
+// Internal launchers shared between the library's translation units.
+#pragma once
+#include <cstddef>
+#include <vector>
+#include <algorithm>
+
+#include "common.cuh"
+
+namespace dfscf {
+
+// ---- integrals (integrals.cu) ------------------------------------------------------
+int launch_int1e(const double* ao_xyz, const double* ao_exp, int nao, const double* nuc_xyz, const double* nuc_z,
+                 int natm, double* S, double* T, double* V, cudaStream_t s);
+int launch_int2c(const double* xyz, const double* ex, int naux, double* M, cudaStream_t s);
+int launch_int3c(const double* ao_xyz, const double* ao_exp, int nao, const double* aux_xyz, const double* aux_exp,
+                 int naux, double* R, long ld, double* pair_tab, cudaStream_t s);
+int launch_enuc(const double* xyz, const double* z, int natm, double* out, cudaStream_t s);
+
+// ---- FP64 linear algebra (linalg.cu) -----------------------------------------------
+int dgemm(bool ta, bool tb, int M, int N, int K, double alpha, const double* A, long lda, long sA, const double* B,
+          long ldb, long sB, double beta, double* C, long ldc, long sC, int batch, cudaStream_t s, long kchunk,
+          int lower_only);
+int cholesky_inplace(double* A, int n, int* d_status, double* d_maxdiag, double tol, cudaStream_t s);
+int forward_substitution(double* R, long ld, long ncol, const double* L, int naux, cudaStream_t s);
+
+// ---- eigensolver (eig.cu) ------------------------------------------------------------
+size_t eigh_scratch_doubles(int n);
+int eigh_rows(double* A, int n, double* w, double* ZT, double* scratch, int* status, cudaStream_t s);
+int transpose(const double* in, int rows, int cols, double* out, cudaStream_t s);
+
+// ---- B layout and J/K (jk.cu, umma.cu) --------------------------------------------------
+struct BLayout {
+  long ld;       // packed row stride (elements)
+  int npad;      // padded orbital dimension of the BF16 planes
+  size_t off64, off32, offhi, offlo, bytes;
+};
+
+struct MixedKWork {
+  void* Chi;     // bf16 [ncpad][npad]  C^T hi
+  void* Clo;     // bf16 [ncpad][npad]  C^T lo
+  void* Xhi;     // bf16 [npad][naux * ncpad]   X hi (row m, column P*ncpad + i)
+  void* Xlo;     // bf16 same
+  float* Kpart;  // fp32 [nsplit][npad][npad] partial K tiles
+  int* err;      // device error flag of the tensor-core kernels
+  int ncpad;     // padded occupied count (multiple of 16, >= 16)
+  int nsplit;    // K-dimension splits of the exchange contraction
+};
+
+struct JKWork {
+  double* Dw;
+  float* Dw32;
+  double* d;
+  double* Jpart;
+  double* X;
+  double* Kpart;
+  int nsplit_j, nsplit_k;
+  MixedKWork mk;
+};
+
+long B_ld(int nao);
+int nao_pad(int nao);
+BLayout B_layout(int nao, int naux, int precision);
+JKWork jk_work_layout(int nao, int naux, int nocc, int precision, Arena* a, Sizer* z);
+void mixed_k_work_layout(int nao, int naux, int nocc, Arena* a, Sizer* z, MixedKWork* w);
+int build_K_mixed(const void* B, const BLayout& L, int nao, int naux, const double* C, int nocc, double* K,
+                  const MixedKWork& w, cudaStream_t s);
+int run_jk(const void* B, int nao, int naux, int precision, const double* D, const double* C, int nocc, double* J,
+           double* K, const JKWork& w, cudaStream_t s);
+int build_B(const double* ao_xyz, const double* ao_exp, int nao, const double* aux_xyz, const double* aux_exp,
+            int naux, const double* Lfac, int precision, void* Bbuf, double* pair_tab, cudaStream_t s);
+
+}  // namespace dfscf

@@ -1,0 +1,471 @@
+// Mixed-precision DF exchange build on the 5th-generation tensor cores (tcgen05).
+//
+// K_mn = sum_P sum_i X_{P,mi} X_{P,ni},  X_P = B_P C   (arXiv 2506.06661, Section
+// "Density fitting": the fitted integrals sum_P B_{P,mk} B_{P,nl} contracted with the
+// occupied coefficients).  Both contractions run as split-BF16 x3 GEMMs: every operand x
+// is stored as hi = RN_bf16(x), lo = RN_bf16(x - hi) and each product is formed as
+// hi*hi + hi*lo + lo*hi with FP32 accumulation in tensor memory (TMEM).
+//
+//   half-transform:  X[(P,m), i] = sum_n B[(P,m), n] C^T[i, n]     (A = B planes, B = C^T)
+//   exchange SYRK:   K[m, n]     = sum_(P,i) X[m, (P,i)] X[n, (P,i)] (A = B = X, lower tiles)
+//
+// Both are "D = A B^T" with A and B K-major in global memory, so one kernel serves both:
+// TMA (SWIZZLE_128B, 64-element K boxes) fills a multi-stage shared-memory ring, one
+// elected lane issues tcgen05.mma (M = 128, N <= 256, K = 16 per instruction, three per
+// K step), tcgen05.commit releases ring slots, and four epilogue warps read the
+// accumulator with tcgen05.ld.  Every mbarrier wait is bounded; on a timeout the kernel
+// raises a device error flag and returns after releasing its TMEM.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace dfscf {
+
+namespace umma {
+
+constexpr int BM = 128;          // rows per tile (TMEM lanes)
+constexpr int BK = 64;           // K elements per stage (128 bytes of bf16: one swizzle row)
+constexpr int MAX_STAGES = 4;
+constexpr int THREADS = 192;     // warp 0 TMA, warp 1 MMA, warps 2..5 epilogue
+constexpr uint32_t WAIT_LIMIT = 1u << 27;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ uint32_t mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok;
+}
+// Bounded wait: false if the phase did not complete within WAIT_LIMIT polls or another
+// role already gave up.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+  for (uint32_t i = 0; i < WAIT_LIMIT; ++i) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((i & 255u) == 255u && *abort_flag) return false;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
+          smem_u32(dst)),
+      "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(x), "r"(y)
+      : "memory");
+}
+__device__ __forceinline__ void tma_prefetch(const CUtensorMap* map) {
+  asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)map) : "memory");
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)), "r"(ncols)
+               : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                          uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\ttcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(
+          d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld_x16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, "
+      "[%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// Shared-memory matrix descriptor (tcgen05 format) for a K-major tile written by TMA
+// with 128-byte swizzling: rows of 128 bytes, 8-row groups 1024 bytes apart.
+__device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);  // start address
+  d |= (uint64_t)1 << 16;                   // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;         // stride byte offset: 8 rows x 128 B
+  d |= (uint64_t)1 << 46;                   // descriptor version for tcgen05
+  d |= (uint64_t)2 << 61;                   // 128-byte swizzle
+  return d;
+}
+
+// Instruction descriptor of kind::f16: BF16 x BF16 -> FP32, both operands K-major.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4)                  // D format FP32
+         | (1u << 7)                // A format BF16
+         | (1u << 10)               // B format BF16
+         | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+enum Mode { HALF_TRANSFORM = 0, SYRK = 1 };
+
+struct Params {
+  int mode;
+  int N;             // tile columns (multiple of 16, <= 256)
+  int num_kb;        // K blocks of BK in the whole K range
+  int kb_per_split;  // K blocks per split (SYRK) or num_kb
+  int stages;
+  uint32_t stage_bytes;
+  uint32_t b_bytes;  // bytes of one B tile (N x 128)
+  // half-transform epilogue
+  int npad;          // rows per P in A
+  long ldx;          // X row stride (elements)
+  int ncx;           // X columns per P
+  __nv_bfloat16* Xhi;
+  __nv_bfloat16* Xlo;
+  // SYRK epilogue
+  float* Kpart;      // [split][npad][npad]
+  int n_lower_tiles;
+  int* err;
+};
+
+__device__ __forceinline__ void lower_tile(int t, int& mt, int& nt) {
+  int m = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+  while (m * (m + 1) / 2 > t) --m;
+  while ((m + 1) * (m + 2) / 2 <= t) ++m;
+  mt = m;
+  nt = t - m * (m + 1) / 2;
+}
+
+__global__ void __launch_bounds__(THREADS, 1) split_bf16_gemm_kernel(const __grid_constant__ CUtensorMap mapAhi,
+                                                                      const __grid_constant__ CUtensorMap mapAlo,
+                                                                      const __grid_constant__ CUtensorMap mapBhi,
+                                                                      const __grid_constant__ CUtensorMap mapBlo,
+                                                                      const Params p) {
+  extern __shared__ uint8_t dyn_smem[];
+  __shared__ uint64_t full_bar[MAX_STAGES];
+  __shared__ uint64_t empty_bar[MAX_STAGES];
+  __shared__ uint64_t accum_bar;
+  __shared__ uint32_t tmem_base;
+  __shared__ int abort_flag;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // tile coordinates
+  int row0, col0, kb0, nkb, split = 0;
+  if (p.mode == HALF_TRANSFORM) {
+    row0 = blockIdx.x * BM;
+    col0 = blockIdx.y * p.N;
+    kb0 = 0;
+    nkb = p.num_kb;
+  } else {
+    int mt, nt;
+    lower_tile(blockIdx.x, mt, nt);
+    row0 = mt * BM;
+    col0 = nt * BM;
+    split = blockIdx.y;
+    kb0 = split * p.kb_per_split;
+    nkb = min(p.kb_per_split, p.num_kb - kb0);
+  }
+  // 1024-byte aligned ring of stages: [A hi | A lo | B hi | B lo]
+  uint32_t base = smem_u32(dyn_smem);
+  uint32_t pad = (1024u - (base & 1023u)) & 1023u;
+  uint8_t* ring = dyn_smem + pad;
+  const uint32_t a_bytes = BM * BK * 2;
+  uint32_t ncols = 32;
+  while ((int)ncols < p.N) ncols <<= 1;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < p.stages; ++s) {
+      mbar_init(&full_bar[s], 1);
+      mbar_init(&empty_bar[s], 1);
+    }
+    mbar_init(&accum_bar, 1);
+    abort_flag = 0;
+    mbar_fence_init();
+  }
+  if (warp == 0 && lane == 0) {
+    tma_prefetch(&mapAhi);
+    tma_prefetch(&mapAlo);
+    tma_prefetch(&mapBhi);
+    tma_prefetch(&mapBlo);
+  }
+  if (warp == 1) {
+    tmem_alloc(&tmem_base, ncols);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base;
+
+  if (warp == 0 && lane == 0 && nkb > 0) {
+    // ---- TMA producer ----------------------------------------------------------------
+    for (int i = 0; i < nkb; ++i) {
+      int s = i % p.stages;
+      uint32_t ph = (uint32_t)(i / p.stages) & 1u;
+      if (!mbar_wait(&empty_bar[s], ph ^ 1u, &abort_flag)) {
+        abort_flag = 1;
+        break;
+      }
+      uint8_t* st = ring + (size_t)s * p.stage_bytes;
+      mbar_arrive_expect_tx(&full_bar[s], p.stage_bytes);
+      int kx = (kb0 + i) * BK;
+      tma_load_2d(st, &mapAhi, &full_bar[s], kx, row0);
+      tma_load_2d(st + a_bytes, &mapAlo, &full_bar[s], kx, row0);
+      tma_load_2d(st + 2 * a_bytes, &mapBhi, &full_bar[s], kx, col0);
+      tma_load_2d(st + 2 * a_bytes + p.b_bytes, &mapBlo, &full_bar[s], kx, col0);
+    }
+  } else if (warp == 1 && lane == 0 && nkb > 0) {
+    // ---- MMA issuer ------------------------------------------------------------------
+    const uint32_t idesc = idesc_bf16(BM, p.N);
+    bool ok = true;
+    for (int i = 0; i < nkb; ++i) {
+      int s = i % p.stages;
+      uint32_t ph = (uint32_t)(i / p.stages) & 1u;
+      if (!mbar_wait(&full_bar[s], ph, &abort_flag)) {
+        abort_flag = 1;
+        ok = false;
+        break;
+      }
+      tc_fence_after();
+      uint32_t st = smem_u32(ring + (size_t)s * p.stage_bytes);
+      uint64_t ahi = desc_sw128(st), alo = desc_sw128(st + a_bytes);
+      uint64_t bhi = desc_sw128(st + 2 * a_bytes), blo = desc_sw128(st + 2 * a_bytes + p.b_bytes);
+#pragma unroll
+      for (int kk = 0; kk < BK / 16; ++kk) {
+        uint64_t off = (uint64_t)(kk * 32) >> 4;  // 16 bf16 = 32 bytes along K inside the swizzle row
+        umma_bf16(tmem, ahi + off, bhi + off, idesc, (i > 0 || kk > 0) ? 1u : 0u);
+        umma_bf16(tmem, ahi + off, blo + off, idesc, 1u);
+        umma_bf16(tmem, alo + off, bhi + off, idesc, 1u);
+      }
+      umma_commit(&empty_bar[s]);  // slot reusable once these MMAs have read it
+    }
+    if (ok) umma_commit(&accum_bar);
+  } else if (warp >= 2) {
+    // ---- epilogue: TMEM -> registers -> global ----------------------------------------
+    const int q = warp & 3;  // TMEM lane quarter this warp may access
+    const int r = q * 32 + lane;
+    bool ok = (nkb > 0) && mbar_wait(&accum_bar, 0, &abort_flag);
+    if (!ok && nkb > 0) abort_flag = 1;
+    tc_fence_after();
+    if (ok) {
+      const int grow = row0 + r;
+      for (int c = 0; c < p.N; c += 16) {
+        uint32_t v[16];
+        tmem_ld_x16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c, v);
+        tmem_wait_ld();
+        if (p.mode == HALF_TRANSFORM) {
+          int P = grow / p.npad, m = grow % p.npad;
+          __align__(16) __nv_bfloat16 h[16], l[16];
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            float x = __uint_as_float(v[j]);
+            h[j] = __float2bfloat16_rn(x);
+            l[j] = __float2bfloat16_rn(x - __bfloat162float(h[j]));
+          }
+          size_t o = (size_t)m * p.ldx + (size_t)P * p.ncx + col0 + c;
+          uint4* dh = reinterpret_cast<uint4*>(p.Xhi + o);
+          uint4* dl = reinterpret_cast<uint4*>(p.Xlo + o);
+          dh[0] = reinterpret_cast<uint4*>(h)[0];
+          dh[1] = reinterpret_cast<uint4*>(h)[1];
+          dl[0] = reinterpret_cast<uint4*>(l)[0];
+          dl[1] = reinterpret_cast<uint4*>(l)[1];
+        } else {
+          float4* dst = reinterpret_cast<float4*>(p.Kpart + ((size_t)split * p.npad + grow) * p.npad + col0 + c);
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+            dst[j] = make_float4(__uint_as_float(v[4 * j]), __uint_as_float(v[4 * j + 1]), __uint_as_float(v[4 * j + 2]),
+                                 __uint_as_float(v[4 * j + 3]));
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (abort_flag && threadIdx.x == 0) atomicExch(p.err, 1);
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem, ncols);
+  }
+}
+
+}  // namespace umma
+
+// ---- host side -------------------------------------------------------------------------
+
+static PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    cudaDriverEntryPointQueryResult q;
+    void* p = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+  }
+  return fn;
+}
+
+// 2-D bf16 tensor map: inner dimension `cols` (K, contiguous), `rows` rows of `ld` elements,
+// box of 64 x box_rows, 128-byte swizzle, zero fill out of bounds.
+static int make_map(CUtensorMap* map, const void* base, uint64_t cols, uint64_t rows, uint64_t ld, uint32_t box_rows) {
+  auto enc = get_encode();
+  DF_REQUIRE(enc, DF_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
+  DF_REQUIRE(((uintptr_t)base & 15) == 0 && (ld * 2) % 16 == 0, DF_ERR_ARG, "tensor map base/stride not 16-byte aligned");
+  cuuint64_t dims[2] = {cols, rows};
+  cuuint64_t strides[1] = {ld * 2};
+  cuuint32_t box[2] = {(cuuint32_t)umma::BK, box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  DF_REQUIRE(r == CUDA_SUCCESS, DF_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+  return DF_OK;
+}
+
+static int launch_gemm(const CUtensorMap& ahi, const CUtensorMap& alo, const CUtensorMap& bhi, const CUtensorMap& blo,
+                       umma::Params p, dim3 grid, cudaStream_t s) {
+  p.b_bytes = (uint32_t)p.N * umma::BK * 2;
+  p.stage_bytes = 2 * umma::BM * umma::BK * 2 + 2 * p.b_bytes;
+  const uint32_t budget = 220 * 1024;
+  p.stages = (int)std::min<uint32_t>(umma::MAX_STAGES, budget / p.stage_bytes);
+  DF_REQUIRE(p.stages >= 2, DF_ERR_ARG, "split-bf16 GEMM: tile too large for shared memory");
+  size_t smem = (size_t)p.stages * p.stage_bytes + 1024;
+  DF_CUDA(cudaFuncSetAttribute(umma::split_bf16_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  umma::split_bf16_gemm_kernel<<<grid, umma::THREADS, smem, s>>>(ahi, alo, bhi, blo, p);
+  DF_LAUNCHED("split_bf16_gemm_kernel");
+  return DF_OK;
+}
+
+// C^T split into bf16 hi / lo planes [ncpad][npad], zero padded.
+__global__ void pack_ct_kernel(const double* __restrict__ C, int nao, int nocc, int npad, int ncpad,
+                               __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo) {
+  long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long)ncpad * npad) return;
+  int i = (int)(e / npad), n = (int)(e % npad);
+  double x = (i < nocc && n < nao) ? C[(size_t)n * nocc + i] : 0.0;
+  __nv_bfloat16 h = __double2bfloat16(x);
+  hi[e] = h;
+  lo[e] = __double2bfloat16(x - (double)__bfloat162float(h));
+}
+
+// K[m][n] = K[n][m] = sum_split Kpart[split][m][n] (FP64 sum of FP32 partials), m >= n.
+__global__ void kmixed_reduce_kernel(const float* __restrict__ Kpart, int nsplit, int npad, int nao,
+                                     double* __restrict__ K) {
+  long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long)nao * nao) return;
+  int m = (int)(e / nao), n = (int)(e % nao);
+  if (n > m) return;
+  double s = 0.0;
+  for (int k = 0; k < nsplit; ++k) s += (double)Kpart[((size_t)k * npad + m) * npad + n];
+  K[(size_t)m * nao + n] = s;
+  K[(size_t)n * nao + m] = s;
+}
+
+static int mixed_ncpad(int nocc) { return std::max(16, (nocc + 15) / 16 * 16); }
+
+static int mixed_nsplit(int npad, int naux, int ncpad) {
+  long kdim = (long)naux * ncpad;
+  long nkb = (kdim + umma::BK - 1) / umma::BK;
+  int tiles = (npad / umma::BM) * (npad / umma::BM + 1) / 2;
+  // FP32 accumulation length per split <= ~16k terms, and several waves of CTAs
+  long want = std::max<long>((kdim + 16383) / 16384, (4L * 152 + tiles - 1) / tiles);
+  return (int)std::max<long>(1, std::min<long>(want, std::min<long>(nkb, 256)));
+}
+
+void mixed_k_work_layout(int nao, int naux, int nocc, Arena* a, Sizer* z, MixedKWork* w) {
+  int npad = nao_pad(nao);
+  int ncpad = mixed_ncpad(std::max(nocc, 1));
+  int nsplit = mixed_nsplit(npad, naux, ncpad);
+  w->ncpad = ncpad;
+  w->nsplit = nsplit;
+  size_t xsize = (size_t)npad * naux * ncpad;
+  if (a) {
+    w->Chi = a->take<__nv_bfloat16>((size_t)ncpad * npad);
+    w->Clo = a->take<__nv_bfloat16>((size_t)ncpad * npad);
+    w->Xhi = a->take<__nv_bfloat16>(xsize);
+    w->Xlo = a->take<__nv_bfloat16>(xsize);
+    w->Kpart = a->take<float>((size_t)nsplit * npad * npad);
+    w->err = a->take<int>(1);
+  } else {
+    z->take<__nv_bfloat16>((size_t)ncpad * npad);
+    z->take<__nv_bfloat16>((size_t)ncpad * npad);
+    z->take<__nv_bfloat16>(xsize);
+    z->take<__nv_bfloat16>(xsize);
+    z->take<float>((size_t)nsplit * npad * npad);
+    z->take<int>(1);
+  }
+}
+
+int build_K_mixed(const void* B, const BLayout& L, int nao, int naux, const double* C, int nocc, double* K,
+                  const MixedKWork& w, cudaStream_t s) {
+  const int npad = L.npad, ncpad = w.ncpad;
+  DF_REQUIRE(nocc <= ncpad, DF_ERR_ARG, "mixed K: workspace sized for %d occupied columns, got %d", ncpad, nocc);
+  DF_REQUIRE(ncpad <= 256, DF_ERR_ARG, "mixed K: more than 256 occupied orbitals per call is not supported");
+  DF_CUDA(cudaMemsetAsync(w.err, 0, sizeof(int), s));
+  long nct = (long)ncpad * npad;
+  pack_ct_kernel<<<(unsigned)((nct + 255) / 256), 256, 0, s>>>(C, nao, nocc, npad, ncpad, (__nv_bfloat16*)w.Chi,
+                                                               (__nv_bfloat16*)w.Clo);
+  DF_LAUNCHED("pack_ct_kernel");
+  const char* base = (const char*)B;
+  CUtensorMap ahi, alo, bhi, blo;
+  // half transform: A = B planes [(P, m)][n], B = C^T [i][n]
+  DF_TRY(make_map(&ahi, base + L.offhi, npad, (uint64_t)naux * npad, npad, umma::BM));
+  DF_TRY(make_map(&alo, base + L.offlo, npad, (uint64_t)naux * npad, npad, umma::BM));
+  DF_TRY(make_map(&bhi, w.Chi, npad, ncpad, npad, ncpad));
+  DF_TRY(make_map(&blo, w.Clo, npad, ncpad, npad, ncpad));
+  umma::Params p{};
+  p.mode = umma::HALF_TRANSFORM;
+  p.N = ncpad;
+  p.num_kb = npad / umma::BK;
+  p.kb_per_split = p.num_kb;
+  p.npad = npad;
+  p.ncx = ncpad;
+  p.ldx = (long)naux * ncpad;
+  p.Xhi = (__nv_bfloat16*)w.Xhi;
+  p.Xlo = (__nv_bfloat16*)w.Xlo;
+  p.err = w.err;
+  long mtiles = (long)naux * npad / umma::BM;
+  DF_REQUIRE(mtiles < (1L << 31), DF_ERR_ARG, "mixed K: too many row tiles");
+  DF_TRY(launch_gemm(ahi, alo, bhi, blo, p, dim3((unsigned)mtiles, 1), s));
+  // exchange SYRK: A = B = X [m][(P, i)], lower 128 x 128 tiles, split over (P, i)
+  long kdim = (long)naux * ncpad;
+  DF_TRY(make_map(&ahi, w.Xhi, kdim, npad, kdim, umma::BM));
+  DF_TRY(make_map(&alo, w.Xlo, kdim, npad, kdim, umma::BM));
+  umma::Params q{};
+  q.mode = umma::SYRK;
+  q.N = umma::BM;
+  q.num_kb = (int)((kdim + umma::BK - 1) / umma::BK);
+  q.kb_per_split = (q.num_kb + w.nsplit - 1) / w.nsplit;
+  int nsplit = (q.num_kb + q.kb_per_split - 1) / q.kb_per_split;
+  q.npad = npad;
+  q.Kpart = w.Kpart;
+  q.n_lower_tiles = (npad / umma::BM) * (npad / umma::BM + 1) / 2;
+  q.err = w.err;
+  DF_TRY(launch_gemm(ahi, alo, ahi, alo, q, dim3((unsigned)q.n_lower_tiles, (unsigned)nsplit), s));
+  long nn = (long)nao * nao;
+  kmixed_reduce_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, s>>>(w.Kpart, nsplit, npad, nao, K);
+  DF_LAUNCHED("kmixed_reduce_kernel");
+  return DF_OK;
+}
+
+}  // namespace dfscf

@@ -1,0 +1,54 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every function that
+include/dfscf.h declares (no GPU needed; nothing is computed)."""
+import ctypes
+import os
+import re
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = []
+    for fn in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if not fn.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", fn)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^(?:const\s+)?\w+[\s\*]+(\w+)\s*\(", text, flags=re.M):
+            names.append(m.group(1))
+    return sorted(set(names))
+
+
+def test_header_declares_core_entry_points():
+    names = declared_functions()
+    for required in ("df_metric_chol", "df_build_B", "df_jk", "scf_run", "df_last_error"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol():
+    import paper_2506_06661_gb300 as dfscf
+    path = dfscf._build.build()
+    lib = ctypes.CDLL(path)
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, f"not exported: {missing}"
+
+
+def test_size_queries_without_gpu():
+    import paper_2506_06661_gb300 as dfscf
+    L = dfscf.lib()
+    assert L.df_B_ld(100) == 5056  # 5050 rounded up to 32
+    assert L.df_nao_pad(100) == 128
+    assert L.df_B_bytes(100, 300, 0) == 300 * 5056 * 8
+    assert L.df_B_bytes(100, 300, 2) == 0
+    assert L.df_jk_work_bytes(100, 300, 10, 0) > 0
+    assert L.scf_work_bytes(100, 300, 10, 0) > L.df_B_bytes(100, 300, 0)
+
+
+def test_argument_errors_are_host_side():
+    import paper_2506_06661_gb300 as dfscf
+    L = dfscf.lib()
+    rc = L.df_jk(None, 100, 300, 0, None, None, 0, None, None, None, 0, None)
+    assert rc == dfscf.DF_ERR_ARG
+    assert b"df_jk" in L.df_last_error()
+    rc = L.df_boys_f0(None, -1, None, None)
+    assert rc == dfscf.DF_ERR_ARG
