@@ -1,0 +1,363 @@
+"""Benchmark: density-fitted Fock builds (J + K) on the 300-centre workload.
+
+Workload (default): 300 hydrogen-like centres at one per 10 bohr^3 (box 14.42 bohr,
+seed 0), 5 orbital + 15 auxiliary s primitives per centre: nao 1500, naux 4500,
+nocc 150; D and C_occ from the core-Hamiltonian guess, fixed.  One step is one Fock
+build (J[D] and K[C_occ]) in FP64; the mixed-precision (split-BF16 x3 on tcgen05) build
+is timed the same way and reported under "mixed".  B (40.5 GB FP64) is far larger
+than L2, so no L2 flush is needed between steps.
+
+--impl reference times the CPU oracle (the plain FP64 C loops in oracle/) on a bounded
+P-slice of the same workload and scales it to one full build.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "DF-JK builds/s + tensor-pipe %; SCF time-to-1e-6 Eh, mixed vs FP64"
+# FP64 ALU peak: 152 SMs x 2 FP64 FMA/clk/SM x 2 flop x 2.07 GHz (1.90 FMA/clk/SM measured)
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+LAUNCHES_FP64 = 7   # kernels per FP64 build: Dw, J pass 1, J pass 2, J reduce, K half-transform, K SYRK, K mirror
+LAUNCHES_MIXED = 8  # Dw, J pass 1, J pass 2, J reduce, C split, tcgen05 half-transform, tcgen05 SYRK, K reduce
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def workload(name: str):
+    import gen
+    if name == "c1":
+        return gen.config_c1(), "300 H centres, 1 per 10 bohr^3 (box 14.42 bohr, seed 0); nao 1500, naux 4500, nocc 150"
+    if name == "c0":
+        return gen.config_c0(), "20 H centres in a 6 bohr cube (seed 0); nao 100, naux 300, nocc 10"
+    raise SystemExit(f"unknown workload {name}")
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ---------------------------------------------------------------------------------------
+def cpu_oracle_sample(mol, rows: int):
+    """Time the oracle's DF-J and DF-K on `rows` auxiliary rows; returns (seconds, rows).
+    The raw three-centre rows stand in for B: the oracle's loop cost does not depend on
+    the values."""
+    import oracle
+    oracle.build_library()
+    R = oracle.int3c(mol.ao_xyz, mol.ao_exp, mol.aux_xyz[:rows], mol.aux_exp[:rows])
+    rng = np.random.default_rng(0)
+    C = 0.05 * rng.standard_normal((mol.nao, mol.nocc))
+    D = 2 * C @ C.T
+    t0 = time.perf_counter()
+    oracle.df_j(R, mol.nao, D)
+    oracle.df_k(R, mol.nao, C)
+    return time.perf_counter() - t0
+
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def cpu_baseline_obj(mol, wl_name):
+    cores = cpu_cores()
+    rows = min(mol.naux, 12 * cores)
+    t = cpu_oracle_sample(mol, rows)
+    per_build = t * mol.naux / rows
+    return {"value": 1.0 / per_build, "unit": "builds/s", "cores": cores, "kind": "oracle",
+            "sample": f"oracle DF-J + DF-K over the first {rows} of {mol.naux} auxiliary rows of the {wl_name} "
+                      f"workload ({t:.1f} s), scaled linearly in naux to one full Fock build"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    mol, desc = workload(args.workload)
+    cores = cpu_cores()
+    rows = min(mol.naux, max(1, 4 * cores))
+    for _ in range(args.warmup):
+        cpu_oracle_sample(mol, rows)
+    times = [cpu_oracle_sample(mol, rows) * mol.naux / rows for _ in range(args.steps)]
+    ms = 1000.0 * statistics.mean(times)
+    v = 1000.0 / ms
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "builds/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": desc, "precision": "fp64"},
+            "cpu_baseline": {"value": v, "unit": "builds/s", "cores": cores, "kind": "oracle",
+                             "sample": f"each step: oracle DF-J + DF-K over {rows} of {mol.naux} auxiliary rows, "
+                                       f"scaled linearly in naux to one full Fock build"},
+            "e2e": {"value": v, "unit": "builds/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------------------
+def time_builds(dfscf, torch, B, D, C, prec, steps, warmup, work, barrier):
+    stream = torch.cuda.current_stream()
+    J = torch.empty_like(D)
+    K = torch.empty_like(D)
+    for _ in range(warmup):
+        dfscf.jk(B, D, C, precision=prec, work=work, out_j=J, out_k=K)
+    barrier()
+    torch.cuda.synchronize()
+    dfscf.profile_reset()
+    dfscf.profile_enable(True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        dfscf.jk(B, D, C, precision=prec, work=work, out_j=J, out_k=K)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    dfscf.profile_enable(False)
+    prof = dfscf.profile_read()
+    barrier()
+    return e0.elapsed_time(e1) / steps, prof
+
+
+def time_e2e(dfscf, torch, B, D, C, prec, steps, work):
+    """Host-buffer Fock builds: pinned D, C copied in, J, K copied out, inside the timed region."""
+    nao, nocc = D.shape[0], C.shape[1]
+    hD = torch.empty(nao, nao, dtype=torch.float64, pin_memory=True).copy_(D.cpu())
+    hC = torch.empty(nao, nocc, dtype=torch.float64, pin_memory=True).copy_(C.cpu())
+    hJ = torch.empty(nao, nao, dtype=torch.float64, pin_memory=True)
+    hK = torch.empty(nao, nao, dtype=torch.float64, pin_memory=True)
+    dD, dC = torch.empty_like(D), torch.empty_like(C)
+    J, K = torch.empty_like(D), torch.empty_like(D)
+    stream = torch.cuda.current_stream()
+
+    def one():
+        dD.copy_(hD, non_blocking=True)
+        dC.copy_(hC, non_blocking=True)
+        dfscf.jk(B, dD, dC, precision=prec, work=work, out_j=J, out_k=K)
+        hJ.copy_(J, non_blocking=True)
+        hK.copy_(K, non_blocking=True)
+
+    one()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        one()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    return ms, (hD.numel() + hC.numel()) * 8, (hJ.numel() + hK.numel()) * 8
+
+
+def roofline_of(prof, name, flops_per_launch=None, bytes_per_launch=None, peak=None, bound="alu", unit="TFLOP/s"):
+    if name not in prof:
+        return None
+    ms, calls = prof[name]
+    avg = ms / max(calls, 1)
+    if flops_per_launch is not None:
+        ach = flops_per_launch / (avg * 1e-3) / 1e12
+    else:
+        ach = bytes_per_launch / (avg * 1e-3) / 1e9
+    return {"kernel": name, "bound": bound, "achieved": ach, "peak": peak, "unit": unit, "frac": ach / peak,
+            "traffic": None, "avg_ms": avg, "launches": calls}
+
+
+def run_ours(args):
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+        barrier = dist.barrier
+    else:
+        def barrier():
+            return None
+    torch.cuda.set_device(local)
+    import paper_2506_06661_gb300 as dfscf
+    peaks, peak_src = load_peaks()
+    mol, desc = workload(args.workload)
+    t_setup = time.perf_counter()
+    md = dfscf.MoleculeOnDevice(mol)
+    L = dfscf.metric_chol(mol.aux_xyz, mol.aux_exp)
+    B = dfscf.build_B(mol.ao_xyz, mol.ao_exp, mol.aux_xyz, mol.aux_exp, L, "mixed" if args.mixed else "fp64")
+    C, D, *_ = dfscf.core_guess(md)
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter() - t_setup
+    nao, naux, nocc = mol.nao, mol.naux, mol.nocc
+    npair = nao * (nao + 1) // 2
+    work64 = dfscf.JKWorkspace(nao, naux, nocc, "fp64")
+
+    with ClockSampler(local) as clk:
+        ms64, prof64 = time_builds(dfscf, torch, B, D, C, "fp64", args.steps, args.warmup, work64, barrier)
+    clocks = clk.summary()
+
+    # max over ranks of the per-step time
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms64], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms64 = float(t.item())
+    value = ws * 1000.0 / ms64
+
+    ht_flops = 2.0 * naux * nao * nao * nocc
+    syrk_flops = 1.0 * naux * nocc * nao * nao
+    j_bytes = 8.0 * naux * dfscf.lib().df_B_ld(nao)
+    rl = {}
+    for name, fl in (("k_halftransform_fp64", ht_flops), ("k_syrk_fp64", syrk_flops)):
+        r = roofline_of(prof64, name, flops_per_launch=fl, peak=FP64_PEAK_TFLOPS, bound="alu")
+        if r:
+            rl[name] = r
+    for name in ("j_pass1_fp64", "j_pass2_fp64"):
+        r = roofline_of(prof64, name, bytes_per_launch=j_bytes, peak=peaks["hbm_gbs"], bound="hbm", unit="GB/s")
+        if r:
+            rl[name] = r
+    dominant = max(rl.values(), key=lambda r: r["avg_ms"] * r["launches"]) if rl else None
+
+    e2e_ms, h2d, d2h = time_e2e(dfscf, torch, B, D, C, "fp64", args.e2e_steps, work64)
+
+    mixed = None
+    if args.mixed:
+        workm = dfscf.JKWorkspace(nao, naux, nocc, "mixed")
+        with ClockSampler(local) as clkm:
+            msm, profm = time_builds(dfscf, torch, B, D, C, "mixed", args.mixed_steps, args.warmup, workm, barrier)
+        # accuracy of this build against the FP64 build of the same inputs
+        Jm, Km = dfscf.jk(B, D, C, precision="mixed", work=workm)
+        J6, K6 = dfscf.jk(B, D, C, precision="fp64", work=work64)
+        errj = float((Jm - J6).abs().max() / J6.abs().max())
+        errk = float((Km - K6).abs().max() / K6.abs().max())
+        npad = dfscf.lib().df_nao_pad(nao)
+        ncpad = max(16, (nocc + 15) // 16 * 16)
+        tc_ht = 3 * 2.0 * naux * npad * npad * ncpad     # tensor-core flops issued (3 split products)
+        tc_syrk = 3 * 2.0 * (naux * ncpad) * (128 * 128) * ((npad // 128) * (npad // 128 + 1) // 2)
+        rlm = {}
+        for name, fl, alg in (("k_halftransform_tc", tc_ht, 3 * ht_flops), ("k_syrk_tc", tc_syrk, 3 * syrk_flops)):
+            r = roofline_of(profm, name, flops_per_launch=alg, peak=peaks["bf16_tflops_sustained"], bound="tensor")
+            if r:
+                r["issued_tflops"] = fl / (r["avg_ms"] * 1e-3) / 1e12
+                rlm[name] = r
+        jb32 = 4.0 * naux * dfscf.lib().df_B_ld(nao)
+        for name in ("j_pass1_fp32", "j_pass2_fp32"):
+            r = roofline_of(profm, name, bytes_per_launch=jb32, peak=peaks["hbm_gbs"], bound="hbm", unit="GB/s")
+            if r:
+                rlm[name] = r
+        mixed = {"value": ws * 1000.0 / msm, "unit": "builds/s", "ms_per_step": msm, "steps": args.mixed_steps,
+                 "dtype": "bf16x3+f32 (K), f32 (J)", "rel_err_vs_fp64": {"J": errj, "K": errk},
+                 "kernels": rlm, "gpu_launches": LAUNCHES_MIXED * args.mixed_steps, "clocks": clkm.summary(),
+                 "phase_ms": {k: v[0] / max(v[1], 1) for k, v in profm.items()}}
+
+    line = {"metric": METRIC, "value": value, "unit": "builds/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms64, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": desc, "precision": "fp64", "step": "one Fock build: J[D] and K[C_occ]",
+                       "l2": "inputs larger than L2 (B is %.1f GB)" % (8.0 * naux * npair / 1e9),
+                       "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
+            "roofline": ({k: v for k, v in dominant.items() if k not in ("avg_ms", "launches")} | {"peak_source": (
+                "derived FP64 ALU peak: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz" if dominant["bound"] == "alu"
+                else f"MEASURED_PEAKS.json ({peak_src})")}) if dominant else None,
+            "kernels": rl,
+            "phase_ms": {k: v[0] / max(v[1], 1) for k, v in prof64.items()},
+            "e2e": {"value": ws * 1000.0 / e2e_ms, "unit": "builds/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h, "steps": args.e2e_steps},
+            "gpu_launches": LAUNCHES_FP64 * args.steps,
+            "clocks": clocks,
+            "setup_s": t_setup,
+            "mixed": mixed}
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_obj(mol, args.workload)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=["c1", "c0"], default="c1")
+    ap.add_argument("--mixed-steps", type=int, default=20)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-mixed", dest="mixed", action="store_false")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -192,6 +192,44 @@ int scf_run(const df_molecule* mol, const scf_opts* opt, const double* dm0, doub
             double* C_out, double* mo_energy, scf_result* res, void* work, size_t work_bytes,
             cudaStream_t s);
 
+/* ---- a13: batched SCF -------------------------------------------------------------------
+ * Runs scf_run's algorithm for nmol molecules of uneven size.  `slots` molecules are in
+ * flight at once, each with its own stream (created by the library, ordered after `s`)
+ * and its own slice of the workspace; a slot that finishes takes the next molecule.  Each
+ * molecule's iteration is captured once per precision into a CUDA graph and replayed.
+ * dm0s (may be NULL; entries may be NULL): device starting densities; D_outs (may be
+ * NULL; entries may be NULL): device [nao][nao] outputs; results: HOST array of nmol.
+ * Returns DF_ERR_NOCONV if any molecule did not converge (all results are still filled).
+ * work: scf_batch_work_bytes(mols, nmol, precision, slots) bytes.  Blocks until done.  */
+size_t scf_batch_work_bytes(const df_molecule* mols, int nmol, int precision, int slots);
+int scf_run_batch(const df_molecule* mols, int nmol, const scf_opts* opt, const double* const* dm0s,
+                  double* const* D_outs, scf_result* results, int slots, void* work, size_t work_bytes,
+                  cudaStream_t s);
+
+/* ---- core-Hamiltonian guess ------------------------------------------------------------
+ * S, h = T + V, canonical orthogonalisation X (eigenvalues of S above lindep), the
+ * nocc = nelec/2 lowest eigenvectors C_occ = X C' of X^T h X and D = 2 C_occ C_occ^T: the
+ * default starting point of the SCF (the paper's initial-guess section).  Outputs are
+ * device buffers and may be NULL except C_occ and D; *nmo_out (HOST, may be NULL) gets the
+ * number of orbitals kept.  Synchronises the stream.
+ * work: df_core_guess_work_bytes(nao, nocc) bytes.                                       */
+size_t df_core_guess_work_bytes(int nao, int nocc);
+int df_core_guess(const df_molecule* mol, double lindep, double* S_out, double* h_out, double* C_occ,
+                  double* D_out, double* mo_energy, int* nmo_out, void* work, size_t work_bytes,
+                  cudaStream_t s);
+
+/* ---- phase profiler ------------------------------------------------------------------
+ * When enabled, the J/K builds bracket each kernel phase with CUDA events on the
+ * launching stream.  df_profile_count() synchronises those events and returns the number
+ * of distinct phases; name / total milliseconds / number of launches per phase follow.
+ * Host-side state, not thread-safe; off by default.                                      */
+void df_profile_enable(int on);
+void df_profile_reset(void);
+int df_profile_count(void);
+const char* df_profile_name(int i);
+double df_profile_ms(int i);
+long df_profile_calls(int i);
+
 #ifdef __cplusplus
 }
 #endif

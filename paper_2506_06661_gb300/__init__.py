@@ -85,9 +85,21 @@ _SIGS = {
     "df_eigh_work_bytes": (_SZ, [_I]),
     "df_eigh": (_I, [_VP, _I, _VP, _VP, _VP, _SZ, _VP]),
     "scf_default_opts": (None, [ctypes.POINTER(ScfOpts)]),
+    "df_core_guess_work_bytes": (_SZ, [_I, _I]),
+    "df_core_guess": (_I, [ctypes.POINTER(DFMolecule), _D, _VP, _VP, _VP, _VP, _VP, ctypes.POINTER(_I), _VP, _SZ,
+                           _VP]),
+    "df_profile_enable": (None, [_I]),
+    "df_profile_reset": (None, []),
+    "df_profile_count": (_I, []),
+    "df_profile_name": (ctypes.c_char_p, [_I]),
+    "df_profile_ms": (_D, [_I]),
+    "df_profile_calls": (_L, [_I]),
     "scf_work_bytes": (_SZ, [_I, _I, _I, _I]),
     "scf_run": (_I, [ctypes.POINTER(DFMolecule), ctypes.POINTER(ScfOpts), _VP, _VP, _VP, _VP,
                      ctypes.POINTER(ScfResultC), _VP, _SZ, _VP]),
+    "scf_batch_work_bytes": (_SZ, [ctypes.POINTER(DFMolecule), _I, _I, _I]),
+    "scf_run_batch": (_I, [ctypes.POINTER(DFMolecule), _I, ctypes.POINTER(ScfOpts), ctypes.POINTER(_VP),
+                           ctypes.POINTER(_VP), ctypes.POINTER(ScfResultC), _I, _VP, _SZ, _VP]),
 }
 
 
@@ -313,3 +325,71 @@ def scf_run(mol, opts: ScfOpts | None = None, dm0=None, work: torch.Tensor | Non
         raise DFError(rc, lib().df_last_error().decode())
     return SCFResult(r.energy, r.e_nuc, r.homo, r.lumo, r.last_de, r.last_err, r.iterations, r.fp64_iterations,
                      bool(r.converged), r.guess, r.nmo, D, C, eps)
+
+
+def core_guess(mol, lindep: float = 1e-8):
+    """Core-Hamiltonian guess on the GPU: returns (C_occ, D, S, h, mo_energy, nmo)."""
+    md = mol if isinstance(mol, MoleculeOnDevice) else MoleculeOnDevice(mol)
+    nao, nocc = md.nao, md.nelec // 2
+    S = torch.empty(nao, nao, dtype=torch.float64, device="cuda")
+    h = torch.empty_like(S)
+    D = torch.empty_like(S)
+    C = torch.empty(nao, nocc, dtype=torch.float64, device="cuda")
+    eps = torch.zeros(nocc + 1, dtype=torch.float64, device="cuda")
+    nmo = ctypes.c_int(0)
+    w = _work(lib().df_core_guess_work_bytes(nao, nocc))
+    _check(lib().df_core_guess(ctypes.byref(md.c), lindep, _ptr(S), _ptr(h), _ptr(C), _ptr(D), _ptr(eps),
+                               ctypes.byref(nmo), _ptr(w), w.numel(), _stream()))
+    return C, D, S, h, eps, nmo.value
+
+
+def profile_enable(on: bool = True) -> None:
+    lib().df_profile_enable(1 if on else 0)
+
+
+def profile_reset() -> None:
+    lib().df_profile_reset()
+
+
+def profile_read() -> dict:
+    """{phase name: (total ms, launches)} since the last reset (synchronises)."""
+    L = lib()
+    n = L.df_profile_count()
+    return {L.df_profile_name(i).decode(): (L.df_profile_ms(i), L.df_profile_calls(i)) for i in range(n)}
+
+
+@dataclass
+class BatchResult:
+    results: list
+    D: list | None
+
+
+def scf_run_batch(mols, opts: ScfOpts | None = None, dm0s=None, slots: int = 16, want_D: bool = False,
+                  work: torch.Tensor | None = None, raise_on_noconv: bool = True, **kw) -> BatchResult:
+    """Batched DF-RHF over molecules of uneven size (scf_run_batch in the C ABI)."""
+    devs = [m if isinstance(m, MoleculeOnDevice) else MoleculeOnDevice(m) for m in mols]
+    n = len(devs)
+    arr = (DFMolecule * n)(*[d.c for d in devs])
+    o = opts if opts is not None else default_opts(**kw)
+    slots = max(1, min(slots, n))
+    nb = int(lib().scf_batch_work_bytes(arr, n, o.precision, slots))
+    if work is None or work.numel() < nb:
+        work = _work(nb)
+    dm0_t = None
+    dm0_arr = None
+    if dm0s is not None:
+        dm0_t = [(_dev(d) if d is not None else None) for d in dm0s]
+        dm0_arr = (_VP * n)(*[(t.data_ptr() if t is not None else None) for t in dm0_t])
+    Ds = None
+    D_arr = None
+    if want_D:
+        Ds = [torch.empty(d.nao, d.nao, dtype=torch.float64, device="cuda") for d in devs]
+        D_arr = (_VP * n)(*[t.data_ptr() for t in Ds])
+    res = (ScfResultC * n)()
+    rc = lib().scf_run_batch(arr, n, ctypes.byref(o), dm0_arr, D_arr, res, slots, _ptr(work), work.numel(),
+                             _stream())
+    if rc != DF_OK and not (rc == DF_ERR_NOCONV and not raise_on_noconv):
+        raise DFError(rc, lib().df_last_error().decode())
+    out = [SCFResult(r.energy, r.e_nuc, r.homo, r.lumo, r.last_de, r.last_err, r.iterations, r.fp64_iterations,
+                     bool(r.converged), r.guess, r.nmo, None, None, None) for r in res]
+    return BatchResult(out, Ds)

@@ -21,3 +21,94 @@ void clear_error() { g_err[0] = '\0'; }
 
 extern "C" const char* df_last_error(void) { return dfscf::g_err; }
 extern "C" int df_version(void) { return 100; }
+
+// ---- phase profiler ----------------------------------------------------------------
+// When enabled, launch sites bracket their kernels with CUDA events on the launching
+// stream; df_profile_* sum the elapsed times per phase name.
+#include <cstring>
+#include <string>
+#include <vector>
+
+namespace dfscf {
+
+struct ProfEntry {
+  std::string name;
+  cudaEvent_t a, b;
+};
+static bool g_prof_on = false;
+static std::vector<ProfEntry> g_prof;
+static std::vector<std::pair<std::string, double>> g_prof_sum;
+static std::vector<std::pair<std::string, long>> g_prof_cnt;
+
+bool prof_on() { return g_prof_on; }
+
+void* prof_begin(const char* name, cudaStream_t s) {
+  if (!g_prof_on) return nullptr;
+  ProfEntry e{name, nullptr, nullptr};
+  cudaEventCreate(&e.a);
+  cudaEventCreate(&e.b);
+  cudaEventRecord(e.a, s);
+  g_prof.push_back(e);
+  return (void*)(g_prof.size());
+}
+
+void prof_end(void* tok, cudaStream_t s) {
+  if (!g_prof_on || !tok) return;
+  size_t i = (size_t)tok - 1;
+  if (i < g_prof.size()) cudaEventRecord(g_prof[i].b, s);
+}
+
+static void prof_collect() {
+  for (auto& e : g_prof) {
+    cudaEventSynchronize(e.b);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e.a, e.b);
+    bool found = false;
+    for (size_t k = 0; k < g_prof_sum.size(); ++k)
+      if (g_prof_sum[k].first == e.name) {
+        g_prof_sum[k].second += ms;
+        g_prof_cnt[k].second += 1;
+        found = true;
+      }
+    if (!found) {
+      g_prof_sum.push_back({e.name, (double)ms});
+      g_prof_cnt.push_back({e.name, 1});
+    }
+    cudaEventDestroy(e.a);
+    cudaEventDestroy(e.b);
+  }
+  g_prof.clear();
+}
+
+}  // namespace dfscf
+
+extern "C" void df_profile_enable(int on) {
+  dfscf::prof_collect();
+  dfscf::g_prof_on = on != 0;
+}
+
+extern "C" void df_profile_reset(void) {
+  dfscf::prof_collect();
+  dfscf::g_prof_sum.clear();
+  dfscf::g_prof_cnt.clear();
+}
+
+extern "C" int df_profile_count(void) {
+  dfscf::prof_collect();
+  return (int)dfscf::g_prof_sum.size();
+}
+
+extern "C" const char* df_profile_name(int i) {
+  if (i < 0 || i >= (int)dfscf::g_prof_sum.size()) return "";
+  return dfscf::g_prof_sum[i].first.c_str();
+}
+
+extern "C" double df_profile_ms(int i) {
+  if (i < 0 || i >= (int)dfscf::g_prof_sum.size()) return 0.0;
+  return dfscf::g_prof_sum[i].second;
+}
+
+extern "C" long df_profile_calls(int i) {
+  if (i < 0 || i >= (int)dfscf::g_prof_cnt.size()) return 0;
+  return dfscf::g_prof_cnt[i].second;
+}

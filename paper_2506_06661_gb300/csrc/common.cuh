@@ -13,6 +13,17 @@ namespace dfscf {
 void set_error(const char* fmt, ...);
 void clear_error();
 
+// Phase profiler (api.cu): CUDA events around kernel phases when enabled.
+bool prof_on();
+void* prof_begin(const char* name, cudaStream_t s);
+void prof_end(void* tok, cudaStream_t s);
+struct ProfScope {
+  void* tok;
+  cudaStream_t s;
+  ProfScope(const char* name, cudaStream_t st) : tok(prof_begin(name, st)), s(st) {}
+  ~ProfScope() { prof_end(tok, s); }
+};
+
 constexpr double kPi = 3.14159265358979323846;
 
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }

@@ -283,7 +283,9 @@ int ksplit_count(int nao, long kdim) {
   return (int)max(1L, min(want, min(maxs, 64L)));
 }
 
-JKWork jk_work_layout(int nao, int naux, int nocc, int precision, Arena* a, Sizer* z) {
+// fp64_k: also carve the FP64 exchange buffers when precision is DF_MIXED (an SCF that
+// switches from mixed to FP64 iterations needs both).
+JKWork jk_work_layout(int nao, int naux, int nocc, int precision, Arena* a, Sizer* z, bool fp64_k) {
   JKWork w{};
   long ld = B_ld(nao);
   int nsplit_j = (naux + JP2_ROWS - 1) / JP2_ROWS;
@@ -296,12 +298,11 @@ JKWork jk_work_layout(int nao, int naux, int nocc, int precision, Arena* a, Size
   TAKE(float, w.Dw32, ld);
   TAKE(double, w.d, naux);
   TAKE(double, w.Jpart, (size_t)nsplit_j * ld);
-  if (precision == DF_FP64) {
+  if (precision == DF_FP64 || fp64_k) {
     TAKE(double, w.X, (size_t)nao * naux * max(nocc, 1));
     TAKE(double, w.Kpart, (size_t)nsplit_k * nao * nao);
-  } else {
-    mixed_k_work_layout(nao, naux, nocc, a, z, &w.mk);
   }
+  if (precision == DF_MIXED) mixed_k_work_layout(nao, naux, nocc, a, z, &w.mk);
 #undef TAKE
   return w;
 }
@@ -315,19 +316,31 @@ int build_J(const void* Bbuf, const BLayout& L, int nao, int naux, int precision
   if (precision == DF_FP64) {
     weighted_packed_density_kernel<double><<<g, 256, 0, s>>>(D, nao, npair, ld, w.Dw);
     DF_LAUNCHED("weighted_packed_density_kernel");
-    jpass1_fp64_kernel<<<naux, 512, 0, s>>>((const double*)(base + L.off64), ld, w.Dw, w.d);
-    DF_LAUNCHED("jpass1_fp64_kernel");
-    dim3 grid2((unsigned)((ld / 2 + 255) / 256), (unsigned)w.nsplit_j);
-    jpass2_fp64_kernel<<<grid2, 256, 0, s>>>((const double*)(base + L.off64), ld, naux, w.d, w.Jpart);
-    DF_LAUNCHED("jpass2_fp64_kernel");
+    {
+      ProfScope ps("j_pass1_fp64", s);
+      jpass1_fp64_kernel<<<naux, 512, 0, s>>>((const double*)(base + L.off64), ld, w.Dw, w.d);
+      DF_LAUNCHED("jpass1_fp64_kernel");
+    }
+    {
+      ProfScope ps("j_pass2_fp64", s);
+      dim3 grid2((unsigned)((ld / 2 + 255) / 256), (unsigned)w.nsplit_j);
+      jpass2_fp64_kernel<<<grid2, 256, 0, s>>>((const double*)(base + L.off64), ld, naux, w.d, w.Jpart);
+      DF_LAUNCHED("jpass2_fp64_kernel");
+    }
   } else {
     weighted_packed_density_kernel<float><<<g, 256, 0, s>>>(D, nao, npair, ld, w.Dw32);
     DF_LAUNCHED("weighted_packed_density_kernel");
-    jpass1_fp32_kernel<<<naux, 512, 0, s>>>((const float*)(base + L.off32), ld, w.Dw32, w.d);
-    DF_LAUNCHED("jpass1_fp32_kernel");
-    dim3 grid2((unsigned)((ld / 4 + 255) / 256), (unsigned)w.nsplit_j);
-    jpass2_fp32_kernel<<<grid2, 256, 0, s>>>((const float*)(base + L.off32), ld, naux, w.d, w.Jpart);
-    DF_LAUNCHED("jpass2_fp32_kernel");
+    {
+      ProfScope ps("j_pass1_fp32", s);
+      jpass1_fp32_kernel<<<naux, 512, 0, s>>>((const float*)(base + L.off32), ld, w.Dw32, w.d);
+      DF_LAUNCHED("jpass1_fp32_kernel");
+    }
+    {
+      ProfScope ps("j_pass2_fp32", s);
+      dim3 grid2((unsigned)((ld / 4 + 255) / 256), (unsigned)w.nsplit_j);
+      jpass2_fp32_kernel<<<grid2, 256, 0, s>>>((const float*)(base + L.off32), ld, naux, w.d, w.Jpart);
+      DF_LAUNCHED("jpass2_fp32_kernel");
+    }
   }
   jreduce_unpack_kernel<<<gp, 256, 0, s>>>(w.Jpart, w.nsplit_j, ld, nao, J);
   DF_LAUNCHED("jreduce_unpack_kernel");
@@ -336,15 +349,21 @@ int build_J(const void* Bbuf, const BLayout& L, int nao, int naux, int precision
 
 int build_K_fp64(const double* B64, long ld, int nao, int naux, const double* C, int nocc, double* K, const JKWork& w,
                  cudaStream_t s) {
-  dim3 grid((nocc + 31) / 32, (nao + 63) / 64, naux);
-  k_halftransform_fp64_kernel<<<grid, 256, 0, s>>>(B64, ld, nao, naux, C, nocc, w.X);
-  DF_LAUNCHED("k_halftransform_fp64_kernel");
+  {
+    ProfScope ps("k_halftransform_fp64", s);
+    dim3 grid((nocc + 31) / 32, (nao + 63) / 64, naux);
+    k_halftransform_fp64_kernel<<<grid, 256, 0, s>>>(B64, ld, nao, naux, C, nocc, w.X);
+    DF_LAUNCHED("k_halftransform_fp64_kernel");
+  }
   long kdim = (long)naux * nocc;
   long kchunk = (kdim + w.nsplit_k - 1) / w.nsplit_k;
   kchunk = (kchunk + 15) / 16 * 16;
   int nsplit = (int)((kdim + kchunk - 1) / kchunk);
-  DF_TRY(dgemm(false, true, nao, nao, (int)kdim, 1.0, w.X, kdim, 0, w.X, kdim, 0, 0.0, w.Kpart, nao,
-               (long)nao * nao, nsplit, s, kchunk, 1));
+  {
+    ProfScope ps("k_syrk_fp64", s);
+    DF_TRY(dgemm(false, true, nao, nao, (int)kdim, 1.0, w.X, kdim, 0, w.X, kdim, 0, 0.0, w.Kpart, nao,
+                 (long)nao * nao, nsplit, s, kchunk, 1));
+  }
   long nn = (long)nao * nao;
   ksum_mirror_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, s>>>(w.Kpart, nsplit, nao, K);
   DF_LAUNCHED("ksum_mirror_kernel");
@@ -356,10 +375,13 @@ int run_jk(const void* B, int nao, int naux, int precision, const double* D, con
   BLayout L = B_layout(nao, naux, precision);
   if (J) DF_TRY(build_J(B, L, nao, naux, precision, D, J, w, s));
   if (K) {
-    if (precision == DF_FP64)
+    if (precision == DF_FP64) {
+      DF_REQUIRE(w.X && w.Kpart, DF_ERR_ARG, "FP64 exchange requested with a workspace laid out for mixed precision");
       DF_TRY(build_K_fp64((const double*)((const char*)B + L.off64), L.ld, nao, naux, C, nocc, K, w, s));
-    else
+    } else {
+      DF_REQUIRE(w.mk.Xhi && w.mk.Kpart, DF_ERR_ARG, "mixed exchange requested with a workspace laid out for FP64");
       DF_TRY(build_K_mixed(B, L, nao, naux, C, nocc, K, w.mk, s));
+    }
   }
   return DF_OK;
 }
@@ -427,7 +449,7 @@ extern "C" int df_B_get_packed(const void* B, int nao, int naux, int P, double* 
 extern "C" size_t df_jk_work_bytes(int nao, int naux, int nocc, int precision) {
   if (nao <= 0 || naux <= 0 || nocc < 0) return 0;
   Sizer z;
-  jk_work_layout(nao, naux, nocc, precision, nullptr, &z);
+  jk_work_layout(nao, naux, nocc, precision, nullptr, &z, false);
   return z.used;
 }
 
@@ -442,7 +464,7 @@ extern "C" int df_jk(const void* B, int nao, int naux, int precision, const doub
   size_t need = df_jk_work_bytes(nao, naux, nocc, precision);
   DF_REQUIRE(work && work_bytes >= need, DF_ERR_NOMEM, "df_jk: workspace of %zu bytes < %zu", work_bytes, need);
   Arena a(work, work_bytes);
-  JKWork w = jk_work_layout(nao, naux, nocc, precision, &a, nullptr);
+  JKWork w = jk_work_layout(nao, naux, nocc, precision, &a, nullptr, false);
   DF_REQUIRE(!a.overflow, DF_ERR_NOMEM, "df_jk: workspace overflow");
   return run_jk(B, nao, naux, precision, D, C, nocc, J, K, w, s);
 }

@@ -60,7 +60,8 @@ struct JKWork {
 long B_ld(int nao);
 int nao_pad(int nao);
 BLayout B_layout(int nao, int naux, int precision);
-JKWork jk_work_layout(int nao, int naux, int nocc, int precision, Arena* a, Sizer* z);
+JKWork jk_work_layout(int nao, int naux, int nocc, int precision, Arena* a, Sizer* z, bool fp64_k);
+int umma_prepare();
 void mixed_k_work_layout(int nao, int naux, int nocc, Arena* a, Sizer* z, MixedKWork* w);
 int build_K_mixed(const void* B, const BLayout& L, int nao, int naux, const double* C, int nocc, double* K,
                   const MixedKWork& w, cudaStream_t s);

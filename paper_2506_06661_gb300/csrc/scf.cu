@@ -1,15 +1,19 @@
 // Restricted Hartree-Fock SCF over the DF Fock build, with Pulay DIIS and the
-// mixed -> FP64 precision switch.  The paper (arXiv 2506.06661) uses DF mean-field
-// methods (Section "Density fitting") and names DIIS as the default accelerator
-// (Section "Second-Order Self-Consistent Field"); the formulas are the textbook ones:
+// mixed -> FP64 precision switch, for one molecule (scf_run) or a batch of molecules of
+// uneven size (scf_run_batch).  The paper (arXiv 2506.06661) uses DF mean-field methods
+// (Section "Density fitting") and names DIIS as the default accelerator (Section
+// "Second-Order Self-Consistent Field"); the formulas are the textbook ones:
 //   F = h + J[D] - K,  K = K[C_occ] = 1/2 K[D] for D = 2 C_occ C_occ^T,
 //   E = 1/2 tr(D (h + F)) + E_nuc,
 //   e = X^T (F D S - S D F) X,  X = U s^-1/2 over eigenvalues s > lindep of S,
 //   Fbar = sum_i c_i F_i with [[B, -1], [-1, 0]] [c, lam] = [0, -1], B_ij = <e_i, e_j>.
-// Every matrix operation runs on the GPU; the host only reads a 64-byte status block per
-// iteration to decide convergence.  A starting density dm0 need not be idempotent
-// (Section "Initial Guess for Mean-field Methods"); its exchange matrix is formed from
-// the eigen-decomposition dm0 = sum_k n_k u_k u_k^T as K[C+] - K[C-].
+// One iteration is a fixed sequence of device work with no host decision inside it: the
+// DIIS ring (slot choice, ageing, restart on a singular system) lives in device memory,
+// so the iteration is captured once per precision into a CUDA graph and replayed.  The
+// host reads one small pinned status block per iteration to decide convergence and the
+// precision switch.  A starting density dm0 need not be idempotent (Section "Initial
+// Guess for Mean-field Methods"); its exchange matrix is formed from the eigen-
+// decomposition dm0 = sum_k n_k u_k u_k^T as K[C+] - K[C-] in an eager first iteration.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -20,15 +24,30 @@
 
 namespace dfscf {
 
+constexpr int DIIS_MAX = 16;
+
 struct ScfStatus {
   double energy;
   double emax;
   double trDS;
   double idem;   // ||D S D - 2 D||_F / ||D||_F
-  int singular;  // DIIS system had no usable pivot
+  double homo, lumo;
+  int singular;  // DIIS system had no usable pivot this iteration
   int nonfinite;
+  int eig_fail;
+  int pad;
 };
 
+struct DiisState {
+  int valid[DIIS_MAX];
+  long age[DIIS_MAX];
+  long tick;
+  int nvalid;
+  int slot;
+  int space;
+};
+
+// ---- elementwise / reduction kernels ----------------------------------------------------
 // F = h + J - K; status.energy = 1/2 sum D (h + F) + enuc; nonfinite flag.
 __global__ void fock_energy_kernel(const double* __restrict__ h, const double* __restrict__ J,
                                    const double* __restrict__ K, const double* __restrict__ D, long nn,
@@ -50,7 +69,7 @@ __global__ void fock_energy_kernel(const double* __restrict__ h, const double* _
   }
 }
 
-// comm = T - T^T (T = F D S);  for the DIIS error this is F D S - S D F.
+// out = T - T^T (T = F D S), i.e. F D S - S D F.
 __global__ void antisym_kernel(const double* __restrict__ T, int n, double* __restrict__ out) {
   long q = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= (long)n * n) return;
@@ -72,36 +91,91 @@ __global__ void absmax_kernel(const double* __restrict__ x, long n, double* out)
   }
 }
 
-// G[slot][j] = G[j][slot] = <E[slot], E[j]> for the occupied history slots.
-// E holds one nmo x nmo error matrix per slot (slot stride nn, ne = nmo*nmo entries used).
-__global__ void diis_gram_kernel(const double* __restrict__ E, long nn, long ne, int space, int slot,
-                                 const int* __restrict__ valid, double* __restrict__ G) {
+// ---- DIIS on device ------------------------------------------------------------------------
+__global__ void diis_reset_kernel(DiisState* d, int space) {
+  if (threadIdx.x != 0) return;
+  for (int k = 0; k < DIIS_MAX; ++k) {
+    d->valid[k] = 0;
+    d->age[k] = 0;
+  }
+  d->tick = 0;
+  d->nvalid = 0;
+  d->slot = 0;
+  d->space = space;
+}
+
+// Slot for the new (F, e) pair: a free one, else the oldest (at most `space` vectors kept).
+__global__ void diis_select_kernel(DiisState* d) {
+  if (threadIdx.x != 0) return;
+  int slot = -1;
+  for (int k = 0; k < d->space; ++k)
+    if (!d->valid[k]) {
+      slot = k;
+      break;
+    }
+  if (slot < 0) {
+    slot = 0;
+    for (int k = 1; k < d->space; ++k)
+      if (d->age[k] < d->age[slot]) slot = k;
+  } else {
+    d->nvalid++;
+  }
+  d->valid[slot] = 1;
+  d->age[slot] = ++d->tick;
+  d->slot = slot;
+}
+
+// Fhist[slot] = F, Ehist[slot] = E (E holds ne = nmo*nmo entries).
+__global__ void diis_store_kernel(const DiisState* __restrict__ d, const double* __restrict__ F,
+                                  const double* __restrict__ E, double* __restrict__ Fh, double* __restrict__ Eh,
+                                  long nn, long ne) {
+  long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  int slot = d->slot;
+  if (i < nn) Fh[(size_t)slot * nn + i] = F[i];
+  if (i < ne) Eh[(size_t)slot * nn + i] = E[i];
+}
+
+// G[slot][j] = G[j][slot] = <E[slot], E[j]> for valid slots j.
+__global__ void diis_gram_kernel(const DiisState* __restrict__ d, const double* __restrict__ Eh, long nn, long ne,
+                                 double* __restrict__ G) {
   __shared__ double sh[32];
   int j = blockIdx.x;
-  if (!valid[j]) return;
-  const double* a = E + (size_t)slot * nn;
-  const double* b = E + (size_t)j * nn;
+  if (j >= d->space || !d->valid[j]) return;
+  int slot = d->slot;
+  const double* a = Eh + (size_t)slot * nn;
+  const double* b = Eh + (size_t)j * nn;
   double s = 0.0;
   for (long i = threadIdx.x; i < ne; i += blockDim.x) s += a[i] * b[i];
   s = block_sum(s, sh);
   if (threadIdx.x == 0) {
-    G[slot * space + j] = s;
-    G[j * space + slot] = s;
+    G[slot * DIIS_MAX + j] = s;
+    G[j * DIIS_MAX + slot] = s;
   }
 }
 
-// Solve the bordered Pulay system for the m valid slots (listed in order[]), one lane.
-// On a singular system the newest vector gets coefficient 1 and st->singular is set.
-__global__ void diis_solve_kernel(const double* __restrict__ G, int space, const int* __restrict__ order, int m,
-                                  int newest, double* __restrict__ coef, ScfStatus* st) {
+// Solve the bordered Pulay system over the valid slots (one lane).  With fewer than two
+// vectors, or when no pivot exceeds 1e-14 of the largest entry, the newest vector gets
+// coefficient 1; in the singular case the history restarts from the newest vector.
+__global__ void diis_solve_kernel(DiisState* d, const double* __restrict__ G, double* __restrict__ coef,
+                                  ScfStatus* st) {
   if (threadIdx.x != 0) return;
-  double A[17][18];
+  int order[DIIS_MAX];
+  int m = 0;
+  for (int k = 0; k < d->space; ++k)
+    if (d->valid[k]) order[m++] = k;
+  for (int i = 0; i < DIIS_MAX; ++i) coef[i] = 0.0;
+  st->singular = 0;
+  if (m < 2) {
+    coef[d->slot] = 1.0;
+    return;
+  }
+  double A[DIIS_MAX + 1][DIIS_MAX + 2];
   int dim = m + 1;
   double scale = 0.0;
-  for (int i = 0; i < m; ++i) scale = fmax(scale, fabs(G[order[i] * space + order[i]]));
+  for (int i = 0; i < m; ++i) scale = fmax(scale, fabs(G[order[i] * DIIS_MAX + order[i]]));
   if (!(scale > 0.0)) scale = 1.0;
   for (int i = 0; i < m; ++i) {
-    for (int j = 0; j < m; ++j) A[i][j] = G[order[i] * space + order[j]] / scale;
+    for (int j = 0; j < m; ++j) A[i][j] = G[order[i] * DIIS_MAX + order[j]] / scale;
     A[i][m] = -1.0;
     A[m][i] = -1.0;
     A[i][dim] = 0.0;
@@ -131,9 +205,8 @@ __global__ void diis_solve_kernel(const double* __restrict__ G, int space, const
       for (int k = c; k <= dim; ++k) A[r][k] -= f * A[c][k];
     }
   }
-  for (int i = 0; i < space; ++i) coef[i] = 0.0;
   if (ok) {
-    double x[17];
+    double x[DIIS_MAX + 1];
     for (int r = dim - 1; r >= 0; --r) {
       double s = A[r][dim];
       for (int k = r + 1; k < dim; ++k) s -= A[r][k] * x[k];
@@ -145,23 +218,26 @@ __global__ void diis_solve_kernel(const double* __restrict__ G, int space, const
     }
   }
   if (!ok) {
-    for (int i = 0; i < space; ++i) coef[i] = 0.0;
-    coef[newest] = 1.0;
+    for (int i = 0; i < DIIS_MAX; ++i) coef[i] = 0.0;
+    coef[d->slot] = 1.0;
+    for (int k = 0; k < DIIS_MAX; ++k) d->valid[k] = (k == d->slot);
+    d->nvalid = 1;
+    st->singular = 1;
   }
-  st->singular = ok ? 0 : 1;
 }
 
-// out = sum_s coef[s] Fh[s] over valid slots.
-__global__ void diis_combine_kernel(const double* __restrict__ Fh, long nn, int space, const double* __restrict__ coef,
-                                    const int* __restrict__ valid, double* __restrict__ out) {
+// out = sum_k coef[k] Fh[k] over valid slots.
+__global__ void diis_combine_kernel(const DiisState* __restrict__ d, const double* __restrict__ Fh, long nn,
+                                    const double* __restrict__ coef, double* __restrict__ out) {
   long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nn) return;
   double s = 0.0;
-  for (int k = 0; k < space; ++k)
-    if (valid[k]) s += coef[k] * Fh[(size_t)k * nn + i];
+  for (int k = 0; k < d->space; ++k)
+    if (d->valid[k]) s += coef[k] * Fh[(size_t)k * nn + i];
   out[i] = s;
 }
 
+// ---- orbitals ---------------------------------------------------------------------------------
 // X[:, j] = U[:, n - nmo + j] / sqrt(s[n - nmo + j]) with U given as rows UT (eigenvector rows).
 __global__ void canonical_x_kernel(const double* __restrict__ UT, const double* __restrict__ s, int n, int nmo,
                                    double* __restrict__ X) {
@@ -180,9 +256,13 @@ __global__ void occ_columns_kernel(const double* __restrict__ ZT, int nmo, int n
   Cp[q] = ZT[(size_t)j * nmo + i];
 }
 
-__global__ void scale_kernel(double* __restrict__ x, long n, double a) {
-  long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) x[i] *= a;
+// HOMO / LUMO of the last diagonalisation and its eigensolver status into the status block.
+__global__ void orbital_status_kernel(const double* __restrict__ eps, int nmo, int nocc, const int* eig_status,
+                                      ScfStatus* st) {
+  if (threadIdx.x != 0) return;
+  st->homo = nocc > 0 ? eps[nocc - 1] : 0.0;
+  st->lumo = nocc < nmo ? eps[nocc] : 0.0;
+  st->eig_fail = *eig_status;
 }
 
 __global__ void axpy_kernel(double* __restrict__ y, const double* __restrict__ x, long n, double a) {
@@ -210,8 +290,7 @@ __global__ void guess_check_kernel(const double* __restrict__ D, const double* _
   }
 }
 
-// Columns of eigenvector rows ZT [n][n] with eigenvalue w > thr (pos) or < -thr (neg),
-// scaled by sqrt(|w|/2):  dm0 / 2 = C+ C+^T - C- C-^T.
+// Columns idx[0..cnt) of eigenvector rows ZT scaled by sqrt(|w|/2): dm0/2 = C+ C+^T - C- C-^T.
 __global__ void split_density_kernel(const double* __restrict__ ZT, const double* __restrict__ w, int n,
                                      const int* __restrict__ idx, int cnt, double* __restrict__ Cout) {
   long q = (long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -223,19 +302,19 @@ __global__ void split_density_kernel(const double* __restrict__ ZT, const double
 
 static unsigned blocks_for(long n, int t = 256) { return (unsigned)((n + t - 1) / t); }
 
+// ---- per-molecule workspace --------------------------------------------------------------
 struct ScfWork {
-  double *L, *pair_tab, *S, *h, *V, *X, *F, *Fbar, *J, *K, *D, *Cocc, *T1, *T2, *E, *Fp, *ZT, *eps, *Fhist, *Ehist,
-      *G, *coef, *eig_scratch, *enuc, *Cchunk;
-  int *valid, *order, *eig_status, *chol_status, *idx;
-  double* maxdiag;
+  double *L, *pair_tab, *S, *h, *V, *X, *F, *Fbar, *J, *K, *D, *Dprev, *Cocc, *Cprev, *Cchunk, *T1, *T2, *E, *Fp,
+      *ZT, *eps, *Fhist, *Ehist, *G, *coef, *eig_scratch, *enuc, *maxdiag;
+  int *eig_status, *chol_status, *idx;
   ScfStatus* st;
+  DiisState* diis;
   void* B;
   JKWork jk;
 };
 
 static void scf_layout(int nao, int naux, int nocc, int precision, Arena* a, Sizer* z, ScfWork* w) {
   size_t nn = (size_t)nao * nao;
-  const int space = 16;
 #define TAKE(T, ptr, count) \
   if (a) ptr = a->take<T>(count); else z->take<T>(count);
   TAKE(double, w->L, (size_t)naux * naux);
@@ -249,7 +328,9 @@ static void scf_layout(int nao, int naux, int nocc, int precision, Arena* a, Siz
   TAKE(double, w->J, nn);
   TAKE(double, w->K, nn);
   TAKE(double, w->D, nn);
+  TAKE(double, w->Dprev, nn);
   TAKE(double, w->Cocc, (size_t)nao * nocc);
+  TAKE(double, w->Cprev, (size_t)nao * nocc);
   TAKE(double, w->Cchunk, (size_t)nao * nocc);
   TAKE(double, w->T1, nn);
   TAKE(double, w->T2, nn);
@@ -257,36 +338,32 @@ static void scf_layout(int nao, int naux, int nocc, int precision, Arena* a, Siz
   TAKE(double, w->Fp, nn);
   TAKE(double, w->ZT, nn);
   TAKE(double, w->eps, nao);
-  TAKE(double, w->Fhist, space * nn);
-  TAKE(double, w->Ehist, space * nn);
-  TAKE(double, w->G, space * space);
-  TAKE(double, w->coef, space);
+  TAKE(double, w->Fhist, DIIS_MAX * nn);
+  TAKE(double, w->Ehist, DIIS_MAX * nn);
+  TAKE(double, w->G, DIIS_MAX * DIIS_MAX);
+  TAKE(double, w->coef, DIIS_MAX);
   TAKE(double, w->eig_scratch, eigh_scratch_doubles(nao));
   TAKE(double, w->enuc, 1);
   TAKE(double, w->maxdiag, 1);
-  TAKE(int, w->valid, space);
-  TAKE(int, w->order, space);
   TAKE(int, w->eig_status, 1);
   TAKE(int, w->chol_status, 1);
   TAKE(int, w->idx, nao);
   TAKE(ScfStatus, w->st, 1);
+  TAKE(DiisState, w->diis, 1);
   if (a) w->B = a->take<char>(df_B_bytes(nao, naux, precision)); else z->take<char>(df_B_bytes(nao, naux, precision));
 #undef TAKE
-  w->jk = jk_work_layout(nao, naux, nocc, precision, a, z);
+  w->jk = jk_work_layout(nao, naux, nocc, precision, a, z, true);
 }
 
-// Eigenpairs of the symmetric n x n matrix in `A` (destroyed): w ascending, rows ZT.
-static int eig_sync(double* A, int n, double* w, double* ZT, ScfWork& W, cudaStream_t s) {
-  DF_TRY(eigh_rows(A, n, w, ZT, W.eig_scratch, W.eig_status, s));
-  return DF_OK;
+static int eig_rows(double* A, int n, double* w, double* ZT, ScfWork& W, cudaStream_t s) {
+  return eigh_rows(A, n, w, ZT, W.eig_scratch, W.eig_status, s);
 }
 
 // Occupied coefficients from a Fock-like matrix: C_occ = X C'_occ, D = 2 C C^T.
 static int diagonalize_fock(const double* Fm, int nao, int nmo, int nocc, ScfWork& W, cudaStream_t s) {
-  // Fp = X^T F X
   DF_TRY(dgemm(false, false, nao, nmo, nao, 1.0, Fm, nao, 0, W.X, nmo, 0, 0.0, W.T1, nmo, 0, 1, s, 0, 0));
   DF_TRY(dgemm(true, false, nmo, nmo, nao, 1.0, W.X, nmo, 0, W.T1, nmo, 0, 0.0, W.Fp, nmo, 0, 1, s, 0, 0));
-  DF_TRY(eig_sync(W.Fp, nmo, W.eps, W.ZT, W, s));
+  DF_TRY(eig_rows(W.Fp, nmo, W.eps, W.ZT, W, s));
   occ_columns_kernel<<<blocks_for((long)nmo * nocc), 256, 0, s>>>(W.ZT, nmo, nocc, W.T2);
   DF_LAUNCHED("occ_columns_kernel");
   DF_TRY(dgemm(false, false, nao, nocc, nmo, 1.0, W.X, nmo, 0, W.T2, nocc, 0, 0.0, W.Cocc, nocc, 0, 1, s, 0, 0));
@@ -294,209 +371,290 @@ static int diagonalize_fock(const double* Fm, int nao, int nmo, int nocc, ScfWor
   return DF_OK;
 }
 
-int scf_driver(const df_molecule* mol, const scf_opts* o, const double* dm0, double* D_out, double* C_out,
-               double* mo_energy, scf_result* res, ScfWork& W, cudaStream_t s) {
-  const int nao = mol->nao, naux = mol->naux, nocc = mol->nelec / 2;
-  const long nn = (long)nao * nao;
-  const int space = o->diis_space;
-  memset(res, 0, sizeof(*res));
-  // ---- integrals, metric, B ----------------------------------------------------------
-  DF_TRY(launch_int1e(mol->ao_xyz, mol->ao_exp, nao, mol->xyz, mol->charges, mol->natm, W.S, W.T1, W.V, s));
-  axpy_kernel<<<blocks_for(nn), 256, 0, s>>>(W.T1, W.V, nn, 1.0);
-  DF_LAUNCHED("axpy_kernel");
-  DF_CUDA(cudaMemcpyAsync(W.h, W.T1, sizeof(double) * nn, cudaMemcpyDeviceToDevice, s));
-  DF_TRY(launch_enuc(mol->xyz, mol->charges, mol->natm, W.enuc, s));
-  DF_TRY(launch_int2c(mol->aux_xyz, mol->aux_exp, naux, W.L, s));
-  DF_TRY(cholesky_inplace(W.L, naux, W.chol_status, W.maxdiag, 1e-14, s));
-  int chol_bad = -1;
-  DF_CUDA(cudaMemcpyAsync(&chol_bad, W.chol_status, sizeof(int), cudaMemcpyDeviceToHost, s));
-  DF_CUDA(cudaStreamSynchronize(s));
-  DF_REQUIRE(chol_bad < 0, DF_ERR_NOT_SPD, "scf_run: auxiliary metric not positive definite at pivot %d", chol_bad);
-  DF_TRY(build_B(mol->ao_xyz, mol->ao_exp, nao, mol->aux_xyz, mol->aux_exp, naux, W.L, o->precision, W.B, W.pair_tab, s));
-  // ---- canonical orthogonalisation ----------------------------------------------------
-  DF_CUDA(cudaMemcpyAsync(W.T1, W.S, sizeof(double) * nn, cudaMemcpyDeviceToDevice, s));
-  DF_TRY(eig_sync(W.T1, nao, W.eps, W.ZT, W, s));
-  std::vector<double> hs(nao);
-  int eig_bad = 0;
-  DF_CUDA(cudaMemcpyAsync(hs.data(), W.eps, sizeof(double) * nao, cudaMemcpyDeviceToHost, s));
-  DF_CUDA(cudaMemcpyAsync(&eig_bad, W.eig_status, sizeof(int), cudaMemcpyDeviceToHost, s));
-  DF_CUDA(cudaMemcpyAsync(&res->e_nuc, W.enuc, sizeof(double), cudaMemcpyDeviceToHost, s));
-  DF_CUDA(cudaStreamSynchronize(s));
-  DF_REQUIRE(eig_bad == 0, DF_ERR_NOCONV, "scf_run: eigensolver failed on S");
-  int nmo = 0;
-  for (int i = 0; i < nao; ++i) nmo += hs[i] > o->lindep;
-  DF_REQUIRE(nmo >= nocc + 1 || (nmo >= nocc && nocc > 0), DF_ERR_ARG, "scf_run: only %d orbitals after lindep", nmo);
-  res->nmo = nmo;
-  canonical_x_kernel<<<blocks_for((long)nao * nmo), 256, 0, s>>>(W.ZT, W.eps, nao, nmo, W.X);
-  DF_LAUNCHED("canonical_x_kernel");
-  // ---- guess ---------------------------------------------------------------------------
-  bool use_dm0 = false;
-  if (dm0) {
-    DF_TRY(dgemm(false, false, nao, nao, nao, 1.0, dm0, nao, 0, W.S, nao, 0, 0.0, W.T1, nao, 0, 1, s, 0, 0));
-    DF_TRY(dgemm(false, false, nao, nao, nao, 1.0, W.T1, nao, 0, dm0, nao, 0, 0.0, W.T2, nao, 0, 1, s, 0, 0));
-    guess_check_kernel<<<1, 1024, 0, s>>>(dm0, W.S, W.T2, nn, W.st);
-    DF_LAUNCHED("guess_check_kernel");
-    ScfStatus hst;
-    DF_CUDA(cudaMemcpyAsync(&hst, W.st, sizeof(hst), cudaMemcpyDeviceToHost, s));
-    DF_CUDA(cudaStreamSynchronize(s));
-    use_dm0 = std::isfinite(hst.trDS) && fabs(hst.trDS - mol->nelec) / mol->nelec < 0.05 && hst.idem < 0.5;
-    res->guess = use_dm0 ? 1 : 2;
-  }
-  if (use_dm0) {
-    DF_CUDA(cudaMemcpyAsync(W.D, dm0, sizeof(double) * nn, cudaMemcpyDeviceToDevice, s));
-  } else {
-    DF_TRY(diagonalize_fock(W.h, nao, nmo, nocc, W, s));
-  }
-  // ---- iterations ----------------------------------------------------------------------
-  std::vector<int> hvalid(space, 0), horder(space, 0);
-  std::vector<long> age(space, 0);
-  int nvalid = 0;
-  long tick = 0;
-  DF_CUDA(cudaMemsetAsync(W.valid, 0, sizeof(int) * space, s));
-  int prec = o->precision;
-  bool switched = (prec == DF_FP64);
+// ---- one molecule's SCF state machine ----------------------------------------------------------
+struct ScfMol {
+  df_molecule mol{};
+  scf_opts opt{};
+  int nao = 0, naux = 0, nocc = 0, nmo = 0;
+  ScfWork W{};
+  cudaStream_t s = nullptr;
+  ScfStatus* hst = nullptr;   // pinned host mirror of W.st
+  int prec = DF_FP64;
+  bool switched = false;
+  bool first_dm0 = false;
   int fp64_done = 0;
   double e_old = 0.0;
   bool have_old = false;
-  bool first_dm0 = use_dm0;
-  ScfStatus hst{};
-  int it = 0;
-  for (it = 1; it <= o->max_cycle; ++it) {
-    // ---- J, K -------------------------------------------------------------------------
-    if (first_dm0) {
-      // K for a general density from its eigen-decomposition (dm0/2 = C+ C+^T - C- C-^T)
-      DF_TRY(run_jk(W.B, nao, naux, prec, W.D, nullptr, 0, W.J, nullptr, W.jk, s));
-      DF_CUDA(cudaMemcpyAsync(W.T1, W.D, sizeof(double) * nn, cudaMemcpyDeviceToDevice, s));
-      DF_TRY(eig_sync(W.T1, nao, W.eps, W.ZT, W, s));
-      std::vector<double> wv(nao);
-      DF_CUDA(cudaMemcpyAsync(wv.data(), W.eps, sizeof(double) * nao, cudaMemcpyDeviceToHost, s));
-      DF_CUDA(cudaStreamSynchronize(s));
-      double wmax = 0.0;
-      for (double x : wv) wmax = fmax(wmax, fabs(x));
-      DF_CUDA(cudaMemsetAsync(W.K, 0, sizeof(double) * nn, s));
-      for (int sign = 1; sign >= -1; sign -= 2) {
-        std::vector<int> ids;
-        for (int k = 0; k < nao; ++k)
-          if (sign * wv[k] > 1e-12 * wmax) ids.push_back(k);
-        for (size_t c0 = 0; c0 < ids.size(); c0 += nocc) {
-          int cnt = (int)std::min((size_t)nocc, ids.size() - c0);
-          DF_CUDA(cudaMemcpyAsync(W.idx, ids.data() + c0, sizeof(int) * cnt, cudaMemcpyHostToDevice, s));
-          split_density_kernel<<<blocks_for((long)nao * cnt), 256, 0, s>>>(W.ZT, W.eps, nao, W.idx, cnt, W.Cchunk);
-          DF_LAUNCHED("split_density_kernel");
-          DF_TRY(run_jk(W.B, nao, naux, prec, nullptr, W.Cchunk, cnt, nullptr, W.T2, W.jk, s));
-          axpy_kernel<<<blocks_for(nn), 256, 0, s>>>(W.K, W.T2, nn, (double)sign);
-          DF_LAUNCHED("axpy_kernel");
-          DF_CUDA(cudaStreamSynchronize(s));  // host vector ids is reused
-        }
-      }
-      first_dm0 = false;
-    } else {
-      DF_TRY(run_jk(W.B, nao, naux, prec, W.D, W.Cocc, nocc, W.J, W.K, W.jk, s));
-    }
-    // ---- Fock, energy, DIIS error -------------------------------------------------------
-    fock_energy_kernel<<<1, 1024, 0, s>>>(W.h, W.J, W.K, W.D, nn, W.enuc, W.F, W.st);
-    DF_LAUNCHED("fock_energy_kernel");
-    DF_TRY(dgemm(false, false, nao, nao, nao, 1.0, W.F, nao, 0, W.D, nao, 0, 0.0, W.T1, nao, 0, 1, s, 0, 0));
-    DF_TRY(dgemm(false, false, nao, nao, nao, 1.0, W.T1, nao, 0, W.S, nao, 0, 0.0, W.T2, nao, 0, 1, s, 0, 0));
-    antisym_kernel<<<blocks_for(nn), 256, 0, s>>>(W.T2, nao, W.T1);
-    DF_LAUNCHED("antisym_kernel");
-    DF_TRY(dgemm(false, false, nao, nmo, nao, 1.0, W.T1, nao, 0, W.X, nmo, 0, 0.0, W.T2, nmo, 0, 1, s, 0, 0));
-    // slot for the new vector: a free one, else the oldest
-    int slot = -1;
-    for (int k = 0; k < space; ++k)
-      if (!hvalid[k]) { slot = k; break; }
-    if (slot < 0) {
-      slot = 0;
-      for (int k = 1; k < space; ++k)
-        if (age[k] < age[slot]) slot = k;
-    }
-    double* Eslot = W.Ehist + (size_t)slot * nn;
-    DF_TRY(dgemm(true, false, nmo, nmo, nao, 1.0, W.X, nmo, 0, W.T2, nmo, 0, 0.0, Eslot, nmo, 0, 1, s, 0, 0));
-    absmax_kernel<<<1, 1024, 0, s>>>(Eslot, (long)nmo * nmo, &W.st->emax);
-    DF_LAUNCHED("absmax_kernel");
-    DF_CUDA(cudaMemcpyAsync(&hst, W.st, sizeof(hst), cudaMemcpyDeviceToHost, s));
+  bool done = false;
+  int rc = DF_OK;
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  scf_result res{};
+  const double* dm0 = nullptr;
+  double* D_out = nullptr;
+  double* C_out = nullptr;
+  double* mo_out = nullptr;
+
+  ~ScfMol() {
+    for (auto& g : graph)
+      if (g) cudaGraphExecDestroy(g);
+  }
+};
+
+// Integrals, metric, B, orthogonalisation and the starting density.  Synchronises s.
+static int scf_setup(ScfMol& M) {
+  const df_molecule* mol = &M.mol;
+  cudaStream_t s = M.s;
+  ScfWork& W = M.W;
+  const int nao = M.nao, naux = M.naux, nocc = M.nocc;
+  const long nn = (long)nao * nao;
+  memset(&M.res, 0, sizeof(M.res));
+  DF_TRY(umma_prepare());
+  DF_TRY(launch_int1e(mol->ao_xyz, mol->ao_exp, nao, mol->xyz, mol->charges, mol->natm, W.S, W.h, W.V, s));
+  axpy_kernel<<<blocks_for(nn), 256, 0, s>>>(W.h, W.V, nn, 1.0);
+  DF_LAUNCHED("axpy_kernel");
+  DF_TRY(launch_enuc(mol->xyz, mol->charges, mol->natm, W.enuc, s));
+  DF_TRY(launch_int2c(mol->aux_xyz, mol->aux_exp, naux, W.L, s));
+  DF_TRY(cholesky_inplace(W.L, naux, W.chol_status, W.maxdiag, 1e-14, s));
+  DF_TRY(build_B(mol->ao_xyz, mol->ao_exp, nao, mol->aux_xyz, mol->aux_exp, naux, W.L, M.opt.precision, W.B,
+                 W.pair_tab, s));
+  DF_CUDA(cudaMemcpyAsync(W.T1, W.S, sizeof(double) * nn, cudaMemcpyDeviceToDevice, s));
+  DF_TRY(eig_rows(W.T1, nao, W.eps, W.ZT, W, s));
+  std::vector<double> hs(nao);
+  int eig_bad = 0, chol_bad = -1;
+  DF_CUDA(cudaMemcpyAsync(hs.data(), W.eps, sizeof(double) * nao, cudaMemcpyDeviceToHost, s));
+  DF_CUDA(cudaMemcpyAsync(&eig_bad, W.eig_status, sizeof(int), cudaMemcpyDeviceToHost, s));
+  DF_CUDA(cudaMemcpyAsync(&chol_bad, W.chol_status, sizeof(int), cudaMemcpyDeviceToHost, s));
+  DF_CUDA(cudaMemcpyAsync(&M.res.e_nuc, W.enuc, sizeof(double), cudaMemcpyDeviceToHost, s));
+  DF_CUDA(cudaStreamSynchronize(s));
+  DF_REQUIRE(chol_bad < 0, DF_ERR_NOT_SPD, "scf: auxiliary metric not positive definite at pivot %d", chol_bad);
+  DF_REQUIRE(eig_bad == 0, DF_ERR_NOCONV, "scf: eigensolver failed on S");
+  int nmo = 0;
+  for (int i = 0; i < nao; ++i) nmo += hs[i] > M.opt.lindep;
+  DF_REQUIRE(nmo >= nocc, DF_ERR_ARG, "scf: only %d orbitals above lindep for %d occupied", nmo, nocc);
+  M.nmo = nmo;
+  M.res.nmo = nmo;
+  canonical_x_kernel<<<blocks_for((long)nao * nmo), 256, 0, s>>>(W.ZT, W.eps, nao, nmo, W.X);
+  DF_LAUNCHED("canonical_x_kernel");
+  bool use_dm0 = false;
+  if (M.dm0) {
+    DF_TRY(dgemm(false, false, nao, nao, nao, 1.0, M.dm0, nao, 0, W.S, nao, 0, 0.0, W.T1, nao, 0, 1, s, 0, 0));
+    DF_TRY(dgemm(false, false, nao, nao, nao, 1.0, W.T1, nao, 0, M.dm0, nao, 0, 0.0, W.T2, nao, 0, 1, s, 0, 0));
+    guess_check_kernel<<<1, 1024, 0, s>>>(M.dm0, W.S, W.T2, nn, W.st);
+    DF_LAUNCHED("guess_check_kernel");
+    DF_CUDA(cudaMemcpyAsync(M.hst, W.st, sizeof(ScfStatus), cudaMemcpyDeviceToHost, s));
     DF_CUDA(cudaStreamSynchronize(s));
-    res->iterations = it;
-    if (prec == DF_FP64) res->fp64_iterations++;
-    DF_REQUIRE(!hst.nonfinite && std::isfinite(hst.emax), DF_ERR_NUMERIC, "scf_run: non-finite Fock matrix at iteration %d", it);
-    double de = have_old ? fabs(hst.energy - e_old) : INFINITY;
-    res->energy = hst.energy;
-    res->last_de = de;
-    res->last_err = hst.emax;
-    if (o->verbose)
-      printf("scf iter %3d  %s  E = %.12f  dE = %.3e  max|e| = %.3e\n", it, prec == DF_FP64 ? "fp64 " : "mixed", hst.energy,
-             de, hst.emax);
-    if (prec == DF_FP64 && switched && fp64_done + 1 >= o->n_fp64_final && have_old && de < o->conv_tol &&
-        hst.emax < o->conv_err) {
-      res->converged = 1;
-      break;
-    }
-    if (prec == DF_FP64) fp64_done++;
-    // ---- DIIS ---------------------------------------------------------------------------
-    DF_CUDA(cudaMemcpyAsync(W.Fhist + (size_t)slot * nn, W.F, sizeof(double) * nn, cudaMemcpyDeviceToDevice, s));
-    if (!hvalid[slot]) nvalid++;
-    hvalid[slot] = 1;
-    age[slot] = ++tick;
-    if (nvalid > space) nvalid = space;
-    // keep at most diis_space vectors: drop the oldest beyond that
-    while (nvalid > o->diis_space) {
-      int old = -1;
-      for (int k = 0; k < space; ++k)
-        if (hvalid[k] && (old < 0 || age[k] < age[old])) old = k;
-      hvalid[old] = 0;
-      nvalid--;
-    }
-    DF_CUDA(cudaMemcpyAsync(W.valid, hvalid.data(), sizeof(int) * space, cudaMemcpyHostToDevice, s));
-    // Gram row of the new vector (E stored with leading dimension nmo, nmo*nmo entries)
-    diis_gram_kernel<<<space, 256, 0, s>>>(W.Ehist, nn, (long)nmo * nmo, space, slot, W.valid, W.G);
-    DF_LAUNCHED("diis_gram_kernel");
-    const double* Fuse = W.F;
-    if (nvalid >= 2) {
-      int m = 0;
-      for (int k = 0; k < space; ++k)
-        if (hvalid[k]) horder[m++] = k;
-      DF_CUDA(cudaMemcpyAsync(W.order, horder.data(), sizeof(int) * m, cudaMemcpyHostToDevice, s));
-      diis_solve_kernel<<<1, 32, 0, s>>>(W.G, space, W.order, m, slot, W.coef, W.st);
-      DF_LAUNCHED("diis_solve_kernel");
-      diis_combine_kernel<<<blocks_for(nn), 256, 0, s>>>(W.Fhist, nn, space, W.coef, W.valid, W.Fbar);
-      DF_LAUNCHED("diis_combine_kernel");
-      Fuse = W.Fbar;
-    }
-    DF_TRY(diagonalize_fock(Fuse, nao, nmo, nocc, W, s));
-    if (nvalid >= 2) {
-      int sing = 0;
-      DF_CUDA(cudaMemcpyAsync(&sing, &W.st->singular, sizeof(int), cudaMemcpyDeviceToHost, s));
-      DF_CUDA(cudaStreamSynchronize(s));
-      if (sing) {  // restart the history from the newest vector
-        for (int k = 0; k < space; ++k) hvalid[k] = (k == slot);
-        nvalid = 1;
-      }
-    }
-    // ---- mixed -> FP64 switch --------------------------------------------------------------
-    if (!switched && have_old && (de < o->switch_tol || hst.emax < o->switch_err)) {
-      switched = true;
-      prec = DF_FP64;
-      for (int k = 0; k < space; ++k) hvalid[k] = 0;
-      nvalid = 0;
-    }
-    e_old = hst.energy;
-    have_old = true;
+    use_dm0 = std::isfinite(M.hst->trDS) && fabs(M.hst->trDS - mol->nelec) / mol->nelec < 0.05 && M.hst->idem < 0.5;
+    M.res.guess = use_dm0 ? 1 : 2;
   }
-  // orbital energies of the last diagonalisation
-  std::vector<double> he(nmo);
-  DF_CUDA(cudaMemcpyAsync(he.data(), W.eps, sizeof(double) * nmo, cudaMemcpyDeviceToHost, s));
-  DF_CUDA(cudaStreamSynchronize(s));
-  res->homo = nocc > 0 ? he[nocc - 1] : 0.0;
-  res->lumo = nocc < nmo ? he[nocc] : 0.0;
-  if (D_out) DF_CUDA(cudaMemcpyAsync(D_out, W.D, sizeof(double) * nn, cudaMemcpyDeviceToDevice, s));
-  if (C_out) DF_CUDA(cudaMemcpyAsync(C_out, W.Cocc, sizeof(double) * nao * nocc, cudaMemcpyDeviceToDevice, s));
-  if (mo_energy) DF_CUDA(cudaMemcpyAsync(mo_energy, W.eps, sizeof(double) * std::min(nmo, nocc + 1), cudaMemcpyDeviceToDevice, s));
-  DF_CUDA(cudaStreamSynchronize(s));
-  if (!res->converged) {
-    set_error("scf_run: not converged after %d iterations (dE %.3e, max|e| %.3e)", res->iterations, res->last_de,
-              res->last_err);
-    return DF_ERR_NOCONV;
+  if (use_dm0) {
+    DF_CUDA(cudaMemcpyAsync(W.D, M.dm0, sizeof(double) * nn, cudaMemcpyDeviceToDevice, s));
+  } else {
+    DF_TRY(diagonalize_fock(W.h, nao, nmo, nocc, W, s));
   }
+  diis_reset_kernel<<<1, 32, 0, s>>>(W.diis, M.opt.diis_space);
+  DF_LAUNCHED("diis_reset_kernel");
+  M.first_dm0 = use_dm0;
+  M.prec = M.opt.precision;
+  M.switched = (M.prec == DF_FP64);
+  return DF_OK;
+}
+
+// J and K for a general starting density (first iteration with dm0), eager launches.
+static int jk_general_density(ScfMol& M) {
+  ScfWork& W = M.W;
+  cudaStream_t s = M.s;
+  const int nao = M.nao, naux = M.naux, nocc = M.nocc;
+  const long nn = (long)nao * nao;
+  DF_TRY(run_jk(W.B, nao, naux, M.prec, W.D, nullptr, 0, W.J, nullptr, W.jk, s));
+  DF_CUDA(cudaMemcpyAsync(W.T1, W.D, sizeof(double) * nn, cudaMemcpyDeviceToDevice, s));
+  DF_TRY(eig_rows(W.T1, nao, W.eps, W.ZT, W, s));
+  std::vector<double> wv(nao);
+  DF_CUDA(cudaMemcpyAsync(wv.data(), W.eps, sizeof(double) * nao, cudaMemcpyDeviceToHost, s));
+  DF_CUDA(cudaStreamSynchronize(s));
+  double wmax = 0.0;
+  for (double x : wv) wmax = fmax(wmax, fabs(x));
+  DF_CUDA(cudaMemsetAsync(W.K, 0, sizeof(double) * nn, s));
+  std::vector<int> ids;
+  for (int sign = 1; sign >= -1; sign -= 2) {
+    ids.clear();
+    for (int k = 0; k < nao; ++k)
+      if (sign * wv[k] > 1e-12 * wmax) ids.push_back(k);
+    for (size_t c0 = 0; c0 < ids.size(); c0 += nocc) {
+      int cnt = (int)std::min((size_t)nocc, ids.size() - c0);
+      DF_CUDA(cudaMemcpyAsync(W.idx, ids.data() + c0, sizeof(int) * cnt, cudaMemcpyHostToDevice, s));
+      split_density_kernel<<<blocks_for((long)nao * cnt), 256, 0, s>>>(W.ZT, W.eps, nao, W.idx, cnt, W.Cchunk);
+      DF_LAUNCHED("split_density_kernel");
+      DF_TRY(run_jk(W.B, nao, naux, M.prec, nullptr, W.Cchunk, cnt, nullptr, W.T2, W.jk, s));
+      axpy_kernel<<<blocks_for(nn), 256, 0, s>>>(W.K, W.T2, nn, (double)sign);
+      DF_LAUNCHED("axpy_kernel");
+      DF_CUDA(cudaStreamSynchronize(s));  // W.idx is refilled from the host vector
+    }
+  }
+  return DF_OK;
+}
+
+// Everything after J and K: Fock, energy, DIIS error and extrapolation, diagonalisation,
+// status readback.  No host decisions: capturable.
+static int iteration_tail(ScfMol& M) {
+  ScfWork& W = M.W;
+  cudaStream_t s = M.s;
+  const int nao = M.nao, nmo = M.nmo, nocc = M.nocc;
+  const long nn = (long)nao * nao, ne = (long)nmo * nmo;
+  fock_energy_kernel<<<1, 1024, 0, s>>>(W.h, W.J, W.K, W.D, nn, W.enuc, W.F, W.st);
+  DF_LAUNCHED("fock_energy_kernel");
+  DF_TRY(dgemm(false, false, nao, nao, nao, 1.0, W.F, nao, 0, W.D, nao, 0, 0.0, W.T1, nao, 0, 1, s, 0, 0));
+  DF_TRY(dgemm(false, false, nao, nao, nao, 1.0, W.T1, nao, 0, W.S, nao, 0, 0.0, W.T2, nao, 0, 1, s, 0, 0));
+  antisym_kernel<<<blocks_for(nn), 256, 0, s>>>(W.T2, nao, W.T1);
+  DF_LAUNCHED("antisym_kernel");
+  DF_TRY(dgemm(false, false, nao, nmo, nao, 1.0, W.T1, nao, 0, W.X, nmo, 0, 0.0, W.T2, nmo, 0, 1, s, 0, 0));
+  DF_TRY(dgemm(true, false, nmo, nmo, nao, 1.0, W.X, nmo, 0, W.T2, nmo, 0, 0.0, W.E, nmo, 0, 1, s, 0, 0));
+  absmax_kernel<<<1, 1024, 0, s>>>(W.E, ne, &W.st->emax);
+  DF_LAUNCHED("absmax_kernel");
+  diis_select_kernel<<<1, 32, 0, s>>>(W.diis);
+  DF_LAUNCHED("diis_select_kernel");
+  diis_store_kernel<<<blocks_for(nn), 256, 0, s>>>(W.diis, W.F, W.E, W.Fhist, W.Ehist, nn, ne);
+  DF_LAUNCHED("diis_store_kernel");
+  diis_gram_kernel<<<DIIS_MAX, 256, 0, s>>>(W.diis, W.Ehist, nn, ne, W.G);
+  DF_LAUNCHED("diis_gram_kernel");
+  diis_solve_kernel<<<1, 32, 0, s>>>(W.diis, W.G, W.coef, W.st);
+  DF_LAUNCHED("diis_solve_kernel");
+  diis_combine_kernel<<<blocks_for(nn), 256, 0, s>>>(W.diis, W.Fhist, nn, W.coef, W.Fbar);
+  DF_LAUNCHED("diis_combine_kernel");
+  DF_TRY(diagonalize_fock(W.Fbar, nao, nmo, nocc, W, s));
+  orbital_status_kernel<<<1, 32, 0, s>>>(W.eps, nmo, nocc, W.eig_status, W.st);
+  DF_LAUNCHED("orbital_status_kernel");
+  DF_CUDA(cudaMemcpyAsync(M.hst, W.st, sizeof(ScfStatus), cudaMemcpyDeviceToHost, s));
+  return DF_OK;
+}
+
+// Body of a regular iteration: keep the incoming density, build J/K, then the tail.
+static int iteration_body(ScfMol& M, int prec) {
+  ScfWork& W = M.W;
+  const long nn = (long)M.nao * M.nao;
+  DF_CUDA(cudaMemcpyAsync(W.Dprev, W.D, sizeof(double) * nn, cudaMemcpyDeviceToDevice, M.s));
+  DF_CUDA(cudaMemcpyAsync(W.Cprev, W.Cocc, sizeof(double) * M.nao * M.nocc, cudaMemcpyDeviceToDevice, M.s));
+  DF_TRY(run_jk(W.B, M.nao, M.naux, prec, W.D, W.Cocc, M.nocc, W.J, W.K, W.jk, M.s));
+  return iteration_tail(M);
+}
+
+// Launch one iteration (asynchronously, except for the eager dm0 iteration).
+static int scf_iter_launch(ScfMol& M, bool use_graphs) {
+  if (M.first_dm0) {
+    const long nn = (long)M.nao * M.nao;
+    DF_CUDA(cudaMemcpyAsync(M.W.Dprev, M.W.D, sizeof(double) * nn, cudaMemcpyDeviceToDevice, M.s));
+    DF_TRY(jk_general_density(M));
+    DF_TRY(iteration_tail(M));
+    M.first_dm0 = false;
+    return DF_OK;
+  }
+  int gi = M.prec == DF_FP64 ? 0 : 1;
+  if (!use_graphs || prof_on()) return iteration_body(M, M.prec);
+  if (!M.graph[gi]) {
+    cudaGraph_t g = nullptr;
+    DF_CUDA(cudaStreamBeginCapture(M.s, cudaStreamCaptureModeThreadLocal));
+    int rc = iteration_body(M, M.prec);
+    cudaError_t ce = cudaStreamEndCapture(M.s, &g);
+    if (rc != DF_OK) {
+      if (g) cudaGraphDestroy(g);
+      return rc;
+    }
+    DF_REQUIRE(ce == cudaSuccess, DF_ERR_CUDA, "scf: graph capture failed: %s", cudaGetErrorString(ce));
+    cudaError_t ie = cudaGraphInstantiate(&M.graph[gi], g, 0);
+    cudaGraphDestroy(g);
+    DF_REQUIRE(ie == cudaSuccess, DF_ERR_CUDA, "scf: graph instantiation failed: %s", cudaGetErrorString(ie));
+  }
+  DF_CUDA(cudaGraphLaunch(M.graph[gi], M.s));
+  return DF_OK;
+}
+
+// After the stream has completed the iteration: convergence, precision switch.
+// Returns true when the molecule is finished (converged, failed or out of iterations).
+static bool scf_iter_finish(ScfMol& M) {
+  const ScfStatus& h = *M.hst;
+  M.res.iterations++;
+  if (M.prec == DF_FP64) M.res.fp64_iterations++;
+  if (h.nonfinite || !std::isfinite(h.emax)) {
+    M.rc = DF_ERR_NUMERIC;
+    set_error("scf: non-finite Fock matrix at iteration %d", M.res.iterations);
+    return true;
+  }
+  if (h.eig_fail) {
+    M.rc = DF_ERR_NOCONV;
+    set_error("scf: eigensolver failed at iteration %d", M.res.iterations);
+    return true;
+  }
+  double de = M.have_old ? fabs(h.energy - M.e_old) : INFINITY;
+  M.res.energy = h.energy;
+  M.res.last_de = de;
+  M.res.last_err = h.emax;
+  if (M.opt.verbose)
+    printf("scf iter %3d  %s  E = %.12f  dE = %.3e  max|e| = %.3e\n", M.res.iterations,
+           M.prec == DF_FP64 ? "fp64 " : "mixed", h.energy, de, h.emax);
+  if (M.prec == DF_FP64 && M.switched && M.fp64_done + 1 >= M.opt.n_fp64_final && M.have_old &&
+      de < M.opt.conv_tol && h.emax < M.opt.conv_err) {
+    M.res.converged = 1;
+    return true;
+  }
+  if (M.prec == DF_FP64) M.fp64_done++;
+  // orbital energies of the diagonalisation that produced the next density
+  M.res.homo = h.homo;
+  M.res.lumo = h.lumo;
+  if (!M.switched && M.have_old && (de < M.opt.switch_tol || h.emax < M.opt.switch_err)) {
+    M.switched = true;
+    M.prec = DF_FP64;
+    diis_reset_kernel<<<1, 32, 0, M.s>>>(M.W.diis, M.opt.diis_space);
+  }
+  M.e_old = h.energy;
+  M.have_old = true;
+  if (M.res.iterations >= M.opt.max_cycle) {
+    M.rc = DF_ERR_NOCONV;
+    set_error("scf: not converged after %d iterations (dE %.3e, max|e| %.3e)", M.res.iterations, M.res.last_de,
+              M.res.last_err);
+    return true;
+  }
+  return false;
+}
+
+// The reported energy belongs to Dprev / Cprev, the density of the last Fock build.
+static int scf_outputs(ScfMol& M) {
+  ScfWork& W = M.W;
+  const long nn = (long)M.nao * M.nao;
+  if (M.D_out) DF_CUDA(cudaMemcpyAsync(M.D_out, W.Dprev, sizeof(double) * nn, cudaMemcpyDeviceToDevice, M.s));
+  if (M.C_out)
+    DF_CUDA(cudaMemcpyAsync(M.C_out, W.Cprev, sizeof(double) * M.nao * M.nocc, cudaMemcpyDeviceToDevice, M.s));
+  if (M.mo_out)
+    DF_CUDA(cudaMemcpyAsync(M.mo_out, W.eps, sizeof(double) * std::min(M.nmo, M.nocc + 1), cudaMemcpyDeviceToDevice,
+                            M.s));
+  return DF_OK;
+}
+
+static int check_molecule(const df_molecule* mol, const scf_opts& o) {
+  DF_REQUIRE(mol, DF_ERR_ARG, "scf: null molecule");
+  DF_REQUIRE(mol->nao > 0 && mol->naux > 0 && mol->natm > 0 && mol->nelec > 0 && mol->nelec % 2 == 0, DF_ERR_ARG,
+             "scf: bad molecule sizes (nao %d naux %d natm %d nelec %d)", mol->nao, mol->naux, mol->natm, mol->nelec);
+  DF_REQUIRE(mol->xyz && mol->charges && mol->ao_xyz && mol->ao_exp && mol->aux_xyz && mol->aux_exp, DF_ERR_ARG,
+             "scf: null molecule array");
+  DF_REQUIRE(o.precision == DF_FP64 || o.precision == DF_MIXED, DF_ERR_ARG, "scf: bad precision");
+  DF_REQUIRE(o.diis_space >= 1 && o.diis_space <= DIIS_MAX, DF_ERR_ARG, "scf: diis_space must be in [1, 16]");
+  DF_REQUIRE(o.max_cycle >= 1 && o.n_fp64_final >= 1, DF_ERR_ARG, "scf: bad iteration limits");
+  DF_REQUIRE(mol->naux <= 65535, DF_ERR_ARG, "scf: naux > 65535");
+  DF_REQUIRE(mol->nelec / 2 <= mol->nao, DF_ERR_ARG, "scf: more occupied orbitals than basis functions");
+  DF_REQUIRE(o.precision == DF_FP64 || mol->nelec / 2 <= 256, DF_ERR_ARG,
+             "scf: mixed precision supports at most 256 occupied orbitals");
+  return DF_OK;
+}
+
+static int init_mol(ScfMol& M, const df_molecule* mol, const scf_opts& o, void* work, size_t work_bytes,
+                    cudaStream_t s) {
+  M.mol = *mol;
+  M.opt = o;
+  M.nao = mol->nao;
+  M.naux = mol->naux;
+  M.nocc = mol->nelec / 2;
+  M.s = s;
+  Arena a(work, work_bytes);
+  scf_layout(M.nao, M.naux, M.nocc, o.precision, &a, nullptr, &M.W);
+  DF_REQUIRE(!a.overflow, DF_ERR_NOMEM, "scf: workspace overflow");
   return DF_OK;
 }
 
@@ -529,24 +687,219 @@ extern "C" size_t scf_work_bytes(int nao, int naux, int nocc, int precision) {
 extern "C" int scf_run(const df_molecule* mol, const scf_opts* opt, const double* dm0, double* D_out, double* C_out,
                        double* mo_energy, scf_result* res, void* work, size_t work_bytes, cudaStream_t s) {
   clear_error();
-  DF_REQUIRE(mol && res, DF_ERR_ARG, "scf_run: null molecule or result");
+  DF_REQUIRE(res, DF_ERR_ARG, "scf_run: null result");
   scf_opts o;
   if (opt) o = *opt; else scf_default_opts(&o);
-  DF_REQUIRE(mol->nao > 0 && mol->naux > 0 && mol->natm > 0 && mol->nelec > 0 && mol->nelec % 2 == 0, DF_ERR_ARG,
-             "scf_run: bad molecule sizes (nao %d naux %d natm %d nelec %d)", mol->nao, mol->naux, mol->natm, mol->nelec);
-  DF_REQUIRE(mol->xyz && mol->charges && mol->ao_xyz && mol->ao_exp && mol->aux_xyz && mol->aux_exp, DF_ERR_ARG,
-             "scf_run: null molecule array");
-  DF_REQUIRE(o.precision == DF_FP64 || o.precision == DF_MIXED, DF_ERR_ARG, "scf_run: bad precision");
-  DF_REQUIRE(o.diis_space >= 1 && o.diis_space <= 16, DF_ERR_ARG, "scf_run: diis_space must be in [1, 16]");
-  DF_REQUIRE(o.max_cycle >= 1 && o.n_fp64_final >= 1, DF_ERR_ARG, "scf_run: bad iteration limits");
-  DF_REQUIRE(mol->naux <= 65535, DF_ERR_ARG, "scf_run: naux > 65535");
-  int nocc = mol->nelec / 2;
-  DF_REQUIRE(nocc <= mol->nao, DF_ERR_ARG, "scf_run: more occupied orbitals than basis functions");
-  size_t need = scf_work_bytes(mol->nao, mol->naux, nocc, o.precision);
+  DF_TRY(check_molecule(mol, o));
+  size_t need = scf_work_bytes(mol->nao, mol->naux, mol->nelec / 2, o.precision);
   DF_REQUIRE(work && work_bytes >= need, DF_ERR_NOMEM, "scf_run: workspace of %zu bytes < %zu", work_bytes, need);
-  Arena a(work, work_bytes);
+  ScfMol M;
+  DF_TRY(init_mol(M, mol, o, work, work_bytes, s));
+  ScfStatus* hst = nullptr;
+  DF_CUDA(cudaMallocHost(&hst, sizeof(ScfStatus)));
+  M.hst = hst;
+  M.dm0 = dm0;
+  M.D_out = D_out;
+  M.C_out = C_out;
+  M.mo_out = mo_energy;
+  int rc = scf_setup(M);
+  while (rc == DF_OK && !M.done) {
+    rc = scf_iter_launch(M, true);
+    if (rc != DF_OK) break;
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+      set_error("scf_run: %s", cudaGetErrorString(e));
+      rc = DF_ERR_CUDA;
+      break;
+    }
+    M.done = scf_iter_finish(M);
+  }
+  if (rc == DF_OK) rc = scf_outputs(M);
+  if (rc == DF_OK && cudaStreamSynchronize(s) != cudaSuccess) rc = DF_ERR_CUDA;
+  *res = M.res;
+  cudaFreeHost(hst);
+  return rc != DF_OK ? rc : M.rc;
+}
+
+// ---- batch ---------------------------------------------------------------------------------------
+extern "C" size_t scf_batch_work_bytes(const df_molecule* mols, int nmol, int precision, int slots) {
+  if (!mols || nmol <= 0 || slots <= 0) return 0;
+  size_t mx = 0;
+  for (int i = 0; i < nmol; ++i)
+    mx = std::max(mx, scf_work_bytes(mols[i].nao, mols[i].naux, std::max(1, mols[i].nelec / 2), precision));
+  return align_up(mx, 256) * (size_t)std::min(slots, nmol);
+}
+
+extern "C" int scf_run_batch(const df_molecule* mols, int nmol, const scf_opts* opt, const double* const* dm0s,
+                             double* const* D_outs, scf_result* results, int slots, void* work, size_t work_bytes,
+                             cudaStream_t s) {
+  clear_error();
+  DF_REQUIRE(mols && nmol > 0 && results && slots > 0, DF_ERR_ARG, "scf_run_batch: bad arguments");
+  scf_opts o;
+  if (opt) o = *opt; else scf_default_opts(&o);
+  o.verbose = 0;
+  for (int i = 0; i < nmol; ++i) DF_TRY(check_molecule(&mols[i], o));
+  slots = std::min(slots, nmol);
+  size_t need = scf_batch_work_bytes(mols, nmol, o.precision, slots);
+  DF_REQUIRE(work && work_bytes >= need, DF_ERR_NOMEM, "scf_run_batch: workspace of %zu bytes < %zu", work_bytes,
+             need);
+  const size_t per_slot = need / slots;
+  memset(results, 0, sizeof(scf_result) * nmol);
+  // stream pool, ordered after the caller's stream
+  std::vector<cudaStream_t> streams(slots, nullptr);
+  cudaEvent_t start;
+  DF_CUDA(cudaEventCreateWithFlags(&start, cudaEventDisableTiming));
+  DF_CUDA(cudaEventRecord(start, s));
+  for (int k = 0; k < slots; ++k) {
+    DF_CUDA(cudaStreamCreateWithFlags(&streams[k], cudaStreamNonBlocking));
+    DF_CUDA(cudaStreamWaitEvent(streams[k], start, 0));
+  }
+  ScfStatus* hst = nullptr;
+  DF_CUDA(cudaMallocHost(&hst, sizeof(ScfStatus) * slots));
+  std::vector<ScfMol*> slot_mol(slots, nullptr);
+  std::vector<int> slot_index(slots, -1);
+  int next = 0, finished = 0, rc = DF_OK;
+  // Each molecule holds a slot (workspace + stream) until it finishes; a freed slot takes
+  // the next molecule, so molecules of uneven size keep every stream busy.
+  auto start_molecule = [&](int k) -> int {
+    int i = next++;
+    ScfMol* M = new ScfMol();
+    slot_mol[k] = M;
+    slot_index[k] = i;
+    DF_TRY(init_mol(*M, &mols[i], o, (char*)work + per_slot * k, per_slot, streams[k]));
+    M->hst = hst + k;
+    M->dm0 = dm0s ? dm0s[i] : nullptr;
+    M->D_out = D_outs ? D_outs[i] : nullptr;
+    int r = scf_setup(*M);
+    if (r != DF_OK) {
+      M->rc = r;
+      M->done = true;
+    }
+    return DF_OK;
+  };
+  for (int k = 0; k < slots && rc == DF_OK; ++k) rc = start_molecule(k);
+  while (rc == DF_OK && finished < nmol) {
+    for (int k = 0; k < slots && rc == DF_OK; ++k) {
+      ScfMol* M = slot_mol[k];
+      if (M && !M->done) rc = scf_iter_launch(*M, true);
+    }
+    if (rc != DF_OK) break;
+    for (int k = 0; k < slots && rc == DF_OK; ++k) {
+      ScfMol* M = slot_mol[k];
+      if (!M) continue;
+      if (!M->done) {
+        cudaError_t e = cudaStreamSynchronize(M->s);
+        if (e != cudaSuccess) {
+          set_error("scf_run_batch: %s", cudaGetErrorString(e));
+          rc = DF_ERR_CUDA;
+          break;
+        }
+        M->done = scf_iter_finish(*M);
+      }
+      if (M->done) {
+        int i = slot_index[k];
+        if (M->rc == DF_OK || M->rc == DF_ERR_NOCONV) scf_outputs(*M);
+        cudaStreamSynchronize(M->s);
+        results[i] = M->res;
+        if (M->rc != DF_OK && M->rc != DF_ERR_NOCONV) rc = M->rc;
+        delete M;
+        slot_mol[k] = nullptr;
+        finished++;
+        if (next < nmol && rc == DF_OK) rc = start_molecule(k);
+      }
+    }
+  }
+  for (int k = 0; k < slots; ++k) {
+    delete slot_mol[k];
+    cudaStreamSynchronize(streams[k]);
+    cudaStreamDestroy(streams[k]);
+  }
+  cudaEventDestroy(start);
+  cudaFreeHost(hst);
+  if (rc != DF_OK) return rc;
+  for (int i = 0; i < nmol; ++i)
+    if (!results[i].converged) {
+      set_error("scf_run_batch: molecule %d did not converge", i);
+      return DF_ERR_NOCONV;
+    }
+  return DF_OK;
+}
+
+// ---- core-Hamiltonian guess -------------------------------------------------------------
+namespace dfscf {
+
+static void guess_layout(int nao, int nocc, Arena* a, Sizer* z, ScfWork* w) {
+  size_t nn = (size_t)nao * nao;
+#define TAKE(T, ptr, count) \
+  if (a) ptr = a->take<T>(count); else z->take<T>(count);
+  TAKE(double, w->S, nn);
+  TAKE(double, w->h, nn);
+  TAKE(double, w->V, nn);
+  TAKE(double, w->X, nn);
+  TAKE(double, w->T1, nn);
+  TAKE(double, w->T2, nn);
+  TAKE(double, w->Fp, nn);
+  TAKE(double, w->ZT, nn);
+  TAKE(double, w->eps, nao);
+  TAKE(double, w->eig_scratch, eigh_scratch_doubles(nao));
+  TAKE(int, w->eig_status, 1);
+  TAKE(double, w->Cocc, (size_t)nao * std::max(nocc, 1));
+  TAKE(double, w->D, nn);
+#undef TAKE
+}
+
+}  // namespace dfscf
+
+extern "C" size_t df_core_guess_work_bytes(int nao, int nocc) {
+  if (nao <= 0 || nocc < 0) return 0;
+  Sizer z;
   ScfWork w;
-  scf_layout(mol->nao, mol->naux, nocc, o.precision, &a, nullptr, &w);
-  DF_REQUIRE(!a.overflow, DF_ERR_NOMEM, "scf_run: workspace overflow");
-  return scf_driver(mol, &o, dm0, D_out, C_out, mo_energy, res, w, s);
+  guess_layout(nao, nocc, nullptr, &z, &w);
+  return z.used;
+}
+
+extern "C" int df_core_guess(const df_molecule* mol, double lindep, double* S_out, double* h_out, double* C_occ,
+                             double* D_out, double* mo_energy, int* nmo_out, void* work, size_t work_bytes,
+                             cudaStream_t s) {
+  clear_error();
+  DF_REQUIRE(mol && mol->nao > 0 && mol->natm > 0 && mol->nelec > 0 && mol->nelec % 2 == 0, DF_ERR_ARG,
+             "df_core_guess: bad molecule");
+  DF_REQUIRE(mol->ao_xyz && mol->ao_exp && mol->xyz && mol->charges, DF_ERR_ARG, "df_core_guess: null array");
+  const int nao = mol->nao, nocc = mol->nelec / 2;
+  DF_REQUIRE(nocc <= nao, DF_ERR_ARG, "df_core_guess: nocc > nao");
+  size_t need = df_core_guess_work_bytes(nao, nocc);
+  DF_REQUIRE(work && work_bytes >= need, DF_ERR_NOMEM, "df_core_guess: workspace of %zu bytes < %zu", work_bytes, need);
+  Arena a(work, work_bytes);
+  ScfWork W;
+  guess_layout(nao, nocc, &a, nullptr, &W);
+  const long nn = (long)nao * nao;
+  DF_TRY(launch_int1e(mol->ao_xyz, mol->ao_exp, nao, mol->xyz, mol->charges, mol->natm, W.S, W.h, W.V, s));
+  axpy_kernel<<<blocks_for(nn), 256, 0, s>>>(W.h, W.V, nn, 1.0);
+  DF_LAUNCHED("axpy_kernel");
+  DF_CUDA(cudaMemcpyAsync(W.T1, W.S, sizeof(double) * nn, cudaMemcpyDeviceToDevice, s));
+  DF_TRY(eig_rows(W.T1, nao, W.eps, W.ZT, W, s));
+  std::vector<double> hs(nao);
+  int bad = 0;
+  DF_CUDA(cudaMemcpyAsync(hs.data(), W.eps, sizeof(double) * nao, cudaMemcpyDeviceToHost, s));
+  DF_CUDA(cudaMemcpyAsync(&bad, W.eig_status, sizeof(int), cudaMemcpyDeviceToHost, s));
+  DF_CUDA(cudaStreamSynchronize(s));
+  DF_REQUIRE(bad == 0, DF_ERR_NOCONV, "df_core_guess: eigensolver failed on S");
+  int nmo = 0;
+  for (int i = 0; i < nao; ++i) nmo += hs[i] > lindep;
+  DF_REQUIRE(nmo >= nocc, DF_ERR_ARG, "df_core_guess: only %d orbitals above lindep", nmo);
+  canonical_x_kernel<<<blocks_for((long)nao * nmo), 256, 0, s>>>(W.ZT, W.eps, nao, nmo, W.X);
+  DF_LAUNCHED("canonical_x_kernel");
+  DF_TRY(diagonalize_fock(W.h, nao, nmo, nocc, W, s));
+  if (S_out) DF_CUDA(cudaMemcpyAsync(S_out, W.S, sizeof(double) * nn, cudaMemcpyDeviceToDevice, s));
+  if (h_out) DF_CUDA(cudaMemcpyAsync(h_out, W.h, sizeof(double) * nn, cudaMemcpyDeviceToDevice, s));
+  if (C_occ) DF_CUDA(cudaMemcpyAsync(C_occ, W.Cocc, sizeof(double) * nao * nocc, cudaMemcpyDeviceToDevice, s));
+  if (D_out) DF_CUDA(cudaMemcpyAsync(D_out, W.D, sizeof(double) * nn, cudaMemcpyDeviceToDevice, s));
+  if (mo_energy)
+    DF_CUDA(cudaMemcpyAsync(mo_energy, W.eps, sizeof(double) * std::min(nmo, nocc + 1), cudaMemcpyDeviceToDevice, s));
+  bad = 0;
+  DF_CUDA(cudaMemcpyAsync(&bad, W.eig_status, sizeof(int), cudaMemcpyDeviceToHost, s));
+  DF_CUDA(cudaStreamSynchronize(s));
+  DF_REQUIRE(bad == 0, DF_ERR_NOCONV, "df_core_guess: eigensolver failed on the core Hamiltonian");
+  if (nmo_out) *nmo_out = nmo;
+  return DF_OK;
 }

@@ -350,7 +350,8 @@ static int launch_gemm(const CUtensorMap& ahi, const CUtensorMap& alo, const CUt
   p.stages = (int)std::min<uint32_t>(umma::MAX_STAGES, budget / p.stage_bytes);
   DF_REQUIRE(p.stages >= 2, DF_ERR_ARG, "split-bf16 GEMM: tile too large for shared memory");
   size_t smem = (size_t)p.stages * p.stage_bytes + 1024;
-  DF_CUDA(cudaFuncSetAttribute(umma::split_bf16_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  DF_REQUIRE(smem <= 220 * 1024 + 1024, DF_ERR_ARG, "split-bf16 GEMM: %zu bytes of shared memory requested", smem);
+  DF_TRY(umma_prepare());
   umma::split_bf16_gemm_kernel<<<grid, umma::THREADS, smem, s>>>(ahi, alo, bhi, blo, p);
   DF_LAUNCHED("split_bf16_gemm_kernel");
   return DF_OK;
@@ -390,6 +391,18 @@ static int mixed_nsplit(int npad, int naux, int ncpad) {
   // FP32 accumulation length per split <= ~16k terms, and several waves of CTAs
   long want = std::max<long>((kdim + 16383) / 16384, (4L * 152 + tiles - 1) / tiles);
   return (int)std::max<long>(1, std::min<long>(want, std::min<long>(nkb, 256)));
+}
+
+// Raise the tensor-core kernel's dynamic shared-memory limit once, before any launch can
+// happen inside a stream capture.
+int umma_prepare() {
+  static bool done = false;
+  if (!done) {
+    DF_CUDA(cudaFuncSetAttribute(umma::split_bf16_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(220 * 1024 + 1024)));
+    done = true;
+  }
+  return DF_OK;
 }
 
 void mixed_k_work_layout(int nao, int naux, int nocc, Arena* a, Sizer* z, MixedKWork* w) {
@@ -446,7 +459,10 @@ int build_K_mixed(const void* B, const BLayout& L, int nao, int naux, const doub
   p.err = w.err;
   long mtiles = (long)naux * npad / umma::BM;
   DF_REQUIRE(mtiles < (1L << 31), DF_ERR_ARG, "mixed K: too many row tiles");
-  DF_TRY(launch_gemm(ahi, alo, bhi, blo, p, dim3((unsigned)mtiles, 1), s));
+  {
+    ProfScope ps("k_halftransform_tc", s);
+    DF_TRY(launch_gemm(ahi, alo, bhi, blo, p, dim3((unsigned)mtiles, 1), s));
+  }
   // exchange SYRK: A = B = X [m][(P, i)], lower 128 x 128 tiles, split over (P, i)
   long kdim = (long)naux * ncpad;
   DF_TRY(make_map(&ahi, w.Xhi, kdim, npad, kdim, umma::BM));
@@ -461,7 +477,10 @@ int build_K_mixed(const void* B, const BLayout& L, int nao, int naux, const doub
   q.Kpart = w.Kpart;
   q.n_lower_tiles = (npad / umma::BM) * (npad / umma::BM + 1) / 2;
   q.err = w.err;
-  DF_TRY(launch_gemm(ahi, alo, ahi, alo, q, dim3((unsigned)q.n_lower_tiles, (unsigned)nsplit), s));
+  {
+    ProfScope ps("k_syrk_tc", s);
+    DF_TRY(launch_gemm(ahi, alo, ahi, alo, q, dim3((unsigned)q.n_lower_tiles, (unsigned)nsplit), s));
+  }
   long nn = (long)nao * nao;
   kmixed_reduce_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, s>>>(w.Kpart, nsplit, npad, nao, K);
   DF_LAUNCHED("kmixed_reduce_kernel");
