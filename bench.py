@@ -96,7 +96,22 @@ def workload(name: str):
         return gen.config_c1(), "300 H centres, 1 per 10 bohr^3 (box 14.42 bohr, seed 0); nao 1500, naux 4500, nocc 150"
     if name == "c0":
         return gen.config_c0(), "20 H centres in a 6 bohr cube (seed 0); nao 100, naux 300, nocc 10"
+    if name in ("m80", "m120"):
+        n = int(name[1:])
+        return gen.make_molecule(n, gen.molecules.box_for(n), 0), \
+            f"{n} H centres, 1 per 10 bohr^3 (seed 0); nao {5 * n}, naux {15 * n}, nocc {n // 2}"
     raise SystemExit(f"unknown workload {name}")
+
+
+def max_over_ranks(x: float, device: str = "cuda") -> float:
+    """Maximum of a per-rank value over all ranks (identity without torch.distributed)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return x
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
 
 
 def dist_env():
@@ -261,12 +276,8 @@ def run_ours(args):
         ms64, prof64 = time_builds(dfscf, torch, B, D, C, "fp64", args.steps, args.warmup, work64, barrier)
     clocks = clk.summary()
 
-    # max over ranks of the per-step time
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms64], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms64 = float(t.item())
+    # max over ranks of the per-step time; every rank ran the same number of builds
+    ms64 = max_over_ranks(ms64)
     value = ws * 1000.0 / ms64
 
     ht_flops = 2.0 * naux * nao * nao * nocc
@@ -348,7 +359,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["c1", "c0"], default="c1")
+    ap.add_argument("--workload", choices=["c1", "c0", "m80", "m120"], default="c1")
     ap.add_argument("--mixed-steps", type=int, default=20)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-mixed", dest="mixed", action="store_false")

@@ -206,6 +206,45 @@ int scf_run_batch(const df_molecule* mols, int nmol, const scf_opts* opt, const 
                   double* const* D_outs, scf_result* results, int slots, void* work, size_t work_bytes,
                   cudaStream_t s);
 
+/* ---- a14: learned initial guess --------------------------------------------------------
+ * A starting density for scf_run / scf_run_batch (dm0), predicted from geometry.  The
+ * paper lets dm0 be any density, idempotent or not (Section "Initial Guess for Mean-field
+ * Methods"); scf_run falls back to the core guess when the trace or idempotency check
+ * fails.  Centres carry 5 orbital functions each (the workload's basis).
+ *   features: for every centre pair p = A(A+1)/2 + B (A >= B), 65 inputs: 32 Gaussian
+ *     radial-basis values exp(-gamma (R - r_k)^2), r_k = 12k/31, gamma = (31/12)^2, and the
+ *     environment env_A = 1/8 sum_{C != A, R_AC <= 12} rbf(R_AC): off-diagonal pairs
+ *     [rbf(R_AB), env_A + env_B, 0], diagonal pairs [0, 2 env_A, 1]; mask[p] = 0 for pairs
+ *     more than 12 bohr apart (their block stays zero).
+ *   network: 65 -> 256 -> 256 -> 256 -> 15, SiLU hidden activations; params is one float
+ *     array of guess_mlp_param_count() values, per layer W [out][in] then b [out].
+ *   outputs: the 15 upper-triangle entries (a <= b, row-major) of a symmetric 5x5 block.
+ * All pointers are device memory; n is the number of pair samples.                        */
+size_t guess_mlp_param_count(void);
+size_t guess_mlp_work_bytes(int n);
+/* feat [natm(natm+1)/2][65], mask [natm(natm+1)/2]; work >= 128*natm bytes.               */
+int guess_features(const double* xyz, int natm, float* feat, float* mask, void* work, size_t work_bytes,
+                   cudaStream_t s);
+/* Y [npairs][15]: symmetrised 5x5 blocks 1/2 (D_AB + D_AB^T) of a converged D [nao][nao]. */
+int guess_targets(const double* D, int natm, float* Y, cudaStream_t s);
+/* out [n][15]; bf16 != 0 runs the BF16 inference path (BF16 weights and activations, FP32
+ * accumulation), else FP32.                                                               */
+int guess_mlp_forward(const float* params, const float* X, int n, float* out, int bf16, void* work,
+                      size_t work_bytes, cudaStream_t s);
+/* loss = sum_p mask_p |out_p - Y_p|^2 / (nvalid * 15) (device float) and its gradient
+ * grad [param_count] in FP32.                                                              */
+int guess_mlp_loss_grad(const float* params, const float* X, const float* Y, const float* mask, int n,
+                        float nvalid, float* loss, float* grad, void* work, size_t work_bytes, cudaStream_t s);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected with step >= 1) on the
+ * mini-batch's loss; adam_m / adam_v [param_count] are the moment buffers; loss may be NULL. */
+int guess_mlp_train_step(float* params, float* adam_m, float* adam_v, int step, float lr, const float* X,
+                         const float* Y, const float* mask, int n, float nvalid, float* loss, void* work,
+                         size_t work_bytes, cudaStream_t s);
+/* dm0 [5 natm][5 natm] for one molecule via BF16 inference.                                */
+size_t guess_density_work_bytes(int natm);
+int guess_density(const float* params, const double* xyz, int natm, double* D0, void* work, size_t work_bytes,
+                  cudaStream_t s);
+
 /* ---- core-Hamiltonian guess ------------------------------------------------------------
  * S, h = T + V, canonical orthogonalisation X (eigenvalues of S above lindep), the
  * nocc = nelec/2 lowest eigenvectors C_occ = X C' of X^T h X and D = 2 C_occ C_occ^T: the

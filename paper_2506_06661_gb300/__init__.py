@@ -97,6 +97,16 @@ _SIGS = {
     "scf_work_bytes": (_SZ, [_I, _I, _I, _I]),
     "scf_run": (_I, [ctypes.POINTER(DFMolecule), ctypes.POINTER(ScfOpts), _VP, _VP, _VP, _VP,
                      ctypes.POINTER(ScfResultC), _VP, _SZ, _VP]),
+    "guess_mlp_param_count": (_SZ, []),
+    "guess_mlp_work_bytes": (_SZ, [_I]),
+    "guess_features": (_I, [_VP, _I, _VP, _VP, _VP, _SZ, _VP]),
+    "guess_targets": (_I, [_VP, _I, _VP, _VP]),
+    "guess_mlp_forward": (_I, [_VP, _VP, _I, _VP, _I, _VP, _SZ, _VP]),
+    "guess_mlp_loss_grad": (_I, [_VP, _VP, _VP, _VP, _I, ctypes.c_float, _VP, _VP, _VP, _SZ, _VP]),
+    "guess_mlp_train_step": (_I, [_VP, _VP, _VP, _I, ctypes.c_float, _VP, _VP, _VP, _I, ctypes.c_float, _VP, _VP,
+                                  _SZ, _VP]),
+    "guess_density_work_bytes": (_SZ, [_I]),
+    "guess_density": (_I, [_VP, _VP, _I, _VP, _VP, _SZ, _VP]),
     "scf_batch_work_bytes": (_SZ, [ctypes.POINTER(DFMolecule), _I, _I, _I]),
     "scf_run_batch": (_I, [ctypes.POINTER(DFMolecule), _I, ctypes.POINTER(ScfOpts), ctypes.POINTER(_VP),
                            ctypes.POINTER(_VP), ctypes.POINTER(ScfResultC), _I, _VP, _SZ, _VP]),

@@ -65,6 +65,8 @@ int umma_prepare();
 void mixed_k_work_layout(int nao, int naux, int nocc, Arena* a, Sizer* z, MixedKWork* w);
 int build_K_mixed(const void* B, const BLayout& L, int nao, int naux, const double* C, int nocc, double* K,
                   const MixedKWork& w, cudaStream_t s);
+int build_J(const void* Bbuf, const BLayout& L, int nao, int naux, int precision, const double* D, double* J,
+            const JKWork& w, cudaStream_t s);
 int run_jk(const void* B, int nao, int naux, int precision, const double* D, const double* C, int nocc, double* J,
            double* K, const JKWork& w, cudaStream_t s);
 int build_B(const double* ao_xyz, const double* ao_exp, int nao, const double* aux_xyz, const double* aux_exp,

@@ -1,0 +1,483 @@
+// Learned initial guess: geometry -> per-centre-pair 5x5 density blocks -> dm0.
+//
+// The paper allows any starting density for a mean-field calculation, idempotent or not
+// and with any electron count (arXiv 2506.06661, Section "Initial Guess for Mean-field
+// Methods").  This file produces such a density from geometry with a small network that
+// is trained on densities the SCF itself converges:
+//   features  32 Gaussian radial-basis values exp(-gamma (R - r_k)^2), r_k = 12 k / 31,
+//             gamma = (31/12)^2, plus the environment env_A = 1/8 sum_{C != A, R <= 12}
+//             rbf(R_AC):  off-diagonal pair (A > B): [rbf(R_AB), env_A + env_B, 0],
+//             diagonal pair (A, A): [0, 2 env_A, 1]; pairs beyond 12 bohr are masked out;
+//   network   65 -> 256 -> 256 -> 256 -> 15 with SiLU on the hidden layers; the 15 outputs
+//             are the upper triangle (a <= b, row-major) of a symmetric 5x5 block;
+//   training  mean squared error against the symmetrised converged blocks, Adam, FP32
+//             weights and FP32 arithmetic on CUDA cores;
+//   inference the same network with BF16 weights and activations, FP32 accumulation.
+// Parameters are one float array: for each layer, W [out][in] then b [out].
+#include <cuda_bf16.h>
+
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace dfscf {
+namespace mlp {
+
+constexpr int NRBF = 32, NIN = 65, NHID = 256, NOUT = 15, NBF = 5;
+constexpr float RCUT = 12.0f;
+constexpr int NLAYER = 4;
+__host__ __device__ constexpr int layer_in(int l) { return l == 0 ? NIN : NHID; }
+__host__ __device__ constexpr int layer_out(int l) { return l == NLAYER - 1 ? NOUT : NHID; }
+__host__ __device__ constexpr size_t w_offset(int l) {
+  size_t o = 0;
+  for (int k = 0; k < l; ++k) o += (size_t)layer_in(k) * layer_out(k) + layer_out(k);
+  return o;
+}
+__host__ __device__ constexpr size_t b_offset(int l) { return w_offset(l) + (size_t)layer_in(l) * layer_out(l); }
+constexpr size_t NPARAM = w_offset(NLAYER);
+
+__device__ __forceinline__ float to_f(float x) { return x; }
+__device__ __forceinline__ float to_f(__nv_bfloat16 x) { return __bfloat162float(x); }
+template <typename T> __device__ __forceinline__ T from_f(float x);
+template <> __device__ __forceinline__ float from_f<float>(float x) { return x; }
+template <> __device__ __forceinline__ __nv_bfloat16 from_f<__nv_bfloat16>(float x) { return __float2bfloat16_rn(x); }
+
+__device__ __forceinline__ float rbf(float r, int k) {
+  const float dr = RCUT / (NRBF - 1);
+  float x = (r - dr * k) / dr;
+  return __expf(-x * x);
+}
+
+// ---- SIMT GEMM with FP32 accumulation ---------------------------------------------------------
+// C[M][N] = alpha * op(A) op(B) + beta * C;  op(A)(m,k) = TA ? A[k*lda+m] : A[m*lda+k];
+// op(B)(k,n) = TB ? B[n*ldb+k] : B[k*ldb+n].  64x64 tiles, 256 lanes with 4x4 outputs.
+template <bool TA, bool TB, typename T>
+__global__ void __launch_bounds__(256) sgemm_kernel(int M, int N, int K, float alpha, const T* __restrict__ A, int lda,
+                                                    const T* __restrict__ B, int ldb, float beta, float* __restrict__ C,
+                                                    int ldc) {
+  __shared__ float As[16][65];
+  __shared__ float Bs[16][65];
+  int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  int m0 = blockIdx.y * 64, n0 = blockIdx.x * 64;
+  float acc[4][4] = {};
+  for (int k0 = 0; k0 < K; k0 += 16) {
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      int idx = threadIdx.x + 256 * r;
+      int mm, kk;
+      if (TA) { kk = idx >> 6; mm = idx & 63; } else { mm = idx >> 4; kk = idx & 15; }
+      int gm = m0 + mm, gk = k0 + kk;
+      As[kk][mm] = (gm < M && gk < K) ? to_f(TA ? A[(size_t)gk * lda + gm] : A[(size_t)gm * lda + gk]) : 0.f;
+      int nn;
+      if (TB) { nn = idx >> 4; kk = idx & 15; } else { kk = idx >> 6; nn = idx & 63; }
+      int gn = n0 + nn;
+      gk = k0 + kk;
+      Bs[kk][nn] = (gn < N && gk < K) ? to_f(TB ? B[(size_t)gn * ldb + gk] : B[(size_t)gk * ldb + gn]) : 0.f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) {
+      float a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    int gm = m0 + ty + 16 * i;
+    if (gm >= M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      int gn = n0 + tx + 16 * j;
+      if (gn >= N) continue;
+      float* c = C + (size_t)gm * ldc + gn;
+      *c = beta == 0.f ? alpha * acc[i][j] : fmaf(alpha, acc[i][j], beta * *c);
+    }
+  }
+}
+
+template <bool TA, bool TB, typename T>
+static int sgemm(int M, int N, int K, float alpha, const T* A, int lda, const T* B, int ldb, float beta, float* C,
+                 int ldc, cudaStream_t s) {
+  if (M <= 0 || N <= 0) return DF_OK;
+  dim3 grid((N + 63) / 64, (M + 63) / 64);
+  DF_REQUIRE(grid.y <= 65535, DF_ERR_ARG, "mlp: batch too large for one GEMM (%d rows)", M);
+  sgemm_kernel<TA, TB, T><<<grid, 256, 0, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+  DF_LAUNCHED("sgemm_kernel");
+  return DF_OK;
+}
+
+// Z += b (broadcast over rows), H = act(Z) in type T (SiLU when act != 0).
+template <typename T>
+__global__ void bias_act_kernel(float* __restrict__ Z, const float* __restrict__ b, int rows, int cols, int act,
+                                T* __restrict__ H) {
+  long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (long)rows * cols) return;
+  float z = Z[i] + b[i % cols];
+  Z[i] = z;
+  float h = act ? z / (1.f + __expf(-z)) : z;
+  H[i] = from_f<T>(h);
+}
+
+// G = 2 (out - Y) mask / (nvalid * 15); loss partial sums atomically into loss[0].
+__global__ void mse_grad_kernel(const float* __restrict__ out, const float* __restrict__ Y,
+                                const float* __restrict__ mask, int n, float inv_count, float* __restrict__ G,
+                                float* __restrict__ loss) {
+  long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  float l = 0.f;
+  if (i < (long)n * NOUT) {
+    float m = mask ? mask[i / NOUT] : 1.f;
+    float d = (out[i] - Y[i]) * m;
+    G[i] = 2.f * d * inv_count;
+    l = d * d * inv_count;
+  }
+  l = warp_sumf(l);
+  if ((threadIdx.x & 31) == 0 && loss) atomicAdd(loss, l);
+}
+
+// dZ = dA * silu'(Z), silu'(z) = s (1 + z (1 - s)), s = sigmoid(z).
+__global__ void silu_backward_kernel(const float* __restrict__ Z, float* __restrict__ dA, long n) {
+  long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float z = Z[i];
+  float s = 1.f / (1.f + __expf(-z));
+  dA[i] *= s * (1.f + z * (1.f - s));
+}
+
+// db[c] = sum_r G[r][c]
+__global__ void column_sum_kernel(const float* __restrict__ G, int rows, int cols, float* __restrict__ db) {
+  int c = blockIdx.x;
+  float s = 0.f;
+  for (int r = threadIdx.x; r < rows; r += blockDim.x) s += G[(size_t)r * cols + c];
+  s = warp_sumf(s);
+  __shared__ float sh[32];
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float t = 0.f;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += sh[k];
+    db[c] = t;
+  }
+}
+
+// Adam (Kingma & Ba): m = b1 m + (1-b1) g, v = b2 v + (1-b2) g^2,
+// p -= lr * (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps).
+__global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
+                            float* __restrict__ v, long n, float lr, float b1, float b2, float eps, float c1, float c2) {
+  long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float gi = g[i];
+  float mi = b1 * m[i] + (1.f - b1) * gi;
+  float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+  m[i] = mi;
+  v[i] = vi;
+  p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+}
+
+__global__ void to_bf16_kernel(const float* __restrict__ x, __nv_bfloat16* __restrict__ y, long n) {
+  long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = __float2bfloat16_rn(x[i]);
+}
+
+// ---- features, targets, density ------------------------------------------------------------
+// env[A][k] = 1/8 sum_{C != A, R_AC <= 12} rbf_k(R_AC)
+__global__ void env_kernel(const double* __restrict__ xyz, int natm, float* __restrict__ env) {
+  int a = blockIdx.x;
+  int k = threadIdx.x;  // 32 lanes, one radial function each
+  if (k >= NRBF) return;
+  float s = 0.f;
+  for (int c = 0; c < natm; ++c) {
+    if (c == a) continue;
+    double dx = xyz[3 * a] - xyz[3 * c], dy = xyz[3 * a + 1] - xyz[3 * c + 1], dz = xyz[3 * a + 2] - xyz[3 * c + 2];
+    float r = (float)sqrt(dx * dx + dy * dy + dz * dz);
+    if (r <= RCUT) s += rbf(r, k);
+  }
+  env[a * NRBF + k] = s * 0.125f;
+}
+
+// Pair p = A(A+1)/2 + B (A >= B): features [p][65] and mask [p] (0 beyond the cutoff).
+template <typename T>
+__global__ void pair_feature_kernel(const double* __restrict__ xyz, int natm, const float* __restrict__ env,
+                                    T* __restrict__ feat, float* __restrict__ mask) {
+  long p = blockIdx.x;
+  int k = threadIdx.x;  // 65 lanes
+  int A, B;
+  unpack_pair(p, A, B);
+  double dx = xyz[3 * A] - xyz[3 * B], dy = xyz[3 * A + 1] - xyz[3 * B + 1], dz = xyz[3 * A + 2] - xyz[3 * B + 2];
+  float r = (float)sqrt(dx * dx + dy * dy + dz * dz);
+  bool diag = A == B;
+  float v = 0.f;
+  if (k < NRBF) v = diag ? 0.f : rbf(r, k);
+  else if (k < 2 * NRBF) v = diag ? 2.f * env[A * NRBF + k - NRBF] : env[A * NRBF + k - NRBF] + env[B * NRBF + k - NRBF];
+  else if (k == 2 * NRBF) v = diag ? 1.f : 0.f;
+  if (k < NIN) feat[p * NIN + k] = from_f<T>(v);
+  if (k == 0) mask[p] = (diag || r <= RCUT) ? 1.f : 0.f;
+}
+
+// Y[p][t] = entries (a <= b) of the symmetrised block 1/2 (D_AB + D_AB^T).
+__global__ void block_targets_kernel(const double* __restrict__ D, int natm, float* __restrict__ Y) {
+  long p = blockIdx.x;
+  int t = threadIdx.x;
+  if (t >= NOUT) return;
+  int A, B;
+  unpack_pair(p, A, B);
+  int a = 0, b = 0, q = t;
+  for (a = 0; a < NBF; ++a) {
+    int len = NBF - a;
+    if (q < len) {
+      b = a + q;
+      break;
+    }
+    q -= len;
+  }
+  int nao = NBF * natm;
+  double x = 0.5 * (D[(size_t)(NBF * A + a) * nao + NBF * B + b] + D[(size_t)(NBF * A + b) * nao + NBF * B + a]);
+  Y[p * NOUT + t] = (float)x;
+}
+
+// dm0 from predicted blocks (masked pairs stay zero).  D must be zeroed beforehand.
+__global__ void assemble_density_kernel(const float* __restrict__ out, const float* __restrict__ mask, int natm,
+                                        double* __restrict__ D) {
+  long p = blockIdx.x;
+  int t = threadIdx.x;
+  if (t >= NOUT || mask[p] == 0.f) return;
+  int A, B;
+  unpack_pair(p, A, B);
+  int a = 0, b = 0, q = t;
+  for (a = 0; a < NBF; ++a) {
+    int len = NBF - a;
+    if (q < len) {
+      b = a + q;
+      break;
+    }
+    q -= len;
+  }
+  int nao = NBF * natm;
+  double v = out[p * NOUT + t];
+  D[(size_t)(NBF * A + a) * nao + NBF * B + b] = v;
+  D[(size_t)(NBF * A + b) * nao + NBF * B + a] = v;
+  D[(size_t)(NBF * B + b) * nao + NBF * A + a] = v;
+  D[(size_t)(NBF * B + a) * nao + NBF * A + b] = v;
+}
+
+// ---- workspace -------------------------------------------------------------------------------
+struct Work {
+  float* Z[NLAYER];   // pre-activations
+  float* H[NLAYER];   // activations (H[3] = output)
+  float* G;           // gradient of the current layer's pre-activation
+  float* dA;          // gradient w.r.t. the previous activation
+  float* grad;        // parameter gradient (NPARAM)
+  float* loss;
+  __nv_bfloat16* Wb;  // BF16 copy of the parameters
+  __nv_bfloat16* Hb[NLAYER];
+  __nv_bfloat16* Xb;
+};
+
+static void layout(int n, Arena* a, Sizer* z, Work* w) {
+#define TAKE(T, ptr, count) \
+  if (a) ptr = a->take<T>(count); else z->take<T>(count);
+  for (int l = 0; l < NLAYER; ++l) {
+    TAKE(float, w->Z[l], (size_t)n * layer_out(l));
+    TAKE(float, w->H[l], (size_t)n * layer_out(l));
+    TAKE(__nv_bfloat16, w->Hb[l], (size_t)n * layer_out(l));
+  }
+  TAKE(float, w->G, (size_t)n * NHID);
+  TAKE(float, w->dA, (size_t)n * NHID);
+  TAKE(float, w->grad, NPARAM);
+  TAKE(float, w->loss, 1);
+  TAKE(__nv_bfloat16, w->Wb, NPARAM);
+  TAKE(__nv_bfloat16, w->Xb, (size_t)n * NIN);
+#undef TAKE
+}
+
+static unsigned nb(long n, int t = 256) { return (unsigned)((n + t - 1) / t); }
+
+// FP32 forward: H[3] = network(X).
+static int forward_fp32(const float* P, const float* X, int n, Work& w, cudaStream_t s) {
+  const float* in = X;
+  for (int l = 0; l < NLAYER; ++l) {
+    int fi = layer_in(l), fo = layer_out(l);
+    DF_TRY((sgemm<false, true, float>(n, fo, fi, 1.f, in, fi, P + w_offset(l), fi, 0.f, w.Z[l], fo, s)));
+    bias_act_kernel<float><<<nb((long)n * fo), 256, 0, s>>>(w.Z[l], P + b_offset(l), n, fo, l < NLAYER - 1, w.H[l]);
+    DF_LAUNCHED("bias_act_kernel");
+    in = w.H[l];
+  }
+  return DF_OK;
+}
+
+// BF16 inference: weights and activations in BF16, FP32 accumulation; output in H[3] (FP32).
+static int forward_bf16(const float* P, const float* X, int n, Work& w, cudaStream_t s) {
+  to_bf16_kernel<<<nb((long)NPARAM), 256, 0, s>>>(P, w.Wb, (long)NPARAM);
+  DF_LAUNCHED("to_bf16_kernel");
+  to_bf16_kernel<<<nb((long)n * NIN), 256, 0, s>>>(X, w.Xb, (long)n * NIN);
+  DF_LAUNCHED("to_bf16_kernel");
+  const __nv_bfloat16* in = w.Xb;
+  for (int l = 0; l < NLAYER; ++l) {
+    int fi = layer_in(l), fo = layer_out(l);
+    DF_TRY((sgemm<false, true, __nv_bfloat16>(n, fo, fi, 1.f, in, fi, w.Wb + w_offset(l), fi, 0.f, w.Z[l], fo, s)));
+    if (l < NLAYER - 1) {
+      bias_act_kernel<__nv_bfloat16><<<nb((long)n * fo), 256, 0, s>>>(w.Z[l], P + b_offset(l), n, fo, 1, w.Hb[l]);
+      in = w.Hb[l];
+    } else {
+      bias_act_kernel<float><<<nb((long)n * fo), 256, 0, s>>>(w.Z[l], P + b_offset(l), n, fo, 0, w.H[l]);
+    }
+    DF_LAUNCHED("bias_act_kernel");
+  }
+  return DF_OK;
+}
+
+// Loss and full parameter gradient (into w.grad) for a batch; loss accumulated into w.loss.
+static int loss_grad(const float* P, const float* X, const float* Y, const float* mask, int n, float nvalid, Work& w,
+                     cudaStream_t s) {
+  DF_TRY(forward_fp32(P, X, n, w, s));
+  DF_CUDA(cudaMemsetAsync(w.loss, 0, sizeof(float), s));
+  float inv = 1.f / (fmaxf(nvalid, 1.f) * NOUT);
+  mse_grad_kernel<<<nb((long)n * NOUT), 256, 0, s>>>(w.H[NLAYER - 1], Y, mask, n, inv, w.G, w.loss);
+  DF_LAUNCHED("mse_grad_kernel");
+  for (int l = NLAYER - 1; l >= 0; --l) {
+    int fi = layer_in(l), fo = layer_out(l);
+    const float* Ain = l == 0 ? X : w.H[l - 1];
+    // dW = G^T A_in  [fo][fi];  db = column sums of G
+    DF_TRY((sgemm<true, false, float>(fo, fi, n, 1.f, w.G, fo, Ain, fi, 0.f, w.grad + w_offset(l), fi, s)));
+    column_sum_kernel<<<fo, 256, 0, s>>>(w.G, n, fo, w.grad + b_offset(l));
+    DF_LAUNCHED("column_sum_kernel");
+    if (l == 0) break;
+    // dA = G W  [n][fi]; then G = dA * silu'(Z_{l-1})
+    DF_TRY((sgemm<false, false, float>(n, fi, fo, 1.f, w.G, fo, P + w_offset(l), fi, 0.f, w.dA, fi, s)));
+    silu_backward_kernel<<<nb((long)n * fi), 256, 0, s>>>(w.Z[l - 1], w.dA, (long)n * fi);
+    DF_LAUNCHED("silu_backward_kernel");
+    std::swap(w.G, w.dA);
+  }
+  return DF_OK;
+}
+
+}  // namespace mlp
+}  // namespace dfscf
+
+using namespace dfscf;
+using namespace dfscf::mlp;
+
+extern "C" size_t guess_mlp_param_count(void) { return NPARAM; }
+
+extern "C" size_t guess_mlp_work_bytes(int batch) {
+  if (batch <= 0) return 0;
+  Sizer z;
+  Work w;
+  layout(batch, nullptr, &z, &w);
+  return z.used;
+}
+
+extern "C" int guess_features(const double* xyz, int natm, float* feat, float* mask, void* work, size_t work_bytes,
+                              cudaStream_t s) {
+  clear_error();
+  DF_REQUIRE(xyz && feat && mask && natm > 0, DF_ERR_ARG, "guess_features: bad arguments");
+  DF_REQUIRE(work && work_bytes >= sizeof(float) * NRBF * (size_t)natm, DF_ERR_NOMEM, "guess_features: workspace");
+  float* env = (float*)work;
+  env_kernel<<<natm, 32, 0, s>>>(xyz, natm, env);
+  DF_LAUNCHED("env_kernel");
+  long npairs = (long)natm * (natm + 1) / 2;
+  pair_feature_kernel<float><<<(unsigned)npairs, 96, 0, s>>>(xyz, natm, env, feat, mask);
+  DF_LAUNCHED("pair_feature_kernel");
+  return DF_OK;
+}
+
+extern "C" int guess_targets(const double* D, int natm, float* Y, cudaStream_t s) {
+  clear_error();
+  DF_REQUIRE(D && Y && natm > 0, DF_ERR_ARG, "guess_targets: bad arguments");
+  long npairs = (long)natm * (natm + 1) / 2;
+  block_targets_kernel<<<(unsigned)npairs, 32, 0, s>>>(D, natm, Y);
+  DF_LAUNCHED("block_targets_kernel");
+  return DF_OK;
+}
+
+extern "C" int guess_mlp_forward(const float* params, const float* X, int n, float* out, int bf16, void* work,
+                                 size_t work_bytes, cudaStream_t s) {
+  clear_error();
+  DF_REQUIRE(params && X && out && n > 0, DF_ERR_ARG, "guess_mlp_forward: bad arguments");
+  DF_REQUIRE(work && work_bytes >= guess_mlp_work_bytes(n), DF_ERR_NOMEM, "guess_mlp_forward: workspace too small");
+  Arena a(work, work_bytes);
+  Work w;
+  layout(n, &a, nullptr, &w);
+  if (bf16) DF_TRY(forward_bf16(params, X, n, w, s));
+  else DF_TRY(forward_fp32(params, X, n, w, s));
+  DF_CUDA(cudaMemcpyAsync(out, w.H[NLAYER - 1], sizeof(float) * n * NOUT, cudaMemcpyDeviceToDevice, s));
+  return DF_OK;
+}
+
+extern "C" int guess_mlp_loss_grad(const float* params, const float* X, const float* Y, const float* mask, int n,
+                                   float nvalid, float* loss, float* grad, void* work, size_t work_bytes,
+                                   cudaStream_t s) {
+  clear_error();
+  DF_REQUIRE(params && X && Y && n > 0 && loss && grad, DF_ERR_ARG, "guess_mlp_loss_grad: bad arguments");
+  DF_REQUIRE(work && work_bytes >= guess_mlp_work_bytes(n), DF_ERR_NOMEM, "guess_mlp_loss_grad: workspace too small");
+  Arena a(work, work_bytes);
+  Work w;
+  layout(n, &a, nullptr, &w);
+  DF_TRY(loss_grad(params, X, Y, mask, n, nvalid, w, s));
+  DF_CUDA(cudaMemcpyAsync(loss, w.loss, sizeof(float), cudaMemcpyDeviceToDevice, s));
+  DF_CUDA(cudaMemcpyAsync(grad, w.grad, sizeof(float) * NPARAM, cudaMemcpyDeviceToDevice, s));
+  return DF_OK;
+}
+
+extern "C" int guess_mlp_train_step(float* params, float* adam_m, float* adam_v, int step, float lr, const float* X,
+                                    const float* Y, const float* mask, int n, float nvalid, float* loss, void* work,
+                                    size_t work_bytes, cudaStream_t s) {
+  clear_error();
+  DF_REQUIRE(params && adam_m && adam_v && X && Y && n > 0 && step >= 1, DF_ERR_ARG, "guess_mlp_train_step: bad args");
+  DF_REQUIRE(work && work_bytes >= guess_mlp_work_bytes(n), DF_ERR_NOMEM, "guess_mlp_train_step: workspace too small");
+  Arena a(work, work_bytes);
+  Work w;
+  layout(n, &a, nullptr, &w);
+  DF_TRY(loss_grad(params, X, Y, mask, n, nvalid, w, s));
+  const float b1 = 0.9f, b2 = 0.999f;
+  float c1 = 1.f - powf(b1, (float)step), c2 = 1.f - powf(b2, (float)step);
+  adam_kernel<<<nb((long)NPARAM), 256, 0, s>>>(params, w.grad, adam_m, adam_v, (long)NPARAM, lr, b1, b2, 1e-8f, c1, c2);
+  DF_LAUNCHED("adam_kernel");
+  if (loss) DF_CUDA(cudaMemcpyAsync(loss, w.loss, sizeof(float), cudaMemcpyDeviceToDevice, s));
+  return DF_OK;
+}
+
+extern "C" size_t guess_density_work_bytes(int natm) {
+  if (natm <= 0) return 0;
+  long np = (long)natm * (natm + 1) / 2;
+  Sizer z;
+  z.take<float>((size_t)NRBF * natm);
+  z.take<float>((size_t)np * NIN);
+  z.take<float>((size_t)np);
+  return z.used + guess_mlp_work_bytes((int)np);
+}
+
+extern "C" int guess_density(const float* params, const double* xyz, int natm, double* D0, void* work,
+                             size_t work_bytes, cudaStream_t s) {
+  clear_error();
+  DF_REQUIRE(params && xyz && D0 && natm > 0, DF_ERR_ARG, "guess_density: bad arguments");
+  DF_REQUIRE(work && work_bytes >= guess_density_work_bytes(natm), DF_ERR_NOMEM, "guess_density: workspace too small");
+  long np = (long)natm * (natm + 1) / 2;
+  DF_REQUIRE(np < 65535L * 64, DF_ERR_ARG, "guess_density: too many centres");
+  Arena a(work, work_bytes);
+  float* env = a.take<float>((size_t)NRBF * natm);
+  float* feat = a.take<float>((size_t)np * NIN);
+  float* mask = a.take<float>((size_t)np);
+  size_t rest = work_bytes - a.used;
+  void* mw = (char*)work + a.used;
+  env_kernel<<<natm, 32, 0, s>>>(xyz, natm, env);
+  DF_LAUNCHED("env_kernel");
+  pair_feature_kernel<float><<<(unsigned)np, 96, 0, s>>>(xyz, natm, env, feat, mask);
+  DF_LAUNCHED("pair_feature_kernel");
+  Arena b(mw, rest);
+  Work w;
+  layout((int)np, &b, nullptr, &w);
+  DF_REQUIRE(!b.overflow, DF_ERR_NOMEM, "guess_density: workspace too small");
+  DF_TRY(forward_bf16(params, feat, (int)np, w, s));
+  int nao = NBF * natm;
+  DF_CUDA(cudaMemsetAsync(D0, 0, sizeof(double) * nao * nao, s));
+  assemble_density_kernel<<<(unsigned)np, 32, 0, s>>>(w.H[NLAYER - 1], mask, natm, D0);
+  DF_LAUNCHED("assemble_density_kernel");
+  return DF_OK;
+}

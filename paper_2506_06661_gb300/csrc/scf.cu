@@ -644,6 +644,9 @@ static int check_molecule(const df_molecule* mol, const scf_opts& o) {
   return DF_OK;
 }
 
+int scf_run_on(const df_molecule* mol, const scf_opts& o, const double* dm0, double* D_out, double* C_out,
+               double* mo_energy, scf_result* res, void* work, size_t work_bytes, cudaStream_t s);
+
 static int init_mol(ScfMol& M, const df_molecule* mol, const scf_opts& o, void* work, size_t work_bytes,
                     cudaStream_t s) {
   M.mol = *mol;
@@ -693,6 +696,27 @@ extern "C" int scf_run(const df_molecule* mol, const scf_opts* opt, const double
   DF_TRY(check_molecule(mol, o));
   size_t need = scf_work_bytes(mol->nao, mol->naux, mol->nelec / 2, o.precision);
   DF_REQUIRE(work && work_bytes >= need, DF_ERR_NOMEM, "scf_run: workspace of %zu bytes < %zu", work_bytes, need);
+  // The iterations are captured into CUDA graphs, which the legacy default stream does
+  // not allow; run on a private stream ordered after the caller's and join back at the end.
+  cudaStream_t ps = nullptr;
+  cudaEvent_t ev = nullptr;
+  DF_CUDA(cudaStreamCreateWithFlags(&ps, cudaStreamNonBlocking));
+  DF_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  DF_CUDA(cudaEventRecord(ev, s));
+  DF_CUDA(cudaStreamWaitEvent(ps, ev, 0));
+  int rc_run = scf_run_on(mol, o, dm0, D_out, C_out, mo_energy, res, work, work_bytes, ps);
+  cudaEventRecord(ev, ps);
+  cudaStreamWaitEvent(s, ev, 0);
+  cudaStreamSynchronize(ps);
+  cudaEventDestroy(ev);
+  cudaStreamDestroy(ps);
+  return rc_run;
+}
+
+namespace dfscf {
+
+int scf_run_on(const df_molecule* mol, const scf_opts& o, const double* dm0, double* D_out, double* C_out,
+               double* mo_energy, scf_result* res, void* work, size_t work_bytes, cudaStream_t s) {
   ScfMol M;
   DF_TRY(init_mol(M, mol, o, work, work_bytes, s));
   ScfStatus* hst = nullptr;
@@ -720,6 +744,8 @@ extern "C" int scf_run(const df_molecule* mol, const scf_opts* opt, const double
   cudaFreeHost(hst);
   return rc != DF_OK ? rc : M.rc;
 }
+
+}  // namespace dfscf
 
 // ---- batch ---------------------------------------------------------------------------------------
 extern "C" size_t scf_batch_work_bytes(const df_molecule* mols, int nmol, int precision, int slots) {

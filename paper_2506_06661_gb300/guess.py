@@ -1,0 +1,191 @@
+"""Learned initial guess: data from converged SCFs, GPU training, evaluation.
+
+Thin orchestration over the library's guess_* entry points (features, targets, MLP
+forward / backward / Adam, density assembly) and scf_run_batch.  The paper lets the SCF
+start from any density (Section "Initial Guess for Mean-field Methods"); the model here
+predicts one from geometry, and scf_run falls back to the core-Hamiltonian guess when
+the prediction fails the trace or idempotency check.
+
+Random numbers (weight initialisation, mini-batch order) are drawn on the host with
+numpy's PCG64 and passed to the GPU.
+"""
+from __future__ import annotations
+
+import ctypes
+import json
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+import torch
+
+from . import (DF_OK, DFError, MoleculeOnDevice, _check, _dev, _ptr, _stream, _work, lib, scf_run_batch)
+
+NIN, NHID, NOUT, NRBF = 65, 256, 15, 32
+LAYERS = [(NIN, NHID), (NHID, NHID), (NHID, NHID), (NHID, NOUT)]
+
+
+def param_count() -> int:
+    return int(lib().guess_mlp_param_count())
+
+
+def init_params(seed: int = 0) -> np.ndarray:
+    """Uniform(-sqrt(3/fan_in), +sqrt(3/fan_in)) weights, zero biases, flattened per layer
+    as W [out][in] then b [out] (the library's parameter layout)."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for fan_in, fan_out in LAYERS:
+        bound = np.sqrt(3.0 / fan_in)
+        parts.append(rng.uniform(-bound, bound, size=(fan_out, fan_in)).ravel())
+        parts.append(np.zeros(fan_out))
+    flat = np.concatenate(parts)
+    assert flat.size == param_count()
+    return flat
+
+
+@dataclass
+class GuessModel:
+    params: torch.Tensor                     # float32 [param_count] on the GPU
+    m: torch.Tensor | None = None            # Adam first moment
+    v: torch.Tensor | None = None            # Adam second moment
+    step: int = 0
+    history: list = field(default_factory=list)
+
+    @classmethod
+    def create(cls, seed: int = 0) -> "GuessModel":
+        p = torch.tensor(init_params(seed), dtype=torch.float32, device="cuda")
+        return cls(p, torch.zeros_like(p), torch.zeros_like(p), 0)
+
+    def save(self, path: str) -> None:
+        np.savez(path, params=self.params.cpu().numpy(), m=self.m.cpu().numpy(), v=self.v.cpu().numpy(),
+                 step=self.step, history=np.array(self.history, dtype=np.float64))
+
+    @classmethod
+    def load(cls, path: str) -> "GuessModel":
+        z = np.load(path)
+        t = lambda a: torch.tensor(a, dtype=torch.float32, device="cuda")  # noqa: E731
+        return cls(t(z["params"]), t(z["m"]), t(z["v"]), int(z["step"]), list(z["history"]))
+
+
+def features(xyz):
+    """(feat [npairs, 65] float32, mask [npairs]) for one geometry (pairs A >= B, packed)."""
+    x = _dev(xyz)
+    natm = x.shape[0]
+    npairs = natm * (natm + 1) // 2
+    feat = torch.empty(npairs, NIN, dtype=torch.float32, device="cuda")
+    mask = torch.empty(npairs, dtype=torch.float32, device="cuda")
+    w = _work(128 * natm)
+    _check(lib().guess_features(_ptr(x), natm, _ptr(feat), _ptr(mask), _ptr(w), w.numel(), _stream()))
+    return feat, mask
+
+
+def targets(D, natm: int) -> torch.Tensor:
+    D = _dev(D)
+    Y = torch.empty(natm * (natm + 1) // 2, NOUT, dtype=torch.float32, device="cuda")
+    _check(lib().guess_targets(_ptr(D), natm, _ptr(Y), _stream()))
+    return Y
+
+
+def forward(params: torch.Tensor, X: torch.Tensor, bf16: bool = False) -> torch.Tensor:
+    n = X.shape[0]
+    out = torch.empty(n, NOUT, dtype=torch.float32, device="cuda")
+    w = _work(lib().guess_mlp_work_bytes(n))
+    _check(lib().guess_mlp_forward(_ptr(params), _ptr(X.contiguous()), n, _ptr(out), 1 if bf16 else 0, _ptr(w),
+                                   w.numel(), _stream()))
+    return out
+
+
+def loss_grad(params: torch.Tensor, X, Y, mask=None):
+    n = X.shape[0]
+    nvalid = float(mask.sum().item()) if mask is not None else float(n)
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    grad = torch.empty_like(params)
+    w = _work(lib().guess_mlp_work_bytes(n))
+    _check(lib().guess_mlp_loss_grad(_ptr(params), _ptr(X), _ptr(Y), _ptr(mask), n, ctypes.c_float(nvalid), _ptr(loss),
+                                     _ptr(grad), _ptr(w), w.numel(), _stream()))
+    return float(loss.item()), grad
+
+
+def predict_density(model_or_params, xyz) -> torch.Tensor:
+    params = model_or_params.params if isinstance(model_or_params, GuessModel) else model_or_params
+    x = _dev(xyz)
+    natm = x.shape[0]
+    D0 = torch.empty(5 * natm, 5 * natm, dtype=torch.float64, device="cuda")
+    w = _work(lib().guess_density_work_bytes(natm))
+    _check(lib().guess_density(_ptr(params), _ptr(x), natm, _ptr(D0), _ptr(w), w.numel(), _stream()))
+    return D0
+
+
+def build_dataset(mols, Ds):
+    """Concatenated (X, Y, mask) over molecules with converged densities Ds."""
+    Xs, Ys, Ms = [], [], []
+    for mol, D in zip(mols, Ds):
+        f, m = features(mol.xyz)
+        Xs.append(f)
+        Ms.append(m)
+        Ys.append(targets(D, mol.natm))
+    return torch.cat(Xs), torch.cat(Ys), torch.cat(Ms)
+
+
+def train(model: GuessModel, X, Y, mask, epochs: int = 10, batch: int = 4096, lr: float = 1e-3, seed: int = 0,
+          log=None):
+    """Mini-batch Adam over valid pair samples; the permutation is drawn on the host."""
+    keep = torch.nonzero(mask > 0).squeeze(1)
+    X, Y = X[keep].contiguous(), Y[keep].contiguous()
+    n = X.shape[0]
+    rng = np.random.default_rng(seed)
+    w = _work(lib().guess_mlp_work_bytes(batch))
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    for ep in range(epochs):
+        perm = torch.tensor(rng.permutation(n), device="cuda")
+        tot, cnt = 0.0, 0
+        for b0 in range(0, n, batch):
+            idx = perm[b0:b0 + batch]
+            xb, yb = X[idx].contiguous(), Y[idx].contiguous()
+            nb = xb.shape[0]
+            model.step += 1
+            _check(lib().guess_mlp_train_step(_ptr(model.params), _ptr(model.m), _ptr(model.v), model.step,
+                                              ctypes.c_float(lr), _ptr(xb), _ptr(yb), None, nb, ctypes.c_float(nb),
+                                              _ptr(loss), _ptr(w), w.numel(), _stream()))
+            tot += float(loss.item()) * nb
+            cnt += nb
+        model.history.append(tot / max(cnt, 1))
+        if log:
+            log(f"epoch {ep + 1}/{epochs}: mse {model.history[-1]:.3e}")
+    return model.history
+
+
+def converged_densities(mols, slots: int = 32, precision: str = "fp64", chunk: int = 512):
+    """Run the batched SCF and return (results, densities) for training data."""
+    res, Ds = [], []
+    for i in range(0, len(mols), chunk):
+        out = scf_run_batch(mols[i:i + chunk], slots=slots, precision=precision, want_D=True,
+                            raise_on_noconv=False)
+        res += out.results
+        Ds += out.D
+    return res, Ds
+
+
+def evaluate(model: GuessModel, mols, slots: int = 32, precision: str = "mixed"):
+    """Batched SCF from the core guess and from the learned guess on the same molecules."""
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    core = scf_run_batch(mols, slots=slots, precision=precision, raise_on_noconv=False).results
+    torch.cuda.synchronize()
+    t_core = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    dm0 = [predict_density(model, m.xyz) for m in mols]
+    learned = scf_run_batch(mols, slots=slots, precision=precision, dm0s=dm0, raise_on_noconv=False).results
+    torch.cuda.synchronize()
+    t_learned = time.perf_counter() - t0
+    both = [i for i in range(len(mols)) if core[i].converged and learned[i].converged]
+    it_core = np.array([core[i].iterations for i in both], dtype=float)
+    it_learn = np.array([learned[i].iterations for i in both], dtype=float)
+    de = np.array([abs(core[i].energy - learned[i].energy) for i in both])
+    return {"molecules": len(mols), "both_converged": len(both),
+            "mean_iter_core": float(it_core.mean()) if both else None,
+            "mean_iter_learned": float(it_learn.mean()) if both else None,
+            "wall_s_core": t_core, "wall_s_learned": t_learned,
+            "guess_used": int(sum(r.guess == 1 for r in learned)), "guess_rejected": int(sum(r.guess == 2 for r in learned)),
+            "max_abs_dE_learned_vs_core": float(de.max()) if both else None, "converged_core": int(sum(r.converged for r in core)),
+            "converged_learned": int(sum(r.converged for r in learned))}
