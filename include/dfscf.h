@@ -257,6 +257,25 @@ int df_core_guess(const df_molecule* mol, double lindep, double* S_out, double* 
                   double* D_out, double* mo_energy, int* nmo_out, void* work, size_t work_bytes,
                   cudaStream_t s);
 
+/* ---- Coulomb build without a caller workspace ------------------------------------------
+ * The paper has no counterpart of this entry point; it exists for callers that cannot
+ * allocate device memory for a workspace (plugins whose host framework owns every device
+ * allocation, and latency-critical services that forbid allocation once running).
+ * Computes exactly what df_jk computes for J in DF_FP64 mode (K is not available here):
+ * J[D]_mn = sum_P d_P B_{P,mn}, d_P = sum_{kl} B_{P,kl} D_kl, from the FP64 packed rows of
+ * a B built by df_build_B in either precision.  B, D [nao][nao] and J [nao][nao] are
+ * device pointers owned by the caller.
+ * Scratch comes from one fixed device array of df_j_noalloc_capacity() bytes (8 MiB)
+ * that the library reserves on every GPU that loads it, until the process exits.  The
+ * call allocates nothing and returns DF_ERR_ARG when (nao, naux) need more than that
+ * (for example nao <= 400 with naux <= 1200 always fits; nao 1500 does not).
+ * The first call on each device looks up the array's device address (with that device
+ * current); make that first call before any stream capture.  Every call shares the array
+ * and it keeps the last call's contents: calls whose GPU work overlaps (other streams or
+ * threads on the same device) race and must be ordered by the caller.                  */
+size_t df_j_noalloc_capacity(void);
+int df_j_noalloc(const void* B, int nao, int naux, const double* D, double* J, cudaStream_t s);
+
 /* ---- phase profiler ------------------------------------------------------------------
  * When enabled, the J/K builds bracket each kernel phase with CUDA events on the
  * launching stream.  df_profile_count() synchronises those events and returns the number

@@ -107,6 +107,8 @@ _SIGS = {
                                   _SZ, _VP]),
     "guess_density_work_bytes": (_SZ, [_I]),
     "guess_density": (_I, [_VP, _VP, _I, _VP, _VP, _SZ, _VP]),
+    "df_j_noalloc_capacity": (_SZ, []),
+    "df_j_noalloc": (_I, [_VP, _I, _I, _VP, _VP, _VP]),
     "scf_batch_work_bytes": (_SZ, [ctypes.POINTER(DFMolecule), _I, _I, _I]),
     "scf_run_batch": (_I, [ctypes.POINTER(DFMolecule), _I, ctypes.POINTER(ScfOpts), ctypes.POINTER(_VP),
                            ctypes.POINTER(_VP), ctypes.POINTER(ScfResultC), _I, _VP, _SZ, _VP]),
