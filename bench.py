@@ -353,6 +353,101 @@ def run_ours(args):
     return 0
 
 
+def run_scenario_scf(args):
+    """Time to convergence of the plain FP64 SCF and the mixed-precision SCF (same molecule)."""
+    import torch
+    import paper_2506_06661_gb300 as dfscf
+    mol, desc = workload(args.workload)
+    md = dfscf.MoleculeOnDevice(mol)
+    out = {"scenario": "scf", "workload": desc}
+    ref = None
+    if args.workload == "c0":
+        from oracle import scf as oscf
+        ref = oscf.rhf(oscf.build_system(mol)).energy
+        out["oracle_energy"] = ref
+    for prec in ("mixed", "fp64"):
+        work = dfscf._work(dfscf.scf_work_bytes(md.nao, md.naux, md.nelec // 2, prec))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = dfscf.scf_run(md, precision=prec, work=work, raise_on_noconv=False)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        # a second, profiled run (graphs bypassed) gives the per-phase split of the time
+        dfscf.profile_reset()
+        dfscf.profile_enable(True)
+        dfscf.scf_run(md, precision=prec, work=work, raise_on_noconv=False)
+        dfscf.profile_enable(False)
+        phases = {k: round(v[0], 3) for k, v in dfscf.profile_read().items()}
+        out[prec] = {"seconds": dt, "energy": r.energy, "iterations": r.iterations,
+                     "fp64_iterations": r.fp64_iterations, "converged": r.converged, "last_dE": r.last_de,
+                     "last_err": r.last_err, "phase_ms_total": phases}
+        if ref is not None:
+            out[prec]["abs_err_vs_oracle"] = abs(r.energy - ref)
+        del work
+    out["mixed_vs_fp64_abs_dE"] = abs(out["mixed"]["energy"] - out["fp64"]["energy"])
+    out["speedup_mixed_over_fp64"] = out["fp64"]["seconds"] / out["mixed"]["seconds"]
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def run_scenario_batch(args):
+    """Batched SCF over molecules of 10-80 centres (uniform size draw, seed 1)."""
+    import torch
+    import gen
+    import paper_2506_06661_gb300 as dfscf
+    mols = gen.batch_molecules(args.nmol, 10, 80, 1)
+    devs = [dfscf.MoleculeOnDevice(m) for m in mols]
+    out = {"scenario": "batch", "molecules": len(mols), "centres": "10-80 (uniform, seed 1)",
+           "nao_range": [min(m.nao for m in mols), max(m.nao for m in mols)], "slots": args.slots}
+    for prec in ("mixed",) + (("fp64",) if args.batch_fp64 else ()):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res = dfscf.scf_run_batch(devs, slots=args.slots, precision=prec, raise_on_noconv=False).results
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        conv = [r for r in res if r.converged]
+        out[prec] = {"seconds": dt, "molecules_per_s": len(mols) / dt, "converged": len(conv),
+                     "mean_iterations": float(np.mean([r.iterations for r in res])),
+                     "energies": [r.energy for r in res]}
+    if "fp64" in out:
+        d = [abs(a - b) for a, b in zip(out["mixed"]["energies"], out["fp64"]["energies"])]
+        out["max_abs_dE_mixed_vs_fp64"] = float(max(d))
+    for prec in ("mixed", "fp64"):
+        if prec in out:
+            out[prec].pop("energies")
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def run_scenario_guess(args):
+    """Learned initial guess: train on converged SCFs of 10-40 centres (seed 2), evaluate
+    mean iterations and wall time against the core guess on unseen 40-120-centre molecules (seed 3)."""
+    import torch
+    import gen
+    from paper_2506_06661_gb300 import guess
+    t0 = time.perf_counter()
+    train = gen.batch_molecules(args.ntrain, 10, 40, 2)
+    res, Ds = guess.converged_densities(train, slots=args.slots, precision="fp64")
+    ok = [i for i, r in enumerate(res) if r.converged]
+    t_data = time.perf_counter() - t0
+    X, Y, M = guess.build_dataset([train[i] for i in ok], [Ds[i] for i in ok])
+    del Ds
+    model = guess.GuessModel.create(seed=2)
+    t0 = time.perf_counter()
+    hist = guess.train(model, X, Y, M, epochs=args.epochs, batch=4096, lr=1e-3, seed=2)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    if args.save_model:
+        model.save(args.save_model)
+    test = gen.batch_molecules(args.neval, 40, 120, 3)
+    ev = guess.evaluate(model, test, slots=args.slots, precision="mixed")
+    out = {"scenario": "guess", "train_molecules": len(train), "train_converged": len(ok),
+           "train_samples": int(M.sum().item()), "data_seconds": t_data, "train_seconds": t_train,
+           "epochs": args.epochs, "mse_first_last": [hist[0], hist[-1]], "eval": ev}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__)
     ap.add_argument("--gpus", type=int, default=1)
@@ -364,7 +459,23 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-mixed", dest="mixed", action="store_false")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--scenario", choices=["fock", "scf", "batch", "guess"], default="fock",
+                    help="fock: Fock-build throughput (the default line); scf: SCF time to convergence, "
+                         "mixed vs FP64; batch: batched SCF of uneven molecules; guess: learned guess")
+    ap.add_argument("--nmol", type=int, default=256)
+    ap.add_argument("--slots", type=int, default=32)
+    ap.add_argument("--batch-fp64", action="store_true")
+    ap.add_argument("--ntrain", type=int, default=20000)
+    ap.add_argument("--neval", type=int, default=512)
+    ap.add_argument("--epochs", type=int, default=20)
+    ap.add_argument("--save-model", default="")
     args = ap.parse_args()
+    if args.scenario == "scf":
+        return run_scenario_scf(args)
+    if args.scenario == "batch":
+        return run_scenario_batch(args)
+    if args.scenario == "guess":
+        return run_scenario_guess(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -132,6 +132,14 @@ int df_jk(const void* B, int nao, int naux, int precision, const double* D, cons
 size_t df_eigh_work_bytes(int n);
 int df_eigh(double* A, int n, double* w, double* Z, void* work, size_t work_bytes, cudaStream_t s);
 
+/* The k lowest eigenpairs only (w [k] ascending, Z [n][k] columns), as the SCF needs for
+ * the occupied orbitals and the LUMO: Householder reduction, Sturm bisection, inverse
+ * iteration on the tridiagonal matrix, back-transformation of the k vectors and
+ * re-orthonormalisation.  A is overwritten.  work: df_eigh_lowest_work_bytes(n, k).
+ * Returns DF_ERR_NOCONV if inverse iteration or re-orthonormalisation breaks down.        */
+size_t df_eigh_lowest_work_bytes(int n, int k);
+int df_eigh_lowest(double* A, int n, int k, double* w, double* Z, void* work, size_t work_bytes, cudaStream_t s);
+
 /* ---- a9..a12: restricted Hartree-Fock SCF --------------------------------------------
  * Mean-field DF-RHF ("density_fit()" mean-field in the paper's DF section) with Pulay
  * DIIS (named as PySCF's default accelerator in the paper's SOSCF section):
@@ -240,9 +248,21 @@ int guess_mlp_loss_grad(const float* params, const float* X, const float* Y, con
 int guess_mlp_train_step(float* params, float* adam_m, float* adam_v, int step, float lr, const float* X,
                          const float* Y, const float* mask, int n, float nvalid, float* loss, void* work,
                          size_t work_bytes, cudaStream_t s);
-/* dm0 [5 natm][5 natm] for one molecule via BF16 inference.                                */
+/* The network's targets are the blocks of the Loewdin-orthogonalised density
+ * Dt = S^1/2 D S^1/2 (its blocks are well conditioned; those of D are not in a strongly
+ * non-orthogonal basis).  guess_density assembles Dt from the predicted blocks (BF16
+ * inference) and returns dm0 = S^-1/2 Dt S^-1/2 [5 natm][5 natm].                        */
 size_t guess_density_work_bytes(int natm);
-int guess_density(const float* params, const double* xyz, int natm, double* D0, void* work, size_t work_bytes,
+int guess_density(const float* params, const double* xyz, int natm, const double* Sinvhalf, double* D0,
+                  void* work, size_t work_bytes, cudaStream_t s);
+/* S^1/2 and S^-1/2 (either may be NULL) of the orbital overlap, over eigenvalues above
+ * lindep (pseudo-inverse below).  Synchronises the stream to check the eigensolver.      */
+size_t df_lowdin_work_bytes(int nao);
+int df_lowdin_factors(const double* ao_xyz, const double* ao_exp, int nao, double lindep, double* Shalf,
+                      double* Sinvhalf, void* work, size_t work_bytes, cudaStream_t s);
+/* out = M A M for n x n matrices (M symmetric), e.g. Dt = S^1/2 D S^1/2.                  */
+size_t df_congruence_work_bytes(int n);
+int df_congruence(const double* M, const double* A, int n, double* out, void* work, size_t work_bytes,
                   cudaStream_t s);
 
 /* ---- core-Hamiltonian guess ------------------------------------------------------------
@@ -275,6 +295,17 @@ int df_core_guess(const df_molecule* mol, double lindep, double* S_out, double* 
  * threads on the same device) race and must be ordered by the caller.                  */
 size_t df_j_noalloc_capacity(void);
 int df_j_noalloc(const void* B, int nao, int naux, const double* D, double* J, cudaStream_t s);
+
+/* ---- tuning knobs ------------------------------------------------------------------------
+ * Launch parameters chosen by the autotuner (paper_2506_06661_gb300/tune.py): "umma_max_stages"
+ * (2..4, shared-memory ring depth of the tensor-core GEMM), "syrk_split" and "fp64_syrk_split"
+ * (K-dimension splits of the exchange SYRK, 0 = built-in heuristic), "jpass2_rows" (32..512,
+ * auxiliary rows per CTA slice of J's second pass).  Host-side process-wide state: change
+ * knobs only between calls and re-query *_work_bytes afterwards (split counts size the
+ * workspaces).  df_tune_set returns DF_ERR_ARG for an unknown name or an out-of-range value;
+ * df_tune_get returns -1 for an unknown name.                                              */
+int df_tune_set(const char* name, int value);
+int df_tune_get(const char* name);
 
 /* ---- phase profiler ------------------------------------------------------------------
  * When enabled, the J/K builds bracket each kernel phase with CUDA events on the

@@ -11,7 +11,10 @@ produces such a density from geometry:
 * features of an off-diagonal pair (A > B): [rbf(R_AB), env_A + env_B, 0];
   of a diagonal pair (A, A): [0, 2 env_A, 1]   (65 inputs, symmetric in A and B);
 * network 65 -> 256 -> 256 -> 256 -> 15 with SiLU after each hidden layer;
-* the 15 outputs are the upper triangle (row-major, a <= b) of a symmetric 5x5 block;
+* the 15 outputs are the upper triangle (row-major, a <= b) of a symmetric 5x5 block of
+  the Loewdin-orthogonalised density Dt = S^1/2 D S^1/2 (eigenvalues 0 or 2 at
+  convergence; the blocks of D itself are ill-conditioned in this strongly
+  non-orthogonal basis); the starting density is D0 = S^-1/2 Dt S^-1/2;
 * loss: mean squared error over all pairs and outputs; optimiser: Adam.
 """
 from __future__ import annotations
@@ -154,10 +157,22 @@ def assemble_density(pred: np.ndarray, pairs: np.ndarray, natm: int) -> np.ndarr
     return D
 
 
-def guess_is_valid(D: np.ndarray, S: np.ndarray, nelec: int, tr_tol: float = 0.05, idem_tol: float = 0.5) -> bool:
-    """Electron count within 5% and ||DSD - 2D||_F / ||D||_F below 0.5."""
+def lowdin_factors(S: np.ndarray, lindep: float = 1e-8):
+    """(S^1/2, S^-1/2) from the eigen-decomposition of S, dropping eigenvalues <= lindep."""
+    s, U = np.linalg.eigh(S)
+    keep = s > lindep
+    U, s = U[:, keep], s[keep]
+    return (U * np.sqrt(s)) @ U.T, (U / np.sqrt(s)) @ U.T
+
+
+def guess_is_valid(D: np.ndarray, S: np.ndarray, nelec: int, tr_tol: float = 0.05, idem_tol: float = 1.0) -> bool:
+    """Electron count tr(DS) within 5% of nelec, and the idempotency error of D measured in
+    an orthonormal basis, ||Dt Dt - 2 Dt||_F / ||Dt||_F with Dt = S^1/2 D S^1/2 (the same for
+    every orthonormal basis), below 1."""
     ne = float(np.sum(D * S))
     if not np.isfinite(ne) or abs(ne - nelec) / nelec >= tr_tol:
         return False
-    nd = np.linalg.norm(D)
-    return bool(nd > 0 and np.linalg.norm(D @ S @ D - 2.0 * D) / nd < idem_tol)
+    Sh, _ = lowdin_factors(S)
+    Dt = Sh @ D @ Sh
+    nd = np.linalg.norm(Dt)
+    return bool(nd > 0 and np.linalg.norm(Dt @ Dt - 2.0 * Dt) / nd < idem_tol)

@@ -84,6 +84,10 @@ _SIGS = {
     "df_jk": (_I, [_VP, _I, _I, _I, _VP, _VP, _I, _VP, _VP, _VP, _SZ, _VP]),
     "df_eigh_work_bytes": (_SZ, [_I]),
     "df_eigh": (_I, [_VP, _I, _VP, _VP, _VP, _SZ, _VP]),
+    "df_tune_set": (_I, [ctypes.c_char_p, _I]),
+    "df_tune_get": (_I, [ctypes.c_char_p]),
+    "df_eigh_lowest_work_bytes": (_SZ, [_I, _I]),
+    "df_eigh_lowest": (_I, [_VP, _I, _I, _VP, _VP, _VP, _SZ, _VP]),
     "scf_default_opts": (None, [ctypes.POINTER(ScfOpts)]),
     "df_core_guess_work_bytes": (_SZ, [_I, _I]),
     "df_core_guess": (_I, [ctypes.POINTER(DFMolecule), _D, _VP, _VP, _VP, _VP, _VP, ctypes.POINTER(_I), _VP, _SZ,
@@ -106,7 +110,11 @@ _SIGS = {
     "guess_mlp_train_step": (_I, [_VP, _VP, _VP, _I, ctypes.c_float, _VP, _VP, _VP, _I, ctypes.c_float, _VP, _VP,
                                   _SZ, _VP]),
     "guess_density_work_bytes": (_SZ, [_I]),
-    "guess_density": (_I, [_VP, _VP, _I, _VP, _VP, _SZ, _VP]),
+    "guess_density": (_I, [_VP, _VP, _I, _VP, _VP, _VP, _SZ, _VP]),
+    "df_lowdin_work_bytes": (_SZ, [_I]),
+    "df_lowdin_factors": (_I, [_VP, _VP, _I, _D, _VP, _VP, _VP, _SZ, _VP]),
+    "df_congruence_work_bytes": (_SZ, [_I]),
+    "df_congruence": (_I, [_VP, _VP, _I, _VP, _VP, _SZ, _VP]),
     "df_j_noalloc_capacity": (_SZ, []),
     "df_j_noalloc": (_I, [_VP, _I, _I, _VP, _VP, _VP]),
     "scf_batch_work_bytes": (_SZ, [ctypes.POINTER(DFMolecule), _I, _I, _I]),
@@ -267,6 +275,17 @@ def eigh(A):
     Z = torch.empty(n, n, dtype=torch.float64, device="cuda")
     work = _work(lib().df_eigh_work_bytes(n))
     _check(lib().df_eigh(_ptr(A), n, _ptr(w), _ptr(Z), _ptr(work), work.numel(), _stream()))
+    return w, Z
+
+
+def eigh_lowest(A, k: int):
+    """k lowest eigenpairs (w [k], Z [n][k]) of a symmetric matrix."""
+    A = _dev(A).clone()
+    n = A.shape[0]
+    w = torch.empty(k, dtype=torch.float64, device="cuda")
+    Z = torch.empty(n, k, dtype=torch.float64, device="cuda")
+    work = _work(lib().df_eigh_lowest_work_bytes(n, k))
+    _check(lib().df_eigh_lowest(_ptr(A), n, k, _ptr(w), _ptr(Z), _ptr(work), work.numel(), _stream()))
     return w, Z
 
 

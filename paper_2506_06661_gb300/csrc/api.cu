@@ -112,3 +112,50 @@ extern "C" long df_profile_calls(int i) {
   if (i < 0 || i >= (int)dfscf::g_prof_cnt.size()) return 0;
   return dfscf::g_prof_cnt[i].second;
 }
+
+// ---- tuning knobs ---------------------------------------------------------------------
+// Launch parameters the autotuner may change between calls.  0 means "use the built-in
+// heuristic" where that is allowed.
+namespace dfscf {
+
+struct Knob {
+  const char* name;
+  int value, lo, hi;
+};
+static Knob g_knobs[] = {
+    {"umma_max_stages", 4, 2, 4},    // shared-memory ring depth of the tcgen05 GEMM
+    {"syrk_split", 0, 0, 4096},      // K-dimension splits of the tcgen05 exchange SYRK
+    {"fp64_syrk_split", 0, 0, 4096}, // K-dimension splits of the FP64 exchange SYRK
+    {"jpass2_rows", 256, 32, 512},   // auxiliary rows per CTA slice of J's second pass
+};
+
+int knob(const char* name) {
+  for (auto& k : g_knobs)
+    if (strcmp(k.name, name) == 0) return k.value;
+  return 0;
+}
+
+}  // namespace dfscf
+
+extern "C" int df_tune_set(const char* name, int value) {
+  dfscf::clear_error();
+  if (!name) return DF_ERR_ARG;
+  for (auto& k : dfscf::g_knobs)
+    if (strcmp(k.name, name) == 0) {
+      if (value < k.lo || value > k.hi) {
+        dfscf::set_error("df_tune_set: %s = %d outside [%d, %d]", name, value, k.lo, k.hi);
+        return DF_ERR_ARG;
+      }
+      k.value = value;
+      return DF_OK;
+    }
+  dfscf::set_error("df_tune_set: unknown knob '%s'", name);
+  return DF_ERR_ARG;
+}
+
+extern "C" int df_tune_get(const char* name) {
+  if (!name) return -1;
+  for (auto& k : dfscf::g_knobs)
+    if (strcmp(k.name, name) == 0) return k.value;
+  return -1;
+}

@@ -13,6 +13,9 @@ namespace dfscf {
 void set_error(const char* fmt, ...);
 void clear_error();
 
+// Tuning knob value by name (api.cu); 0 for an unknown name.
+int knob(const char* name);
+
 // Phase profiler (api.cu): CUDA events around kernel phases when enabled.
 bool prof_on();
 void* prof_begin(const char* name, cudaStream_t s);

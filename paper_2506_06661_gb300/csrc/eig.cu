@@ -34,13 +34,12 @@ __device__ double cta_sum(double v, EigShared& sh) {
   return t;
 }
 
-// A [n][n] symmetric (full storage), overwritten.  Outputs w [n] ascending and
-// ZT [n][n] with eigenvector k in row k.  Scratch: d, e, beta, v (n each), cs, sn (n each).
-__device__ int eigh_cta(double* __restrict__ A, int n, double* __restrict__ w, double* __restrict__ ZT,
-                        double* __restrict__ d, double* __restrict__ e, double* __restrict__ beta,
-                        double* __restrict__ v, double* __restrict__ cs, double* __restrict__ sn, EigShared& sh) {
+// Householder reduction of the symmetric A [n][n] (full storage) to tridiag(d, e): reflector
+// k (k = 0..n-3) is H_k = I - beta[k] v v^T with v stored in column k below the diagonal.
+__device__ void tridiagonalize_cta(double* __restrict__ A, int n, double* __restrict__ d, double* __restrict__ e,
+                                   double* __restrict__ beta, double* __restrict__ v, double* __restrict__ cs,
+                                   double* __restrict__ sn, EigShared& sh) {
   const int tid = threadIdx.x, nt = blockDim.x;
-  // ---- 1. tridiagonalisation --------------------------------------------------------
   for (int k = 0; k + 2 < n; ++k) {
     int len = n - k - 1;                      // x = A[k+1..n)[k]
     double part = 0.0;
@@ -101,6 +100,16 @@ __device__ int eigh_cta(double* __restrict__ A, int n, double* __restrict__ w, d
     e[n - 1] = 0.0;
   }
   __syncthreads();
+}
+
+// A [n][n] symmetric (full storage), overwritten.  Outputs w [n] ascending and
+// ZT [n][n] with eigenvector k in row k.  Scratch: d, e, beta, v (n each), cs, sn (n each).
+__device__ int eigh_cta(double* __restrict__ A, int n, double* __restrict__ w, double* __restrict__ ZT,
+                        double* __restrict__ d, double* __restrict__ e, double* __restrict__ beta,
+                        double* __restrict__ v, double* __restrict__ cs, double* __restrict__ sn, EigShared& sh) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  // ---- 1. tridiagonalisation --------------------------------------------------------
+  tridiagonalize_cta(A, n, d, e, beta, v, cs, sn, sh);
   // ---- 2. Q = H_0 H_1 ... H_{n-3}, built as rows ZT = Q^T -----------------------------
   // Work on Q directly in ZT's storage as Q[i][j] = ZT[j][i] would be strided; instead build
   // Q (row-major) and transpose in place at the end of this phase.
@@ -134,6 +143,16 @@ __device__ int eigh_cta(double* __restrict__ A, int n, double* __restrict__ w, d
   }
   __syncthreads();
   // ---- 3. implicit QL ---------------------------------------------------------------
+  // An off-diagonal element is negligible when it is below eps relative to its two
+  // diagonal neighbours, or below eps relative to the whole matrix (needed for clusters of
+  // zero eigenvalues, where the neighbours themselves vanish).
+  if (tid == 0) {
+    double t = 0.0;
+    for (int i = 0; i < n; ++i) t = fmax(t, fabs(d[i]) + fabs(e[i]) + (i > 0 ? fabs(e[i - 1]) : 0.0));
+    sh.scal[3] = t;
+  }
+  __syncthreads();
+  const double tnorm = sh.scal[3];
   int fail = 0;
   for (int l = 0; l < n; ++l) {
     int iter = 0;
@@ -143,7 +162,7 @@ __device__ int eigh_cta(double* __restrict__ A, int n, double* __restrict__ w, d
         int m = l;
         for (; m < n - 1; ++m) {
           double dd = fabs(d[m]) + fabs(d[m + 1]);
-          if (fabs(e[m]) <= DBL_EPSILON * dd) break;
+          if (fabs(e[m]) <= DBL_EPSILON * dd || fabs(e[m]) <= DBL_EPSILON * tnorm) break;
         }
         int lo = l, hi = l - 1;   // rotations cs/sn[i] for i in [lo, hi], applied from hi down to lo
         if (m != l) {
@@ -201,12 +220,17 @@ __device__ int eigh_cta(double* __restrict__ A, int n, double* __restrict__ w, d
         break;
       }
       // apply rotations hi, hi-1, ..., lo to vector rows (i, i+1), element-parallel
+      // (the updated row i is the next rotation's row i+1: carry it in a register)
       for (int col = tid; col < n; col += nt) {
+        if (hi < lo) break;
+        double carry = ZT[(size_t)(hi + 1) * n + col];
         for (int i = hi; i >= lo; --i) {
-          double zi = ZT[(size_t)i * n + col], zi1 = ZT[(size_t)(i + 1) * n + col];
-          ZT[(size_t)(i + 1) * n + col] = sn[i] * zi + cs[i] * zi1;
-          ZT[(size_t)i * n + col] = cs[i] * zi - sn[i] * zi1;
+          double zi = ZT[(size_t)i * n + col];
+          double c = cs[i], s_ = sn[i];
+          ZT[(size_t)(i + 1) * n + col] = s_ * zi + c * carry;
+          carry = c * zi - s_ * carry;
         }
+        ZT[(size_t)lo * n + col] = carry;
       }
       __syncthreads();
     }
@@ -252,6 +276,203 @@ __global__ void __launch_bounds__(1024) eigh_batched_kernel(double* A, int n, lo
   if (threadIdx.x == 0 && status) status[b] = rc;
 }
 
+// ---- k lowest eigenpairs --------------------------------------------------------------------
+// The SCF needs only the occupied orbitals and the LUMO.  After the same Householder
+// reduction, eigenvalues come from Sturm-sequence bisection (one lane per eigenvalue),
+// eigenvectors of the tridiagonal matrix from inverse iteration with a partially pivoted
+// LU of T - lambda I (one lane per vector), then the reflectors are applied to those k
+// vectors only (one warp per vector) and the vectors are re-orthonormalised by classical
+// Gram-Schmidt applied twice.  Cost O(n^3) for the reduction plus O(n^2 k), instead of the
+// O(n^3) vector updates of the full QL sweep.
+
+// Eigenvalues of tridiag(d, e) that are < x (count of negative pivots of T - x I).
+__device__ int sturm_count(const double* __restrict__ d, const double* __restrict__ e, int n, double x,
+                           double pivmin) {
+  int c = 0;
+  double q = d[0] - x;
+  if (fabs(q) < pivmin) q = -pivmin;
+  c += q < 0.0;
+  for (int i = 1; i < n; ++i) {
+    q = d[i] - x - e[i - 1] * e[i - 1] / q;
+    if (fabs(q) < pivmin) q = -pivmin;
+    c += q < 0.0;
+  }
+  return c;
+}
+
+// Lane t: inverse iteration for eigenvalue lam of tridiag(d, e) into x (interleaved
+// storage: element i of lane t at [i * kk + t]).  dl, dd, du, du2, pv: LU workspace.
+__device__ bool inverse_iteration(const double* __restrict__ d, const double* __restrict__ e, int n, double lam,
+                                  double tnorm, int t, int kk, double* __restrict__ dl, double* __restrict__ dd,
+                                  double* __restrict__ du, double* __restrict__ du2, double* __restrict__ pv,
+                                  double* __restrict__ x) {
+#define IX(a, i) a[(size_t)(i) * kk + t]
+  const double small = DBL_EPSILON * tnorm + 1e-300;
+  // LU with partial pivoting of T - lam I (rows i, i+1 interchanged when |sub| > |diag|)
+  for (int i = 0; i < n; ++i) {
+    IX(dd, i) = d[i] - lam;
+    if (i + 1 < n) {
+      IX(dl, i) = e[i];
+      IX(du, i) = e[i];
+    }
+    if (i + 2 < n) IX(du2, i) = 0.0;
+  }
+  for (int i = 0; i + 1 < n; ++i) {
+    double di = IX(dd, i), li = IX(dl, i);
+    if (fabs(di) >= fabs(li)) {
+      IX(pv, i) = 0.0;
+      double f = (di != 0.0) ? li / di : 0.0;
+      IX(dl, i) = f;
+      IX(dd, i + 1) -= f * IX(du, i);
+    } else {
+      IX(pv, i) = 1.0;
+      double f = di / li;
+      IX(dd, i) = li;
+      IX(dl, i) = f;
+      double tmp = IX(du, i);
+      IX(du, i) = IX(dd, i + 1);
+      IX(dd, i + 1) = tmp - f * IX(dd, i + 1);
+      if (i + 2 < n) {
+        IX(du2, i) = IX(du, i + 1);
+        IX(du, i + 1) = -f * IX(du, i + 1);
+      }
+    }
+  }
+  for (int i = 0; i < n; ++i)
+    if (fabs(IX(dd, i)) < small) IX(dd, i) = copysign(small, IX(dd, i) == 0.0 ? 1.0 : IX(dd, i));
+  // deterministic start vector with all components non-zero
+  for (int i = 0; i < n; ++i) IX(x, i) = 1.0 + 0.5 * sin(0.7 * i + 1.3 * t + 0.1);
+  for (int it = 0; it < 4; ++it) {
+    for (int i = 0; i + 1 < n; ++i) {
+      if (IX(pv, i) == 0.0) {
+        IX(x, i + 1) -= IX(dl, i) * IX(x, i);
+      } else {
+        double tmp = IX(x, i);
+        IX(x, i) = IX(x, i + 1);
+        IX(x, i + 1) = tmp - IX(dl, i) * IX(x, i + 1);
+      }
+    }
+    IX(x, n - 1) /= IX(dd, n - 1);
+    if (n >= 2) IX(x, n - 2) = (IX(x, n - 2) - IX(du, n - 2) * IX(x, n - 1)) / IX(dd, n - 2);
+    for (int i = n - 3; i >= 0; --i)
+      IX(x, i) = (IX(x, i) - IX(du, i) * IX(x, i + 1) - IX(du2, i) * IX(x, i + 2)) / IX(dd, i);
+    double mx = 0.0;
+    for (int i = 0; i < n; ++i) mx = fmax(mx, fabs(IX(x, i)));
+    if (!(mx > 0.0) || !isfinite(mx)) return false;
+    double s2 = 0.0;
+    for (int i = 0; i < n; ++i) {
+      double v = IX(x, i) / mx;
+      IX(x, i) = v;
+      s2 += v * v;
+    }
+    double inv = 1.0 / sqrt(s2);
+    for (int i = 0; i < n; ++i) IX(x, i) *= inv;
+  }
+  return true;
+#undef IX
+}
+
+// A [n][n] (destroyed); outputs w [k] ascending and ZT [k][n] (eigenvector rows).
+// Scratch: 4 n + 6 n k doubles.  Returns 0 on success.
+__device__ int eigh_lowest_cta(double* __restrict__ A, int n, int k, double* __restrict__ w, double* __restrict__ ZT,
+                               double* __restrict__ scr, EigShared& sh) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  double* d = scr;
+  double* e = d + n;
+  double* beta = e + n;
+  double* v = beta + n;
+  double* lu = v + n;  // 6 n k
+  tridiagonalize_cta(A, n, d, e, beta, v, lu, lu + n, sh);
+  // reflector k into row k of the (now unused) upper triangle, for coalesced reads
+  for (long q = tid; q < (long)n * n; q += nt) {
+    int i = (int)(q / n), j = (int)(q % n);
+    if (j > i + 0) A[(size_t)i * n + j] = A[(size_t)j * n + i];
+  }
+  if (tid == 0) sh.flag = 0;
+  __syncthreads();
+  // Gershgorin interval and ||T||
+  double glo = INFINITY, ghi = -INFINITY, emax2 = 0.0;
+  for (int i = 0; i < n; ++i) {
+    double r = (i > 0 ? fabs(e[i - 1]) : 0.0) + (i + 1 < n ? fabs(e[i]) : 0.0);
+    glo = fmin(glo, d[i] - r);
+    ghi = fmax(ghi, d[i] + r);
+    if (i + 1 < n) emax2 = fmax(emax2, e[i] * e[i]);
+  }
+  const double tnorm = fmax(fabs(glo), fabs(ghi));
+  const double pivmin = DBL_MIN * fmax(1.0, emax2);
+  double* x = lu + 5 * (size_t)n * k;
+  for (int t = tid; t < k; t += nt) {
+    double lo = glo - 2.0 * DBL_EPSILON * tnorm, hi = ghi + 2.0 * DBL_EPSILON * tnorm;
+    for (int it = 0; it < 200; ++it) {
+      double mid = 0.5 * (lo + hi);
+      if (sturm_count(d, e, n, mid, pivmin) > t) hi = mid;
+      else lo = mid;
+      if (hi - lo <= 2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)) + pivmin) break;
+    }
+    double lam = 0.5 * (lo + hi);
+    w[t] = lam;
+    bool ok = inverse_iteration(d, e, n, lam, tnorm, t, k, lu, lu + (size_t)n * k, lu + 2 * (size_t)n * k,
+                                lu + 3 * (size_t)n * k, lu + 4 * (size_t)n * k, x);
+    if (!ok) atomicExch(&sh.flag, 1);
+  }
+  __syncthreads();
+  if (sh.flag) return 1;
+  // back-transform: z <- H_0 H_1 ... H_{n-3} z, one warp per vector
+  const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+  for (int t = wid; t < k; t += nw) {
+    double* z = ZT + (size_t)t * n;
+    for (int i = lane; i < n; i += 32) z[i] = x[(size_t)i * k + t];
+    __syncwarp();
+    for (int r = n - 3; r >= 0; --r) {
+      double b = beta[r];
+      if (b == 0.0) continue;
+      const double* vr = A + (size_t)r * n + r + 1;
+      double s = 0.0;
+      for (int i = lane; i < n - r - 1; i += 32) s += vr[i] * z[r + 1 + i];
+      s = b * warp_sum(s);
+      for (int i = lane; i < n - r - 1; i += 32) z[r + 1 + i] -= s * vr[i];
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  // classical Gram-Schmidt, twice, row by row; coefficients in lu (k doubles)
+  double* coef = lu;
+  for (int a = 0; a < k; ++a) {
+    double* za = ZT + (size_t)a * n;
+    for (int pass = 0; pass < 2; ++pass) {
+      for (int b = wid; b < a; b += nw) {
+        const double* zb = ZT + (size_t)b * n;
+        double s = 0.0;
+        for (int i = lane; i < n; i += 32) s += zb[i] * za[i];
+        s = warp_sum(s);
+        if (lane == 0) coef[b] = s;
+      }
+      __syncthreads();
+      for (int i = tid; i < n; i += nt) {
+        double s = za[i];
+        for (int b = 0; b < a; ++b) s -= coef[b] * ZT[(size_t)b * n + i];
+        za[i] = s;
+      }
+      __syncthreads();
+    }
+    double s2 = 0.0;
+    for (int i = tid; i < n; i += nt) s2 += za[i] * za[i];
+    s2 = cta_sum(s2, sh);
+    if (!(s2 > 1e-20)) return 2;
+    double inv = 1.0 / sqrt(s2);
+    for (int i = tid; i < n; i += nt) za[i] *= inv;
+    __syncthreads();
+  }
+  return 0;
+}
+
+__global__ void __launch_bounds__(1024) eigh_lowest_kernel(double* A, int n, int k, double* w, double* ZT,
+                                                           double* scratch, int* status) {
+  __shared__ EigShared sh;
+  int rc = eigh_lowest_cta(A, n, k, w, ZT, scratch, sh);
+  if (threadIdx.x == 0 && status) *status = rc;
+}
+
 __global__ void transpose_kernel(const double* __restrict__ in, int rows, int cols, double* __restrict__ out) {
   __shared__ double t[32][33];
   int bx = blockIdx.x * 32, by = blockIdx.y * 32;
@@ -274,6 +495,14 @@ int transpose(const double* in, int rows, int cols, double* out, cudaStream_t s)
 }
 
 size_t eigh_scratch_doubles(int n) { return (size_t)6 * n; }
+
+size_t eigh_lowest_scratch_doubles(int n, int k) { return (size_t)4 * n + (size_t)6 * n * std::max(k, 1); }
+
+int eigh_lowest_rows(double* A, int n, int k, double* w, double* ZT, double* scratch, int* status, cudaStream_t s) {
+  eigh_lowest_kernel<<<1, 1024, 0, s>>>(A, n, k, w, ZT, scratch, status);
+  DF_LAUNCHED("eigh_lowest_kernel");
+  return DF_OK;
+}
 
 int eigh_rows(double* A, int n, double* w, double* ZT, double* scratch, int* status, cudaStream_t s) {
   eigh_batched_kernel<<<1, 1024, 0, s>>>(A, n, 0, w, 0, ZT, 0, scratch, 0, status);
@@ -308,5 +537,32 @@ extern "C" int df_eigh(double* A, int n, double* w, double* Z, void* work, size_
   DF_CUDA(cudaMemcpyAsync(&h, status, sizeof(int), cudaMemcpyDeviceToHost, s));
   DF_CUDA(cudaStreamSynchronize(s));
   DF_REQUIRE(h == 0, DF_ERR_NOCONV, "df_eigh: QL iteration did not converge");
+  return DF_OK;
+}
+
+extern "C" size_t df_eigh_lowest_work_bytes(int n, int k) {
+  if (n <= 0 || k <= 0 || k > n) return 0;
+  Sizer z;
+  z.take<double>(eigh_lowest_scratch_doubles(n, k));
+  z.take<double>((size_t)n * k);
+  z.take<int>(1);
+  return z.used;
+}
+
+extern "C" int df_eigh_lowest(double* A, int n, int k, double* w, double* Z, void* work, size_t work_bytes,
+                              cudaStream_t s) {
+  clear_error();
+  DF_REQUIRE(A && w && Z && n > 0 && k > 0 && k <= n, DF_ERR_ARG, "df_eigh_lowest: bad arguments");
+  DF_REQUIRE(work && work_bytes >= df_eigh_lowest_work_bytes(n, k), DF_ERR_NOMEM, "df_eigh_lowest: workspace too small");
+  Arena a(work, work_bytes);
+  double* scratch = a.take<double>(eigh_lowest_scratch_doubles(n, k));
+  double* ZT = a.take<double>((size_t)n * k);
+  int* status = a.take<int>(1);
+  DF_TRY(eigh_lowest_rows(A, n, k, w, ZT, scratch, status, s));
+  DF_TRY(transpose(ZT, k, n, Z, s));
+  int h = 0;
+  DF_CUDA(cudaMemcpyAsync(&h, status, sizeof(int), cudaMemcpyDeviceToHost, s));
+  DF_CUDA(cudaStreamSynchronize(s));
+  DF_REQUIRE(h == 0, DF_ERR_NOCONV, "df_eigh_lowest: inverse iteration or re-orthogonalisation failed (%d)", h);
   return DF_OK;
 }

@@ -134,14 +134,14 @@ __global__ void __launch_bounds__(512) jpass1_fp32_kernel(const float* __restric
   if (threadIdx.x == 0) d[blockIdx.x] = t;
 }
 
-constexpr int JP2_ROWS = 256;  // P rows per split of pass 2
+constexpr int JP2_MAX_ROWS = 512;  // largest P slice of pass 2 (shared-memory copy of d)
 
 // Jpart[split][ij] = sum_{P in split} d_P B[P][ij]; one lane per two packed columns.
-__global__ void __launch_bounds__(256) jpass2_fp64_kernel(const double* __restrict__ B, long ld, int naux,
+__global__ void __launch_bounds__(256) jpass2_fp64_kernel(const double* __restrict__ B, long ld, int naux, int rows,
                                                           const double* __restrict__ d, double* __restrict__ Jpart) {
-  __shared__ double sd[JP2_ROWS];
-  int p0 = blockIdx.y * JP2_ROWS;
-  int np = min(JP2_ROWS, naux - p0);
+  __shared__ double sd[JP2_MAX_ROWS];
+  int p0 = blockIdx.y * rows;
+  int np = min(rows, naux - p0);
   for (int i = threadIdx.x; i < np; i += blockDim.x) sd[i] = d[p0 + i];
   __syncthreads();
   long c2 = (long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -162,11 +162,11 @@ __global__ void __launch_bounds__(256) jpass2_fp64_kernel(const double* __restri
   reinterpret_cast<double2*>(Jpart + (size_t)blockIdx.y * ld)[c2] = make_double2(ax + bx, ay + by);
 }
 
-__global__ void __launch_bounds__(256) jpass2_fp32_kernel(const float* __restrict__ B, long ld, int naux,
+__global__ void __launch_bounds__(256) jpass2_fp32_kernel(const float* __restrict__ B, long ld, int naux, int rows,
                                                           const double* __restrict__ d, double* __restrict__ Jpart) {
-  __shared__ float sd[JP2_ROWS];
-  int p0 = blockIdx.y * JP2_ROWS;
-  int np = min(JP2_ROWS, naux - p0);
+  __shared__ float sd[JP2_MAX_ROWS];
+  int p0 = blockIdx.y * rows;
+  int np = min(rows, naux - p0);
   for (int i = threadIdx.x; i < np; i += blockDim.x) sd[i] = (float)d[p0 + i];
   __syncthreads();
   long c4 = (long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -280,6 +280,8 @@ int ksplit_count(int nao, long kdim) {
   long tiles = (long)((nao + 63) / 64) * ((nao + 63) / 64 + 1) / 2;
   long want = (4L * 152 * 4 + tiles - 1) / tiles;
   long maxs = max(1L, kdim / 512);
+  int forced = knob("fp64_syrk_split");
+  if (forced > 0) return (int)max(1L, min((long)forced, max(1L, kdim / 16)));
   return (int)max(1L, min(want, min(maxs, 64L)));
 }
 
@@ -288,7 +290,8 @@ int ksplit_count(int nao, long kdim) {
 JKWork jk_work_layout(int nao, int naux, int nocc, int precision, Arena* a, Sizer* z, bool fp64_k) {
   JKWork w{};
   long ld = B_ld(nao);
-  int nsplit_j = (naux + JP2_ROWS - 1) / JP2_ROWS;
+  int rows = max(32, min(JP2_MAX_ROWS, knob("jpass2_rows")));
+  int nsplit_j = (naux + rows - 1) / rows;
   int nsplit_k = ksplit_count(nao, (long)naux * max(nocc, 1));
   w.nsplit_j = nsplit_j;
   w.nsplit_k = nsplit_k;
@@ -311,6 +314,8 @@ int build_J(const void* Bbuf, const BLayout& L, int nao, int naux, int precision
             const JKWork& w, cudaStream_t s) {
   long npair = npair_of(nao), ld = L.ld;
   const char* base = (const char*)Bbuf;
+  const int rows = (naux + w.nsplit_j - 1) / w.nsplit_j;  // P rows per slice of pass 2
+  DF_REQUIRE(rows <= JP2_MAX_ROWS, DF_ERR_ARG, "J: %d auxiliary rows per slice exceed %d", rows, JP2_MAX_ROWS);
   unsigned g = (unsigned)((ld + 255) / 256);
   unsigned gp = (unsigned)((npair + 255) / 256);
   if (precision == DF_FP64) {
@@ -324,7 +329,7 @@ int build_J(const void* Bbuf, const BLayout& L, int nao, int naux, int precision
     {
       ProfScope ps("j_pass2_fp64", s);
       dim3 grid2((unsigned)((ld / 2 + 255) / 256), (unsigned)w.nsplit_j);
-      jpass2_fp64_kernel<<<grid2, 256, 0, s>>>((const double*)(base + L.off64), ld, naux, w.d, w.Jpart);
+      jpass2_fp64_kernel<<<grid2, 256, 0, s>>>((const double*)(base + L.off64), ld, naux, rows, w.d, w.Jpart);
       DF_LAUNCHED("jpass2_fp64_kernel");
     }
   } else {
@@ -338,7 +343,7 @@ int build_J(const void* Bbuf, const BLayout& L, int nao, int naux, int precision
     {
       ProfScope ps("j_pass2_fp32", s);
       dim3 grid2((unsigned)((ld / 4 + 255) / 256), (unsigned)w.nsplit_j);
-      jpass2_fp32_kernel<<<grid2, 256, 0, s>>>((const float*)(base + L.off32), ld, naux, w.d, w.Jpart);
+      jpass2_fp32_kernel<<<grid2, 256, 0, s>>>((const float*)(base + L.off32), ld, naux, rows, w.d, w.Jpart);
       DF_LAUNCHED("jpass2_fp32_kernel");
     }
   }

@@ -450,20 +450,25 @@ extern "C" size_t guess_density_work_bytes(int natm) {
   z.take<float>((size_t)NRBF * natm);
   z.take<float>((size_t)np * NIN);
   z.take<float>((size_t)np);
+  z.take<double>((size_t)NBF * natm * NBF * natm);
+  z.take<double>((size_t)NBF * natm * NBF * natm);
   return z.used + guess_mlp_work_bytes((int)np);
 }
 
-extern "C" int guess_density(const float* params, const double* xyz, int natm, double* D0, void* work,
-                             size_t work_bytes, cudaStream_t s) {
+extern "C" int guess_density(const float* params, const double* xyz, int natm, const double* Sinvhalf, double* D0,
+                             void* work, size_t work_bytes, cudaStream_t s) {
   clear_error();
-  DF_REQUIRE(params && xyz && D0 && natm > 0, DF_ERR_ARG, "guess_density: bad arguments");
+  DF_REQUIRE(params && xyz && D0 && Sinvhalf && natm > 0, DF_ERR_ARG, "guess_density: bad arguments");
   DF_REQUIRE(work && work_bytes >= guess_density_work_bytes(natm), DF_ERR_NOMEM, "guess_density: workspace too small");
   long np = (long)natm * (natm + 1) / 2;
   DF_REQUIRE(np < 65535L * 64, DF_ERR_ARG, "guess_density: too many centres");
+  const int nao = NBF * natm;
   Arena a(work, work_bytes);
   float* env = a.take<float>((size_t)NRBF * natm);
   float* feat = a.take<float>((size_t)np * NIN);
   float* mask = a.take<float>((size_t)np);
+  double* Dt = a.take<double>((size_t)nao * nao);
+  double* T = a.take<double>((size_t)nao * nao);
   size_t rest = work_bytes - a.used;
   void* mw = (char*)work + a.used;
   env_kernel<<<natm, 32, 0, s>>>(xyz, natm, env);
@@ -475,9 +480,11 @@ extern "C" int guess_density(const float* params, const double* xyz, int natm, d
   layout((int)np, &b, nullptr, &w);
   DF_REQUIRE(!b.overflow, DF_ERR_NOMEM, "guess_density: workspace too small");
   DF_TRY(forward_bf16(params, feat, (int)np, w, s));
-  int nao = NBF * natm;
-  DF_CUDA(cudaMemsetAsync(D0, 0, sizeof(double) * nao * nao, s));
-  assemble_density_kernel<<<(unsigned)np, 32, 0, s>>>(w.H[NLAYER - 1], mask, natm, D0);
+  // orthonormal-basis density from the predicted blocks, then D0 = S^-1/2 Dt S^-1/2
+  DF_CUDA(cudaMemsetAsync(Dt, 0, sizeof(double) * nao * nao, s));
+  assemble_density_kernel<<<(unsigned)np, 32, 0, s>>>(w.H[NLAYER - 1], mask, natm, Dt);
   DF_LAUNCHED("assemble_density_kernel");
+  DF_TRY(dgemm(false, false, nao, nao, nao, 1.0, Dt, nao, 0, Sinvhalf, nao, 0, 0.0, T, nao, 0, 1, s, 0, 0));
+  DF_TRY(dgemm(false, false, nao, nao, nao, 1.0, Sinvhalf, nao, 0, T, nao, 0, 0.0, D0, nao, 0, 1, s, 0, 0));
   return DF_OK;
 }

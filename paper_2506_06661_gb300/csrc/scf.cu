@@ -15,8 +15,10 @@
 // Guess for Mean-field Methods"); its exchange matrix is formed from the eigen-
 // decomposition dm0 = sum_k n_k u_k u_k^T as K[C+] - K[C-] in an eager first iteration.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstring>
+#include <thread>
 #include <vector>
 
 #include "common.cuh"
@@ -270,16 +272,18 @@ __global__ void axpy_kernel(double* __restrict__ y, const double* __restrict__ x
   if (i < n) y[i] += a * x[i];
 }
 
-// trDS = sum D S;  idem = ||D S D - 2 D||_F / ||D||_F  (T = D S D given).
-__global__ void guess_check_kernel(const double* __restrict__ D, const double* __restrict__ S,
-                                   const double* __restrict__ T, long nn, ScfStatus* st) {
+// For a density Dx in an orthonormal basis (n x n) and T = Dx Dx:
+// trDS = tr(Dx) (= tr(D S)), idem = ||Dx Dx - 2 Dx||_F / ||Dx||_F (the same in every
+// orthonormal basis).
+__global__ void guess_check_kernel(const double* __restrict__ Dx, const double* __restrict__ T, int n,
+                                   ScfStatus* st) {
   __shared__ double sh[32];
   double tr = 0.0, r2 = 0.0, d2 = 0.0;
-  for (long i = threadIdx.x; i < nn; i += blockDim.x) {
-    tr += D[i] * S[i];
-    double r = T[i] - 2.0 * D[i];
+  for (long i = threadIdx.x; i < (long)n * n; i += blockDim.x) {
+    if (i / n == i % n) tr += Dx[i];
+    double r = T[i] - 2.0 * Dx[i];
     r2 += r * r;
-    d2 += D[i] * D[i];
+    d2 += Dx[i] * Dx[i];
   }
   tr = block_sum(tr, sh);
   r2 = block_sum(r2, sh);
@@ -342,7 +346,7 @@ static void scf_layout(int nao, int naux, int nocc, int precision, Arena* a, Siz
   TAKE(double, w->Ehist, DIIS_MAX * nn);
   TAKE(double, w->G, DIIS_MAX * DIIS_MAX);
   TAKE(double, w->coef, DIIS_MAX);
-  TAKE(double, w->eig_scratch, eigh_scratch_doubles(nao));
+  TAKE(double, w->eig_scratch, std::max(eigh_scratch_doubles(nao), eigh_lowest_scratch_doubles(nao, nocc + 1)));
   TAKE(double, w->enuc, 1);
   TAKE(double, w->maxdiag, 1);
   TAKE(int, w->eig_status, 1);
@@ -363,7 +367,15 @@ static int eig_rows(double* A, int n, double* w, double* ZT, ScfWork& W, cudaStr
 static int diagonalize_fock(const double* Fm, int nao, int nmo, int nocc, ScfWork& W, cudaStream_t s) {
   DF_TRY(dgemm(false, false, nao, nmo, nao, 1.0, Fm, nao, 0, W.X, nmo, 0, 0.0, W.T1, nmo, 0, 1, s, 0, 0));
   DF_TRY(dgemm(true, false, nmo, nmo, nao, 1.0, W.X, nmo, 0, W.T1, nmo, 0, 0.0, W.Fp, nmo, 0, 1, s, 0, 0));
-  DF_TRY(eig_rows(W.Fp, nmo, W.eps, W.ZT, W, s));
+  // only the occupied orbitals and the LUMO are needed: k lowest eigenpairs when k << nmo
+  const int k = std::min(nocc + 1, nmo);
+  {
+    ProfScope ps("scf_eigensolver", s);
+    if (nmo >= 16 && 2 * k <= nmo)
+      DF_TRY(eigh_lowest_rows(W.Fp, nmo, k, W.eps, W.ZT, W.eig_scratch, W.eig_status, s));
+    else
+      DF_TRY(eig_rows(W.Fp, nmo, W.eps, W.ZT, W, s));
+  }
   occ_columns_kernel<<<blocks_for((long)nmo * nocc), 256, 0, s>>>(W.ZT, nmo, nocc, W.T2);
   DF_LAUNCHED("occ_columns_kernel");
   DF_TRY(dgemm(false, false, nao, nocc, nmo, 1.0, W.X, nmo, 0, W.T2, nocc, 0, 0.0, W.Cocc, nocc, 0, 1, s, 0, 0));
@@ -385,6 +397,8 @@ struct ScfMol {
   int fp64_done = 0;
   double e_old = 0.0;
   bool have_old = false;
+  double best_de = INFINITY;  // smallest |dE| of the mixed phase so far
+  int stall = 0;              // mixed iterations since best_de last improved
   bool done = false;
   int rc = DF_OK;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
@@ -393,6 +407,12 @@ struct ScfMol {
   double* D_out = nullptr;
   double* C_out = nullptr;
   double* mo_out = nullptr;
+  // Set-up runs as asynchronous phases so that a batch never blocks on one molecule:
+  // SETUP (integrals, metric, B, eig(S) enqueued) -> ORTHO (host reads eig(S)) ->
+  // GUESS_CHECK (only with dm0) -> READY -> ITER (an iteration is in flight) -> DONE.
+  enum Phase { SETUP, GUESS_CHECK, READY, ITER, DONE } phase = SETUP;
+  double* h_eps = nullptr;  // pinned: eigenvalues of S, then E_nuc (nao + 1 doubles)
+  int* h_ints = nullptr;    // pinned: [0] eigensolver status, [1] Cholesky status
 
   ~ScfMol() {
     for (auto& g : graph)
@@ -400,12 +420,13 @@ struct ScfMol {
   }
 };
 
-// Integrals, metric, B, orthogonalisation and the starting density.  Synchronises s.
-static int scf_setup(ScfMol& M) {
+// Phase SETUP: enqueue integrals, metric Cholesky, B and eig(S), plus asynchronous copies of
+// what the host needs next.  Does not synchronise.
+static int setup_launch(ScfMol& M) {
   const df_molecule* mol = &M.mol;
   cudaStream_t s = M.s;
   ScfWork& W = M.W;
-  const int nao = M.nao, naux = M.naux, nocc = M.nocc;
+  const int nao = M.nao, naux = M.naux;
   const long nn = (long)nao * nao;
   memset(&M.res, 0, sizeof(M.res));
   DF_TRY(umma_prepare());
@@ -419,43 +440,83 @@ static int scf_setup(ScfMol& M) {
                  W.pair_tab, s));
   DF_CUDA(cudaMemcpyAsync(W.T1, W.S, sizeof(double) * nn, cudaMemcpyDeviceToDevice, s));
   DF_TRY(eig_rows(W.T1, nao, W.eps, W.ZT, W, s));
-  std::vector<double> hs(nao);
-  int eig_bad = 0, chol_bad = -1;
-  DF_CUDA(cudaMemcpyAsync(hs.data(), W.eps, sizeof(double) * nao, cudaMemcpyDeviceToHost, s));
-  DF_CUDA(cudaMemcpyAsync(&eig_bad, W.eig_status, sizeof(int), cudaMemcpyDeviceToHost, s));
-  DF_CUDA(cudaMemcpyAsync(&chol_bad, W.chol_status, sizeof(int), cudaMemcpyDeviceToHost, s));
-  DF_CUDA(cudaMemcpyAsync(&M.res.e_nuc, W.enuc, sizeof(double), cudaMemcpyDeviceToHost, s));
-  DF_CUDA(cudaStreamSynchronize(s));
-  DF_REQUIRE(chol_bad < 0, DF_ERR_NOT_SPD, "scf: auxiliary metric not positive definite at pivot %d", chol_bad);
-  DF_REQUIRE(eig_bad == 0, DF_ERR_NOCONV, "scf: eigensolver failed on S");
+  DF_CUDA(cudaMemcpyAsync(M.h_eps, W.eps, sizeof(double) * nao, cudaMemcpyDeviceToHost, s));
+  DF_CUDA(cudaMemcpyAsync(M.h_ints, W.eig_status, sizeof(int), cudaMemcpyDeviceToHost, s));
+  DF_CUDA(cudaMemcpyAsync(M.h_ints + 1, W.chol_status, sizeof(int), cudaMemcpyDeviceToHost, s));
+  DF_CUDA(cudaMemcpyAsync(M.h_eps + nao, W.enuc, sizeof(double), cudaMemcpyDeviceToHost, s));
+  M.phase = ScfMol::SETUP;
+  return DF_OK;
+}
+
+static int finish_guess(ScfMol& M, bool use_dm0) {
+  ScfWork& W = M.W;
+  const long nn = (long)M.nao * M.nao;
+  if (use_dm0) {
+    DF_CUDA(cudaMemcpyAsync(W.D, M.dm0, sizeof(double) * nn, cudaMemcpyDeviceToDevice, M.s));
+  } else {
+    DF_TRY(diagonalize_fock(W.h, M.nao, M.nmo, M.nocc, W, M.s));
+  }
+  diis_reset_kernel<<<1, 32, 0, M.s>>>(W.diis, M.opt.diis_space);
+  DF_LAUNCHED("diis_reset_kernel");
+  M.first_dm0 = use_dm0;
+  M.prec = M.opt.precision;
+  M.switched = (M.prec == DF_FP64);
+  M.phase = ScfMol::READY;
+  return DF_OK;
+}
+
+// After SETUP completed on the stream: canonical orthogonalisation, then either the core
+// guess (-> READY) or the enqueued dm0 checks (-> GUESS_CHECK).
+static int setup_orthogonalize(ScfMol& M) {
+  ScfWork& W = M.W;
+  cudaStream_t s = M.s;
+  const int nao = M.nao, nocc = M.nocc;
+  const long nn = (long)nao * nao;
+  M.res.e_nuc = M.h_eps[nao];
+  DF_REQUIRE(M.h_ints[1] < 0, DF_ERR_NOT_SPD, "scf: auxiliary metric not positive definite at pivot %d", M.h_ints[1]);
+  DF_REQUIRE(M.h_ints[0] == 0, DF_ERR_NOCONV, "scf: eigensolver failed on S");
   int nmo = 0;
-  for (int i = 0; i < nao; ++i) nmo += hs[i] > M.opt.lindep;
+  for (int i = 0; i < nao; ++i) nmo += M.h_eps[i] > M.opt.lindep;
   DF_REQUIRE(nmo >= nocc, DF_ERR_ARG, "scf: only %d orbitals above lindep for %d occupied", nmo, nocc);
   M.nmo = nmo;
   M.res.nmo = nmo;
   canonical_x_kernel<<<blocks_for((long)nao * nmo), 256, 0, s>>>(W.ZT, W.eps, nao, nmo, W.X);
   DF_LAUNCHED("canonical_x_kernel");
-  bool use_dm0 = false;
-  if (M.dm0) {
-    DF_TRY(dgemm(false, false, nao, nao, nao, 1.0, M.dm0, nao, 0, W.S, nao, 0, 0.0, W.T1, nao, 0, 1, s, 0, 0));
-    DF_TRY(dgemm(false, false, nao, nao, nao, 1.0, W.T1, nao, 0, M.dm0, nao, 0, 0.0, W.T2, nao, 0, 1, s, 0, 0));
-    guess_check_kernel<<<1, 1024, 0, s>>>(M.dm0, W.S, W.T2, nn, W.st);
-    DF_LAUNCHED("guess_check_kernel");
-    DF_CUDA(cudaMemcpyAsync(M.hst, W.st, sizeof(ScfStatus), cudaMemcpyDeviceToHost, s));
-    DF_CUDA(cudaStreamSynchronize(s));
-    use_dm0 = std::isfinite(M.hst->trDS) && fabs(M.hst->trDS - mol->nelec) / mol->nelec < 0.05 && M.hst->idem < 0.5;
-    M.res.guess = use_dm0 ? 1 : 2;
+  if (!M.dm0) return finish_guess(M, false);
+  // dm0 in the orthonormal basis X: Dx = X^T S dm0 S X; then the checks on Dx and Dx Dx
+  DF_TRY(dgemm(false, false, nao, nao, nao, 1.0, W.S, nao, 0, M.dm0, nao, 0, 0.0, W.T1, nao, 0, 1, s, 0, 0));
+  DF_TRY(dgemm(false, false, nao, nao, nao, 1.0, W.T1, nao, 0, W.S, nao, 0, 0.0, W.T2, nao, 0, 1, s, 0, 0));
+  DF_TRY(dgemm(false, false, nao, nmo, nao, 1.0, W.T2, nao, 0, W.X, nmo, 0, 0.0, W.T1, nmo, 0, 1, s, 0, 0));
+  DF_TRY(dgemm(true, false, nmo, nmo, nao, 1.0, W.X, nmo, 0, W.T1, nmo, 0, 0.0, W.Fp, nmo, 0, 1, s, 0, 0));
+  DF_TRY(dgemm(false, false, nmo, nmo, nmo, 1.0, W.Fp, nmo, 0, W.Fp, nmo, 0, 0.0, W.T2, nmo, 0, 1, s, 0, 0));
+  guess_check_kernel<<<1, 1024, 0, s>>>(W.Fp, W.T2, nmo, W.st);
+  DF_LAUNCHED("guess_check_kernel");
+  (void)nn;
+  DF_CUDA(cudaMemcpyAsync(M.hst, W.st, sizeof(ScfStatus), cudaMemcpyDeviceToHost, s));
+  M.phase = ScfMol::GUESS_CHECK;
+  return DF_OK;
+}
+
+// After GUESS_CHECK completed: accept dm0 when its electron count is within 5% and its
+// idempotency error in the orthonormal basis, ||Dx Dx - 2 Dx|| / ||Dx||, is below 1; else
+// fall back to the core guess.
+static int setup_guess(ScfMol& M) {
+  const ScfStatus& h = *M.hst;
+  int ne = M.mol.nelec;
+  bool use = std::isfinite(h.trDS) && fabs(h.trDS - ne) / ne < 0.05 && h.idem < 1.0;
+  M.res.guess = use ? 1 : 2;
+  return finish_guess(M, use);
+}
+
+// Whole set-up for one molecule, synchronising between the phases.
+static int scf_setup(ScfMol& M) {
+  DF_TRY(setup_launch(M));
+  DF_CUDA(cudaStreamSynchronize(M.s));
+  DF_TRY(setup_orthogonalize(M));
+  if (M.phase == ScfMol::GUESS_CHECK) {
+    DF_CUDA(cudaStreamSynchronize(M.s));
+    DF_TRY(setup_guess(M));
   }
-  if (use_dm0) {
-    DF_CUDA(cudaMemcpyAsync(W.D, M.dm0, sizeof(double) * nn, cudaMemcpyDeviceToDevice, s));
-  } else {
-    DF_TRY(diagonalize_fock(W.h, nao, nmo, nocc, W, s));
-  }
-  diis_reset_kernel<<<1, 32, 0, s>>>(W.diis, M.opt.diis_space);
-  DF_LAUNCHED("diis_reset_kernel");
-  M.first_dm0 = use_dm0;
-  M.prec = M.opt.precision;
-  M.switched = (M.prec == DF_FP64);
   return DF_OK;
 }
 
@@ -469,8 +530,11 @@ static int jk_general_density(ScfMol& M) {
   DF_CUDA(cudaMemcpyAsync(W.T1, W.D, sizeof(double) * nn, cudaMemcpyDeviceToDevice, s));
   DF_TRY(eig_rows(W.T1, nao, W.eps, W.ZT, W, s));
   std::vector<double> wv(nao);
+  int eig_bad = 0;
   DF_CUDA(cudaMemcpyAsync(wv.data(), W.eps, sizeof(double) * nao, cudaMemcpyDeviceToHost, s));
+  DF_CUDA(cudaMemcpyAsync(&eig_bad, W.eig_status, sizeof(int), cudaMemcpyDeviceToHost, s));
   DF_CUDA(cudaStreamSynchronize(s));
+  DF_REQUIRE(eig_bad == 0, DF_ERR_NOCONV, "scf: eigensolver failed on the starting density");
   double wmax = 0.0;
   for (double x : wv) wmax = fmax(wmax, fabs(x));
   DF_CUDA(cudaMemsetAsync(W.K, 0, sizeof(double) * nn, s));
@@ -500,16 +564,23 @@ static int iteration_tail(ScfMol& M) {
   cudaStream_t s = M.s;
   const int nao = M.nao, nmo = M.nmo, nocc = M.nocc;
   const long nn = (long)nao * nao, ne = (long)nmo * nmo;
-  fock_energy_kernel<<<1, 1024, 0, s>>>(W.h, W.J, W.K, W.D, nn, W.enuc, W.F, W.st);
-  DF_LAUNCHED("fock_energy_kernel");
-  DF_TRY(dgemm(false, false, nao, nao, nao, 1.0, W.F, nao, 0, W.D, nao, 0, 0.0, W.T1, nao, 0, 1, s, 0, 0));
-  DF_TRY(dgemm(false, false, nao, nao, nao, 1.0, W.T1, nao, 0, W.S, nao, 0, 0.0, W.T2, nao, 0, 1, s, 0, 0));
-  antisym_kernel<<<blocks_for(nn), 256, 0, s>>>(W.T2, nao, W.T1);
-  DF_LAUNCHED("antisym_kernel");
-  DF_TRY(dgemm(false, false, nao, nmo, nao, 1.0, W.T1, nao, 0, W.X, nmo, 0, 0.0, W.T2, nmo, 0, 1, s, 0, 0));
-  DF_TRY(dgemm(true, false, nmo, nmo, nao, 1.0, W.X, nmo, 0, W.T2, nmo, 0, 0.0, W.E, nmo, 0, 1, s, 0, 0));
-  absmax_kernel<<<1, 1024, 0, s>>>(W.E, ne, &W.st->emax);
-  DF_LAUNCHED("absmax_kernel");
+  {
+    ProfScope ps("scf_fock_energy", s);
+    fock_energy_kernel<<<1, 1024, 0, s>>>(W.h, W.J, W.K, W.D, nn, W.enuc, W.F, W.st);
+    DF_LAUNCHED("fock_energy_kernel");
+  }
+  {
+    ProfScope ps("scf_diis_error", s);
+    DF_TRY(dgemm(false, false, nao, nao, nao, 1.0, W.F, nao, 0, W.D, nao, 0, 0.0, W.T1, nao, 0, 1, s, 0, 0));
+    DF_TRY(dgemm(false, false, nao, nao, nao, 1.0, W.T1, nao, 0, W.S, nao, 0, 0.0, W.T2, nao, 0, 1, s, 0, 0));
+    antisym_kernel<<<blocks_for(nn), 256, 0, s>>>(W.T2, nao, W.T1);
+    DF_LAUNCHED("antisym_kernel");
+    DF_TRY(dgemm(false, false, nao, nmo, nao, 1.0, W.T1, nao, 0, W.X, nmo, 0, 0.0, W.T2, nmo, 0, 1, s, 0, 0));
+    DF_TRY(dgemm(true, false, nmo, nmo, nao, 1.0, W.X, nmo, 0, W.T2, nmo, 0, 0.0, W.E, nmo, 0, 1, s, 0, 0));
+    absmax_kernel<<<1, 1024, 0, s>>>(W.E, ne, &W.st->emax);
+    DF_LAUNCHED("absmax_kernel");
+  }
+  ProfScope ps_diis("scf_diis_and_diagonalize", s);
   diis_select_kernel<<<1, 32, 0, s>>>(W.diis);
   DF_LAUNCHED("diis_select_kernel");
   diis_store_kernel<<<blocks_for(nn), 256, 0, s>>>(W.diis, W.F, W.E, W.Fhist, W.Ehist, nn, ne);
@@ -599,10 +670,23 @@ static bool scf_iter_finish(ScfMol& M) {
   // orbital energies of the diagonalisation that produced the next density
   M.res.homo = h.homo;
   M.res.lumo = h.lumo;
-  if (!M.switched && M.have_old && (de < M.opt.switch_tol || h.emax < M.opt.switch_err)) {
+  // Mixed phase: switch on the thresholds, or when |dE| has not improved for 3 iterations
+  // (the split-BF16 error floor), or after half the iteration budget.
+  bool stalled = false;
+  if (!M.switched && M.have_old) {
+    if (de < M.best_de) {
+      M.best_de = de;
+      M.stall = 0;
+    } else {
+      M.stall++;
+    }
+    stalled = M.stall >= 3 || M.res.iterations >= M.opt.max_cycle / 2;
+  }
+  if (!M.switched && M.have_old && (de < M.opt.switch_tol || h.emax < M.opt.switch_err || stalled)) {
+    // The DIIS history is kept: the mixed-precision Fock matrices are close to the FP64
+    // ones and keep the extrapolation informed; new FP64 vectors replace them as they age.
     M.switched = true;
     M.prec = DF_FP64;
-    diis_reset_kernel<<<1, 32, 0, M.s>>>(M.W.diis, M.opt.diis_space);
   }
   M.e_old = h.energy;
   M.have_old = true;
@@ -720,8 +804,14 @@ int scf_run_on(const df_molecule* mol, const scf_opts& o, const double* dm0, dou
   ScfMol M;
   DF_TRY(init_mol(M, mol, o, work, work_bytes, s));
   ScfStatus* hst = nullptr;
+  double* heps = nullptr;
+  int* hints = nullptr;
   DF_CUDA(cudaMallocHost(&hst, sizeof(ScfStatus)));
+  DF_CUDA(cudaMallocHost(&heps, sizeof(double) * (mol->nao + 1)));
+  DF_CUDA(cudaMallocHost(&hints, sizeof(int) * 2));
   M.hst = hst;
+  M.h_eps = heps;
+  M.h_ints = hints;
   M.dm0 = dm0;
   M.D_out = D_out;
   M.C_out = C_out;
@@ -742,6 +832,8 @@ int scf_run_on(const df_molecule* mol, const scf_opts& o, const double* dm0, dou
   if (rc == DF_OK && cudaStreamSynchronize(s) != cudaSuccess) rc = DF_ERR_CUDA;
   *res = M.res;
   cudaFreeHost(hst);
+  cudaFreeHost(heps);
+  cudaFreeHost(hints);
   return rc != DF_OK ? rc : M.rc;
 }
 
@@ -780,13 +872,21 @@ extern "C" int scf_run_batch(const df_molecule* mols, int nmol, const scf_opts* 
     DF_CUDA(cudaStreamCreateWithFlags(&streams[k], cudaStreamNonBlocking));
     DF_CUDA(cudaStreamWaitEvent(streams[k], start, 0));
   }
+  int max_nao = 0;
+  for (int i = 0; i < nmol; ++i) max_nao = std::max(max_nao, mols[i].nao);
   ScfStatus* hst = nullptr;
+  double* heps = nullptr;
+  int* hints = nullptr;
   DF_CUDA(cudaMallocHost(&hst, sizeof(ScfStatus) * slots));
+  DF_CUDA(cudaMallocHost(&heps, sizeof(double) * (size_t)(max_nao + 1) * slots));
+  DF_CUDA(cudaMallocHost(&hints, sizeof(int) * 2 * slots));
   std::vector<ScfMol*> slot_mol(slots, nullptr);
   std::vector<int> slot_index(slots, -1);
   int next = 0, finished = 0, rc = DF_OK;
   // Each molecule holds a slot (workspace + stream) until it finishes; a freed slot takes
-  // the next molecule, so molecules of uneven size keep every stream busy.
+  // the next molecule, so molecules of uneven size keep every stream busy.  The host polls
+  // the streams and advances whichever slot's stream has drained: it never blocks on one
+  // molecule while others could run.
   auto start_molecule = [&](int k) -> int {
     int i = next++;
     ScfMol* M = new ScfMol();
@@ -794,54 +894,85 @@ extern "C" int scf_run_batch(const df_molecule* mols, int nmol, const scf_opts* 
     slot_index[k] = i;
     DF_TRY(init_mol(*M, &mols[i], o, (char*)work + per_slot * k, per_slot, streams[k]));
     M->hst = hst + k;
+    M->h_eps = heps + (size_t)(max_nao + 1) * k;
+    M->h_ints = hints + 2 * k;
     M->dm0 = dm0s ? dm0s[i] : nullptr;
     M->D_out = D_outs ? D_outs[i] : nullptr;
-    int r = scf_setup(*M);
+    int r = setup_launch(*M);
     if (r != DF_OK) {
       M->rc = r;
-      M->done = true;
+      M->phase = ScfMol::DONE;
+    }
+    return DF_OK;
+  };
+  // Advance one slot whose stream is idle; returns a fatal status.
+  auto advance = [&](int k) -> int {
+    ScfMol* M = slot_mol[k];
+    int r = DF_OK;
+    switch (M->phase) {
+      case ScfMol::SETUP:
+        r = setup_orthogonalize(*M);
+        break;
+      case ScfMol::GUESS_CHECK:
+        r = setup_guess(*M);
+        break;
+      case ScfMol::READY:
+        r = scf_iter_launch(*M, true);
+        if (r == DF_OK) M->phase = ScfMol::ITER;
+        break;
+      case ScfMol::ITER:
+        if (scf_iter_finish(*M)) {
+          M->phase = ScfMol::DONE;
+        } else {
+          r = scf_iter_launch(*M, true);
+        }
+        break;
+      case ScfMol::DONE:
+        break;
+    }
+    if (r != DF_OK) {
+      // a per-molecule failure (metric, eigensolver, guess) ends that molecule only
+      if (r == DF_ERR_CUDA) return r;
+      M->rc = r;
+      M->phase = ScfMol::DONE;
+    }
+    if (M->phase == ScfMol::DONE) {
+      int i = slot_index[k];
+      if (M->rc == DF_OK || M->rc == DF_ERR_NOCONV) DF_TRY(scf_outputs(*M));
+      results[i] = M->res;
+      delete M;  // the outputs are ordered before the next molecule's work on this stream
+      slot_mol[k] = nullptr;
+      finished++;
+      if (next < nmol) DF_TRY(start_molecule(k));
     }
     return DF_OK;
   };
   for (int k = 0; k < slots && rc == DF_OK; ++k) rc = start_molecule(k);
   while (rc == DF_OK && finished < nmol) {
+    bool progressed = false;
     for (int k = 0; k < slots && rc == DF_OK; ++k) {
-      ScfMol* M = slot_mol[k];
-      if (M && !M->done) rc = scf_iter_launch(*M, true);
-    }
-    if (rc != DF_OK) break;
-    for (int k = 0; k < slots && rc == DF_OK; ++k) {
-      ScfMol* M = slot_mol[k];
-      if (!M) continue;
-      if (!M->done) {
-        cudaError_t e = cudaStreamSynchronize(M->s);
-        if (e != cudaSuccess) {
-          set_error("scf_run_batch: %s", cudaGetErrorString(e));
-          rc = DF_ERR_CUDA;
-          break;
-        }
-        M->done = scf_iter_finish(*M);
+      if (!slot_mol[k]) continue;
+      cudaError_t q = cudaStreamQuery(streams[k]);
+      if (q == cudaErrorNotReady) continue;
+      if (q != cudaSuccess) {
+        set_error("scf_run_batch: %s", cudaGetErrorString(q));
+        rc = DF_ERR_CUDA;
+        break;
       }
-      if (M->done) {
-        int i = slot_index[k];
-        if (M->rc == DF_OK || M->rc == DF_ERR_NOCONV) scf_outputs(*M);
-        cudaStreamSynchronize(M->s);
-        results[i] = M->res;
-        if (M->rc != DF_OK && M->rc != DF_ERR_NOCONV) rc = M->rc;
-        delete M;
-        slot_mol[k] = nullptr;
-        finished++;
-        if (next < nmol && rc == DF_OK) rc = start_molecule(k);
-      }
+      progressed = true;
+      rc = advance(k);
     }
+    if (!progressed && rc == DF_OK) std::this_thread::sleep_for(std::chrono::microseconds(20));
   }
   for (int k = 0; k < slots; ++k) {
-    delete slot_mol[k];
     cudaStreamSynchronize(streams[k]);
+    delete slot_mol[k];
     cudaStreamDestroy(streams[k]);
   }
   cudaEventDestroy(start);
   cudaFreeHost(hst);
+  cudaFreeHost(heps);
+  cudaFreeHost(hints);
   if (rc != DF_OK) return rc;
   for (int i = 0; i < nmol; ++i)
     if (!results[i].converged) {
@@ -867,7 +998,7 @@ static void guess_layout(int nao, int nocc, Arena* a, Sizer* z, ScfWork* w) {
   TAKE(double, w->Fp, nn);
   TAKE(double, w->ZT, nn);
   TAKE(double, w->eps, nao);
-  TAKE(double, w->eig_scratch, eigh_scratch_doubles(nao));
+  TAKE(double, w->eig_scratch, std::max(eigh_scratch_doubles(nao), eigh_lowest_scratch_doubles(nao, nocc + 1)));
   TAKE(int, w->eig_status, 1);
   TAKE(double, w->Cocc, (size_t)nao * std::max(nocc, 1));
   TAKE(double, w->D, nn);

@@ -347,7 +347,8 @@ static int launch_gemm(const CUtensorMap& ahi, const CUtensorMap& alo, const CUt
   p.b_bytes = (uint32_t)p.N * umma::BK * 2;
   p.stage_bytes = 2 * umma::BM * umma::BK * 2 + 2 * p.b_bytes;
   const uint32_t budget = 220 * 1024;
-  p.stages = (int)std::min<uint32_t>(umma::MAX_STAGES, budget / p.stage_bytes);
+  p.stages = (int)std::min<uint32_t>(std::min(umma::MAX_STAGES, std::max(2, knob("umma_max_stages"))),
+                                     budget / p.stage_bytes);
   DF_REQUIRE(p.stages >= 2, DF_ERR_ARG, "split-bf16 GEMM: tile too large for shared memory");
   size_t smem = (size_t)p.stages * p.stage_bytes + 1024;
   DF_REQUIRE(smem <= 220 * 1024 + 1024, DF_ERR_ARG, "split-bf16 GEMM: %zu bytes of shared memory requested", smem);
@@ -390,6 +391,7 @@ static int mixed_nsplit(int npad, int naux, int ncpad) {
   int tiles = (npad / umma::BM) * (npad / umma::BM + 1) / 2;
   // FP32 accumulation length per split <= ~16k terms, and several waves of CTAs
   long want = std::max<long>((kdim + 16383) / 16384, (4L * 152 + tiles - 1) / tiles);
+  if (knob("syrk_split") > 0) want = knob("syrk_split");
   return (int)std::max<long>(1, std::min<long>(want, std::min<long>(nkb, 256)));
 }
 

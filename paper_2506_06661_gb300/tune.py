@@ -1,0 +1,132 @@
+"""Autotuner for the Fock-build launch parameters and the batched-SCF slot count.
+
+The library exposes its launch choices as named knobs (df_tune_set / df_tune_get):
+the tcgen05 GEMM's shared-memory ring depth, the K-dimension splits of the exchange
+SYRK (tensor-core and FP64), and the auxiliary-row slice of J's second pass.  This module
+times df_jk with CUDA events on the caller's stream for candidate values (coordinate
+descent: one knob at a time, keeping the best), and stores the winners in a JSON cache
+keyed by a problem-size bucket, so later runs of the same size class reuse them.
+"""
+from __future__ import annotations
+
+import ctypes
+import json
+import math
+import os
+
+import torch
+
+from . import _check, lib
+
+CACHE = os.environ.get("DFSCF_TUNE_CACHE", os.path.join(os.path.dirname(os.path.abspath(__file__)), "tune_cache.json"))
+
+CANDIDATES = {
+    "fp64": {"fp64_syrk_split": [0, 4, 9, 18, 36], "jpass2_rows": [128, 256, 512]},
+    "mixed": {"umma_max_stages": [2, 3, 4], "syrk_split": [0, 16, 44, 88, 176], "jpass2_rows": [128, 256, 512]},
+}
+
+
+def set_knob(name: str, value: int) -> None:
+    _check(lib().df_tune_set(name.encode(), int(value)))
+
+
+def get_knob(name: str) -> int:
+    return int(lib().df_tune_get(name.encode()))
+
+
+def bucket(nao: int, naux: int, nocc: int, precision: str) -> str:
+    p2 = lambda x: 1 << max(0, math.ceil(math.log2(max(1, x))))  # noqa: E731
+    return f"{precision}:nao{p2(nao)}:naux{p2(naux)}:nocc{p2(nocc)}"
+
+
+def load_cache(path: str = CACHE) -> dict:
+    try:
+        with open(path) as fh:
+            return json.load(fh)
+    except (OSError, ValueError):
+        return {}
+
+
+def save_cache(cache: dict, path: str = CACHE) -> None:
+    tmp = path + ".tmp"
+    with open(tmp, "w") as fh:
+        json.dump(cache, fh, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+
+
+def apply(key: str, cache: dict | None = None) -> dict:
+    """Set the knobs stored for `key`; returns them ({} when the bucket is not cached)."""
+    c = load_cache() if cache is None else cache
+    knobs = c.get(key, {}).get("knobs", {})
+    for k, v in knobs.items():
+        set_knob(k, v)
+    return knobs
+
+
+def _time_jk(dfscf, B, D, C, precision: str, reps: int) -> float:
+    work = dfscf.JKWorkspace(B.nao, B.naux, C.shape[1], precision)
+    J = torch.empty_like(D)
+    K = torch.empty_like(D)
+    dfscf.jk(B, D, C, precision=precision, work=work, out_j=J, out_k=K)
+    s = torch.cuda.current_stream()
+    times = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        dfscf.jk(B, D, C, precision=precision, work=work, out_j=J, out_k=K)
+        e1.record(s)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    del work
+    return sorted(times)[len(times) // 2]
+
+
+def tune_fock(B, D, C, precision: str = "mixed", reps: int = 3, log=None) -> dict:
+    """Coordinate descent over the knobs of `precision`; returns {knobs, ms, baseline_ms}."""
+    import paper_2506_06661_gb300 as dfscf
+    cands = CANDIDATES[precision]
+    best = {k: get_knob(k) for k in cands}
+    for k, v in best.items():
+        set_knob(k, v)
+    base = _time_jk(dfscf, B, D, C, precision, reps)
+    best_ms = base
+    for name, values in cands.items():
+        for v in values:
+            if v == best[name]:
+                continue
+            set_knob(name, v)
+            ms = _time_jk(dfscf, B, D, C, precision, reps)
+            if log:
+                log(f"  {name}={v}: {ms:.3f} ms")
+            if ms < best_ms * 0.995:
+                best_ms, best[name] = ms, v
+            set_knob(name, best[name])
+    return {"knobs": best, "ms": best_ms, "baseline_ms": base}
+
+
+def tune_and_store(B, D, C, nocc: int, precision: str, reps: int = 3, log=None) -> dict:
+    key = bucket(B.nao, B.naux, nocc, precision)
+    res = tune_fock(B, D, C, precision, reps, log)
+    cache = load_cache()
+    cache[key] = res
+    save_cache(cache)
+    return {"key": key, **res}
+
+
+def tune_batch_slots(mols, precision: str = "mixed", candidates=(16, 32, 64), sample: int = 64) -> dict:
+    """Slots (molecules in flight) that give the highest molecules/s on a sample."""
+    import time
+    import paper_2506_06661_gb300 as dfscf
+    devs = [dfscf.MoleculeOnDevice(m) for m in mols[:sample]]
+    out = {}
+    for s in candidates:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        dfscf.scf_run_batch(devs, slots=s, precision=precision, raise_on_noconv=False)
+        torch.cuda.synchronize()
+        out[s] = len(devs) / (time.perf_counter() - t0)
+    best = max(out, key=out.get)
+    cache = load_cache()
+    cache[f"batch:{precision}"] = {"slots": best, "molecules_per_s": out}
+    save_cache(cache)
+    return {"slots": best, "molecules_per_s": out}

@@ -52,3 +52,19 @@ def test_argument_errors_are_host_side():
     assert b"df_jk" in L.df_last_error()
     rc = L.df_boys_f0(None, -1, None, None)
     assert rc == dfscf.DF_ERR_ARG
+
+
+def test_tuning_knobs_host_side():
+    import paper_2506_06661_gb300 as dfscf
+    from paper_2506_06661_gb300 import tune
+    L = dfscf.lib()
+    assert L.df_tune_get(b"jpass2_rows") == 256
+    assert L.df_tune_get(b"nope") == -1
+    assert L.df_tune_set(b"jpass2_rows", 9999) == dfscf.DF_ERR_ARG
+    w0 = L.df_jk_work_bytes(1500, 4500, 150, 0)
+    tune.set_knob("jpass2_rows", 128)
+    try:
+        assert L.df_jk_work_bytes(1500, 4500, 150, 0) > w0   # more J slices, larger partial buffer
+    finally:
+        tune.set_knob("jpass2_rows", 256)
+    assert tune.bucket(1500, 4500, 150, "mixed") == "mixed:nao2048:naux8192:nocc256"

@@ -183,3 +183,49 @@ def test_jk_workspace_too_small(c0_gpu_B, c0):
     rc = L.df_jk(dfscf._ptr(c0_gpu_B.buf), c0.nao, c0.naux, 0, dfscf._ptr(D), None, 0, dfscf._ptr(J), None,
                  dfscf._ptr(tiny), 16, dfscf._stream())
     assert rc == dfscf.DF_ERR_NOMEM
+
+
+@pytest.mark.parametrize("n,k", [(16, 1), (100, 11), (257, 40), (400, 41)])
+def test_eigh_lowest_matches_library(n, k):
+    rng = np.random.default_rng(n + k)
+    A = rng.standard_normal((n, n))
+    A = A + A.T
+    w, Z = dfscf.eigh_lowest(A, k)
+    w, Z = w.cpu().numpy(), Z.cpu().numpy()
+    wr = np.linalg.eigvalsh(A)[:k]
+    scale = max(1.0, np.max(np.abs(np.linalg.eigvalsh(A))))
+    assert np.max(np.abs(w - wr)) <= 1e-12 * scale
+    assert np.max(np.abs(A @ Z - Z * w)) <= 1e-10 * scale
+    assert np.max(np.abs(Z.T @ Z - np.eye(k))) <= 1e-12
+
+
+def test_eigh_lowest_near_degenerate_spectrum():
+    """Pairs of eigenvalues 1e-9 apart: the vectors must still span the right subspace."""
+    n, k = 60, 10
+    rng = np.random.default_rng(3)
+    Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    lam = np.sort(np.concatenate([np.repeat(np.linspace(-3, -1, 5), 2) + np.tile([0, 1e-9], 5),
+                                  np.linspace(0, 5, n - 10)]))
+    A = (Q * lam) @ Q.T
+    A = 0.5 * (A + A.T)
+    w, Z = dfscf.eigh_lowest(A, k)
+    Z = Z.cpu().numpy()
+    assert np.max(np.abs(Z.T @ Z - np.eye(k))) <= 1e-10
+    P = Z @ Z.T
+    Pref = Q[:, :k] @ Q[:, :k].T
+    assert np.max(np.abs(P - Pref)) <= 1e-8
+
+
+@pytest.mark.parametrize("n,rank", [(40, 5), (100, 10), (257, 31)])
+def test_eigh_rank_deficient_density(n, rank):
+    """A density-like matrix 2 C C^T: n - rank zero eigenvalues (a degenerate spectrum)."""
+    rng = np.random.default_rng(n)
+    C = 0.3 * rng.standard_normal((n, rank))
+    A = 2 * C @ C.T
+    w, Z = dfscf.eigh(A)
+    w, Z = w.cpu().numpy(), Z.cpu().numpy()
+    wr = np.linalg.eigvalsh(A)
+    scale = np.max(np.abs(wr))
+    assert np.max(np.abs(w - wr)) <= 1e-12 * scale
+    assert np.max(np.abs(A @ Z - Z * w)) <= 1e-11 * scale
+    assert np.max(np.abs(Z.T @ Z - np.eye(n))) <= 1e-12

@@ -88,9 +88,27 @@ def test_block_round_trip(c0, c0_scf):
         assert np.allclose(D[5 * a:5 * a + 5, 5 * b:5 * b + 5], 0.5 * (blk + blk.T))
 
 
+def test_lowdin_factors_invert_each_other(c0_system):
+    Sh, Sih = mlp.lowdin_factors(c0_system.S)
+    assert np.allclose(Sh @ Sh, c0_system.S, atol=1e-10)
+    assert np.allclose(Sh @ Sih, np.eye(len(Sh)), atol=1e-8)
+
+
 def test_validity_checks(c0_system, c0_scf):
     assert mlp.guess_is_valid(c0_scf.D, c0_system.S, c0_system.nelec)
+    # the orthonormal-basis idempotency of a converged density vanishes
+    Sh, _ = mlp.lowdin_factors(c0_system.S)
+    Dt = Sh @ c0_scf.D @ Sh
+    assert np.linalg.norm(Dt @ Dt - 2 * Dt) <= 1e-9 * np.linalg.norm(Dt)
     assert not mlp.guess_is_valid(1.3 * c0_scf.D, c0_system.S, c0_system.nelec)
-    bad = c0_scf.D + 0.5 * np.random.default_rng(0).standard_normal(c0_scf.D.shape)
-    bad = 0.5 * (bad + bad.T)
+    # right electron count, wrong occupations: 1.5 x the density of half the electrons...
+    Sh, Sih = mlp.lowdin_factors(c0_system.S)
+    Dt = Sh @ c0_scf.D @ Sh
+    w, U = np.linalg.eigh(Dt)
+    occ = np.where(w > 1.0)[0]
+    w2 = w.copy()
+    w2[occ] = 0.0
+    w2[occ[: len(occ) // 2]] = 4.0   # same trace, far from idempotent
+    bad = Sih @ (U * w2) @ U.T @ Sih
+    assert abs(np.sum(bad * c0_system.S) - c0_system.nelec) < 1e-6
     assert not mlp.guess_is_valid(bad, c0_system.S, c0_system.nelec)
