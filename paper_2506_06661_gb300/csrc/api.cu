@@ -127,6 +127,7 @@ static Knob g_knobs[] = {
     {"syrk_split", 0, 0, 4096},      // K-dimension splits of the tcgen05 exchange SYRK
     {"fp64_syrk_split", 0, 0, 4096}, // K-dimension splits of the FP64 exchange SYRK
     {"jpass2_rows", 256, 32, 512},   // auxiliary rows per CTA slice of J's second pass
+    {"eig_ctas", 0, 0, 4096},        // CTAs of the multi-SM eigensolver (0 auto, 1 single CTA)
 };
 
 int knob(const char* name) {

@@ -473,6 +473,224 @@ __global__ void __launch_bounds__(1024) eigh_lowest_kernel(double* A, int n, int
   if (threadIdx.x == 0 && status) *status = rc;
 }
 
+// ---- k lowest eigenpairs on many SMs -------------------------------------------------------
+// Same algorithm as eigh_lowest_cta with the O(n^3) reduction spread over G co-resident CTAs
+// (cooperative launch): in step k every CTA recomputes the Householder vector of column k
+// itself (same data, same reduction order, so the same bits), updates p = beta A22 v for
+// its share of rows (row r belongs to CTA (r - k - 1) mod G), and after a grid barrier
+// applies the rank-2 update to those rows.  Two grid barriers per column.  Barrier waits
+// are bounded; a timeout sets the error flag and every CTA returns.
+struct GridBarrier {
+  unsigned count;
+  unsigned gen;
+  int err;
+};
+
+__device__ bool grid_sync(GridBarrier* b, unsigned nblocks) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* vgen = &b->gen;
+    volatile int* verr = &b->err;
+    unsigned g = *vgen;
+    __threadfence();
+    if (atomicAdd(&b->count, 1u) == nblocks - 1) {
+      b->count = 0;
+      __threadfence();
+      atomicAdd(&b->gen, 1u);
+    } else {
+      for (unsigned it = 0; *vgen == g; ++it) {
+        if (it > (1u << 24) || *verr) {
+          atomicExch(&b->err, 1);
+          break;
+        }
+        __nanosleep(100);
+      }
+    }
+    __threadfence();
+    ok = (*verr == 0);
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+__global__ void __launch_bounds__(256) eigh_lowest_coop_kernel(double* __restrict__ A, int n, int k,
+                                                                double* __restrict__ w, double* __restrict__ ZT,
+                                                                double* __restrict__ scr, double* __restrict__ pbuf,
+                                                                GridBarrier* bar, int* status) {
+  extern __shared__ double smem_d[];
+  __shared__ EigShared sh;
+  const unsigned G = gridDim.x;
+  const int cta = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
+  const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+  double* v = smem_d;       // n
+  double* wv = smem_d + n;  // n
+  double* d = scr;
+  double* e = d + n;
+  double* beta = e + n;
+  double* lu = beta + 2 * n;  // 6 n k (after one spare n)
+  // ---- 1. tridiagonalisation -------------------------------------------------------------
+  for (int kk = 0; kk + 2 < n; ++kk) {
+    const int len = n - kk - 1;
+    double part = 0.0;
+    for (int i = tid + 1; i < len; i += nt) {
+      double x = A[(size_t)(kk + 1 + i) * n + kk];
+      part += x * x;
+    }
+    double sigma = cta_sum(part, sh);
+    double x0 = A[(size_t)(kk + 1) * n + kk];
+    double alpha, b;
+    if (sigma == 0.0) {
+      alpha = x0;
+      b = 0.0;
+    } else {
+      double nrm = sqrt(x0 * x0 + sigma);
+      alpha = (x0 >= 0.0) ? -nrm : nrm;
+      double v0 = x0 - alpha;
+      b = 2.0 / (v0 * v0 + sigma);
+    }
+    for (int i = tid; i < len; i += nt) v[i] = (i == 0) ? (x0 - alpha) : A[(size_t)(kk + 1 + i) * n + kk];
+    if (cta == 0 && tid == 0) {
+      d[kk] = A[(size_t)kk * n + kk];
+      e[kk] = alpha;
+      beta[kk] = b;
+    }
+    __syncthreads();
+    if (b != 0.0) {
+      for (int i = cta + (int)G * wid; i < len; i += (int)G * nw) {
+        const double* row = A + (size_t)(kk + 1 + i) * n + kk + 1;
+        double s = 0.0;
+        for (int j = lane; j < len; j += 32) s += row[j] * v[j];
+        s = warp_sum(s);
+        if (lane == 0) pbuf[i] = b * s;
+      }
+    }
+    if (!grid_sync(bar, G)) break;
+    if (b != 0.0) {
+      double pv = 0.0;
+      for (int i = tid; i < len; i += nt) {
+        double p = pbuf[i];
+        wv[i] = p;
+        pv += p * v[i];
+      }
+      double Kf = 0.5 * b * cta_sum(pv, sh);
+      for (int i = tid; i < len; i += nt) wv[i] -= Kf * v[i];
+      __syncthreads();
+      for (int i = cta + (int)G * wid; i < len; i += (int)G * nw) {
+        double* row = A + (size_t)(kk + 1 + i) * n + kk + 1;
+        const double vi = v[i], wi = wv[i];
+        for (int j = lane; j < len; j += 32) row[j] -= vi * wv[j] + wi * v[j];
+      }
+    }
+    // reflector into column kk, rows owned by this CTA
+    for (int i = cta + (int)G * tid; i < len; i += (int)G * nt) A[(size_t)(kk + 1 + i) * n + kk] = v[i];
+    if (!grid_sync(bar, G)) break;
+  }
+  if (bar->err) {
+    if (cta == 0 && tid == 0) *status = 3;
+    return;
+  }
+  if (cta == 0 && tid == 0) {
+    if (n >= 2) {
+      d[n - 2] = A[(size_t)(n - 2) * n + n - 2];
+      e[n - 2] = A[(size_t)(n - 1) * n + n - 2];
+    }
+    d[n - 1] = A[(size_t)(n - 1) * n + n - 1];
+    e[n - 1] = 0.0;
+  }
+  // reflectors into the upper triangle rows for coalesced reads
+  for (long q = (long)cta * nt + tid; q < (long)n * n; q += (long)G * nt) {
+    int i = (int)(q / n), j = (int)(q % n);
+    if (j > i) A[(size_t)i * n + j] = A[(size_t)j * n + i];
+  }
+  if (!grid_sync(bar, G)) {
+    if (cta == 0 && tid == 0) *status = 3;
+    return;
+  }
+  // ---- 2. bisection and inverse iteration, one lane per eigenvalue ---------------------------
+  double glo = INFINITY, ghi = -INFINITY, emax2 = 0.0;
+  for (int i = 0; i < n; ++i) {
+    double r = (i > 0 ? fabs(e[i - 1]) : 0.0) + (i + 1 < n ? fabs(e[i]) : 0.0);
+    glo = fmin(glo, d[i] - r);
+    ghi = fmax(ghi, d[i] + r);
+    if (i + 1 < n) emax2 = fmax(emax2, e[i] * e[i]);
+  }
+  const double tnorm = fmax(fabs(glo), fabs(ghi));
+  const double pivmin = DBL_MIN * fmax(1.0, emax2);
+  double* x = lu + 5 * (size_t)n * k;
+  for (int t = cta * nt + tid; t < k; t += (int)G * nt) {
+    double lo = glo - 2.0 * DBL_EPSILON * tnorm, hi = ghi + 2.0 * DBL_EPSILON * tnorm;
+    for (int it = 0; it < 200; ++it) {
+      double mid = 0.5 * (lo + hi);
+      if (sturm_count(d, e, n, mid, pivmin) > t) hi = mid;
+      else lo = mid;
+      if (hi - lo <= 2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)) + pivmin) break;
+    }
+    double lam = 0.5 * (lo + hi);
+    w[t] = lam;
+    if (!inverse_iteration(d, e, n, lam, tnorm, t, k, lu, lu + (size_t)n * k, lu + 2 * (size_t)n * k,
+                           lu + 3 * (size_t)n * k, lu + 4 * (size_t)n * k, x))
+      atomicExch(&bar->err, 2);
+  }
+  if (!grid_sync(bar, G)) {
+    if (cta == 0 && tid == 0) *status = 1;
+    return;
+  }
+  // ---- 3. back-transformation, one warp per vector -------------------------------------------
+  for (int t = cta * nw + wid; t < k; t += (int)G * nw) {
+    double* z = ZT + (size_t)t * n;
+    for (int i = lane; i < n; i += 32) z[i] = x[(size_t)i * k + t];
+    __syncwarp();
+    for (int r = n - 3; r >= 0; --r) {
+      double bb = beta[r];
+      if (bb == 0.0) continue;
+      const double* vr = A + (size_t)r * n + r + 1;
+      double s = 0.0;
+      for (int i = lane; i < n - r - 1; i += 32) s += vr[i] * z[r + 1 + i];
+      s = bb * warp_sum(s);
+      for (int i = lane; i < n - r - 1; i += 32) z[r + 1 + i] -= s * vr[i];
+      __syncwarp();
+    }
+  }
+  if (!grid_sync(bar, G)) {
+    if (cta == 0 && tid == 0) *status = 3;
+    return;
+  }
+  if (cta != 0) return;
+  // ---- 4. classical Gram-Schmidt twice (one CTA) -------------------------------------------
+  double* coef = lu;
+  for (int a = 0; a < k; ++a) {
+    double* za = ZT + (size_t)a * n;
+    for (int pass = 0; pass < 2; ++pass) {
+      for (int bI = wid; bI < a; bI += nw) {
+        const double* zb = ZT + (size_t)bI * n;
+        double s = 0.0;
+        for (int i = lane; i < n; i += 32) s += zb[i] * za[i];
+        s = warp_sum(s);
+        if (lane == 0) coef[bI] = s;
+      }
+      __syncthreads();
+      for (int i = tid; i < n; i += nt) {
+        double s = za[i];
+        for (int bI = 0; bI < a; ++bI) s -= coef[bI] * ZT[(size_t)bI * n + i];
+        za[i] = s;
+      }
+      __syncthreads();
+    }
+    double s2 = 0.0;
+    for (int i = tid; i < n; i += nt) s2 += za[i] * za[i];
+    s2 = cta_sum(s2, sh);
+    if (!(s2 > 1e-20)) {
+      if (tid == 0) *status = 2;
+      return;
+    }
+    double inv = 1.0 / sqrt(s2);
+    for (int i = tid; i < n; i += nt) za[i] *= inv;
+    __syncthreads();
+  }
+  if (tid == 0) *status = 0;
+}
+
 __global__ void transpose_kernel(const double* __restrict__ in, int rows, int cols, double* __restrict__ out) {
   __shared__ double t[32][33];
   int bx = blockIdx.x * 32, by = blockIdx.y * 32;
@@ -498,7 +716,47 @@ size_t eigh_scratch_doubles(int n) { return (size_t)6 * n; }
 
 size_t eigh_lowest_scratch_doubles(int n, int k) { return (size_t)4 * n + (size_t)6 * n * std::max(k, 1); }
 
-int eigh_lowest_rows(double* A, int n, int k, double* w, double* ZT, double* scratch, int* status, cudaStream_t s) {
+size_t eigh_coop_aux_bytes(int n) { return align_up(sizeof(double) * (size_t)n, 256) + 256; }
+
+// Number of CTAs for the multi-SM path (0: use one CTA).  Knob "eig_ctas" overrides.
+static int coop_ctas(int n) {
+  int forced = knob("eig_ctas");
+  if (forced == 1) return 0;
+  if (forced == 0 && n < 160) return 0;
+  int dev = 0, sms = 0, per_sm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  size_t smem = 2 * sizeof(double) * (size_t)n;
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(eigh_lowest_coop_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, eigh_lowest_coop_kernel, 256, smem) != cudaSuccess)
+    return 0;
+  int cap = sms * std::max(per_sm, 0);
+  int want = forced > 1 ? forced : std::min(sms, std::max(8, n / 16));
+  return std::min(want, cap);
+}
+
+// aux: coop_aux_bytes(n) of scratch for the multi-SM path (p vector and grid barrier).
+int eigh_lowest_rows(double* A, int n, int k, double* w, double* ZT, double* scratch, int* status, cudaStream_t s,
+                     void* aux) {
+  int G = aux ? coop_ctas(n) : 0;
+  if (G >= 2) {
+    double* pbuf = (double*)aux;
+    GridBarrier* bar = (GridBarrier*)((char*)aux + align_up(sizeof(double) * (size_t)n, 256));
+    DF_CUDA(cudaMemsetAsync(bar, 0, sizeof(GridBarrier), s));
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(G);
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = 2 * sizeof(double) * (size_t)n;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    DF_CUDA(cudaLaunchKernelEx(&cfg, eigh_lowest_coop_kernel, A, n, k, w, ZT, scratch, pbuf, bar, status));
+    return DF_OK;
+  }
   eigh_lowest_kernel<<<1, 1024, 0, s>>>(A, n, k, w, ZT, scratch, status);
   DF_LAUNCHED("eigh_lowest_kernel");
   return DF_OK;
@@ -546,6 +804,7 @@ extern "C" size_t df_eigh_lowest_work_bytes(int n, int k) {
   z.take<double>(eigh_lowest_scratch_doubles(n, k));
   z.take<double>((size_t)n * k);
   z.take<int>(1);
+  z.take<char>(eigh_coop_aux_bytes(n));
   return z.used;
 }
 
@@ -558,7 +817,8 @@ extern "C" int df_eigh_lowest(double* A, int n, int k, double* w, double* Z, voi
   double* scratch = a.take<double>(eigh_lowest_scratch_doubles(n, k));
   double* ZT = a.take<double>((size_t)n * k);
   int* status = a.take<int>(1);
-  DF_TRY(eigh_lowest_rows(A, n, k, w, ZT, scratch, status, s));
+  void* aux = a.take<char>(eigh_coop_aux_bytes(n));
+  DF_TRY(eigh_lowest_rows(A, n, k, w, ZT, scratch, status, s, aux));
   DF_TRY(transpose(ZT, k, n, Z, s));
   int h = 0;
   DF_CUDA(cudaMemcpyAsync(&h, status, sizeof(int), cudaMemcpyDeviceToHost, s));

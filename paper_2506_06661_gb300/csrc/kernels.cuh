@@ -27,7 +27,9 @@ int forward_substitution(double* R, long ld, long ncol, const double* L, int nau
 size_t eigh_scratch_doubles(int n);
 int eigh_rows(double* A, int n, double* w, double* ZT, double* scratch, int* status, cudaStream_t s);
 size_t eigh_lowest_scratch_doubles(int n, int k);
-int eigh_lowest_rows(double* A, int n, int k, double* w, double* ZT, double* scratch, int* status, cudaStream_t s);
+size_t eigh_coop_aux_bytes(int n);
+int eigh_lowest_rows(double* A, int n, int k, double* w, double* ZT, double* scratch, int* status, cudaStream_t s,
+                     void* aux);
 int transpose(const double* in, int rows, int cols, double* out, cudaStream_t s);
 
 // ---- B layout and J/K (jk.cu, umma.cu) --------------------------------------------------

@@ -311,6 +311,7 @@ struct ScfWork {
   double *L, *pair_tab, *S, *h, *V, *X, *F, *Fbar, *J, *K, *D, *Dprev, *Cocc, *Cprev, *Cchunk, *T1, *T2, *E, *Fp,
       *ZT, *eps, *Fhist, *Ehist, *G, *coef, *eig_scratch, *enuc, *maxdiag;
   int *eig_status, *chol_status, *idx;
+  void* eig_aux;  // p vector and grid barrier of the multi-SM eigensolver
   ScfStatus* st;
   DiisState* diis;
   void* B;
@@ -350,6 +351,7 @@ static void scf_layout(int nao, int naux, int nocc, int precision, Arena* a, Siz
   TAKE(double, w->enuc, 1);
   TAKE(double, w->maxdiag, 1);
   TAKE(int, w->eig_status, 1);
+  TAKE(char, w->eig_aux, eigh_coop_aux_bytes(nao));
   TAKE(int, w->chol_status, 1);
   TAKE(int, w->idx, nao);
   TAKE(ScfStatus, w->st, 1);
@@ -372,7 +374,7 @@ static int diagonalize_fock(const double* Fm, int nao, int nmo, int nocc, ScfWor
   {
     ProfScope ps("scf_eigensolver", s);
     if (nmo >= 16 && 2 * k <= nmo)
-      DF_TRY(eigh_lowest_rows(W.Fp, nmo, k, W.eps, W.ZT, W.eig_scratch, W.eig_status, s));
+      DF_TRY(eigh_lowest_rows(W.Fp, nmo, k, W.eps, W.ZT, W.eig_scratch, W.eig_status, s, W.eig_aux));
     else
       DF_TRY(eig_rows(W.Fp, nmo, W.eps, W.ZT, W, s));
   }
@@ -1000,6 +1002,7 @@ static void guess_layout(int nao, int nocc, Arena* a, Sizer* z, ScfWork* w) {
   TAKE(double, w->eps, nao);
   TAKE(double, w->eig_scratch, std::max(eigh_scratch_doubles(nao), eigh_lowest_scratch_doubles(nao, nocc + 1)));
   TAKE(int, w->eig_status, 1);
+  TAKE(char, w->eig_aux, eigh_coop_aux_bytes(nao));
   TAKE(double, w->Cocc, (size_t)nao * std::max(nocc, 1));
   TAKE(double, w->D, nn);
 #undef TAKE
