@@ -29,7 +29,8 @@ METRIC = "DF-JK builds/s + tensor-pipe %; SCF time-to-1e-6 Eh, mixed vs FP64"
 # FP64 ALU peak: 152 SMs x 2 FP64 FMA/clk/SM x 2 flop x 2.07 GHz (1.90 FMA/clk/SM measured)
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 LAUNCHES_FP64 = 7   # kernels per FP64 build: Dw, J pass 1, J pass 2, J reduce, K half-transform, K SYRK, K mirror
-LAUNCHES_MIXED = 8  # Dw, J pass 1, J pass 2, J reduce, C split, tcgen05 half-transform, tcgen05 SYRK, K reduce
+LAUNCHES_MIXED = 9  # Dw, J pass 1, J pass 2, J reduce, C^T planes, tcgen05 half-transform, X planes, tcgen05 SYRK,
+#                     K reduce
 
 
 def load_peaks():
@@ -308,21 +309,29 @@ def run_ours(args):
         errk = float((Km - K6).abs().max() / K6.abs().max())
         npad = dfscf.lib().df_nao_pad(nao)
         ncpad = max(16, (nocc + 15) // 16 * 16)
-        tc_ht = 3 * 2.0 * naux * npad * npad * ncpad     # tensor-core flops issued (3 split products)
-        tc_syrk = 3 * 2.0 * (naux * ncpad) * (128 * 128) * ((npad // 128) * (npad // 128 + 1) // 2)
+        planes = int(dfscf.lib().df_tune_get(b"mixed_planes"))
+        products = planes * (planes + 1) // 2
+        max_n = min(256, (512 // planes) // 16 * 16)         # one TMEM accumulator per product order
+        ntc = -(-ncpad // max_n)
+        nht = (-(-ncpad // ntc) + 15) // 16 * 16
+        # tensor-core flops issued (padded tiles) and the algorithmic count of the same products
+        tc_ht = products * 2.0 * naux * npad * npad * (nht * ntc)
+        tc_syrk = products * 2.0 * (naux * ncpad) * (128 * 128) * ((npad // 128) * (npad // 128 + 1) // 2)
         rlm = {}
-        for name, fl, alg in (("k_halftransform_tc", tc_ht, 3 * ht_flops), ("k_syrk_tc", tc_syrk, 3 * syrk_flops)):
+        for name, fl, alg in (("k_halftransform_tc", tc_ht, products * ht_flops),
+                              ("k_syrk_tc", tc_syrk, products * syrk_flops)):
             r = roofline_of(profm, name, flops_per_launch=alg, peak=peaks["bf16_tflops_sustained"], bound="tensor")
             if r:
                 r["issued_tflops"] = fl / (r["avg_ms"] * 1e-3) / 1e12
+                r["issued_frac"] = r["issued_tflops"] / peaks["bf16_tflops_sustained"]
                 rlm[name] = r
-        jb32 = 4.0 * naux * dfscf.lib().df_B_ld(nao)
-        for name in ("j_pass1_fp32", "j_pass2_fp32"):
-            r = roofline_of(profm, name, bytes_per_launch=jb32, peak=peaks["hbm_gbs"], bound="hbm", unit="GB/s")
+        for name in ("j_pass1_fp64", "j_pass2_fp64"):
+            r = roofline_of(profm, name, bytes_per_launch=j_bytes, peak=peaks["hbm_gbs"], bound="hbm", unit="GB/s")
             if r:
                 rlm[name] = r
         mixed = {"value": ws * 1000.0 / msm, "unit": "builds/s", "ms_per_step": msm, "steps": args.mixed_steps,
-                 "dtype": "bf16x3+f32 (K), f32 (J)", "rel_err_vs_fp64": {"J": errj, "K": errk},
+                 "dtype": f"bf16 planes x{planes}, {products} products, fp32 accumulator per order (K); f64 (J)",
+                 "rel_err_vs_fp64": {"J": errj, "K": errk},
                  "kernels": rlm, "gpu_launches": LAUNCHES_MIXED * args.mixed_steps, "clocks": clkm.summary(),
                  "phase_ms": {k: v[0] / max(v[1], 1) for k, v in profm.items()}}
 

@@ -49,10 +49,21 @@ extern "C" {
 
 /* ---- precision modes -------------------------------------------------------------- */
 #define DF_FP64 0            /* every contraction in FP64                               */
-#define DF_MIXED 1           /* K contractions as split-BF16 x3 on tcgen05 tensor cores
-                                (hi = RN_bf16(x), lo = RN_bf16(x - hi); products
-                                hi*hi + hi*lo + lo*hi, FP32 accumulation), J in FP32
-                                with FP64 reduction                                       */
+#define DF_MIXED 1           /* K contractions as split-BF16 GEMMs on tcgen05 tensor
+                                cores.  Every operand row is held as BF16 planes:
+                                p0 = x rounded to 8 bits on the power-of-two grid just
+                                above the row's max |x| (an integer times a scale fixed
+                                along the contraction), p1 = RN_bf16(x - p0),
+                                p2 = RN_bf16(x - p0 - p1).  Plane products pa*qb with
+                                a + b < planes accumulate in FP32, one accumulator per
+                                order a + b; order 0 sums integers on one grid and is
+                                exact.  planes = 3 (default: six products) or 2 (three
+                                products), set by the knob "mixed_planes" before
+                                workspaces are sized.  J is the FP64 streaming pass in
+                                both modes.  An FP32 J, or products summed in a single
+                                FP32 accumulator, leaves an error in F that the
+                                orthogonal-basis DIIS commutator amplifies to ~1e-3 on
+                                ill-conditioned bases, where the mixed SCF then stalls. */
 
 /* Message describing the last error on the calling thread ("" if none). */
 const char* df_last_error(void);
@@ -99,8 +110,7 @@ int df_metric_chol(const double* aux_xyz, const double* aux_exp, int naux, doubl
  * holding, in this order:
  *   [0]  FP64 packed rows: naux rows of df_B_ld(nao) doubles, entry mn at m(m+1)/2+n,
  *        padding zero;
- *   [1]  (DF_MIXED only) FP32 copy of [0], same row layout;
- *   [2]  (DF_MIXED only) BF16 hi and lo planes of the full symmetric B_P, each
+ *   [1]  (DF_MIXED only) BF16 planes p0, p1, p2 of the full symmetric B_P, each
  *        naux x npad x npad with npad = df_nao_pad(nao), padding zero.
  * L is the factor from df_metric_chol.  work: df_build_B_work_bytes(...) bytes.         */
 long df_B_ld(int nao);
@@ -147,12 +157,15 @@ int df_eigh_lowest(double* A, int n, int k, double* w, double* Z, void* work, si
  *   e = X^T (F D S - S D F) X with canonical orthogonalisation X = U s^-1/2 (s > lindep),
  *   extrapolation over <= diis_space vectors, aufbau occupation of nocc = nelec/2.
  * Converged when |dE| < conv_tol and max|e| < conv_err.  In DF_MIXED mode the loop runs
- * with mixed-precision J/K until |dE| < switch_tol or max|e| < switch_err, then at least
- * n_fp64_final FP64 iterations follow and the reported energy is the FP64 one.
+ * with mixed-precision K until |dE| < switch_tol or max|e| < switch_err, or until max|e|,
+ * once below 1e-2, has not improved by 10% for 5 iterations (the mixed-precision floor), or
+ * for half of max_cycle; then at least n_fp64_final FP64 iterations follow and the
+ * reported energy is the FP64 one.
  * dm0 (device [nao][nao], may be NULL): initial density; it need not be idempotent nor
  * have the right electron count (paper, Section "Initial Guess for Mean-field Methods").
  * If dm0 fails the checks |tr(dm0 S) - nelec| / nelec < 0.05 and
- * ||dm0 S dm0 - 2 dm0||_F / ||dm0||_F < 0.5 the core-Hamiltonian guess is used instead.
+ * ||Dx Dx - 2 Dx||_F / ||Dx||_F < 1 with Dx = X^T S dm0 S X (dm0 in the orthonormal basis
+ * of X) the core-Hamiltonian guess is used instead.
  * Outputs (device, may be NULL): D_out [nao][nao], C_out [nao][nocc], mo_energy [nocc+1].
  * res is HOST memory.  The host loop reads one small status block per iteration.       */
 typedef struct {
@@ -251,10 +264,15 @@ int guess_mlp_train_step(float* params, float* adam_m, float* adam_v, int step, 
 /* The network's targets are the blocks of the Loewdin-orthogonalised density
  * Dt = S^1/2 D S^1/2 (its blocks are well conditioned; those of D are not in a strongly
  * non-orthogonal basis).  guess_density assembles Dt from the predicted blocks (BF16
- * inference) and returns dm0 = S^-1/2 Dt S^-1/2 [5 natm][5 natm].                        */
+ * inference), scales it to tr(Dt) = nelec when nelec > 0 (nelec = 0 keeps the raw
+ * assembly; a non-positive trace is left unscaled), and returns
+ * dm0 = S^-1/2 Dt S^-1/2 [5 natm][5 natm].  Since tr(dm0 S) = tr(Dt) for a full-rank S,
+ * the scaled guess carries the right electron count (the paper's Section "Initial Guess
+ * for Mean-field Methods" allows dm0 with any count; the scaling only removes the
+ * network's systematic overshoot, which the electron-count check would otherwise reject). */
 size_t guess_density_work_bytes(int natm);
-int guess_density(const float* params, const double* xyz, int natm, const double* Sinvhalf, double* D0,
-                  void* work, size_t work_bytes, cudaStream_t s);
+int guess_density(const float* params, const double* xyz, int natm, int nelec, const double* Sinvhalf,
+                  double* D0, void* work, size_t work_bytes, cudaStream_t s);
 /* S^1/2 and S^-1/2 (either may be NULL) of the orbital overlap, over eigenvalues above
  * lindep (pseudo-inverse below).  Synchronises the stream to check the eigensolver.      */
 size_t df_lowdin_work_bytes(int nao);

@@ -157,6 +157,14 @@ def assemble_density(pred: np.ndarray, pairs: np.ndarray, natm: int) -> np.ndarr
     return D
 
 
+def normalise_trace(Dt: np.ndarray, nelec: int) -> np.ndarray:
+    """Orthonormal-basis density scaled to tr(Dt) = nelec; a non-positive trace is left as it
+    is.  The starting density may carry any electron count (Section "Initial Guess for
+    Mean-field Methods"); the scaling removes the network's systematic overshoot."""
+    t = float(np.trace(Dt))
+    return Dt * (nelec / t) if t > 0.0 else Dt.copy()
+
+
 def lowdin_factors(S: np.ndarray, lindep: float = 1e-8):
     """(S^1/2, S^-1/2) from the eigen-decomposition of S, dropping eigenvalues <= lindep."""
     s, U = np.linalg.eigh(S)

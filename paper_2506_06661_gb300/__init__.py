@@ -110,7 +110,7 @@ _SIGS = {
     "guess_mlp_train_step": (_I, [_VP, _VP, _VP, _I, ctypes.c_float, _VP, _VP, _VP, _I, ctypes.c_float, _VP, _VP,
                                   _SZ, _VP]),
     "guess_density_work_bytes": (_SZ, [_I]),
-    "guess_density": (_I, [_VP, _VP, _I, _VP, _VP, _VP, _SZ, _VP]),
+    "guess_density": (_I, [_VP, _VP, _I, _I, _VP, _VP, _VP, _SZ, _VP]),
     "df_lowdin_work_bytes": (_SZ, [_I]),
     "df_lowdin_factors": (_I, [_VP, _VP, _I, _D, _VP, _VP, _VP, _SZ, _VP]),
     "df_congruence_work_bytes": (_SZ, [_I]),

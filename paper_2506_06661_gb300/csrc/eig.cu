@@ -34,6 +34,33 @@ __device__ double cta_sum(double v, EigShared& sh) {
   return t;
 }
 
+__device__ double cta_max(double v, EigShared& sh) {
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int o = 16; o; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  __syncthreads();
+  if (lane == 0) sh.red[wid] = v;
+  __syncthreads();
+  double t = -INFINITY;
+  for (int i = 0; i < nw; ++i) t = fmax(t, sh.red[i]);
+  __syncthreads();
+  return t;
+}
+
+// Gershgorin interval [glo, ghi] of tridiag(d, e) and max e^2, reduced over the CTA.
+__device__ void gershgorin_cta(const double* __restrict__ d, const double* __restrict__ e, int n, double& glo,
+                               double& ghi, double& emax2, EigShared& sh) {
+  double lo = INFINITY, hi = -INFINITY, em = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    double r = (i > 0 ? fabs(e[i - 1]) : 0.0) + (i + 1 < n ? fabs(e[i]) : 0.0);
+    lo = fmin(lo, d[i] - r);
+    hi = fmax(hi, d[i] + r);
+    if (i + 1 < n) em = fmax(em, e[i] * e[i]);
+  }
+  glo = -cta_max(-lo, sh);
+  ghi = cta_max(hi, sh);
+  emax2 = cta_max(em, sh);
+}
+
 // Householder reduction of the symmetric A [n][n] (full storage) to tridiag(d, e): reflector
 // k (k = 0..n-3) is H_k = I - beta[k] v v^T with v stored in column k below the diagonal.
 __device__ void tridiagonalize_cta(double* __restrict__ A, int n, double* __restrict__ d, double* __restrict__ e,
@@ -285,89 +312,116 @@ __global__ void __launch_bounds__(1024) eigh_batched_kernel(double* A, int n, lo
 // Gram-Schmidt applied twice.  Cost O(n^3) for the reduction plus O(n^2 k), instead of the
 // O(n^3) vector updates of the full QL sweep.
 
-// Eigenvalues of tridiag(d, e) that are < x (count of negative pivots of T - x I).
-__device__ int sturm_count(const double* __restrict__ d, const double* __restrict__ e, int n, double x,
+// Eigenvalues of tridiag(d, e) that are < x (count of negative pivots of T - x I);
+// ee[i] = e[i]^2.
+__device__ int sturm_count(const double* __restrict__ d, const double* __restrict__ ee, int n, double x,
                            double pivmin) {
   int c = 0;
   double q = d[0] - x;
   if (fabs(q) < pivmin) q = -pivmin;
   c += q < 0.0;
   for (int i = 1; i < n; ++i) {
-    q = d[i] - x - e[i - 1] * e[i - 1] / q;
+    q = (d[i] - x) - ee[i - 1] / q;
     if (fabs(q) < pivmin) q = -pivmin;
     c += q < 0.0;
   }
   return c;
 }
 
-// Lane t: inverse iteration for eigenvalue lam of tridiag(d, e) into x (interleaved
-// storage: element i of lane t at [i * kk + t]).  dl, dd, du, du2, pv: LU workspace.
+// Deterministic start component in [1, 1.5) from an integer hash of (i, t): every
+// component non-zero, no transcendental FP64 work.
+__device__ __forceinline__ double start_component(int i, int t) {
+  unsigned h = (unsigned)i * 0x9E3779B1u ^ ((unsigned)t + 0x7F4A7C15u) * 0x85EBCA77u;
+  h ^= h >> 15;
+  h *= 0x2C1B3C6Du;
+  h ^= h >> 12;
+  return 1.0 + (double)(h >> 8) * (0.5 / 16777216.0);
+}
+
+// Lane t: inverse iteration for eigenvalue lam of tridiag(d, e) into x (interleaved storage:
+// element i of lane t at [i * kk + t]).  T - lam I = P L U with partial pivoting (rows i and
+// i+1 interchanged when |sub| > |diag|); the factors are stored as L (multipliers), piv,
+// ru0 = 1/U(i,i) (pivots below eps ||T|| raised to it), u1 = U(i,i+1), u2 = U(i,i+2).  The
+// elimination and both triangular sweeps carry their recurrences in registers, so the only
+// dependent chain is the FP64 arithmetic itself.  Each solve's result is divided by its
+// max-norm on the next sweep (no overflow); three solves, then a 2-norm normalisation.
 __device__ bool inverse_iteration(const double* __restrict__ d, const double* __restrict__ e, int n, double lam,
-                                  double tnorm, int t, int kk, double* __restrict__ dl, double* __restrict__ dd,
-                                  double* __restrict__ du, double* __restrict__ du2, double* __restrict__ pv,
+                                  double tnorm, int t, int kk, double* __restrict__ L, double* __restrict__ ru0,
+                                  double* __restrict__ u1, double* __restrict__ u2, double* __restrict__ piv,
                                   double* __restrict__ x) {
 #define IX(a, i) a[(size_t)(i) * kk + t]
   const double small = DBL_EPSILON * tnorm + 1e-300;
-  // LU with partial pivoting of T - lam I (rows i, i+1 interchanged when |sub| > |diag|)
-  for (int i = 0; i < n; ++i) {
-    IX(dd, i) = d[i] - lam;
-    if (i + 1 < n) {
-      IX(dl, i) = e[i];
-      IX(du, i) = e[i];
-    }
-    if (i + 2 < n) IX(du2, i) = 0.0;
-  }
+  double di = d[0] - lam;
+  double ui = n > 1 ? e[0] : 0.0;
   for (int i = 0; i + 1 < n; ++i) {
-    double di = IX(dd, i), li = IX(dl, i);
+    const double li = e[i], dn = d[i + 1] - lam, un = i + 2 < n ? e[i + 1] : 0.0;
+    double piv_d, f;
     if (fabs(di) >= fabs(li)) {
-      IX(pv, i) = 0.0;
-      double f = (di != 0.0) ? li / di : 0.0;
-      IX(dl, i) = f;
-      IX(dd, i + 1) -= f * IX(du, i);
+      f = di != 0.0 ? li / di : 0.0;
+      piv_d = di;
+      IX(piv, i) = 0.0;
+      IX(u1, i) = ui;
+      IX(u2, i) = 0.0;
+      di = dn - f * ui;
+      ui = un;
     } else {
-      IX(pv, i) = 1.0;
-      double f = di / li;
-      IX(dd, i) = li;
-      IX(dl, i) = f;
-      double tmp = IX(du, i);
-      IX(du, i) = IX(dd, i + 1);
-      IX(dd, i + 1) = tmp - f * IX(dd, i + 1);
-      if (i + 2 < n) {
-        IX(du2, i) = IX(du, i + 1);
-        IX(du, i + 1) = -f * IX(du, i + 1);
-      }
+      f = di / li;
+      piv_d = li;
+      IX(piv, i) = 1.0;
+      IX(u1, i) = dn;
+      IX(u2, i) = un;
+      di = ui - f * dn;
+      ui = -f * un;
     }
+    IX(L, i) = f;
+    if (fabs(piv_d) < small) piv_d = copysign(small, piv_d == 0.0 ? 1.0 : piv_d);
+    IX(ru0, i) = 1.0 / piv_d;
   }
-  for (int i = 0; i < n; ++i)
-    if (fabs(IX(dd, i)) < small) IX(dd, i) = copysign(small, IX(dd, i) == 0.0 ? 1.0 : IX(dd, i));
-  // deterministic start vector with all components non-zero
-  for (int i = 0; i < n; ++i) IX(x, i) = 1.0 + 0.5 * sin(0.7 * i + 1.3 * t + 0.1);
-  for (int it = 0; it < 4; ++it) {
+  if (fabs(di) < small) di = copysign(small, di == 0.0 ? 1.0 : di);
+  IX(ru0, n - 1) = 1.0 / di;
+  if (n >= 1) {
+    IX(u1, n - 1) = 0.0;
+    IX(u2, n - 1) = 0.0;
+  }
+  if (n >= 2) IX(u2, n - 2) = 0.0;
+  double scale = 1.0;
+  for (int it = 0; it < 3; ++it) {
+    // forward: apply P and L^-1 to scale * x (the start vector on the first solve)
+    double xi = it == 0 ? start_component(0, t) : scale * IX(x, 0);
     for (int i = 0; i + 1 < n; ++i) {
-      if (IX(pv, i) == 0.0) {
-        IX(x, i + 1) -= IX(dl, i) * IX(x, i);
+      const double xn = it == 0 ? start_component(i + 1, t) : scale * IX(x, i + 1);
+      const double f = IX(L, i);
+      double out, carry;
+      if (IX(piv, i) == 0.0) {
+        out = xi;
+        carry = xn - f * xi;
       } else {
-        double tmp = IX(x, i);
-        IX(x, i) = IX(x, i + 1);
-        IX(x, i + 1) = tmp - IX(dl, i) * IX(x, i + 1);
+        out = xn;
+        carry = xi - f * xn;
       }
+      IX(x, i) = out;
+      xi = carry;
     }
-    IX(x, n - 1) /= IX(dd, n - 1);
-    if (n >= 2) IX(x, n - 2) = (IX(x, n - 2) - IX(du, n - 2) * IX(x, n - 1)) / IX(dd, n - 2);
-    for (int i = n - 3; i >= 0; --i)
-      IX(x, i) = (IX(x, i) - IX(du, i) * IX(x, i + 1) - IX(du2, i) * IX(x, i + 2)) / IX(dd, i);
-    double mx = 0.0;
-    for (int i = 0; i < n; ++i) mx = fmax(mx, fabs(IX(x, i)));
-    if (!(mx > 0.0) || !isfinite(mx)) return false;
-    double s2 = 0.0;
-    for (int i = 0; i < n; ++i) {
-      double v = IX(x, i) / mx;
+    IX(x, n - 1) = xi;
+    // backward: U^-1, tracking the max-norm
+    double x1 = 0.0, x2 = 0.0, mx = 0.0;
+    for (int i = n - 1; i >= 0; --i) {
+      const double v = (IX(x, i) - IX(u1, i) * x1 - IX(u2, i) * x2) * IX(ru0, i);
       IX(x, i) = v;
-      s2 += v * v;
+      mx = fmax(mx, fabs(v));
+      x2 = x1;
+      x1 = v;
     }
-    double inv = 1.0 / sqrt(s2);
-    for (int i = 0; i < n; ++i) IX(x, i) *= inv;
+    if (!(mx > 0.0) || !isfinite(mx)) return false;
+    scale = 1.0 / mx;
   }
+  double s2 = 0.0;
+  for (int i = 0; i < n; ++i) {
+    const double v = IX(x, i) * scale;
+    s2 += v * v;
+  }
+  const double inv = scale / sqrt(s2);
+  for (int i = 0; i < n; ++i) IX(x, i) *= inv;
   return true;
 #undef IX
 }
@@ -391,21 +445,19 @@ __device__ int eigh_lowest_cta(double* __restrict__ A, int n, int k, double* __r
   if (tid == 0) sh.flag = 0;
   __syncthreads();
   // Gershgorin interval and ||T||
-  double glo = INFINITY, ghi = -INFINITY, emax2 = 0.0;
-  for (int i = 0; i < n; ++i) {
-    double r = (i > 0 ? fabs(e[i - 1]) : 0.0) + (i + 1 < n ? fabs(e[i]) : 0.0);
-    glo = fmin(glo, d[i] - r);
-    ghi = fmax(ghi, d[i] + r);
-    if (i + 1 < n) emax2 = fmax(emax2, e[i] * e[i]);
-  }
+  double glo, ghi, emax2;
+  gershgorin_cta(d, e, n, glo, ghi, emax2, sh);
   const double tnorm = fmax(fabs(glo), fabs(ghi));
   const double pivmin = DBL_MIN * fmax(1.0, emax2);
   double* x = lu + 5 * (size_t)n * k;
+  double* ee = v;  // the reduction's work vector is free now
+  for (int i = tid; i + 1 < n; i += nt) ee[i] = e[i] * e[i];
+  __syncthreads();
   for (int t = tid; t < k; t += nt) {
     double lo = glo - 2.0 * DBL_EPSILON * tnorm, hi = ghi + 2.0 * DBL_EPSILON * tnorm;
     for (int it = 0; it < 200; ++it) {
       double mid = 0.5 * (lo + hi);
-      if (sturm_count(d, e, n, mid, pivmin) > t) hi = mid;
+      if (sturm_count(d, ee, n, mid, pivmin) > t) hi = mid;
       else lo = mid;
       if (hi - lo <= 2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)) + pivmin) break;
     }
@@ -474,38 +526,45 @@ __global__ void __launch_bounds__(1024) eigh_lowest_kernel(double* A, int n, int
 }
 
 // ---- k lowest eigenpairs on many SMs -------------------------------------------------------
-// Same algorithm as eigh_lowest_cta with the O(n^3) reduction spread over G co-resident CTAs
-// (cooperative launch): in step k every CTA recomputes the Householder vector of column k
-// itself (same data, same reduction order, so the same bits), updates p = beta A22 v for
-// its share of rows (row r belongs to CTA (r - k - 1) mod G), and after a grid barrier
-// applies the rank-2 update to those rows.  Two grid barriers per column.  Barrier waits
-// are bounded; a timeout sets the error flag and every CTA returns.
+// Same algorithm as eigh_lowest_cta spread over G co-resident CTAs (cooperative launch).
+// FP64 issues at a small fraction of the FP32 rate on this GPU, so every serial FP64 chain
+// is spread over as many SMs as possible:
+//   1. reduction: in step k every CTA recomputes the Householder vector of column k itself
+//      (same data, same reduction order, so the same bits), updates p = beta A22 v for its
+//      share of rows (row r belongs to CTA (r - k - 1) mod G), and after a grid barrier
+//      applies the rank-2 update to those rows (two grid barriers per column);
+//   2. eigenvalues: one warp per eigenvalue, consecutive eigenvalues on different CTAs; each
+//      round evaluates 32 Sturm counts at the interior points of a 33-way split of the
+//      bracket (the interval shrinks 33-fold per round instead of 2-fold);
+//   3. inverse iteration: one lane per eigenvalue, 32 per warp, warps on different CTAs;
+//   4. back-transformation: one warp per vector with the vector staged in shared memory;
+//   5. classical Gram-Schmidt twice, each projection spread over the whole grid.
+// Barrier waits are bounded; a timeout sets the error flag and every CTA returns.
 struct GridBarrier {
-  unsigned count;
-  unsigned gen;
+  unsigned count;  // arrivals since launch (monotone; zeroed before the launch)
+  unsigned pad;
   int err;
 };
 
-__device__ bool grid_sync(GridBarrier* b, unsigned nblocks) {
+// Grid barrier on a monotone arrival counter: the b-th barrier completes when the counter
+// reaches b * G.  Thread 0 of each CTA arrives after a device-scope fence and polls with
+// acquire loads; at most 2^22 polls (seconds), then the error flag is raised.
+__device__ bool grid_sync(GridBarrier* b, unsigned G) {
   __shared__ int ok;
   __syncthreads();
   if (threadIdx.x == 0) {
-    volatile unsigned* vgen = &b->gen;
-    volatile int* verr = &b->err;
-    unsigned g = *vgen;
     __threadfence();
-    if (atomicAdd(&b->count, 1u) == nblocks - 1) {
-      b->count = 0;
-      __threadfence();
-      atomicAdd(&b->gen, 1u);
-    } else {
-      for (unsigned it = 0; *vgen == g; ++it) {
-        if (it > (1u << 24) || *verr) {
-          atomicExch(&b->err, 1);
-          break;
-        }
-        __nanosleep(100);
+    const unsigned old = atomicAdd(&b->count, 1u);
+    const unsigned target = (old / G + 1u) * G;
+    unsigned cur = old + 1u;
+    volatile int* verr = &b->err;
+    for (unsigned it = 0; (int)(cur - target) < 0; ++it) {
+      if (it > (1u << 22)) {
+        atomicCAS(&b->err, 0, 1);
+        break;
       }
+      if ((it & 255u) == 0u && *verr) break;
+      asm volatile("ld.acquire.gpu.u32 %0, [%1];" : "=r"(cur) : "l"(&b->count) : "memory");
     }
     __threadfence();
     ok = (*verr == 0);
@@ -514,10 +573,139 @@ __device__ bool grid_sync(GridBarrier* b, unsigned nblocks) {
   return ok != 0;
 }
 
-__global__ void __launch_bounds__(256) eigh_lowest_coop_kernel(double* __restrict__ A, int n, int k,
+// aux layout (eigh_coop_aux_bytes): p vector [n], Gram-Schmidt coefficients [n], per-CTA
+// partial sums [kCoopMaxCtas], barrier.
+constexpr int kCoopMaxCtas = 1024;
+
+// Phases 2-5 on the tridiagonal form (d, e, beta; reflector r in row r of A, columns
+// r+1..n-1), shared by both reductions.  zsm: zw * n doubles of shared memory.
+__device__ void coop_tail(const double* __restrict__ A, int n, int k, double* __restrict__ w, double* __restrict__ ZT,
+                          double* __restrict__ d, double* __restrict__ e, double* __restrict__ beta,
+                          double* __restrict__ ee, double* __restrict__ lu, double* __restrict__ coef,
+                          double* __restrict__ part, int zw, double* zsm, GridBarrier* bar, int* status,
+                          EigShared& sh) {
+  const unsigned G = gridDim.x;
+  const int cta = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
+  const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+  // ---- 2. eigenvalues: 33-way multisection, one warp per eigenvalue -----------------------
+  double glo, ghi, emax2;
+  gershgorin_cta(d, e, n, glo, ghi, emax2, sh);
+  for (int i = cta * nt + tid; i + 1 < n; i += (int)G * nt) ee[i] = e[i] * e[i];
+  if (!grid_sync(bar, G)) {
+    if (cta == 0 && tid == 0) *status = 3;
+    return;
+  }
+  const double tnorm = fmax(fabs(glo), fabs(ghi));
+  const double pivmin = DBL_MIN * fmax(1.0, emax2);
+  for (int t = wid * (int)G + cta; t < k; t += (int)G * nw) {
+    double lo = glo - 2.0 * DBL_EPSILON * tnorm, hi = ghi + 2.0 * DBL_EPSILON * tnorm;
+    for (int round = 0; round < 64; ++round) {
+      if (hi - lo <= 2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)) + pivmin) break;
+      const double h = (hi - lo) * (1.0 / 33.0);
+      const double xj = fmin(lo + (double)(lane + 1) * h, hi);
+      const unsigned above = __ballot_sync(0xffffffffu, sturm_count(d, ee, n, xj, pivmin) > t);
+      if (above == 0u) {
+        lo = __shfl_sync(0xffffffffu, xj, 31);
+      } else {
+        const int j = __ffs(above) - 1;
+        const double xhi = __shfl_sync(0xffffffffu, xj, j);
+        const double xlo = __shfl_sync(0xffffffffu, xj, j > 0 ? j - 1 : 0);
+        if (j > 0) lo = xlo;
+        hi = xhi;
+      }
+    }
+    if (lane == 0) w[t] = 0.5 * (lo + hi);
+  }
+  if (!grid_sync(bar, G)) {
+    if (cta == 0 && tid == 0) *status = 3;
+    return;
+  }
+  // ---- 3. inverse iteration, one lane per eigenvalue, warps on different CTAs ---------------
+  double* x = lu + 5 * (size_t)n * k;
+  for (int t = (wid * (int)G + cta) * 32 + lane; t - lane < k; t += (int)G * nw * 32) {
+    if (t < k &&
+        !inverse_iteration(d, e, n, w[t], tnorm, t, k, lu, lu + (size_t)n * k, lu + 2 * (size_t)n * k,
+                           lu + 3 * (size_t)n * k, lu + 4 * (size_t)n * k, x))
+      atomicExch(&bar->err, 2);
+  }
+  if (!grid_sync(bar, G)) {
+    if (cta == 0 && tid == 0) *status = bar->err == 2 ? 1 : 3;
+    return;
+  }
+  // ---- 4. back-transformation, one warp per vector staged in shared memory ------------------
+  if (wid < zw) {
+    double* zs = zsm + (size_t)wid * n;
+    for (int t = wid * (int)G + cta; t < k; t += (int)G * zw) {
+      for (int i = lane; i < n; i += 32) zs[i] = x[(size_t)i * k + t];
+      __syncwarp();
+      for (int r = n - 3; r >= 0; --r) {
+        const double bb = beta[r];
+        if (bb == 0.0) continue;
+        const double* vr = A + (size_t)r * n + r + 1;
+        double* zr = zs + r + 1;
+        const int len = n - r - 1;
+        double s = 0.0;
+        for (int i = lane; i < len; i += 32) s += vr[i] * zr[i];
+        s = bb * warp_sum(s);
+        for (int i = lane; i < len; i += 32) zr[i] -= s * vr[i];
+        __syncwarp();
+      }
+      double* z = ZT + (size_t)t * n;
+      for (int i = lane; i < n; i += 32) z[i] = zs[i];
+      __syncwarp();
+    }
+  }
+  if (!grid_sync(bar, G)) {
+    if (cta == 0 && tid == 0) *status = 3;
+    return;
+  }
+  // ---- 5. classical Gram-Schmidt twice over the grid ----------------------------------------
+  const int gw = wid * (int)G + cta, ngw = (int)G * nw;
+  const int gt = cta * nt + tid, ngt = (int)G * nt;
+  for (int a = 0; a < k; ++a) {
+    double* za = ZT + (size_t)a * n;
+    for (int pass = 0; a > 0 && pass < 2; ++pass) {
+      for (int b = gw; b < a; b += ngw) {
+        const double* zb = ZT + (size_t)b * n;
+        double s = 0.0;
+        for (int i = lane; i < n; i += 32) s += zb[i] * za[i];
+        s = warp_sum(s);
+        if (lane == 0) coef[b] = s;
+      }
+      if (!grid_sync(bar, G)) break;
+      for (int i = gt; i < n; i += ngt) {
+        double s = za[i];
+        for (int b = 0; b < a; ++b) s -= coef[b] * ZT[(size_t)b * n + i];
+        za[i] = s;
+      }
+      if (!grid_sync(bar, G)) break;
+    }
+    if (bar->err) break;
+    double s2 = 0.0;
+    for (int i = gt; i < n; i += ngt) s2 += za[i] * za[i];
+    s2 = cta_sum(s2, sh);
+    if (tid == 0) part[cta] = s2;
+    if (!grid_sync(bar, G)) break;
+    double tot = 0.0;
+    for (unsigned c = 0; c < G; ++c) tot += part[c];  // same order in every CTA
+    if (!(tot > 1e-20)) {
+      if (cta == 0 && tid == 0) *status = 2;
+      return;
+    }
+    const double inv = 1.0 / sqrt(tot);
+    for (int i = gt; i < n; i += ngt) za[i] *= inv;
+    if (!grid_sync(bar, G)) break;
+  }
+  if (cta == 0 && tid == 0) *status = bar->err ? 3 : 0;
+}
+
+// Reduction with the trailing matrix in global memory (any n).  Dynamic shared memory:
+// v, w [n] for the reduction, then zw vectors [n] for the back-transformation.
+__global__ void __launch_bounds__(256, 1) eigh_lowest_coop_kernel(double* __restrict__ A, int n, int k,
                                                                 double* __restrict__ w, double* __restrict__ ZT,
                                                                 double* __restrict__ scr, double* __restrict__ pbuf,
-                                                                GridBarrier* bar, int* status) {
+                                                                double* __restrict__ coef, double* __restrict__ part,
+                                                                int zw, GridBarrier* bar, int* status) {
   extern __shared__ double smem_d[];
   __shared__ EigShared sh;
   const unsigned G = gridDim.x;
@@ -528,7 +716,8 @@ __global__ void __launch_bounds__(256) eigh_lowest_coop_kernel(double* __restric
   double* d = scr;
   double* e = d + n;
   double* beta = e + n;
-  double* lu = beta + 2 * n;  // 6 n k (after one spare n)
+  double* ee = beta + n;
+  double* lu = beta + 2 * n;  // 6 n k
   // ---- 1. tridiagonalisation -------------------------------------------------------------
   for (int kk = 0; kk + 2 < n; ++kk) {
     const int len = n - kk - 1;
@@ -607,88 +796,144 @@ __global__ void __launch_bounds__(256) eigh_lowest_coop_kernel(double* __restric
     if (cta == 0 && tid == 0) *status = 3;
     return;
   }
-  // ---- 2. bisection and inverse iteration, one lane per eigenvalue ---------------------------
-  double glo = INFINITY, ghi = -INFINITY, emax2 = 0.0;
-  for (int i = 0; i < n; ++i) {
-    double r = (i > 0 ? fabs(e[i - 1]) : 0.0) + (i + 1 < n ? fabs(e[i]) : 0.0);
-    glo = fmin(glo, d[i] - r);
-    ghi = fmax(ghi, d[i] + r);
-    if (i + 1 < n) emax2 = fmax(emax2, e[i] * e[i]);
+  coop_tail(A, n, k, w, ZT, d, e, beta, ee, lu, coef, part, zw, smem_d + 2 * (size_t)n, bar, status, sh);
+}
+
+// Reduction with the rows of the trailing matrix in shared memory: row r lives in CTA
+// r mod G at slot r / G (R = ceil(n / G) slots of n doubles).  Every CTA keeps the current
+// column x = A[kk+1.., kk] and recomputes the reflector (v, beta) from it; the owners of the
+// rows compute p = beta A22 v and publish p together with the old column kk+1; after the one
+// grid barrier of the step every CTA forms w = p - (beta p.v / 2) v, updates its rows and
+// derives the next column from the old one with the same rank-2 formula, so all CTAs hold
+// the same bits.  Exchange buffers are double-buffered by step parity.  The reflector goes to
+// row kk of A (global) for the back-transformation.  Dynamic shared memory: 4 n + max(R, zw) n
+// doubles (the back-transformation's vectors reuse the row slots).
+__device__ __forceinline__ double rank2(double vi, double wj, double wi, double vj) {
+  return __fma_rn(vi, wj, __dmul_rn(wi, vj));
+}
+
+__global__ void __launch_bounds__(256, 1) eigh_lowest_coop_smem_kernel(double* __restrict__ A, int n, int k,
+                                                                     double* __restrict__ w, double* __restrict__ ZT,
+                                                                     double* __restrict__ scr,
+                                                                     double* __restrict__ xbuf, int R,
+                                                                     double* __restrict__ coef,
+                                                                     double* __restrict__ part, int zw,
+                                                                     GridBarrier* bar, int* status) {
+  extern __shared__ double smem_d[];
+  __shared__ EigShared sh;
+  const unsigned G = gridDim.x;
+  const int cta = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
+  const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+  double* v = smem_d;            // n: reflector
+  double* wv = smem_d + n;       // n: p, then w
+  double* x = smem_d + 2 * n;    // n: current column below the diagonal
+  double* c = smem_d + 3 * n;    // n: old next column
+  double* rows = smem_d + 4 * n; // R n
+  double* d = scr;
+  double* e = d + n;
+  double* beta = e + n;
+  double* ee = beta + n;
+  double* lu = beta + 2 * n;  // 6 n k
+  // owned rows into shared memory; column 0 below the diagonal into x
+  for (int s = 0; s < R; ++s) {
+    const int r = s * (int)G + cta;
+    if (r >= n) break;
+    for (int j = tid; j < n; j += nt) rows[(size_t)s * n + j] = A[(size_t)r * n + j];
   }
-  const double tnorm = fmax(fabs(glo), fabs(ghi));
-  const double pivmin = DBL_MIN * fmax(1.0, emax2);
-  double* x = lu + 5 * (size_t)n * k;
-  for (int t = cta * nt + tid; t < k; t += (int)G * nt) {
-    double lo = glo - 2.0 * DBL_EPSILON * tnorm, hi = ghi + 2.0 * DBL_EPSILON * tnorm;
-    for (int it = 0; it < 200; ++it) {
-      double mid = 0.5 * (lo + hi);
-      if (sturm_count(d, e, n, mid, pivmin) > t) hi = mid;
-      else lo = mid;
-      if (hi - lo <= 2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)) + pivmin) break;
-    }
-    double lam = 0.5 * (lo + hi);
-    w[t] = lam;
-    if (!inverse_iteration(d, e, n, lam, tnorm, t, k, lu, lu + (size_t)n * k, lu + 2 * (size_t)n * k,
-                           lu + 3 * (size_t)n * k, lu + 4 * (size_t)n * k, x))
-      atomicExch(&bar->err, 2);
-  }
-  if (!grid_sync(bar, G)) {
-    if (cta == 0 && tid == 0) *status = 1;
-    return;
-  }
-  // ---- 3. back-transformation, one warp per vector -------------------------------------------
-  for (int t = cta * nw + wid; t < k; t += (int)G * nw) {
-    double* z = ZT + (size_t)t * n;
-    for (int i = lane; i < n; i += 32) z[i] = x[(size_t)i * k + t];
-    __syncwarp();
-    for (int r = n - 3; r >= 0; --r) {
-      double bb = beta[r];
-      if (bb == 0.0) continue;
-      const double* vr = A + (size_t)r * n + r + 1;
-      double s = 0.0;
-      for (int i = lane; i < n - r - 1; i += 32) s += vr[i] * z[r + 1 + i];
-      s = bb * warp_sum(s);
-      for (int i = lane; i < n - r - 1; i += 32) z[r + 1 + i] -= s * vr[i];
-      __syncwarp();
-    }
-  }
+  for (int i = tid; i + 1 < n; i += nt) x[i] = A[(size_t)(i + 1) * n];
+  // all CTAs have read A before any reflector is written back into it
   if (!grid_sync(bar, G)) {
     if (cta == 0 && tid == 0) *status = 3;
     return;
   }
-  if (cta != 0) return;
-  // ---- 4. classical Gram-Schmidt twice (one CTA) -------------------------------------------
-  double* coef = lu;
-  for (int a = 0; a < k; ++a) {
-    double* za = ZT + (size_t)a * n;
-    for (int pass = 0; pass < 2; ++pass) {
-      for (int bI = wid; bI < a; bI += nw) {
-        const double* zb = ZT + (size_t)bI * n;
-        double s = 0.0;
-        for (int i = lane; i < n; i += 32) s += zb[i] * za[i];
-        s = warp_sum(s);
-        if (lane == 0) coef[bI] = s;
-      }
-      __syncthreads();
-      for (int i = tid; i < n; i += nt) {
-        double s = za[i];
-        for (int bI = 0; bI < a; ++bI) s -= coef[bI] * ZT[(size_t)bI * n + i];
-        za[i] = s;
-      }
-      __syncthreads();
+  // ---- 1. tridiagonalisation -------------------------------------------------------------
+  for (int kk = 0; kk + 2 < n; ++kk) {
+    const int len = n - kk - 1;  // x = A[kk+1..n)[kk]
+    double part_s = 0.0;
+    for (int i = tid + 1; i < len; i += nt) part_s += x[i] * x[i];
+    const double sigma = cta_sum(part_s, sh);
+    const double x0 = x[0];
+    double alpha, b;
+    if (sigma == 0.0) {
+      alpha = x0;
+      b = 0.0;
+    } else {
+      const double nrm = sqrt(x0 * x0 + sigma);
+      alpha = (x0 >= 0.0) ? -nrm : nrm;
+      const double v0 = x0 - alpha;
+      b = 2.0 / (v0 * v0 + sigma);
     }
-    double s2 = 0.0;
-    for (int i = tid; i < n; i += nt) s2 += za[i] * za[i];
-    s2 = cta_sum(s2, sh);
-    if (!(s2 > 1e-20)) {
-      if (tid == 0) *status = 2;
-      return;
+    for (int i = tid; i < len; i += nt) v[i] = (i == 0) ? (x0 - alpha) : x[i];
+    if (cta == 0 && tid == 0) {
+      e[kk] = alpha;
+      beta[kk] = b;
     }
-    double inv = 1.0 / sqrt(s2);
-    for (int i = tid; i < n; i += nt) za[i] *= inv;
+    if (kk % (int)G == cta && tid == 0) d[kk] = rows[(size_t)(kk / (int)G) * n + kk];
+    __syncthreads();
+    // p for the owned rows of the trailing block, and their entries in column kk+1
+    double* pg = xbuf + (size_t)(kk & 1) * 2 * n;
+    double* cg = pg + n;
+    {
+      const int s0 = (kk + 1 - cta + (int)G - 1) / (int)G;  // first slot with row > kk
+      for (int s = s0 + wid; s < R; s += nw) {
+        const int r = s * (int)G + cta;
+        if (r >= n) break;
+        const double* row = rows + (size_t)s * n + kk + 1;
+        double acc = 0.0;
+        if (b != 0.0)
+          for (int j = lane; j < len; j += 32) acc += row[j] * v[j];
+        acc = warp_sum(acc);
+        if (lane == 0) {
+          pg[r - kk - 1] = b * acc;
+          cg[r - kk - 1] = row[0];
+        }
+      }
+    }
+    // the reflector, for the back-transformation
+    if (kk % (int)G == cta)
+      for (int i = tid; i < len; i += nt) A[(size_t)kk * n + kk + 1 + i] = v[i];
+    if (!grid_sync(bar, G)) break;
+    double pv = 0.0;
+    for (int i = tid; i < len; i += nt) {
+      const double pi = pg[i];
+      wv[i] = pi;
+      c[i] = cg[i];
+      pv += pi * v[i];
+    }
+    const double Kf = 0.5 * b * cta_sum(pv, sh);
+    for (int i = tid; i < len; i += nt) wv[i] -= Kf * v[i];
+    __syncthreads();
+    // next column x' = A'[kk+2.., kk+1] from the old column and the same rank-2 formula
+    const double v0 = v[0], w0 = wv[0];
+    for (int i = tid; i + 1 < len; i += nt) x[i] = c[i + 1] - rank2(v[i + 1], w0, wv[i + 1], v0);
+    if (b != 0.0) {
+      const int s0 = (kk + 1 - cta + (int)G - 1) / (int)G;
+      for (int s = s0 + wid; s < R; s += nw) {
+        const int r = s * (int)G + cta;
+        if (r >= n) break;
+        const int i = r - kk - 1;
+        double* row = rows + (size_t)s * n + kk + 1;
+        const double vi = v[i], wi = wv[i];
+        for (int j = lane; j < len; j += 32) row[j] -= rank2(vi, wv[j], wi, v[j]);
+      }
+    }
     __syncthreads();
   }
-  if (tid == 0) *status = 0;
+  if (bar->err) {
+    if (cta == 0 && tid == 0) *status = 3;
+    return;
+  }
+  if (n >= 2) {
+    if ((n - 2) % (int)G == cta && tid == 0) d[n - 2] = rows[(size_t)((n - 2) / (int)G) * n + n - 2];
+    if (cta == 0 && tid == 0) e[n - 2] = x[0];
+  }
+  if ((n - 1) % (int)G == cta && tid == 0) d[n - 1] = rows[(size_t)((n - 1) / (int)G) * n + n - 1];
+  if (cta == 0 && tid == 0) e[n - 1] = 0.0;
+  if (!grid_sync(bar, G)) {
+    if (cta == 0 && tid == 0) *status = 3;
+    return;
+  }
+  coop_tail(A, n, k, w, ZT, d, e, beta, ee, lu, coef, part, zw, rows, bar, status, sh);
 }
 
 __global__ void transpose_kernel(const double* __restrict__ in, int rows, int cols, double* __restrict__ out) {
@@ -716,45 +961,105 @@ size_t eigh_scratch_doubles(int n) { return (size_t)6 * n; }
 
 size_t eigh_lowest_scratch_doubles(int n, int k) { return (size_t)4 * n + (size_t)6 * n * std::max(k, 1); }
 
-size_t eigh_coop_aux_bytes(int n) { return align_up(sizeof(double) * (size_t)n, 256) + 256; }
-
-// Number of CTAs for the multi-SM path (0: use one CTA).  Knob "eig_ctas" overrides.
-static int coop_ctas(int n) {
-  int forced = knob("eig_ctas");
-  if (forced == 1) return 0;
-  if (forced == 0 && n < 160) return 0;
-  int dev = 0, sms = 0, per_sm = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  size_t smem = 2 * sizeof(double) * (size_t)n;
-  if (smem > 48 * 1024)
-    cudaFuncSetAttribute(eigh_lowest_coop_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, eigh_lowest_coop_kernel, 256, smem) != cudaSuccess)
-    return 0;
-  int cap = sms * std::max(per_sm, 0);
-  int want = forced > 1 ? forced : std::min(sms, std::max(8, n / 16));
-  return std::min(want, cap);
+size_t eigh_coop_aux_bytes(int n) {
+  return align_up(4 * sizeof(double) * (size_t)n, 256) + align_up(sizeof(double) * (size_t)n, 256) +
+         align_up(sizeof(double) * kCoopMaxCtas, 256) + 256;
 }
 
-// aux: coop_aux_bytes(n) of scratch for the multi-SM path (p vector and grid barrier).
+namespace {
+constexpr size_t kSmemMax = 227 * 1024;
+
+// Warps per CTA that hold a vector in the back-transformation.
+int coop_zw(int k, int G) { return std::min(8, std::max(1, (k + G - 1) / G)); }
+
+struct CoopPlan {
+  int G = 0;         // CTAs (0: one-CTA kernel)
+  bool rows = false; // trailing rows in shared memory
+  int R = 0;         // row slots per CTA
+  int zw = 0;
+  size_t smem = 0;
+};
+
+size_t plan_smem(int n, int k, int G, bool rows) {
+  const int zw = coop_zw(k, G);
+  if (rows) return sizeof(double) * (size_t)n * (4 + std::max((n + G - 1) / G, zw));
+  return sizeof(double) * (size_t)n * (2 + zw);
+}
+
+bool fits(const void* kern, size_t smem, int G, int sms) {
+  if (smem > kSmemMax) return false;
+  if (smem > 48 * 1024 && cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+                              cudaSuccess)
+    return false;
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem) != cudaSuccess) return false;
+  return G <= sms * per_sm;
+}
+
+// Multi-SM plan (G = 0: use one CTA).  Knob "eig_ctas" overrides the CTA count; the default
+// takes up to one CTA per SM once n is large enough for the reduction to gain from it, and
+// keeps the trailing rows in shared memory whenever they fit.
+CoopPlan coop_plan(int n, int k) {
+  CoopPlan P;
+  int forced = knob("eig_ctas");
+  if (forced == 1) return P;
+  if (forced == 0 && n < 160) return P;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return P;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  int G = forced > 1 ? forced : std::min(sms, std::max(32, n / 8));
+  G = std::min(G, kCoopMaxCtas);
+  if (G < 2) return P;
+  size_t sm_rows = plan_smem(n, k, G, true);
+  if (fits((const void*)eigh_lowest_coop_smem_kernel, sm_rows, G, sms)) {
+    P.G = G;
+    P.rows = true;
+    P.R = (n + G - 1) / G;
+    P.zw = coop_zw(k, G);
+    P.smem = sm_rows;
+    return P;
+  }
+  size_t sm_glob = plan_smem(n, k, G, false);
+  if (fits((const void*)eigh_lowest_coop_kernel, sm_glob, G, sms)) {
+    P.G = G;
+    P.zw = coop_zw(k, G);
+    P.smem = sm_glob;
+  }
+  return P;
+}
+}  // namespace
+
+// aux: coop_aux_bytes(n) of scratch for the multi-SM path.
 int eigh_lowest_rows(double* A, int n, int k, double* w, double* ZT, double* scratch, int* status, cudaStream_t s,
                      void* aux) {
-  int G = aux ? coop_ctas(n) : 0;
-  if (G >= 2) {
-    double* pbuf = (double*)aux;
-    GridBarrier* bar = (GridBarrier*)((char*)aux + align_up(sizeof(double) * (size_t)n, 256));
+  CoopPlan P;
+  if (aux) P = coop_plan(n, k);
+  if (P.G >= 2) {
+    char* p = (char*)aux;
+    double* xbuf = (double*)p;
+    p += align_up(4 * sizeof(double) * (size_t)n, 256);
+    double* coef = (double*)p;
+    p += align_up(sizeof(double) * (size_t)n, 256);
+    double* part = (double*)p;
+    p += align_up(sizeof(double) * kCoopMaxCtas, 256);
+    GridBarrier* bar = (GridBarrier*)p;
     DF_CUDA(cudaMemsetAsync(bar, 0, sizeof(GridBarrier), s));
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(G);
+    cfg.gridDim = dim3(P.G);
     cfg.blockDim = dim3(256);
-    cfg.dynamicSmemBytes = 2 * sizeof(double) * (size_t)n;
+    cfg.dynamicSmemBytes = P.smem;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    DF_CUDA(cudaLaunchKernelEx(&cfg, eigh_lowest_coop_kernel, A, n, k, w, ZT, scratch, pbuf, bar, status));
+    if (P.rows)
+      DF_CUDA(cudaLaunchKernelEx(&cfg, eigh_lowest_coop_smem_kernel, A, n, k, w, ZT, scratch, xbuf, P.R, coef, part,
+                                 P.zw, bar, status));
+    else
+      DF_CUDA(cudaLaunchKernelEx(&cfg, eigh_lowest_coop_kernel, A, n, k, w, ZT, scratch, xbuf, coef, part, P.zw, bar,
+                                 status));
     return DF_OK;
   }
   eigh_lowest_kernel<<<1, 1024, 0, s>>>(A, n, k, w, ZT, scratch, status);

@@ -5,16 +5,18 @@
 //   K_mn = sum_P sum_i X_{P,mi} X_{P,ni},  X_P = B_P C
 //
 // B layout (one caller-owned buffer):
-//   FP64 packed rows   naux x ld doubles,   ld = npair rounded up to 32 (256-byte rows)
-//   FP32 packed rows   naux x ld floats     (mixed mode)
-//   BF16 hi, lo planes naux x npad x npad   (mixed mode; full symmetric B_P, npad = nao
-//                                            rounded up to 128, zero padding)
-// J streams the packed rows (each symmetric pair stored once, weight 2 off the diagonal);
-// the mixed K reads the BF16 planes through TMA as plain K-major GEMM operands.
+//   FP64 packed rows        naux x ld doubles,  ld = npair rounded up to 32 (256-byte rows)
+//   BF16 planes 0..3        naux x npad x npad  (mixed mode; full symmetric B_P, npad = nao
+//                                                rounded up to 128, zero padding)
+// Plane 0 is x rounded to 8 bits on a grid fixed along the row (the power of two just above
+// the row's max |x|); planes 1..3 are BF16 roundings of what is left (planes.cuh).  J streams the FP64 packed rows in both modes (each symmetric pair stored once,
+// weight 2 off the diagonal); the mixed K reads the BF16 planes through TMA as plain
+// K-major GEMM operands.
 #include <cuda_bf16.h>
 
 #include "common.cuh"
 #include "kernels.cuh"
+#include "planes.cuh"
 
 namespace dfscf {
 
@@ -29,57 +31,61 @@ BLayout B_layout(int nao, int naux, int precision) {
   L.off64 = off;
   off += align_up(sizeof(double) * (size_t)naux * L.ld, 256);
   if (precision == DF_MIXED) {
-    L.off32 = off;
-    off += align_up(sizeof(float) * (size_t)naux * L.ld, 256);
-    L.offhi = off;
-    off += align_up(sizeof(__nv_bfloat16) * (size_t)naux * L.npad * L.npad, 256);
-    L.offlo = off;
-    off += align_up(sizeof(__nv_bfloat16) * (size_t)naux * L.npad * L.npad, 256);
+    for (int j = 0; j < kMixedPlanes; ++j) {
+      L.offp[j] = off;
+      off += align_up(sizeof(__nv_bfloat16) * (size_t)naux * L.npad * L.npad, 256);
+    }
   }
   L.bytes = off;
   return L;
 }
 
-// ---- mixed-precision copies of B ----------------------------------------------------
-__global__ void b_to_fp32_kernel(const double* __restrict__ B64, float* __restrict__ B32, size_t n) {
-  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) B32[i] = (float)B64[i];
-}
+// ---- BF16 planes of B ------------------------------------------------------------------
+// Row (P, m) of the full symmetric B_P (over n) as kMixedPlanes row-scaled planes (planes.cuh;
+// residuals in FP64).  One CTA per row; padding (m or n >= nao) is zero.
+struct PlaneOut {
+  __nv_bfloat16* p[kMixedPlanes];
+};
 
-// hi = RN_bf16(x), lo = RN_bf16(x - hi), written for both (m,n) and (n,m) of row P.
-__global__ void b_to_split_bf16_kernel(const double* __restrict__ B64, long ld, int nao, int npad,
-                                       __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo) {
-  int P = blockIdx.y;
-  long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= (long)npad * npad) return;
-  int m = (int)(e / npad), n = (int)(e % npad);
-  double x = 0.0;
-  if (m < nao && n < nao) {
+__global__ void __launch_bounds__(128) b_to_planes_kernel(const double* __restrict__ B64, long ld, int nao, int npad,
+                                                          PlaneOut out) {
+  __shared__ double sh[4];
+  const int m = blockIdx.x, P = blockIdx.y;
+  const double* row = B64 + (size_t)P * ld;
+  auto load = [&](int n) -> double {
+    if (m >= nao || n >= nao) return 0.0;
     int a = max(m, n), b = min(m, n);
-    x = B64[(size_t)P * ld + (size_t)a * (a + 1) / 2 + b];
+    return row[(size_t)a * (a + 1) / 2 + b];
+  };
+  double amax = 0.0;
+  for (int n = threadIdx.x; n < npad; n += blockDim.x) amax = fmax(amax, fabs(load(n)));
+  for (int o = 16; o; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = amax;
+  __syncthreads();
+  const double sig = row_scale(fmax(fmax(sh[0], sh[1]), fmax(sh[2], sh[3])));
+  const size_t o = ((size_t)P * npad + m) * npad;
+  for (int n = threadIdx.x; n < npad; n += blockDim.x) {
+    __nv_bfloat16 q[kPlanesMax];
+    split_row_value(load(n), sig, q);
+#pragma unroll
+    for (int j = 0; j < kMixedPlanes; ++j) out.p[j][o + n] = q[j];
   }
-  __nv_bfloat16 h = __double2bfloat16(x);
-  __nv_bfloat16 l = __double2bfloat16(x - (double)__bfloat162float(h));
-  size_t o = (size_t)P * npad * npad + e;
-  hi[o] = h;
-  lo[o] = l;
 }
 
 // ---- J --------------------------------------------------------------------------------
 // Dw_mn = w_mn D_mn for packed m >= n (w = 2 off the diagonal, 1 on it); padding zero.
-template <typename T>
 __global__ void weighted_packed_density_kernel(const double* __restrict__ D, int nao, long npair, long ld,
-                                               T* __restrict__ Dw) {
+                                               double* __restrict__ Dw) {
   long ij = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (ij >= ld) return;
   if (ij >= npair) {
-    Dw[ij] = (T)0;
+    Dw[ij] = 0.0;
     return;
   }
   int m, n;
   unpack_pair(ij, m, n);
   double w = (m == n) ? 1.0 : 2.0;
-  Dw[ij] = (T)(w * 0.5 * (D[(size_t)m * nao + n] + D[(size_t)n * nao + m]));
+  Dw[ij] = w * 0.5 * (D[(size_t)m * nao + n] + D[(size_t)n * nao + m]);
 }
 
 // d_P = sum_ij B[P][ij] Dw[ij]; one CTA per row, 128-bit loads.
@@ -104,33 +110,6 @@ __global__ void __launch_bounds__(512) jpass1_fp64_kernel(const double* __restri
     acc0 = fma(b0.x, w0.x, acc0); acc1 = fma(b0.y, w0.y, acc1);
   }
   double t = block_sum(acc0 + acc1, sh);
-  if (threadIdx.x == 0) d[blockIdx.x] = t;
-}
-
-// Mixed: FP32 products and FP32 partial sums over 8 elements, FP64 accumulation.
-__global__ void __launch_bounds__(512) jpass1_fp32_kernel(const float* __restrict__ B, long ld,
-                                                          const float* __restrict__ Dw, double* __restrict__ d) {
-  __shared__ double sh[16];
-  const float4* row = reinterpret_cast<const float4*>(B + (size_t)blockIdx.x * ld);
-  const float4* dw = reinterpret_cast<const float4*>(Dw);
-  long n4 = ld / 4;
-  double acc = 0.0;
-  long i = threadIdx.x;
-  for (; i + 512 < n4; i += 2 * 512) {
-    float4 b0 = __ldcs(row + i), b1 = __ldcs(row + i + 512);
-    float4 w0 = dw[i], w1 = dw[i + 512];
-    float s = b0.x * w0.x;
-    s = fmaf(b0.y, w0.y, s); s = fmaf(b0.z, w0.z, s); s = fmaf(b0.w, w0.w, s);
-    s = fmaf(b1.x, w1.x, s); s = fmaf(b1.y, w1.y, s); s = fmaf(b1.z, w1.z, s); s = fmaf(b1.w, w1.w, s);
-    acc += (double)s;
-  }
-  for (; i < n4; i += 512) {
-    float4 b0 = __ldcs(row + i), w0 = dw[i];
-    float s = b0.x * w0.x;
-    s = fmaf(b0.y, w0.y, s); s = fmaf(b0.z, w0.z, s); s = fmaf(b0.w, w0.w, s);
-    acc += (double)s;
-  }
-  double t = block_sum(acc, sh);
   if (threadIdx.x == 0) d[blockIdx.x] = t;
 }
 
@@ -160,33 +139,6 @@ __global__ void __launch_bounds__(256) jpass2_fp64_kernel(const double* __restri
     ax = fma(sd[p], v0.x, ax); ay = fma(sd[p], v0.y, ay);
   }
   reinterpret_cast<double2*>(Jpart + (size_t)blockIdx.y * ld)[c2] = make_double2(ax + bx, ay + by);
-}
-
-__global__ void __launch_bounds__(256) jpass2_fp32_kernel(const float* __restrict__ B, long ld, int naux, int rows,
-                                                          const double* __restrict__ d, double* __restrict__ Jpart) {
-  __shared__ float sd[JP2_MAX_ROWS];
-  int p0 = blockIdx.y * rows;
-  int np = min(rows, naux - p0);
-  for (int i = threadIdx.x; i < np; i += blockDim.x) sd[i] = (float)d[p0 + i];
-  __syncthreads();
-  long c4 = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (c4 * 4 >= ld) return;
-  const float4* col = reinterpret_cast<const float4*>(B + (size_t)p0 * ld) + c4;
-  long st = ld / 4;
-  double a[4] = {0, 0, 0, 0};
-  for (int p = 0; p < np; p += 8) {
-    float s[4] = {0.f, 0.f, 0.f, 0.f};
-    int pe = min(np, p + 8);
-    for (int q = p; q < pe; ++q) {
-      float4 v = __ldcs(col + (size_t)q * st);
-      s[0] = fmaf(sd[q], v.x, s[0]); s[1] = fmaf(sd[q], v.y, s[1]);
-      s[2] = fmaf(sd[q], v.z, s[2]); s[3] = fmaf(sd[q], v.w, s[3]);
-    }
-#pragma unroll
-    for (int k = 0; k < 4; ++k) a[k] += (double)s[k];
-  }
-  double* out = Jpart + (size_t)blockIdx.y * ld + c4 * 4;
-  out[0] = a[0]; out[1] = a[1]; out[2] = a[2]; out[3] = a[3];
 }
 
 // J[m][n] = J[n][m] = sum_split Jpart[split][mn].
@@ -298,7 +250,6 @@ JKWork jk_work_layout(int nao, int naux, int nocc, int precision, Arena* a, Size
 #define TAKE(T, ptr, count) \
   if (a) ptr = a->take<T>(count); else z->take<T>(count);
   TAKE(double, w.Dw, ld);
-  TAKE(float, w.Dw32, ld);
   TAKE(double, w.d, naux);
   TAKE(double, w.Jpart, (size_t)nsplit_j * ld);
   if (precision == DF_FP64 || fp64_k) {
@@ -318,34 +269,19 @@ int build_J(const void* Bbuf, const BLayout& L, int nao, int naux, int precision
   DF_REQUIRE(rows <= JP2_MAX_ROWS, DF_ERR_ARG, "J: %d auxiliary rows per slice exceed %d", rows, JP2_MAX_ROWS);
   unsigned g = (unsigned)((ld + 255) / 256);
   unsigned gp = (unsigned)((npair + 255) / 256);
-  if (precision == DF_FP64) {
-    weighted_packed_density_kernel<double><<<g, 256, 0, s>>>(D, nao, npair, ld, w.Dw);
-    DF_LAUNCHED("weighted_packed_density_kernel");
-    {
-      ProfScope ps("j_pass1_fp64", s);
-      jpass1_fp64_kernel<<<naux, 512, 0, s>>>((const double*)(base + L.off64), ld, w.Dw, w.d);
-      DF_LAUNCHED("jpass1_fp64_kernel");
-    }
-    {
-      ProfScope ps("j_pass2_fp64", s);
-      dim3 grid2((unsigned)((ld / 2 + 255) / 256), (unsigned)w.nsplit_j);
-      jpass2_fp64_kernel<<<grid2, 256, 0, s>>>((const double*)(base + L.off64), ld, naux, rows, w.d, w.Jpart);
-      DF_LAUNCHED("jpass2_fp64_kernel");
-    }
-  } else {
-    weighted_packed_density_kernel<float><<<g, 256, 0, s>>>(D, nao, npair, ld, w.Dw32);
-    DF_LAUNCHED("weighted_packed_density_kernel");
-    {
-      ProfScope ps("j_pass1_fp32", s);
-      jpass1_fp32_kernel<<<naux, 512, 0, s>>>((const float*)(base + L.off32), ld, w.Dw32, w.d);
-      DF_LAUNCHED("jpass1_fp32_kernel");
-    }
-    {
-      ProfScope ps("j_pass2_fp32", s);
-      dim3 grid2((unsigned)((ld / 4 + 255) / 256), (unsigned)w.nsplit_j);
-      jpass2_fp32_kernel<<<grid2, 256, 0, s>>>((const float*)(base + L.off32), ld, naux, rows, w.d, w.Jpart);
-      DF_LAUNCHED("jpass2_fp32_kernel");
-    }
+  (void)precision;  // J streams the FP64 rows in both modes
+  weighted_packed_density_kernel<<<g, 256, 0, s>>>(D, nao, npair, ld, w.Dw);
+  DF_LAUNCHED("weighted_packed_density_kernel");
+  {
+    ProfScope ps("j_pass1_fp64", s);
+    jpass1_fp64_kernel<<<naux, 512, 0, s>>>((const double*)(base + L.off64), ld, w.Dw, w.d);
+    DF_LAUNCHED("jpass1_fp64_kernel");
+  }
+  {
+    ProfScope ps("j_pass2_fp64", s);
+    dim3 grid2((unsigned)((ld / 2 + 255) / 256), (unsigned)w.nsplit_j);
+    jpass2_fp64_kernel<<<grid2, 256, 0, s>>>((const double*)(base + L.off64), ld, naux, rows, w.d, w.Jpart);
+    DF_LAUNCHED("jpass2_fp64_kernel");
   }
   jreduce_unpack_kernel<<<gp, 256, 0, s>>>(w.Jpart, w.nsplit_j, ld, nao, J);
   DF_LAUNCHED("jreduce_unpack_kernel");
@@ -384,7 +320,7 @@ int run_jk(const void* B, int nao, int naux, int precision, const double* D, con
       DF_REQUIRE(w.X && w.Kpart, DF_ERR_ARG, "FP64 exchange requested with a workspace laid out for mixed precision");
       DF_TRY(build_K_fp64((const double*)((const char*)B + L.off64), L.ld, nao, naux, C, nocc, K, w, s));
     } else {
-      DF_REQUIRE(w.mk.Xhi && w.mk.Kpart, DF_ERR_ARG, "mixed exchange requested with a workspace laid out for FP64");
+      DF_REQUIRE(w.mk.Xp[0] && w.mk.Kpart, DF_ERR_ARG, "mixed exchange requested with a workspace laid out for FP64");
       DF_TRY(build_K_mixed(B, L, nao, naux, C, nocc, K, w.mk, s));
     }
   }
@@ -398,14 +334,11 @@ int build_B(const double* ao_xyz, const double* ao_exp, int nao, const double* a
   DF_TRY(launch_int3c(ao_xyz, ao_exp, nao, aux_xyz, aux_exp, naux, B64, L.ld, pair_tab, s));
   DF_TRY(forward_substitution(B64, L.ld, L.ld, Lfac, naux, s));
   if (precision == DF_MIXED) {
-    size_t n = (size_t)naux * L.ld;
-    b_to_fp32_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(B64, (float*)((char*)Bbuf + L.off32), n);
-    DF_LAUNCHED("b_to_fp32_kernel");
-    dim3 grid((unsigned)(((long)L.npad * L.npad + 255) / 256), (unsigned)naux);
     DF_REQUIRE(naux <= 65535, DF_ERR_ARG, "naux too large");
-    b_to_split_bf16_kernel<<<grid, 256, 0, s>>>(B64, L.ld, nao, L.npad, (__nv_bfloat16*)((char*)Bbuf + L.offhi),
-                                                (__nv_bfloat16*)((char*)Bbuf + L.offlo));
-    DF_LAUNCHED("b_to_split_bf16_kernel");
+    PlaneOut po{};
+    for (int j = 0; j < kMixedPlanes; ++j) po.p[j] = (__nv_bfloat16*)((char*)Bbuf + L.offp[j]);
+    b_to_planes_kernel<<<dim3((unsigned)L.npad, (unsigned)naux), 128, 0, s>>>(B64, L.ld, nao, L.npad, po);
+    DF_LAUNCHED("b_to_planes_kernel");
   }
   return DF_OK;
 }

@@ -33,26 +33,29 @@ int eigh_lowest_rows(double* A, int n, int k, double* w, double* ZT, double* scr
 int transpose(const double* in, int rows, int cols, double* out, cudaStream_t s);
 
 // ---- B layout and J/K (jk.cu, umma.cu) --------------------------------------------------
+// BF16 planes kept of B for the mixed exchange; kernels use the first mixed_planes of them.
+constexpr int kMixedPlanes = 4;
+
 struct BLayout {
   long ld;       // packed row stride (elements)
   int npad;      // padded orbital dimension of the BF16 planes
-  size_t off64, off32, offhi, offlo, bytes;
+  size_t off64, offp[kMixedPlanes], bytes;
 };
 
 struct MixedKWork {
-  void* Chi;     // bf16 [ncpad][npad]  C^T hi
-  void* Clo;     // bf16 [ncpad][npad]  C^T lo
-  void* Xhi;     // bf16 [npad][naux * ncpad]   X hi (row m, column P*ncpad + i)
-  void* Xlo;     // bf16 same
-  float* Kpart;  // fp32 [nsplit][npad][npad] partial K tiles
-  int* err;      // device error flag of the tensor-core kernels
-  int ncpad;     // padded occupied count (multiple of 16, >= 16)
-  int nsplit;    // K-dimension splits of the exchange contraction
+  void* Cp[kMixedPlanes];  // bf16 [ncpad][npad]  planes of C^T
+  void* Xp[kMixedPlanes];  // bf16 [npad][naux * ncpad]  planes of X (row m, column P*ncpad + i)
+  float* X32;              // fp32 [npad][naux * ncpad]  X from the half transform
+  unsigned* xmax;          // [npad] max |X| of row m (FP32 bits)
+  float* Kpart;            // fp32 [nsplit][npad][npad] partial K tiles
+  int* err;                // device error flag of the tensor-core kernels
+  int ncpad;               // padded occupied count (multiple of 16, >= 16)
+  int nsplit;              // K-dimension splits of the exchange contraction
+  int planes;              // BF16 planes per operand (2: 3 products, 3: 6 products)
 };
 
 struct JKWork {
   double* Dw;
-  float* Dw32;
   double* d;
   double* Jpart;
   double* X;

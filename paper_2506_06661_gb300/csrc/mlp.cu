@@ -266,6 +266,21 @@ __global__ void assemble_density_kernel(const float* __restrict__ out, const flo
   D[(size_t)(NBF * B + a) * nao + NBF * A + b] = v;
 }
 
+// Factor that brings tr(Dt) to nelec (one block); a non-positive trace gives 1 and the
+// validity gate then rejects the guess.
+__global__ void trace_scale_kernel(const double* __restrict__ D, int nao, int nelec, double* __restrict__ scale) {
+  __shared__ double sh[32];
+  double t = 0.0;
+  for (int i = threadIdx.x; i < nao; i += blockDim.x) t += D[(size_t)i * nao + i];
+  t = block_sum(t, sh);
+  if (threadIdx.x == 0) *scale = t > 0.0 ? (double)nelec / t : 1.0;
+}
+
+__global__ void scale_kernel(double* __restrict__ D, size_t n, const double* __restrict__ scale) {
+  const double c = *scale;
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) D[k] *= c;
+}
+
 // ---- workspace -------------------------------------------------------------------------------
 struct Work {
   float* Z[NLAYER];   // pre-activations
@@ -452,13 +467,14 @@ extern "C" size_t guess_density_work_bytes(int natm) {
   z.take<float>((size_t)np);
   z.take<double>((size_t)NBF * natm * NBF * natm);
   z.take<double>((size_t)NBF * natm * NBF * natm);
+  z.take<double>(1);
   return z.used + guess_mlp_work_bytes((int)np);
 }
 
-extern "C" int guess_density(const float* params, const double* xyz, int natm, const double* Sinvhalf, double* D0,
-                             void* work, size_t work_bytes, cudaStream_t s) {
+extern "C" int guess_density(const float* params, const double* xyz, int natm, int nelec, const double* Sinvhalf,
+                             double* D0, void* work, size_t work_bytes, cudaStream_t s) {
   clear_error();
-  DF_REQUIRE(params && xyz && D0 && Sinvhalf && natm > 0, DF_ERR_ARG, "guess_density: bad arguments");
+  DF_REQUIRE(params && xyz && D0 && Sinvhalf && natm > 0 && nelec >= 0, DF_ERR_ARG, "guess_density: bad arguments");
   DF_REQUIRE(work && work_bytes >= guess_density_work_bytes(natm), DF_ERR_NOMEM, "guess_density: workspace too small");
   long np = (long)natm * (natm + 1) / 2;
   DF_REQUIRE(np < 65535L * 64, DF_ERR_ARG, "guess_density: too many centres");
@@ -469,6 +485,7 @@ extern "C" int guess_density(const float* params, const double* xyz, int natm, c
   float* mask = a.take<float>((size_t)np);
   double* Dt = a.take<double>((size_t)nao * nao);
   double* T = a.take<double>((size_t)nao * nao);
+  double* scale = a.take<double>(1);
   size_t rest = work_bytes - a.used;
   void* mw = (char*)work + a.used;
   env_kernel<<<natm, 32, 0, s>>>(xyz, natm, env);
@@ -484,6 +501,12 @@ extern "C" int guess_density(const float* params, const double* xyz, int natm, c
   DF_CUDA(cudaMemsetAsync(Dt, 0, sizeof(double) * nao * nao, s));
   assemble_density_kernel<<<(unsigned)np, 32, 0, s>>>(w.H[NLAYER - 1], mask, natm, Dt);
   DF_LAUNCHED("assemble_density_kernel");
+  if (nelec > 0) {
+    trace_scale_kernel<<<1, 1024, 0, s>>>(Dt, nao, nelec, scale);
+    DF_LAUNCHED("trace_scale_kernel");
+    scale_kernel<<<nb((long)nao * nao), 256, 0, s>>>(Dt, (size_t)nao * nao, scale);
+    DF_LAUNCHED("scale_kernel");
+  }
   DF_TRY(dgemm(false, false, nao, nao, nao, 1.0, Dt, nao, 0, Sinvhalf, nao, 0, 0.0, T, nao, 0, 1, s, 0, 0));
   DF_TRY(dgemm(false, false, nao, nao, nao, 1.0, Sinvhalf, nao, 0, T, nao, 0, 0.0, D0, nao, 0, 1, s, 0, 0));
   return DF_OK;

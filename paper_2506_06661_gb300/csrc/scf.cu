@@ -399,8 +399,8 @@ struct ScfMol {
   int fp64_done = 0;
   double e_old = 0.0;
   bool have_old = false;
-  double best_de = INFINITY;  // smallest |dE| of the mixed phase so far
-  int stall = 0;              // mixed iterations since best_de last improved
+  double best_err = INFINITY;  // smallest max|e| of the mixed phase so far
+  int stall = 0;               // mixed iterations without a 10% gain on best_err
   bool done = false;
   int rc = DF_OK;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
@@ -672,17 +672,19 @@ static bool scf_iter_finish(ScfMol& M) {
   // orbital energies of the diagonalisation that produced the next density
   M.res.homo = h.homo;
   M.res.lumo = h.lumo;
-  // Mixed phase: switch on the thresholds, or when |dE| has not improved for 3 iterations
-  // (the split-BF16 error floor), or after half the iteration budget.
+  // Mixed phase: switch on the thresholds; or when the DIIS error, already below 1e-2, has
+  // not improved by 10% for 5 iterations (the floor of the mixed-precision Fock matrix; the
+  // energy of the first iterations oscillates too much to judge by |dE|); or after half the
+  // iteration budget.
   bool stalled = false;
-  if (!M.switched && M.have_old) {
-    if (de < M.best_de) {
-      M.best_de = de;
+  if (!M.switched) {
+    if (h.emax < 0.9 * M.best_err) {
+      M.best_err = h.emax;
       M.stall = 0;
     } else {
       M.stall++;
     }
-    stalled = M.stall >= 3 || M.res.iterations >= M.opt.max_cycle / 2;
+    stalled = (M.stall >= 5 && M.best_err < 1e-2) || M.res.iterations >= M.opt.max_cycle / 2;
   }
   if (!M.switched && M.have_old && (de < M.opt.switch_tol || h.emax < M.opt.switch_err || stalled)) {
     // The DIIS history is kept: the mixed-precision Fock matrices are close to the FP64

@@ -2,17 +2,24 @@
 //
 // K_mn = sum_P sum_i X_{P,mi} X_{P,ni},  X_P = B_P C   (arXiv 2506.06661, Section
 // "Density fitting": the fitted integrals sum_P B_{P,mk} B_{P,nl} contracted with the
-// occupied coefficients).  Both contractions run as split-BF16 x3 GEMMs: every operand x
-// is stored as hi = RN_bf16(x), lo = RN_bf16(x - hi) and each product is formed as
-// hi*hi + hi*lo + lo*hi with FP32 accumulation in tensor memory (TMEM).
+// occupied coefficients).  Both contractions run as split-BF16 GEMMs: every operand row is
+// stored as NP BF16 planes, p0 = x rounded to 8 bits on a power-of-two grid fixed along the
+// row (an integer in [-128, 128] times the row's scale), p1 = RN_bf16(x - p0),
+// p2 = RN_bf16(x - p0 - p1).  A product is formed from the plane products pa*qb with
+// a + b < NP; the products of each order a + b go to an FP32 accumulator of their own in
+// tensor memory (TMEM).  Order 0 (p0*q0) sums integers on one grid and is exact in FP32;
+// orders 1 and 2 are 2^-8 and 2^-16 smaller, so their rounding stays below 2^-24 of the
+// result.  With a single accumulator the FP32 rounding of long sums with cancellation,
+// not the operand split, limits the accuracy.  NP = 2: three products; NP = 3: six.
 //
 //   half-transform:  X[(P,m), i] = sum_n B[(P,m), n] C^T[i, n]     (A = B planes, B = C^T)
 //   exchange SYRK:   K[m, n]     = sum_(P,i) X[m, (P,i)] X[n, (P,i)] (A = B = X, lower tiles)
 //
 // Both are "D = A B^T" with A and B K-major in global memory, so one kernel serves both:
-// TMA (SWIZZLE_128B, 64-element K boxes) fills a multi-stage shared-memory ring, one
-// elected lane issues tcgen05.mma (M = 128, N <= 256, K = 16 per instruction, three per
-// K step), tcgen05.commit releases ring slots, and four epilogue warps read the
+// TMA (128-byte swizzle and 64-element K boxes; 64-byte swizzle and 32-element boxes for
+// four planes, whose stages are twice as wide) fills a multi-stage shared-memory ring, one
+// elected lane issues tcgen05.mma (M = 128, N <= 256, K = 16 per instruction, one per
+// plane product and K step), tcgen05.commit releases ring slots, and four epilogue warps read the
 // accumulator with tcgen05.ld.  Every mbarrier wait is bounded; on a timeout the kernel
 // raises a device error flag and returns after releasing its TMEM.
 #include <cuda.h>
@@ -21,13 +28,15 @@
 
 #include "common.cuh"
 #include "kernels.cuh"
+#include "planes.cuh"
 
 namespace dfscf {
 
 namespace umma {
 
 constexpr int BM = 128;          // rows per tile (TMEM lanes)
-constexpr int BK = 64;           // K elements per stage (128 bytes of bf16: one swizzle row)
+// K elements per stage: one swizzle row of bf16 (128 bytes; 64 bytes for four planes)
+__host__ __device__ constexpr int bk_of(int np) { return np >= 4 ? 32 : 64; }
 constexpr int MAX_STAGES = 4;
 constexpr int THREADS = 192;     // warp 0 TMA, warp 1 MMA, warps 2..5 epilogue
 constexpr uint32_t WAIT_LIMIT = 1u << 27;
@@ -107,15 +116,17 @@ __device__ __forceinline__ void tmem_ld_x16(uint32_t taddr, uint32_t (&r)[16]) {
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
-// Shared-memory matrix descriptor (tcgen05 format) for a K-major tile written by TMA
-// with 128-byte swizzling: rows of 128 bytes, 8-row groups 1024 bytes apart.
-__device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
+// Shared-memory matrix descriptor (tcgen05 format) for a K-major tile written by TMA with
+// BK-element rows (2 BK bytes) swizzled at that width: 8-row groups 16 BK bytes apart.
+template <int BK>
+__device__ __forceinline__ uint64_t desc_sw(uint32_t saddr) {
+  static_assert(BK == 64 || BK == 32, "swizzle width");
   uint64_t d = 0;
-  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);  // start address
-  d |= (uint64_t)1 << 16;                   // leading byte offset (unused for swizzled K-major)
-  d |= (uint64_t)(1024 >> 4) << 32;         // stride byte offset: 8 rows x 128 B
-  d |= (uint64_t)1 << 46;                   // descriptor version for tcgen05
-  d |= (uint64_t)2 << 61;                   // 128-byte swizzle
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);     // start address
+  d |= (uint64_t)1 << 16;                      // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)((8 * 2 * BK) >> 4) << 32;    // stride byte offset: 8 rows
+  d |= (uint64_t)1 << 46;                      // descriptor version for tcgen05
+  d |= (uint64_t)(BK == 64 ? 2 : 4) << 61;     // 128-byte or 64-byte swizzle
   return d;
 }
 
@@ -132,17 +143,17 @@ enum Mode { HALF_TRANSFORM = 0, SYRK = 1 };
 struct Params {
   int mode;
   int N;             // tile columns (multiple of 16, <= 256)
-  int num_kb;        // K blocks of BK in the whole K range
+  int num_kb;        // K blocks of bk_of(NP) in the whole K range
   int kb_per_split;  // K blocks per split (SYRK) or num_kb
   int stages;
   uint32_t stage_bytes;
   uint32_t b_bytes;  // bytes of one B tile (N x 128)
-  // half-transform epilogue
+  // half-transform epilogue: X in FP32 and the max |X| of every row m
   int npad;          // rows per P in A
   long ldx;          // X row stride (elements)
   int ncx;           // X columns per P
-  __nv_bfloat16* Xhi;
-  __nv_bfloat16* Xlo;
+  float* X32;
+  unsigned* xmax;    // FP32 bit patterns of max |X| per row m (non-negative: integer order)
   // SYRK epilogue
   float* Kpart;      // [split][npad][npad]
   int n_lower_tiles;
@@ -157,11 +168,16 @@ __device__ __forceinline__ void lower_tile(int t, int& mt, int& nt) {
   nt = t - m * (m + 1) / 2;
 }
 
-__global__ void __launch_bounds__(THREADS, 1) split_bf16_gemm_kernel(const __grid_constant__ CUtensorMap mapAhi,
-                                                                      const __grid_constant__ CUtensorMap mapAlo,
-                                                                      const __grid_constant__ CUtensorMap mapBhi,
-                                                                      const __grid_constant__ CUtensorMap mapBlo,
+// Tensor maps of the operand planes (A planes, then B planes); entries >= NP unused.
+struct Maps {
+  CUtensorMap a[4];
+  CUtensorMap b[4];
+};
+
+template <int NP>
+__global__ void __launch_bounds__(THREADS, 1) split_bf16_gemm_kernel(const __grid_constant__ Maps maps,
                                                                       const Params p) {
+  constexpr int BK = bk_of(NP);
   extern __shared__ uint8_t dyn_smem[];
   __shared__ uint64_t full_bar[MAX_STAGES];
   __shared__ uint64_t empty_bar[MAX_STAGES];
@@ -186,13 +202,13 @@ __global__ void __launch_bounds__(THREADS, 1) split_bf16_gemm_kernel(const __gri
     kb0 = split * p.kb_per_split;
     nkb = min(p.kb_per_split, p.num_kb - kb0);
   }
-  // 1024-byte aligned ring of stages: [A hi | A lo | B hi | B lo]
+  // 1024-byte aligned ring of stages: [A planes | B planes]
   uint32_t base = smem_u32(dyn_smem);
   uint32_t pad = (1024u - (base & 1023u)) & 1023u;
   uint8_t* ring = dyn_smem + pad;
   const uint32_t a_bytes = BM * BK * 2;
   uint32_t ncols = 32;
-  while ((int)ncols < p.N) ncols <<= 1;
+  while ((int)ncols < NP * p.N) ncols <<= 1;  // one accumulator of N columns per product order
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < p.stages; ++s) {
@@ -204,10 +220,11 @@ __global__ void __launch_bounds__(THREADS, 1) split_bf16_gemm_kernel(const __gri
     mbar_fence_init();
   }
   if (warp == 0 && lane == 0) {
-    tma_prefetch(&mapAhi);
-    tma_prefetch(&mapAlo);
-    tma_prefetch(&mapBhi);
-    tma_prefetch(&mapBlo);
+#pragma unroll
+    for (int j = 0; j < NP; ++j) {
+      tma_prefetch(&maps.a[j]);
+      tma_prefetch(&maps.b[j]);
+    }
   }
   if (warp == 1) {
     tmem_alloc(&tmem_base, ncols);
@@ -230,10 +247,11 @@ __global__ void __launch_bounds__(THREADS, 1) split_bf16_gemm_kernel(const __gri
       uint8_t* st = ring + (size_t)s * p.stage_bytes;
       mbar_arrive_expect_tx(&full_bar[s], p.stage_bytes);
       int kx = (kb0 + i) * BK;
-      tma_load_2d(st, &mapAhi, &full_bar[s], kx, row0);
-      tma_load_2d(st + a_bytes, &mapAlo, &full_bar[s], kx, row0);
-      tma_load_2d(st + 2 * a_bytes, &mapBhi, &full_bar[s], kx, col0);
-      tma_load_2d(st + 2 * a_bytes + p.b_bytes, &mapBlo, &full_bar[s], kx, col0);
+#pragma unroll
+      for (int j = 0; j < NP; ++j) {
+        tma_load_2d(st + j * a_bytes, &maps.a[j], &full_bar[s], kx, row0);
+        tma_load_2d(st + NP * a_bytes + j * p.b_bytes, &maps.b[j], &full_bar[s], kx, col0);
+      }
     }
   } else if (warp == 1 && lane == 0 && nkb > 0) {
     // ---- MMA issuer ------------------------------------------------------------------
@@ -249,14 +267,22 @@ __global__ void __launch_bounds__(THREADS, 1) split_bf16_gemm_kernel(const __gri
       }
       tc_fence_after();
       uint32_t st = smem_u32(ring + (size_t)s * p.stage_bytes);
-      uint64_t ahi = desc_sw128(st), alo = desc_sw128(st + a_bytes);
-      uint64_t bhi = desc_sw128(st + 2 * a_bytes), blo = desc_sw128(st + 2 * a_bytes + p.b_bytes);
+      uint64_t ad[NP], bd[NP];
+#pragma unroll
+      for (int j = 0; j < NP; ++j) {
+        ad[j] = desc_sw<BK>(st + j * a_bytes);
+        bd[j] = desc_sw<BK>(st + NP * a_bytes + j * p.b_bytes);
+      }
 #pragma unroll
       for (int kk = 0; kk < BK / 16; ++kk) {
         uint64_t off = (uint64_t)(kk * 32) >> 4;  // 16 bf16 = 32 bytes along K inside the swizzle row
-        umma_bf16(tmem, ahi + off, bhi + off, idesc, (i > 0 || kk > 0) ? 1u : 0u);
-        umma_bf16(tmem, ahi + off, blo + off, idesc, 1u);
-        umma_bf16(tmem, alo + off, bhi + off, idesc, 1u);
+        // plane products of order t = a + b into accumulator t: (0,0); (0,1) (1,0); (0,2) (1,1) (2,0)
+#pragma unroll
+        for (int t = 0; t < NP; ++t)
+#pragma unroll
+          for (int a = 0; a <= t; ++a)
+            umma_bf16(tmem + (uint32_t)(t * p.N), ad[a] + off, bd[t - a] + off, idesc,
+                      (i > 0 || kk > 0 || a > 0) ? 1u : 0u);
       }
       umma_commit(&empty_bar[s]);  // slot reusable once these MMAs have read it
     }
@@ -270,34 +296,37 @@ __global__ void __launch_bounds__(THREADS, 1) split_bf16_gemm_kernel(const __gri
     tc_fence_after();
     if (ok) {
       const int grow = row0 + r;
+      float lmax = 0.0f;
       for (int c = 0; c < p.N; c += 16) {
-        uint32_t v[16];
-        tmem_ld_x16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c, v);
+        if (p.mode == HALF_TRANSFORM && col0 + c >= p.ncx) break;  // column tiles past ncpad
+        uint32_t v[NP][16];
+#pragma unroll
+        for (int t = 0; t < NP; ++t) tmem_ld_x16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(t * p.N + c), v[t]);
         tmem_wait_ld();
+        float x[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          float acc = __uint_as_float(v[NP - 1][j]);  // smallest order first
+#pragma unroll
+          for (int t = NP - 2; t >= 0; --t) acc += __uint_as_float(v[t][j]);
+          x[j] = acc;
+        }
         if (p.mode == HALF_TRANSFORM) {
           int P = grow / p.npad, m = grow % p.npad;
-          __align__(16) __nv_bfloat16 h[16], l[16];
+          float4* dst = reinterpret_cast<float4*>(p.X32 + (size_t)m * p.ldx + (size_t)P * p.ncx + col0 + c);
 #pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            float x = __uint_as_float(v[j]);
-            h[j] = __float2bfloat16_rn(x);
-            l[j] = __float2bfloat16_rn(x - __bfloat162float(h[j]));
+          for (int j = 0; j < 4; ++j) {
+            dst[j] = make_float4(x[4 * j], x[4 * j + 1], x[4 * j + 2], x[4 * j + 3]);
+            lmax = fmaxf(lmax, fmaxf(fmaxf(fabsf(x[4 * j]), fabsf(x[4 * j + 1])),
+                                     fmaxf(fabsf(x[4 * j + 2]), fabsf(x[4 * j + 3]))));
           }
-          size_t o = (size_t)m * p.ldx + (size_t)P * p.ncx + col0 + c;
-          uint4* dh = reinterpret_cast<uint4*>(p.Xhi + o);
-          uint4* dl = reinterpret_cast<uint4*>(p.Xlo + o);
-          dh[0] = reinterpret_cast<uint4*>(h)[0];
-          dh[1] = reinterpret_cast<uint4*>(h)[1];
-          dl[0] = reinterpret_cast<uint4*>(l)[0];
-          dl[1] = reinterpret_cast<uint4*>(l)[1];
         } else {
           float4* dst = reinterpret_cast<float4*>(p.Kpart + ((size_t)split * p.npad + grow) * p.npad + col0 + c);
 #pragma unroll
-          for (int j = 0; j < 4; ++j)
-            dst[j] = make_float4(__uint_as_float(v[4 * j]), __uint_as_float(v[4 * j + 1]), __uint_as_float(v[4 * j + 2]),
-                                 __uint_as_float(v[4 * j + 3]));
+          for (int j = 0; j < 4; ++j) dst[j] = make_float4(x[4 * j], x[4 * j + 1], x[4 * j + 2], x[4 * j + 3]);
         }
       }
+      if (p.mode == HALF_TRANSFORM) atomicMax(p.xmax + grow % p.npad, __float_as_uint(lmax));
     }
   }
   tc_fence_before();
@@ -326,26 +355,30 @@ static PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
 }
 
 // 2-D bf16 tensor map: inner dimension `cols` (K, contiguous), `rows` rows of `ld` elements,
-// box of 64 x box_rows, 128-byte swizzle, zero fill out of bounds.
-static int make_map(CUtensorMap* map, const void* base, uint64_t cols, uint64_t rows, uint64_t ld, uint32_t box_rows) {
+// box of bk x box_rows swizzled at the box width (bk = 64: 128 bytes; 32: 64 bytes), zero
+// fill out of bounds.
+static int make_map(CUtensorMap* map, const void* base, uint64_t cols, uint64_t rows, uint64_t ld, uint32_t box_rows,
+                    int bk) {
   auto enc = get_encode();
   DF_REQUIRE(enc, DF_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
   DF_REQUIRE(((uintptr_t)base & 15) == 0 && (ld * 2) % 16 == 0, DF_ERR_ARG, "tensor map base/stride not 16-byte aligned");
   cuuint64_t dims[2] = {cols, rows};
   cuuint64_t strides[1] = {ld * 2};
-  cuuint32_t box[2] = {(cuuint32_t)umma::BK, box_rows};
+  cuuint32_t box[2] = {(cuuint32_t)bk, box_rows};
   cuuint32_t estr[2] = {1, 1};
   CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
-                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, bk == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   DF_REQUIRE(r == CUDA_SUCCESS, DF_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
   return DF_OK;
 }
 
-static int launch_gemm(const CUtensorMap& ahi, const CUtensorMap& alo, const CUtensorMap& bhi, const CUtensorMap& blo,
-                       umma::Params p, dim3 grid, cudaStream_t s) {
-  p.b_bytes = (uint32_t)p.N * umma::BK * 2;
-  p.stage_bytes = 2 * umma::BM * umma::BK * 2 + 2 * p.b_bytes;
+template <int NP>
+static int launch_gemm(const umma::Maps& maps, umma::Params p, dim3 grid, cudaStream_t s) {
+  constexpr int BK = umma::bk_of(NP);
+  p.b_bytes = (uint32_t)p.N * BK * 2;
+  p.stage_bytes = NP * (umma::BM * BK * 2 + p.b_bytes);
   const uint32_t budget = 220 * 1024;
   p.stages = (int)std::min<uint32_t>(std::min(umma::MAX_STAGES, std::max(2, knob("umma_max_stages"))),
                                      budget / p.stage_bytes);
@@ -353,21 +386,48 @@ static int launch_gemm(const CUtensorMap& ahi, const CUtensorMap& alo, const CUt
   size_t smem = (size_t)p.stages * p.stage_bytes + 1024;
   DF_REQUIRE(smem <= 220 * 1024 + 1024, DF_ERR_ARG, "split-bf16 GEMM: %zu bytes of shared memory requested", smem);
   DF_TRY(umma_prepare());
-  umma::split_bf16_gemm_kernel<<<grid, umma::THREADS, smem, s>>>(ahi, alo, bhi, blo, p);
+  umma::split_bf16_gemm_kernel<NP><<<grid, umma::THREADS, smem, s>>>(maps, p);
   DF_LAUNCHED("split_bf16_gemm_kernel");
   return DF_OK;
 }
 
-// C^T split into bf16 hi / lo planes [ncpad][npad], zero padded.
-__global__ void pack_ct_kernel(const double* __restrict__ C, int nao, int nocc, int npad, int ncpad,
-                               __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo) {
-  long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= (long)ncpad * npad) return;
-  int i = (int)(e / npad), n = (int)(e % npad);
-  double x = (i < nocc && n < nao) ? C[(size_t)n * nocc + i] : 0.0;
-  __nv_bfloat16 h = __double2bfloat16(x);
-  hi[e] = h;
-  lo[e] = __double2bfloat16(x - (double)__bfloat162float(h));
+struct PlanePtrs {
+  __nv_bfloat16* p[4];
+};
+
+// C^T [ncpad][npad] as row-scaled planes (row i = column i of C over n); one CTA per row,
+// zero padding.
+__global__ void __launch_bounds__(256) pack_ct_kernel(const double* __restrict__ C, int nao, int nocc, int npad,
+                                                      int planes, PlanePtrs out) {
+  __shared__ double sh[8];
+  const int i = blockIdx.x;
+  double amax = 0.0;
+  if (i < nocc)
+    for (int n = threadIdx.x; n < nao; n += blockDim.x) amax = fmax(amax, fabs(C[(size_t)n * nocc + i]));
+  for (int o = 16; o; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = amax;
+  __syncthreads();
+  double t = 0.0;
+  for (int w = 0; w < 8; ++w) t = fmax(t, sh[w]);
+  const double sig = row_scale(t);
+  for (int n = threadIdx.x; n < npad; n += blockDim.x) {
+    const double x = (i < nocc && n < nao) ? C[(size_t)n * nocc + i] : 0.0;
+    __nv_bfloat16 q[4];
+    split_row_value(x, sig, q);
+    const size_t e = (size_t)i * npad + n;
+    for (int j = 0; j < planes; ++j) out.p[j][e] = q[j];
+  }
+}
+
+// X [npad][kdim] (FP32) into row-scaled planes, the scale of row m from xmax[m].
+__global__ void x_to_planes_kernel(const float* __restrict__ X, const unsigned* __restrict__ xmax, long kdim,
+                                   long n, int planes, PlanePtrs out) {
+  for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x) {
+    const float sig = row_scale_f(__uint_as_float(xmax[e / kdim]));
+    __nv_bfloat16 q[4];
+    split_row_value_f(X[e], sig, q);
+    for (int j = 0; j < planes; ++j) out.p[j][e] = q[j];
+  }
 }
 
 // K[m][n] = K[n][m] = sum_split Kpart[split][m][n] (FP64 sum of FP32 partials), m >= n.
@@ -385,9 +445,9 @@ __global__ void kmixed_reduce_kernel(const float* __restrict__ Kpart, int nsplit
 
 static int mixed_ncpad(int nocc) { return std::max(16, (nocc + 15) / 16 * 16); }
 
-static int mixed_nsplit(int npad, int naux, int ncpad) {
+static int mixed_nsplit(int npad, int naux, int ncpad, int bk) {
   long kdim = (long)naux * ncpad;
-  long nkb = (kdim + umma::BK - 1) / umma::BK;
+  long nkb = (kdim + bk - 1) / bk;
   int tiles = (npad / umma::BM) * (npad / umma::BM + 1) / 2;
   // FP32 accumulation length per split <= ~16k terms, and several waves of CTAs
   long want = std::max<long>((kdim + 16383) / 16384, (4L * 152 + tiles - 1) / tiles);
@@ -400,32 +460,49 @@ static int mixed_nsplit(int npad, int naux, int ncpad) {
 int umma_prepare() {
   static bool done = false;
   if (!done) {
-    DF_CUDA(cudaFuncSetAttribute(umma::split_bf16_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    DF_CUDA(cudaFuncSetAttribute(umma::split_bf16_gemm_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(220 * 1024 + 1024)));
+    DF_CUDA(cudaFuncSetAttribute(umma::split_bf16_gemm_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)(220 * 1024 + 1024)));
     done = true;
   }
   return DF_OK;
 }
 
+// BF16 planes per operand of the mixed exchange (knob "mixed_planes": 3 or 4).
+int mixed_planes() { return knob("mixed_planes") == 3 ? 3 : 4; }
+
 void mixed_k_work_layout(int nao, int naux, int nocc, Arena* a, Sizer* z, MixedKWork* w) {
   int npad = nao_pad(nao);
   int ncpad = mixed_ncpad(std::max(nocc, 1));
-  int nsplit = mixed_nsplit(npad, naux, ncpad);
+  w->planes = mixed_planes();
+  int nsplit = mixed_nsplit(npad, naux, ncpad, umma::bk_of(w->planes));
   w->ncpad = ncpad;
   w->nsplit = nsplit;
   size_t xsize = (size_t)npad * naux * ncpad;
+  for (int j = 0; j < kMixedPlanes; ++j) {
+    w->Cp[j] = nullptr;
+    w->Xp[j] = nullptr;
+  }
+  for (int j = 0; j < w->planes; ++j) {
+    if (a) w->Cp[j] = a->take<__nv_bfloat16>((size_t)ncpad * npad);
+    else z->take<__nv_bfloat16>((size_t)ncpad * npad);
+  }
+  for (int j = 0; j < w->planes; ++j) {
+    if (a) w->Xp[j] = a->take<__nv_bfloat16>(xsize);
+    else z->take<__nv_bfloat16>(xsize);
+  }
   if (a) {
-    w->Chi = a->take<__nv_bfloat16>((size_t)ncpad * npad);
-    w->Clo = a->take<__nv_bfloat16>((size_t)ncpad * npad);
-    w->Xhi = a->take<__nv_bfloat16>(xsize);
-    w->Xlo = a->take<__nv_bfloat16>(xsize);
+    w->X32 = a->take<float>(xsize);
+    w->xmax = a->take<unsigned>((size_t)npad);
+  } else {
+    z->take<float>(xsize);
+    z->take<unsigned>((size_t)npad);
+  }
+  if (a) {
     w->Kpart = a->take<float>((size_t)nsplit * npad * npad);
     w->err = a->take<int>(1);
   } else {
-    z->take<__nv_bfloat16>((size_t)ncpad * npad);
-    z->take<__nv_bfloat16>((size_t)ncpad * npad);
-    z->take<__nv_bfloat16>(xsize);
-    z->take<__nv_bfloat16>(xsize);
     z->take<float>((size_t)nsplit * npad * npad);
     z->take<int>(1);
   }
@@ -433,46 +510,66 @@ void mixed_k_work_layout(int nao, int naux, int nocc, Arena* a, Sizer* z, MixedK
 
 int build_K_mixed(const void* B, const BLayout& L, int nao, int naux, const double* C, int nocc, double* K,
                   const MixedKWork& w, cudaStream_t s) {
-  const int npad = L.npad, ncpad = w.ncpad;
+  const int npad = L.npad, ncpad = w.ncpad, NP = w.planes;
   DF_REQUIRE(nocc <= ncpad, DF_ERR_ARG, "mixed K: workspace sized for %d occupied columns, got %d", ncpad, nocc);
   DF_REQUIRE(ncpad <= 256, DF_ERR_ARG, "mixed K: more than 256 occupied orbitals per call is not supported");
+  DF_REQUIRE(NP == 3 || NP == 4, DF_ERR_ARG, "mixed K: %d planes", NP);
   DF_CUDA(cudaMemsetAsync(w.err, 0, sizeof(int), s));
-  long nct = (long)ncpad * npad;
-  pack_ct_kernel<<<(unsigned)((nct + 255) / 256), 256, 0, s>>>(C, nao, nocc, npad, ncpad, (__nv_bfloat16*)w.Chi,
-                                                               (__nv_bfloat16*)w.Clo);
+  DF_CUDA(cudaMemsetAsync(w.xmax, 0, sizeof(unsigned) * (size_t)npad, s));
+  PlanePtrs cpp{}, xpp{};
+  for (int j = 0; j < NP; ++j) {
+    cpp.p[j] = (__nv_bfloat16*)w.Cp[j];
+    xpp.p[j] = (__nv_bfloat16*)w.Xp[j];
+  }
+  pack_ct_kernel<<<(unsigned)ncpad, 256, 0, s>>>(C, nao, nocc, npad, NP, cpp);
   DF_LAUNCHED("pack_ct_kernel");
+  // column tiles of the half transform: NP accumulators of N columns fit in 512 TMEM columns
+  const int maxN = std::min(256, (512 / NP) / 16 * 16);
+  const int ntc = (ncpad + maxN - 1) / maxN;
+  const int Nht = ((ncpad + ntc - 1) / ntc + 15) / 16 * 16;
   const char* base = (const char*)B;
-  CUtensorMap ahi, alo, bhi, blo;
+  umma::Maps maps{};
   // half transform: A = B planes [(P, m)][n], B = C^T [i][n]
-  DF_TRY(make_map(&ahi, base + L.offhi, npad, (uint64_t)naux * npad, npad, umma::BM));
-  DF_TRY(make_map(&alo, base + L.offlo, npad, (uint64_t)naux * npad, npad, umma::BM));
-  DF_TRY(make_map(&bhi, w.Chi, npad, ncpad, npad, ncpad));
-  DF_TRY(make_map(&blo, w.Clo, npad, ncpad, npad, ncpad));
+  for (int j = 0; j < NP; ++j) {
+    DF_TRY(make_map(&maps.a[j], base + L.offp[j], npad, (uint64_t)naux * npad, npad, umma::BM, umma::bk_of(NP)));
+    DF_TRY(make_map(&maps.b[j], w.Cp[j], npad, ncpad, npad, Nht, umma::bk_of(NP)));
+  }
   umma::Params p{};
   p.mode = umma::HALF_TRANSFORM;
-  p.N = ncpad;
-  p.num_kb = npad / umma::BK;
+  p.N = Nht;
+  const int bk = umma::bk_of(NP);
+  p.num_kb = npad / bk;
   p.kb_per_split = p.num_kb;
   p.npad = npad;
   p.ncx = ncpad;
   p.ldx = (long)naux * ncpad;
-  p.Xhi = (__nv_bfloat16*)w.Xhi;
-  p.Xlo = (__nv_bfloat16*)w.Xlo;
+  p.X32 = w.X32;
+  p.xmax = w.xmax;
   p.err = w.err;
   long mtiles = (long)naux * npad / umma::BM;
   DF_REQUIRE(mtiles < (1L << 31), DF_ERR_ARG, "mixed K: too many row tiles");
   {
     ProfScope ps("k_halftransform_tc", s);
-    DF_TRY(launch_gemm(ahi, alo, bhi, blo, p, dim3((unsigned)mtiles, 1), s));
+    if (NP == 4) DF_TRY(launch_gemm<4>(maps, p, dim3((unsigned)mtiles, (unsigned)ntc), s));
+    else DF_TRY(launch_gemm<3>(maps, p, dim3((unsigned)mtiles, (unsigned)ntc), s));
+  }
+  {
+    long nx = (long)npad * naux * ncpad;
+    ProfScope ps("k_x_planes", s);
+    x_to_planes_kernel<<<(unsigned)std::min<long>((nx + 255) / 256, 152L * 64), 256, 0, s>>>(
+        w.X32, w.xmax, (long)naux * ncpad, nx, NP, xpp);
+    DF_LAUNCHED("x_to_planes_kernel");
   }
   // exchange SYRK: A = B = X [m][(P, i)], lower 128 x 128 tiles, split over (P, i)
   long kdim = (long)naux * ncpad;
-  DF_TRY(make_map(&ahi, w.Xhi, kdim, npad, kdim, umma::BM));
-  DF_TRY(make_map(&alo, w.Xlo, kdim, npad, kdim, umma::BM));
+  for (int j = 0; j < NP; ++j) {
+    DF_TRY(make_map(&maps.a[j], w.Xp[j], kdim, npad, kdim, umma::BM, bk));
+    maps.b[j] = maps.a[j];
+  }
   umma::Params q{};
   q.mode = umma::SYRK;
   q.N = umma::BM;
-  q.num_kb = (int)((kdim + umma::BK - 1) / umma::BK);
+  q.num_kb = (int)((kdim + bk - 1) / bk);
   q.kb_per_split = (q.num_kb + w.nsplit - 1) / w.nsplit;
   int nsplit = (q.num_kb + q.kb_per_split - 1) / q.kb_per_split;
   q.npad = npad;
@@ -481,7 +578,9 @@ int build_K_mixed(const void* B, const BLayout& L, int nao, int naux, const doub
   q.err = w.err;
   {
     ProfScope ps("k_syrk_tc", s);
-    DF_TRY(launch_gemm(ahi, alo, ahi, alo, q, dim3((unsigned)q.n_lower_tiles, (unsigned)nsplit), s));
+    dim3 grid((unsigned)q.n_lower_tiles, (unsigned)nsplit);
+    if (NP == 4) DF_TRY(launch_gemm<4>(maps, q, grid, s));
+    else DF_TRY(launch_gemm<3>(maps, q, grid, s));
   }
   long nn = (long)nao * nao;
   kmixed_reduce_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, s>>>(w.Kpart, nsplit, npad, nao, K);

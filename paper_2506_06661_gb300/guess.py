@@ -131,15 +131,16 @@ def loss_grad(params: torch.Tensor, X, Y, mask=None):
     return float(loss.item()), grad
 
 
-def predict_density(model_or_params, mol) -> torch.Tensor:
-    """Starting density dm0 = S^-1/2 Dt S^-1/2 from the network's Loewdin-basis blocks."""
+def predict_density(model_or_params, mol, normalise: bool = True) -> torch.Tensor:
+    """Starting density dm0 = S^-1/2 Dt S^-1/2 from the network's Loewdin-basis blocks, with
+    Dt scaled to tr(Dt) = nelec unless normalise is False."""
     params = model_or_params.params if isinstance(model_or_params, GuessModel) else model_or_params
     _, Sih = lowdin_factors(mol)
     x = _dev(mol.xyz)
     natm = x.shape[0]
     D0 = torch.empty(5 * natm, 5 * natm, dtype=torch.float64, device="cuda")
     w = _work(lib().guess_density_work_bytes(natm))
-    _check(lib().guess_density(_ptr(params), _ptr(x), natm, _ptr(Sih), _ptr(D0), _ptr(w), w.numel(), _stream()))
+    _check(lib().guess_density(_ptr(params), _ptr(x), natm, int(mol.nelec) if normalise else 0, _ptr(Sih), _ptr(D0), _ptr(w), w.numel(), _stream()))
     return D0
 
 

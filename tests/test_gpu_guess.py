@@ -97,29 +97,39 @@ def test_lowdin_targets_match_oracle(c0, c0_system, c0_scf):
 
 
 def test_predicted_density_matches_oracle_assembly(c0, c0_system):
-    flat, P = gpu_params(8)
-    D0 = guess.predict_density(P, c0)
+    flat, _ = gpu_params(8)
+    # lift the diagonal outputs of the final bias so that tr(Dt) is well away from zero
+    flat[-omlp.NOUT:][[k for k, (a, b) in enumerate(omlp.TRIU) if a == b]] += 0.4
+    P = torch.tensor(flat, dtype=torch.float32, device="cuda")
     Sh, _ = guess.lowdin_factors(c0)
-    Dt = guess.congruence(Sh, D0).cpu().numpy()       # back to the orthonormal basis
     pairs, f = omlp.pair_features(c0.xyz)
     out, _ = omlp.forward(unflatten(flat), f)
     ref = omlp.assemble_density(out, pairs, c0.natm)
+    assert np.trace(ref) > 0.5 * c0.nelec
     # BF16 inference against the FP64 oracle forward, compared block by block
+    Dt = guess.congruence(Sh, guess.predict_density(P, c0, normalise=False)).cpu().numpy()
     assert np.max(np.abs(Dt - ref)) <= 5e-2 * np.max(np.abs(ref))
+    # scaled to the electron count: tr(Dt) = nelec, and the oracle's scaling of its own assembly
+    Dn = guess.congruence(Sh, guess.predict_density(P, c0)).cpu().numpy()
+    assert abs(np.trace(Dn) - c0.nelec) <= 1e-9 * c0.nelec
+    ref_n = omlp.normalise_trace(ref, c0.nelec)
+    assert np.max(np.abs(Dn - ref_n)) <= 5e-2 * np.max(np.abs(ref_n))
     Sh_o, _ = omlp.lowdin_factors(c0_system.S)
     assert np.max(np.abs(Sh.cpu().numpy() - Sh_o)) <= 1e-9 * np.max(np.abs(Sh_o))
 
 
 def test_trained_guess_reduces_iterations():
     train_mols = [gen.make_molecule(int(n), gen.molecules.box_for(int(n)), (7, i))
-                  for i, n in enumerate(gen.batch_sizes(160, 8, 14, 7))]
+                  for i, n in enumerate(gen.batch_sizes(480, 8, 14, 7))]
     res, Ds = guess.converged_densities(train_mols, slots=32)
     ok = [i for i, r in enumerate(res) if r.converged]
     # plain DIIS oscillates on a few charged clusters (the oracle does too); keep the rest
     assert len(ok) >= 0.9 * len(train_mols)
     X, Y, M = guess.build_dataset([train_mols[i] for i in ok], [Ds[i] for i in ok])
     model = guess.GuessModel.create(seed=11)
-    hist = guess.train(model, X, Y, M, epochs=40, batch=1024, lr=1e-3, seed=1)
+    # a network trained on fewer molecules (160, 40 epochs) still leaves outliers that take
+    # several times the core-guess iterations; 480 molecules and 80 epochs remove them
+    hist = guess.train(model, X, Y, M, epochs=80, batch=1024, lr=1e-3, seed=1)
     # pair-distance features explain about half of the block variance (a torch model on
     # the same data plateaus at the same loss); the gain is judged by SCF iterations below
     assert hist[-1] < 0.8 * hist[0]
@@ -130,5 +140,6 @@ def test_trained_guess_reduces_iterations():
     # most molecules reach the same SCF solution from either start, to 1e-6 Eh
     assert ev["same_state"] >= 0.75 * ev["both_converged"]
     assert ev["max_abs_dE_same_state"] <= 1e-6
-    assert ev["guess_used"] >= len(test_mols) // 2
+    # the network's blocks scaled to the electron count pass the validity gate
+    assert ev["guess_used"] >= (3 * len(test_mols)) // 4
     assert ev["mean_iter_learned"] < ev["mean_iter_core"]

@@ -112,3 +112,22 @@ def test_validity_checks(c0_system, c0_scf):
     bad = Sih @ (U * w2) @ U.T @ Sih
     assert abs(np.sum(bad * c0_system.S) - c0_system.nelec) < 1e-6
     assert not mlp.guess_is_valid(bad, c0_system.S, c0_system.nelec)
+
+
+def test_trace_normalisation_restores_electron_count(c0_system, c0_scf):
+    # a converged density scaled by 1.3 fails the electron-count gate; scaling its
+    # orthonormal-basis form back to tr = nelec recovers the converged density exactly,
+    # and tr(dm0 S) = tr(Dt) under dm0 = S^-1/2 Dt S^-1/2 for a full-rank S
+    S, ne = c0_system.S, c0_system.nelec
+    Sh, Sih = mlp.lowdin_factors(S)
+    Dt = Sh @ c0_scf.D @ Sh
+    fixed = mlp.normalise_trace(1.3 * Dt, ne)
+    assert abs(np.trace(fixed) - ne) <= 1e-10 * ne
+    assert np.allclose(fixed, Dt, rtol=0, atol=1e-12 * np.max(np.abs(Dt)))
+    dm0 = Sih @ fixed @ Sih
+    assert abs(np.sum(dm0 * S) - ne) <= 1e-8 * ne
+    assert not mlp.guess_is_valid(Sih @ (1.3 * Dt) @ Sih, S, ne)
+    assert mlp.guess_is_valid(dm0, S, ne)
+    # a density with non-positive trace is returned unchanged (the gate rejects it)
+    neg = -0.5 * Dt
+    assert np.array_equal(mlp.normalise_trace(neg, ne), neg)
