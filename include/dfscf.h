@@ -159,7 +159,7 @@ int df_eigh_lowest(double* A, int n, int k, double* w, double* Z, void* work, si
  * Converged when |dE| < conv_tol and max|e| < conv_err.  In DF_MIXED mode the loop runs
  * with mixed-precision K until |dE| < switch_tol or max|e| < switch_err, or until max|e|,
  * once below 1e-2, has not improved by 10% for 5 iterations (the mixed-precision floor), or
- * for half of max_cycle; then at least n_fp64_final FP64 iterations follow and the
+ * for three quarters of max_cycle; then at least n_fp64_final FP64 iterations follow and the
  * reported energy is the FP64 one.
  * dm0 (device [nao][nao], may be NULL): initial density; it need not be idempotent nor
  * have the right electron count (paper, Section "Initial Guess for Mean-field Methods").

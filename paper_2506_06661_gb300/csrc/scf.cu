@@ -674,8 +674,8 @@ static bool scf_iter_finish(ScfMol& M) {
   M.res.lumo = h.lumo;
   // Mixed phase: switch on the thresholds; or when the DIIS error, already below 1e-2, has
   // not improved by 10% for 5 iterations (the floor of the mixed-precision Fock matrix; the
-  // energy of the first iterations oscillates too much to judge by |dE|); or after half the
-  // iteration budget.
+  // energy of the first iterations oscillates too much to judge by |dE|); or after three
+  // quarters of the iteration budget.
   bool stalled = false;
   if (!M.switched) {
     if (h.emax < 0.9 * M.best_err) {
@@ -684,7 +684,7 @@ static bool scf_iter_finish(ScfMol& M) {
     } else {
       M.stall++;
     }
-    stalled = (M.stall >= 5 && M.best_err < 1e-2) || M.res.iterations >= M.opt.max_cycle / 2;
+    stalled = (M.stall >= 5 && M.best_err < 1e-2) || 4 * M.res.iterations >= 3 * M.opt.max_cycle;
   }
   if (!M.switched && M.have_old && (de < M.opt.switch_tol || h.emax < M.opt.switch_err || stalled)) {
     // The DIIS history is kept: the mixed-precision Fock matrices are close to the FP64

@@ -6,11 +6,11 @@
 // stored as NP BF16 planes, p0 = x rounded to 8 bits on a power-of-two grid fixed along the
 // row (an integer in [-128, 128] times the row's scale), p1 = RN_bf16(x - p0),
 // p2 = RN_bf16(x - p0 - p1).  A product is formed from the plane products pa*qb with
-// a + b < NP; the products of each order a + b go to an FP32 accumulator of their own in
-// tensor memory (TMEM).  Order 0 (p0*q0) sums integers on one grid and is exact in FP32;
-// orders 1 and 2 are 2^-8 and 2^-16 smaller, so their rounding stays below 2^-24 of the
-// result.  With a single accumulator the FP32 rounding of long sums with cancellation,
-// not the operand split, limits the accuracy.  NP = 2: three products; NP = 3: six.
+// a + b < NP in two FP32 accumulators in tensor memory (TMEM): order 0 (p0*q0) sums
+// integers on one grid and is exact in FP32; the higher orders are at most 2^-8 of it, so
+// their rounding stays near 2^-32 of the result.  With a single accumulator the FP32
+// rounding of long sums with cancellation, not the operand split, limits the accuracy.
+// NP = 3: six products; NP = 4: ten.
 //
 //   half-transform:  X[(P,m), i] = sum_n B[(P,m), n] C^T[i, n]     (A = B planes, B = C^T)
 //   exchange SYRK:   K[m, n]     = sum_(P,i) X[m, (P,i)] X[n, (P,i)] (A = B = X, lower tiles)
@@ -160,12 +160,17 @@ struct Params {
   int* err;
 };
 
-__device__ __forceinline__ void lower_tile(int t, int& mt, int& nt) {
-  int m = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
-  while (m * (m + 1) / 2 > t) --m;
-  while ((m + 1) * (m + 2) / 2 <= t) ++m;
+// Tile t of the lower triangle in row blocks of 128 and column blocks of 128 * wide: row
+// block mt needs (mt + wide) / wide column blocks to reach its diagonal.
+__host__ __device__ __forceinline__ int lower_tiles_in_row(int mt, int wide) { return (mt + wide) / wide; }
+__device__ __forceinline__ void lower_tile(int t, int wide, int& mt, int& nt) {
+  int m = 0;
+  while (t >= lower_tiles_in_row(m, wide)) {
+    t -= lower_tiles_in_row(m, wide);
+    ++m;
+  }
   mt = m;
-  nt = t - m * (m + 1) / 2;
+  nt = t;
 }
 
 // Tensor maps of the operand planes (A planes, then B planes); entries >= NP unused.
@@ -195,9 +200,9 @@ __global__ void __launch_bounds__(THREADS, 1) split_bf16_gemm_kernel(const __gri
     nkb = p.num_kb;
   } else {
     int mt, nt;
-    lower_tile(blockIdx.x, mt, nt);
+    lower_tile(blockIdx.x, p.N / BM, mt, nt);
     row0 = mt * BM;
-    col0 = nt * BM;
+    col0 = nt * p.N;
     split = blockIdx.y;
     kb0 = split * p.kb_per_split;
     nkb = min(p.kb_per_split, p.num_kb - kb0);
@@ -208,7 +213,7 @@ __global__ void __launch_bounds__(THREADS, 1) split_bf16_gemm_kernel(const __gri
   uint8_t* ring = dyn_smem + pad;
   const uint32_t a_bytes = BM * BK * 2;
   uint32_t ncols = 32;
-  while ((int)ncols < NP * p.N) ncols <<= 1;  // one accumulator of N columns per product order
+  while ((int)ncols < 2 * p.N) ncols <<= 1;  // accumulators of N columns: order 0, higher orders
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < p.stages; ++s) {
@@ -276,13 +281,14 @@ __global__ void __launch_bounds__(THREADS, 1) split_bf16_gemm_kernel(const __gri
 #pragma unroll
       for (int kk = 0; kk < BK / 16; ++kk) {
         uint64_t off = (uint64_t)(kk * 32) >> 4;  // 16 bf16 = 32 bytes along K inside the swizzle row
-        // plane products of order t = a + b into accumulator t: (0,0); (0,1) (1,0); (0,2) (1,1) (2,0)
+        // plane products of order t = a + b: (0,0) into accumulator 0; (0,1) (1,0), (0,2) (1,1)
+        // (2,0), ... into accumulator 1
 #pragma unroll
         for (int t = 0; t < NP; ++t)
 #pragma unroll
           for (int a = 0; a <= t; ++a)
-            umma_bf16(tmem + (uint32_t)(t * p.N), ad[a] + off, bd[t - a] + off, idesc,
-                      (i > 0 || kk > 0 || a > 0) ? 1u : 0u);
+            umma_bf16(tmem + (uint32_t)(t > 0 ? p.N : 0), ad[a] + off, bd[t - a] + off, idesc,
+                      (i > 0 || kk > 0 || (t > 1 || a > 0)) ? 1u : 0u);
       }
       umma_commit(&empty_bar[s]);  // slot reusable once these MMAs have read it
     }
@@ -299,18 +305,14 @@ __global__ void __launch_bounds__(THREADS, 1) split_bf16_gemm_kernel(const __gri
       float lmax = 0.0f;
       for (int c = 0; c < p.N; c += 16) {
         if (p.mode == HALF_TRANSFORM && col0 + c >= p.ncx) break;  // column tiles past ncpad
-        uint32_t v[NP][16];
+        if (p.mode == SYRK && col0 + c >= p.npad) break;            // last wide tile past npad
+        uint32_t v[2][16];
 #pragma unroll
-        for (int t = 0; t < NP; ++t) tmem_ld_x16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(t * p.N + c), v[t]);
+        for (int t = 0; t < 2; ++t) tmem_ld_x16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(t * p.N + c), v[t]);
         tmem_wait_ld();
         float x[16];
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          float acc = __uint_as_float(v[NP - 1][j]);  // smallest order first
-#pragma unroll
-          for (int t = NP - 2; t >= 0; --t) acc += __uint_as_float(v[t][j]);
-          x[j] = acc;
-        }
+        for (int j = 0; j < 16; ++j) x[j] = __uint_as_float(v[0][j]) + __uint_as_float(v[1][j]);
         if (p.mode == HALF_TRANSFORM) {
           int P = grow / p.npad, m = grow % p.npad;
           float4* dst = reinterpret_cast<float4*>(p.X32 + (size_t)m * p.ldx + (size_t)P * p.ncx + col0 + c);
@@ -419,14 +421,28 @@ __global__ void __launch_bounds__(256) pack_ct_kernel(const double* __restrict__
   }
 }
 
-// X [npad][kdim] (FP32) into row-scaled planes, the scale of row m from xmax[m].
-__global__ void x_to_planes_kernel(const float* __restrict__ X, const unsigned* __restrict__ xmax, long kdim,
-                                   long n, int planes, PlanePtrs out) {
-  for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x) {
-    const float sig = row_scale_f(__uint_as_float(xmax[e / kdim]));
-    __nv_bfloat16 q[4];
-    split_row_value_f(X[e], sig, q);
-    for (int j = 0; j < planes; ++j) out.p[j][e] = q[j];
+// X [npad][kdim] (FP32) into row-scaled planes, the scale of row m from xmax[m].  Row m is
+// blockIdx.y; four consecutive elements per thread (kdim is a multiple of 16).
+template <int NP>
+__global__ void __launch_bounds__(256) x_to_planes_kernel(const float* __restrict__ X,
+                                                          const unsigned* __restrict__ xmax, long kdim,
+                                                          PlanePtrs out) {
+  const int m = blockIdx.y;
+  const float sig = row_scale_f(__uint_as_float(xmax[m]));
+  const size_t row = (size_t)m * kdim;
+  for (long c = ((long)blockIdx.x * blockDim.x + threadIdx.x) * 4; c < kdim; c += (long)gridDim.x * blockDim.x * 4) {
+    const float4 x = *reinterpret_cast<const float4*>(X + row + c);
+    const float xs[4] = {x.x, x.y, x.z, x.w};
+    __align__(8) __nv_bfloat16 q[NP][4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      __nv_bfloat16 t[kPlanesMax];
+      split_row_value_f(xs[u], sig, t);
+#pragma unroll
+      for (int j = 0; j < NP; ++j) q[j][u] = t[j];
+    }
+#pragma unroll
+    for (int j = 0; j < NP; ++j) *reinterpret_cast<uint2*>(out.p[j] + row + c) = *reinterpret_cast<uint2*>(q[j]);
   }
 }
 
@@ -445,14 +461,25 @@ __global__ void kmixed_reduce_kernel(const float* __restrict__ Kpart, int nsplit
 
 static int mixed_ncpad(int nocc) { return std::max(16, (nocc + 15) / 16 * 16); }
 
-static int mixed_nsplit(int npad, int naux, int ncpad, int bk) {
+// Columns of an exchange SYRK tile: 256 for four planes (the 32-element K boxes leave room
+// for two stages of a 128 x 256 tile), else 128.
+static int syrk_n(int planes) { return planes >= 4 ? 256 : 128; }
+
+static int syrk_tiles(int npad, int planes) {
+  int t = 0;
+  for (int mt = 0; mt < npad / umma::BM; ++mt) t += umma::lower_tiles_in_row(mt, syrk_n(planes) / umma::BM);
+  return t;
+}
+
+static int mixed_nsplit(int npad, int naux, int ncpad, int planes) {
+  const int bk = umma::bk_of(planes);
   long kdim = (long)naux * ncpad;
   long nkb = (kdim + bk - 1) / bk;
-  int tiles = (npad / umma::BM) * (npad / umma::BM + 1) / 2;
-  // FP32 accumulation length per split <= ~16k terms, and several waves of CTAs
+  int tiles = syrk_tiles(npad, planes);
+  // several waves of CTAs; splits of at most ~16k terms
   long want = std::max<long>((kdim + 16383) / 16384, (4L * 152 + tiles - 1) / tiles);
   if (knob("syrk_split") > 0) want = knob("syrk_split");
-  return (int)std::max<long>(1, std::min<long>(want, std::min<long>(nkb, 256)));
+  return (int)std::max<long>(1, std::min<long>(want, std::min<long>(nkb, 1024)));
 }
 
 // Raise the tensor-core kernel's dynamic shared-memory limit once, before any launch can
@@ -476,7 +503,7 @@ void mixed_k_work_layout(int nao, int naux, int nocc, Arena* a, Sizer* z, MixedK
   int npad = nao_pad(nao);
   int ncpad = mixed_ncpad(std::max(nocc, 1));
   w->planes = mixed_planes();
-  int nsplit = mixed_nsplit(npad, naux, ncpad, umma::bk_of(w->planes));
+  int nsplit = mixed_nsplit(npad, naux, ncpad, w->planes);
   w->ncpad = ncpad;
   w->nsplit = nsplit;
   size_t xsize = (size_t)npad * naux * ncpad;
@@ -523,8 +550,8 @@ int build_K_mixed(const void* B, const BLayout& L, int nao, int naux, const doub
   }
   pack_ct_kernel<<<(unsigned)ncpad, 256, 0, s>>>(C, nao, nocc, npad, NP, cpp);
   DF_LAUNCHED("pack_ct_kernel");
-  // column tiles of the half transform: NP accumulators of N columns fit in 512 TMEM columns
-  const int maxN = std::min(256, (512 / NP) / 16 * 16);
+  // column tiles of the half transform: two accumulators of N columns in 512 TMEM columns
+  const int maxN = 256;
   const int ntc = (ncpad + maxN - 1) / maxN;
   const int Nht = ((ncpad + ntc - 1) / ntc + 15) / 16 * 16;
   const char* base = (const char*)B;
@@ -554,27 +581,30 @@ int build_K_mixed(const void* B, const BLayout& L, int nao, int naux, const doub
     else DF_TRY(launch_gemm<3>(maps, p, dim3((unsigned)mtiles, (unsigned)ntc), s));
   }
   {
-    long nx = (long)npad * naux * ncpad;
+    const long kd = (long)naux * ncpad;
+    DF_REQUIRE(npad <= 65535, DF_ERR_ARG, "mixed K: npad %d too large", npad);
     ProfScope ps("k_x_planes", s);
-    x_to_planes_kernel<<<(unsigned)std::min<long>((nx + 255) / 256, 152L * 64), 256, 0, s>>>(
-        w.X32, w.xmax, (long)naux * ncpad, nx, NP, xpp);
+    dim3 grid((unsigned)std::min<long>((kd / 4 + 255) / 256, 64L), (unsigned)npad);
+    if (NP == 4) x_to_planes_kernel<4><<<grid, 256, 0, s>>>(w.X32, w.xmax, kd, xpp);
+    else x_to_planes_kernel<3><<<grid, 256, 0, s>>>(w.X32, w.xmax, kd, xpp);
     DF_LAUNCHED("x_to_planes_kernel");
   }
-  // exchange SYRK: A = B = X [m][(P, i)], lower 128 x 128 tiles, split over (P, i)
+  // exchange SYRK: A = B = X [m][(P, i)], lower tiles of 128 x syrk_n, split over (P, i)
   long kdim = (long)naux * ncpad;
+  const int ns = syrk_n(NP);
   for (int j = 0; j < NP; ++j) {
     DF_TRY(make_map(&maps.a[j], w.Xp[j], kdim, npad, kdim, umma::BM, bk));
-    maps.b[j] = maps.a[j];
+    DF_TRY(make_map(&maps.b[j], w.Xp[j], kdim, npad, kdim, ns, bk));
   }
   umma::Params q{};
   q.mode = umma::SYRK;
-  q.N = umma::BM;
+  q.N = ns;
   q.num_kb = (int)((kdim + bk - 1) / bk);
   q.kb_per_split = (q.num_kb + w.nsplit - 1) / w.nsplit;
   int nsplit = (q.num_kb + q.kb_per_split - 1) / q.kb_per_split;
   q.npad = npad;
   q.Kpart = w.Kpart;
-  q.n_lower_tiles = (npad / umma::BM) * (npad / umma::BM + 1) / 2;
+  q.n_lower_tiles = syrk_tiles(npad, NP);
   q.err = w.err;
   {
     ProfScope ps("k_syrk_tc", s);
