@@ -158,7 +158,7 @@ int df_eigh_lowest(double* A, int n, int k, double* w, double* Z, void* work, si
  *   extrapolation over <= diis_space vectors, aufbau occupation of nocc = nelec/2.
  * Converged when |dE| < conv_tol and max|e| < conv_err.  In DF_MIXED mode the loop runs
  * with mixed-precision K until |dE| < switch_tol or max|e| < switch_err, or until max|e|,
- * once below 1e-2, has not improved by 10% for 5 iterations (the mixed-precision floor), or
+ * once below 1e-3, has not improved by 10% for 10 iterations (the mixed-precision floor), or
  * for three quarters of max_cycle; then at least n_fp64_final FP64 iterations follow and the
  * reported energy is the FP64 one.
  * dm0 (device [nao][nao], may be NULL): initial density; it need not be idempotent nor
@@ -189,8 +189,8 @@ typedef struct {
   double conv_tol;    /* |dE| threshold                         (1e-8)          */
   double conv_err;    /* max|e| threshold                       (1e-5)          */
   double lindep;      /* canonical orthogonalisation cut        (1e-8)          */
-  double switch_tol;  /* mixed -> FP64 switch on |dE|           (1e-7)          */
-  double switch_err;  /* mixed -> FP64 switch on max|e|         (1e-4)          */
+  double switch_tol;  /* mixed -> FP64 switch on |dE|           (3e-8)          */
+  double switch_err;  /* mixed -> FP64 switch on max|e|         (3e-5)          */
   int verbose;        /* print one line per iteration to stdout (0)             */
 } scf_opts;
 

@@ -91,9 +91,9 @@ __device__ void tridiagonalize_cta(double* __restrict__ A, int n, double* __rest
     d[k] = A[(size_t)k * n + k];
     e[k] = alpha;
     if (tid == 0) beta[k] = b;
+    const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
     if (b != 0.0) {
       // p = b * A22 v  (one warp per row)
-      int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
       for (int i = wid; i < len; i += nw) {
         const double* row = A + (size_t)(k + 1 + i) * n + k + 1;
         double s = 0.0;
@@ -107,9 +107,11 @@ __device__ void tridiagonalize_cta(double* __restrict__ A, int n, double* __rest
       double K = 0.5 * b * cta_sum(pv, sh);
       for (int i = tid; i < len; i += nt) sn[i] = cs[i] - K * v[i];  // w
       __syncthreads();
-      for (long q = tid; q < (long)len * len; q += nt) {
-        int i = (int)(q / len), j = (int)(q % len);
-        A[(size_t)(k + 1 + i) * n + k + 1 + j] -= v[i] * sn[j] + sn[i] * v[j];
+      // rank-2 update, one warp per row, lanes along the row
+      for (int i = wid; i < len; i += nw) {
+        double* row = A + (size_t)(k + 1 + i) * n + k + 1;
+        const double vi = v[i], wi = sn[i];
+        for (int j = lane; j < len; j += 32) row[j] -= vi * sn[j] + wi * v[j];
       }
     }
     // keep the reflector in column k below the diagonal
@@ -453,17 +455,45 @@ __device__ int eigh_lowest_cta(double* __restrict__ A, int n, int k, double* __r
   double* ee = v;  // the reduction's work vector is free now
   for (int i = tid; i + 1 < n; i += nt) ee[i] = e[i] * e[i];
   __syncthreads();
-  for (int t = tid; t < k; t += nt) {
-    double lo = glo - 2.0 * DBL_EPSILON * tnorm, hi = ghi + 2.0 * DBL_EPSILON * tnorm;
-    for (int it = 0; it < 200; ++it) {
-      double mid = 0.5 * (lo + hi);
-      if (sturm_count(d, ee, n, mid, pivmin) > t) hi = mid;
-      else lo = mid;
-      if (hi - lo <= 2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)) + pivmin) break;
+  // eigenvalues: groups of G lanes per eigenvalue split the bracket (G+1)-way per round; G is
+  // chosen so that about four warps work (one per FP64 pipe of the SM)
+  int G = 1;
+  while (G < 32 && k * (2 * G) <= 128) G *= 2;
+  {
+    const int lane = tid & 31, sub = tid % G, base = lane - sub;
+    const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << base);
+    for (int t0 = tid / G; t0 - (lane / G) < k; t0 += nt / G) {  // every lane of a warp iterates together
+      const int t = t0;
+      const bool live = t < k;
+      double lo = glo - 2.0 * DBL_EPSILON * tnorm, hi = ghi + 2.0 * DBL_EPSILON * tnorm;
+      bool done = !live;
+      for (int round = 0; round < 200; ++round) {
+        if (!done && hi - lo <= 2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)) + pivmin) done = true;
+        if (__all_sync(0xffffffffu, done)) break;
+        const double h = (hi - lo) / (double)(G + 1);
+        const double xj = fmin(lo + (double)(sub + 1) * h, hi);
+        const bool up = live && sturm_count(d, ee, n, xj, pivmin) > t;
+        const unsigned above = (__ballot_sync(0xffffffffu, up) & gmask) >> base;
+        const double xlast = __shfl_sync(0xffffffffu, xj, base + G - 1);
+        const int j = above ? __ffs(above) - 1 : 0;
+        const double xhi = __shfl_sync(0xffffffffu, xj, base + j);
+        const double xlo = __shfl_sync(0xffffffffu, xj, base + (j > 0 ? j - 1 : 0));
+        if (!done) {
+          if (above == 0u) {
+            lo = xlast;
+          } else {
+            if (j > 0) lo = xlo;
+            hi = xhi;
+          }
+        }
+      }
+      if (live && sub == 0) w[t] = 0.5 * (lo + hi);
     }
-    double lam = 0.5 * (lo + hi);
-    w[t] = lam;
-    bool ok = inverse_iteration(d, e, n, lam, tnorm, t, k, lu, lu + (size_t)n * k, lu + 2 * (size_t)n * k,
+  }
+  __syncthreads();
+  // eigenvectors of T: inverse iteration, one lane per eigenvalue
+  for (int t = tid; t < k; t += nt) {
+    bool ok = inverse_iteration(d, e, n, w[t], tnorm, t, k, lu, lu + (size_t)n * k, lu + 2 * (size_t)n * k,
                                 lu + 3 * (size_t)n * k, lu + 4 * (size_t)n * k, x);
     if (!ok) atomicExch(&sh.flag, 1);
   }

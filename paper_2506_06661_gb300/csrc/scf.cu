@@ -672,10 +672,11 @@ static bool scf_iter_finish(ScfMol& M) {
   // orbital energies of the diagonalisation that produced the next density
   M.res.homo = h.homo;
   M.res.lumo = h.lumo;
-  // Mixed phase: switch on the thresholds; or when the DIIS error, already below 1e-2, has
-  // not improved by 10% for 5 iterations (the floor of the mixed-precision Fock matrix; the
-  // energy of the first iterations oscillates too much to judge by |dE|); or after three
-  // quarters of the iteration budget.
+  // Mixed phase: switch on the thresholds; or when the DIIS error, already below 1e-3, has
+  // not improved by 10% for 10 iterations (the floor of the mixed-precision Fock matrix; the
+  // energy of the first iterations oscillates too much to judge by |dE|, and slowly
+  // converging systems plateau for several iterations in FP64 too); or after three quarters
+  // of the iteration budget.
   bool stalled = false;
   if (!M.switched) {
     if (h.emax < 0.9 * M.best_err) {
@@ -684,7 +685,7 @@ static bool scf_iter_finish(ScfMol& M) {
     } else {
       M.stall++;
     }
-    stalled = (M.stall >= 5 && M.best_err < 1e-2) || 4 * M.res.iterations >= 3 * M.opt.max_cycle;
+    stalled = (M.stall >= 10 && M.best_err < 1e-3) || 4 * M.res.iterations >= 3 * M.opt.max_cycle;
   }
   if (!M.switched && M.have_old && (de < M.opt.switch_tol || h.emax < M.opt.switch_err || stalled)) {
     // The DIIS history is kept: the mixed-precision Fock matrices are close to the FP64
@@ -762,8 +763,8 @@ extern "C" void scf_default_opts(scf_opts* o) {
   o->conv_tol = 1e-8;
   o->conv_err = 1e-5;
   o->lindep = 1e-8;
-  o->switch_tol = 1e-7;
-  o->switch_err = 1e-4;
+  o->switch_tol = 3e-8;
+  o->switch_err = 3e-5;
   o->verbose = 0;
 }
 
@@ -897,6 +898,10 @@ extern "C" int scf_run_batch(const df_molecule* mols, int nmol, const scf_opts* 
     slot_mol[k] = M;
     slot_index[k] = i;
     DF_TRY(init_mol(*M, &mols[i], o, (char*)work + per_slot * k, per_slot, streams[k]));
+    // With several slots each molecule diagonalises on one CTA: many one-CTA eigensolvers
+    // fill the SMs in parallel, while cooperative grids from different streams (one CTA per
+    // SM each) would contend for co-residency.
+    if (slots > 1) M->W.eig_aux = nullptr;
     M->hst = hst + k;
     M->h_eps = heps + (size_t)(max_nao + 1) * k;
     M->h_ints = hints + 2 * k;
