@@ -333,7 +333,7 @@ def run_ours(args):
             if r:
                 rlm[name] = r
         mixed = {"value": ws * 1000.0 / msm, "unit": "builds/s", "ms_per_step": msm, "steps": args.mixed_steps,
-                 "dtype": f"bf16 planes x{planes}, {products} products, fp32 accumulator per order (K); f64 (J)",
+                 "dtype": f"bf16 planes x{planes}, {products} products, fp32 accumulators: exact order 0 + higher orders (K); f64 (J)",
                  "rel_err_vs_fp64": {"J": errj, "K": errk},
                  "kernels": rlm, "gpu_launches": LAUNCHES_MIXED * args.mixed_steps, "clocks": clkm.summary(),
                  "phase_ms": {k: v[0] / max(v[1], 1) for k, v in profm.items()}}
@@ -440,7 +440,8 @@ def run_scenario_guess(args):
     from paper_2506_06661_gb300 import guess
     t0 = time.perf_counter()
     train = gen.batch_molecules(args.ntrain, 10, 40, 2)
-    res, Ds = guess.converged_densities(train, slots=args.slots, precision="fp64")
+    # mixed precision ends with FP64 iterations, so the densities are FP64-converged
+    res, Ds = guess.converged_densities(train, slots=args.slots, precision="mixed")
     ok = [i for i, r in enumerate(res) if r.converged]
     t_data = time.perf_counter() - t0
     X, Y, M = guess.build_dataset([train[i] for i in ok], [Ds[i] for i in ok])
@@ -456,7 +457,8 @@ def run_scenario_guess(args):
     ev = guess.evaluate(model, test, slots=args.slots, precision="mixed")
     out = {"scenario": "guess", "train_molecules": len(train), "train_converged": len(ok),
            "train_samples": int(M.sum().item()), "data_seconds": t_data, "train_seconds": t_train,
-           "epochs": args.epochs, "mse_first_last": [hist[0], hist[-1]], "eval": ev}
+           "epochs": args.epochs, "mse_first_last": [hist[0], hist[-1]], "eval_molecules": len(test),
+           "eval_centres": "40-120 (uniform, seed 3)", "eval": ev}
     print(json.dumps(out), flush=True)
     return 0
 

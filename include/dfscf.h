@@ -137,8 +137,11 @@ int df_jk(const void* B, int nao, int naux, int precision, const double* D, cons
 
 /* ---- a11: symmetric eigensolver ----------------------------------------------------
  * Eigenvalues w[0..n) ascending and eigenvectors (columns of Z, [n][n]) of the
- * symmetric matrix A [n][n] (A is overwritten).  Householder tridiagonalisation and
- * implicit QL.  work: df_eigh_work_bytes(n).                                           */
+ * symmetric matrix A [n][n] (A is overwritten).  Householder tridiagonalisation, then
+ * implicit QL on one thread block (n < 160), or for larger n the multi-SM path of
+ * df_eigh_lowest with k = n (Sturm multisection, inverse iteration, back-transformation,
+ * two Gram-Schmidt passes).  Synchronises the stream; DF_ERR_NOCONV if the solver breaks
+ * down.  work: df_eigh_work_bytes(n).                                                    */
 size_t df_eigh_work_bytes(int n);
 int df_eigh(double* A, int n, double* w, double* Z, void* work, size_t work_bytes, cudaStream_t s);
 

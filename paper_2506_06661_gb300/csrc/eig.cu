@@ -1097,6 +1097,18 @@ int eigh_lowest_rows(double* A, int n, int k, double* w, double* ZT, double* scr
   return DF_OK;
 }
 
+size_t eigh_full_scratch_doubles(int n) {
+  return std::max(eigh_scratch_doubles(n), eigh_lowest_scratch_doubles(n, n));
+}
+
+// Full spectrum: the multi-SM solver with k = n where it applies (aux given, n large enough),
+// else one CTA with implicit QL.  scratch: eigh_full_scratch_doubles(n).
+int eigh_full_rows(double* A, int n, double* w, double* ZT, double* scratch, int* status, cudaStream_t s,
+                   void* aux) {
+  if (aux && coop_plan(n, n).G >= 2) return eigh_lowest_rows(A, n, n, w, ZT, scratch, status, s, aux);
+  return eigh_rows(A, n, w, ZT, scratch, status, s);
+}
+
 int eigh_rows(double* A, int n, double* w, double* ZT, double* scratch, int* status, cudaStream_t s) {
   eigh_batched_kernel<<<1, 1024, 0, s>>>(A, n, 0, w, 0, ZT, 0, scratch, 0, status);
   DF_LAUNCHED("eigh_batched_kernel");
@@ -1110,9 +1122,10 @@ using namespace dfscf;
 extern "C" size_t df_eigh_work_bytes(int n) {
   if (n <= 0) return 0;
   Sizer z;
-  z.take<double>(eigh_scratch_doubles(n));
+  z.take<double>(eigh_full_scratch_doubles(n));
   z.take<double>((size_t)n * n);
   z.take<int>(1);
+  z.take<char>(eigh_coop_aux_bytes(n));
   return z.used;
 }
 
@@ -1121,15 +1134,16 @@ extern "C" int df_eigh(double* A, int n, double* w, double* Z, void* work, size_
   DF_REQUIRE(A && w && Z && n > 0, DF_ERR_ARG, "df_eigh: bad arguments");
   DF_REQUIRE(work && work_bytes >= df_eigh_work_bytes(n), DF_ERR_NOMEM, "df_eigh: workspace too small");
   Arena a(work, work_bytes);
-  double* scratch = a.take<double>(eigh_scratch_doubles(n));
+  double* scratch = a.take<double>(eigh_full_scratch_doubles(n));
   double* ZT = a.take<double>((size_t)n * n);
   int* status = a.take<int>(1);
-  DF_TRY(eigh_rows(A, n, w, ZT, scratch, status, s));
+  void* aux = a.take<char>(eigh_coop_aux_bytes(n));
+  DF_TRY(eigh_full_rows(A, n, w, ZT, scratch, status, s, aux));
   DF_TRY(transpose(ZT, n, n, Z, s));
   int h = 0;
   DF_CUDA(cudaMemcpyAsync(&h, status, sizeof(int), cudaMemcpyDeviceToHost, s));
   DF_CUDA(cudaStreamSynchronize(s));
-  DF_REQUIRE(h == 0, DF_ERR_NOCONV, "df_eigh: QL iteration did not converge");
+  DF_REQUIRE(h == 0, DF_ERR_NOCONV, "df_eigh: eigensolver failed (status %d)", h);
   return DF_OK;
 }
 

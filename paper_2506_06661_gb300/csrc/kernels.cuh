@@ -28,6 +28,8 @@ size_t eigh_scratch_doubles(int n);
 int eigh_rows(double* A, int n, double* w, double* ZT, double* scratch, int* status, cudaStream_t s);
 size_t eigh_lowest_scratch_doubles(int n, int k);
 size_t eigh_coop_aux_bytes(int n);
+size_t eigh_full_scratch_doubles(int n);
+int eigh_full_rows(double* A, int n, double* w, double* ZT, double* scratch, int* status, cudaStream_t s, void* aux);
 int eigh_lowest_rows(double* A, int n, int k, double* w, double* ZT, double* scratch, int* status, cudaStream_t s,
                      void* aux);
 int transpose(const double* in, int rows, int cols, double* out, cudaStream_t s);

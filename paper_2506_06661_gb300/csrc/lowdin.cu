@@ -32,8 +32,9 @@ extern "C" size_t df_lowdin_work_bytes(int nao) {
   z.take<double>((size_t)nao * nao);  // eigenvector rows
   z.take<double>((size_t)nao * nao);  // scaled rows
   z.take<double>(nao);                // eigenvalues
-  z.take<double>(eigh_scratch_doubles(nao));
+  z.take<double>(eigh_full_scratch_doubles(nao));
   z.take<int>(1);
+  z.take<char>(eigh_coop_aux_bytes(nao));
   return z.used;
 }
 
@@ -47,11 +48,12 @@ extern "C" int df_lowdin_factors(const double* ao_xyz, const double* ao_exp, int
   double* ZT = a.take<double>((size_t)nao * nao);
   double* W = a.take<double>((size_t)nao * nao);
   double* w = a.take<double>(nao);
-  double* scr = a.take<double>(eigh_scratch_doubles(nao));
+  double* scr = a.take<double>(eigh_full_scratch_doubles(nao));
   int* status = a.take<int>(1);
+  void* aux = a.take<char>(eigh_coop_aux_bytes(nao));
   const long nn = (long)nao * nao;
   DF_TRY(launch_int1e(ao_xyz, ao_exp, nao, nullptr, nullptr, 0, S, nullptr, nullptr, s));
-  DF_TRY(eigh_rows(S, nao, w, ZT, scr, status, s));
+  DF_TRY(eigh_full_rows(S, nao, w, ZT, scr, status, s, aux));
   // S^p = sum_k u_k s_k^p u_k^T = ZT^T diag(s^p) ZT
   if (Shalf) {
     scaled_rows_kernel<<<nblk(nn), 256, 0, s>>>(ZT, w, nao, lindep, 0.5, W);

@@ -347,7 +347,7 @@ static void scf_layout(int nao, int naux, int nocc, int precision, Arena* a, Siz
   TAKE(double, w->Ehist, DIIS_MAX * nn);
   TAKE(double, w->G, DIIS_MAX * DIIS_MAX);
   TAKE(double, w->coef, DIIS_MAX);
-  TAKE(double, w->eig_scratch, std::max(eigh_scratch_doubles(nao), eigh_lowest_scratch_doubles(nao, nocc + 1)));
+  TAKE(double, w->eig_scratch, eigh_full_scratch_doubles(nao));
   TAKE(double, w->enuc, 1);
   TAKE(double, w->maxdiag, 1);
   TAKE(int, w->eig_status, 1);
@@ -362,7 +362,7 @@ static void scf_layout(int nao, int naux, int nocc, int precision, Arena* a, Siz
 }
 
 static int eig_rows(double* A, int n, double* w, double* ZT, ScfWork& W, cudaStream_t s) {
-  return eigh_rows(A, n, w, ZT, W.eig_scratch, W.eig_status, s);
+  return eigh_full_rows(A, n, w, ZT, W.eig_scratch, W.eig_status, s, W.eig_aux);
 }
 
 // Occupied coefficients from a Fock-like matrix: C_occ = X C'_occ, D = 2 C C^T.
@@ -1007,7 +1007,7 @@ static void guess_layout(int nao, int nocc, Arena* a, Sizer* z, ScfWork* w) {
   TAKE(double, w->Fp, nn);
   TAKE(double, w->ZT, nn);
   TAKE(double, w->eps, nao);
-  TAKE(double, w->eig_scratch, std::max(eigh_scratch_doubles(nao), eigh_lowest_scratch_doubles(nao, nocc + 1)));
+  TAKE(double, w->eig_scratch, eigh_full_scratch_doubles(nao));
   TAKE(int, w->eig_status, 1);
   TAKE(char, w->eig_aux, eigh_coop_aux_bytes(nao));
   TAKE(double, w->Cocc, (size_t)nao * std::max(nocc, 1));

@@ -124,7 +124,7 @@ def test_jk_only_j_or_only_k(c0, c0_system, c0_gpu_B):
     assert J is None and rel(K, oracle.df_k(c0_system.B, c0.nao, C)) <= 1e-10
 
 
-@pytest.mark.parametrize("n", [1, 2, 3, 7, 64, 129])
+@pytest.mark.parametrize("n", [1, 2, 3, 7, 64, 129, 200, 400])
 def test_eigh_matches_library(n):
     rng = np.random.default_rng(n)
     A = rng.standard_normal((n, n))
@@ -135,6 +135,26 @@ def test_eigh_matches_library(n):
     assert np.max(np.abs(w - wr)) <= 1e-12 * max(1.0, np.max(np.abs(wr)))
     assert np.max(np.abs(A @ Z - Z * w)) <= 1e-11 * max(1.0, np.max(np.abs(wr)))
     assert np.max(np.abs(Z.T @ Z - np.eye(n))) <= 1e-12
+
+
+def test_eigh_full_spectrum_multi_sm_overlap():
+    """Full spectrum above n = 160 runs on the multi-SM path: the overlap matrix of the
+    80-centre molecule (eigenvalues from ~1e-5 to ~10, small ones clustered) and a
+    density of rank 31 (a 269-fold zero eigenvalue)."""
+    mol = gen.make_molecule(80, gen.molecules.box_for(80), 0)
+    _, _, S, *_ = dfscf.core_guess(mol)
+    S = S.cpu().numpy()
+    rng = np.random.default_rng(31)
+    C = 0.3 * rng.standard_normal((300, 31))
+    for A in (S, 2 * C @ C.T):
+        n = A.shape[0]
+        w, Z = dfscf.eigh(A)
+        w, Z = w.cpu().numpy(), Z.cpu().numpy()
+        wr = np.linalg.eigvalsh(A)
+        scale = max(1.0, np.max(np.abs(wr)))
+        assert np.max(np.abs(w - wr)) <= 1e-12 * scale
+        assert np.max(np.abs(A @ Z - Z * w)) <= 1e-11 * scale
+        assert np.max(np.abs(Z.T @ Z - np.eye(n))) <= 1e-11
 
 
 def test_scf_fp64_matches_oracle(c0, c0_scf):
@@ -195,6 +215,27 @@ def test_eigh_lowest_matches_library(n, k):
     wr = np.linalg.eigvalsh(A)[:k]
     scale = max(1.0, np.max(np.abs(np.linalg.eigvalsh(A))))
     assert np.max(np.abs(w - wr)) <= 1e-12 * scale
+    assert np.max(np.abs(A @ Z - Z * w)) <= 1e-10 * scale
+    assert np.max(np.abs(Z.T @ Z - np.eye(k))) <= 1e-12
+
+
+@pytest.mark.parametrize("n,k,ctas", [(257, 40, 1), (120, 100, 1), (300, 31, 4), (200, 21, 152)])
+def test_eigh_lowest_forced_launch_shapes(n, k, ctas):
+    """The one-CTA solver at sizes the default picks the cooperative grid for (grouped Sturm
+    multisection with 2 and 1 lanes per eigenvalue), and cooperative grids of 4 and 152 CTAs."""
+    lib = dfscf.lib()
+    lib.df_tune_set(b"eig_ctas", ctas)
+    try:
+        rng = np.random.default_rng(n * k)
+        A = rng.standard_normal((n, n))
+        A = A + A.T
+        w, Z = dfscf.eigh_lowest(A, k)
+    finally:
+        lib.df_tune_set(b"eig_ctas", 0)
+    w, Z = w.cpu().numpy(), Z.cpu().numpy()
+    ev = np.linalg.eigvalsh(A)
+    scale = max(1.0, np.max(np.abs(ev)))
+    assert np.max(np.abs(w - ev[:k])) <= 1e-12 * scale
     assert np.max(np.abs(A @ Z - Z * w)) <= 1e-10 * scale
     assert np.max(np.abs(Z.T @ Z - np.eye(k))) <= 1e-12
 
