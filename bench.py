@@ -271,6 +271,18 @@ def run_ours(args):
     t_setup = time.perf_counter() - t_setup
     nao, naux, nocc = mol.nao, mol.naux, mol.nocc
     npair = nao * (nao + 1) // 2
+    # launch knobs: the autotuner's cached winners for this size bucket (or a fresh tuning
+    # with --tune, stored in the cache), else the library defaults
+    from paper_2506_06661_gb300 import tune
+    knobs = {}
+    for prec in ("fp64", "mixed") if args.mixed else ("fp64",):
+        key = tune.bucket(nao, naux, nocc, prec)
+        if args.tune:
+            res = tune.tune_and_store(B, D, C, nocc, prec)
+            knobs[prec] = {"bucket": key, "source": "tuned now", **res["knobs"]}
+        else:
+            got = tune.apply(key)
+            knobs[prec] = {"bucket": key, "source": "tune cache" if got else "defaults", **got}
     work64 = dfscf.JKWorkspace(nao, naux, nocc, "fp64")
 
     with ClockSampler(local) as clk:
@@ -294,6 +306,16 @@ def run_ours(args):
         if r:
             rl[name] = r
     dominant = max(rl.values(), key=lambda r: r["avg_ms"] * r["launches"]) if rl else None
+    # DRAM traffic of the FP64 half-transform: the ncu capture on the 80-centre workload
+    # (profiles/ncu_exchange_kernels_80centres.md) read 771.98 MB and wrote 144.12 MB against
+    # 926.0 MB of algorithmic bytes (B read once, X written once); traffic grows with those
+    # bytes, so one launch here moves that ratio times its own algorithmic bytes
+    if dominant and dominant["kernel"] == "k_halftransform_fp64":
+        ht_bytes = 8.0 * naux * dfscf.lib().df_B_ld(nao) + 8.0 * nao * naux * nocc
+        m80_bytes = 8.0 * 1200 * dfscf.lib().df_B_ld(400) + 8.0 * 400 * 1200 * 40
+        dominant["traffic"] = (771.981056e6 + 144.117504e6) / m80_bytes * ht_bytes
+        dominant["traffic_source"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of the 80-centre capture, "
+                                      "scaled by the algorithmic bytes of this launch")
 
     e2e_ms, h2d, d2h = time_e2e(dfscf, torch, B, D, C, "fp64", args.e2e_steps, work64)
 
@@ -311,12 +333,13 @@ def run_ours(args):
         ncpad = max(16, (nocc + 15) // 16 * 16)
         planes = int(dfscf.lib().df_tune_get(b"mixed_planes"))
         products = planes * (planes + 1) // 2
-        max_n = min(256, (512 // planes) // 16 * 16)         # one TMEM accumulator per product order
+        bk = 32 if planes >= 4 else 64                       # K box of the tcgen05 ring
+        max_n = min(256, ((220 * 1024 // 2) // planes - 128 * bk * 2) // (bk * 2) // 16 * 16)
         ntc = -(-ncpad // max_n)
         nht = (-(-ncpad // ntc) + 15) // 16 * 16
         # tensor-core flops issued (padded tiles) and the algorithmic count of the same products
         tc_ht = products * 2.0 * naux * npad * npad * (nht * ntc)
-        syrk_n = 256 if planes >= 4 else 128                  # 128 x syrk_n lower tiles
+        syrk_n = 128                                          # 128 x 128 lower tiles (4 accumulators)
         wide = syrk_n // 128
         syrk_tiles = sum((mt + wide) // wide for mt in range(npad // 128))
         tc_syrk = products * 2.0 * (naux * ncpad) * (128 * syrk_n) * syrk_tiles
@@ -333,7 +356,7 @@ def run_ours(args):
             if r:
                 rlm[name] = r
         mixed = {"value": ws * 1000.0 / msm, "unit": "builds/s", "ms_per_step": msm, "steps": args.mixed_steps,
-                 "dtype": f"bf16 planes x{planes}, {products} products, fp32 accumulators: exact order 0 + higher orders (K); f64 (J)",
+                 "dtype": f"bf16 planes x{planes}, {products} products, two fixed-point planes, exact fp32 sums of their products (K); f64 (J)",
                  "rel_err_vs_fp64": {"J": errj, "K": errk},
                  "kernels": rlm, "gpu_launches": LAUNCHES_MIXED * args.mixed_steps, "clocks": clkm.summary(),
                  "phase_ms": {k: v[0] / max(v[1], 1) for k, v in profm.items()}}
@@ -342,6 +365,7 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": ms64, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": desc, "precision": "fp64", "step": "one Fock build: J[D] and K[C_occ]",
+                       "knobs": knobs,
                        "l2": "inputs larger than L2 (B is %.1f GB)" % (8.0 * naux * npair / 1e9),
                        "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
             "roofline": ({k: v for k, v in dominant.items() if k not in ("avg_ms", "launches")} | {"peak_source": (
@@ -408,14 +432,24 @@ def run_scenario_batch(args):
     import torch
     import gen
     import paper_2506_06661_gb300 as dfscf
+    from paper_2506_06661_gb300 import tune
     mols = gen.batch_molecules(args.nmol, 10, 80, 1)
     devs = [dfscf.MoleculeOnDevice(m) for m in mols]
+    slots, src = args.slots, "command line"
+    if slots <= 0:
+        # molecules in flight: the autotuner's choice (cached, else measured on a sample now)
+        cached = tune.load_cache().get("batch:mixed")
+        if cached and not args.tune:
+            slots, src = int(cached["slots"]), "tune cache"
+        else:
+            t = tune.tune_batch_slots(mols, precision="mixed", candidates=(16, 32, 64), sample=64)
+            slots, src = int(t["slots"]), f"tuned now on 64 molecules: {t['molecules_per_s']}"
     out = {"scenario": "batch", "molecules": len(mols), "centres": "10-80 (uniform, seed 1)",
-           "nao_range": [min(m.nao for m in mols), max(m.nao for m in mols)], "slots": args.slots}
+           "nao_range": [min(m.nao for m in mols), max(m.nao for m in mols)], "slots": slots, "slots_source": src}
     for prec in ("mixed",) + (("fp64",) if args.batch_fp64 else ()):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        res = dfscf.scf_run_batch(devs, slots=args.slots, precision=prec, raise_on_noconv=False).results
+        res = dfscf.scf_run_batch(devs, slots=slots, precision=prec, raise_on_noconv=False).results
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
         conv = [r for r in res if r.converged]
@@ -441,7 +475,8 @@ def run_scenario_guess(args):
     t0 = time.perf_counter()
     train = gen.batch_molecules(args.ntrain, 10, 40, 2)
     # mixed precision ends with FP64 iterations, so the densities are FP64-converged
-    res, Ds = guess.converged_densities(train, slots=args.slots, precision="mixed")
+    slots = args.slots if args.slots > 0 else 32
+    res, Ds = guess.converged_densities(train, slots=slots, precision="mixed")
     ok = [i for i, r in enumerate(res) if r.converged]
     t_data = time.perf_counter() - t0
     X, Y, M = guess.build_dataset([train[i] for i in ok], [Ds[i] for i in ok])
@@ -454,7 +489,7 @@ def run_scenario_guess(args):
     if args.save_model:
         model.save(args.save_model)
     test = gen.batch_molecules(args.neval, 40, 120, 3)
-    ev = guess.evaluate(model, test, slots=args.slots, precision="mixed")
+    ev = guess.evaluate(model, test, slots=slots, precision="mixed")
     out = {"scenario": "guess", "train_molecules": len(train), "train_converged": len(ok),
            "train_samples": int(M.sum().item()), "data_seconds": t_data, "train_seconds": t_train,
            "epochs": args.epochs, "mse_first_last": [hist[0], hist[-1]], "eval_molecules": len(test),
@@ -480,7 +515,8 @@ def main():
     ap.add_argument("--max-cycle", type=int, default=200, help="SCF iteration budget (scf, batch scenarios)")
     ap.add_argument("--phases", action="store_true", help="scf scenario: add a profiled run per precision")
     ap.add_argument("--nmol", type=int, default=256)
-    ap.add_argument("--slots", type=int, default=32)
+    ap.add_argument("--slots", type=int, default=0, help="molecules in flight (0: the autotuner's choice)")
+    ap.add_argument("--tune", action="store_true", help="run the autotuner and store its winners in the cache")
     ap.add_argument("--batch-fp64", action="store_true")
     ap.add_argument("--ntrain", type=int, default=20000)
     ap.add_argument("--neval", type=int, default=512)

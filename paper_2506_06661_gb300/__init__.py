@@ -405,6 +405,13 @@ def scf_run_batch(mols, opts: ScfOpts | None = None, dm0s=None, slots: int = 16,
     slots = max(1, min(slots, n))
     nb = int(lib().scf_batch_work_bytes(arr, n, o.precision, slots))
     if work is None or work.numel() < nb:
+        # every slot is sized for the largest molecule: fewer slots when they do not fit in
+        # 85% of the free device memory
+        free = torch.cuda.mem_get_info()[0] + (work.numel() if work is not None else 0)
+        while slots > 1 and nb > 0.85 * free:
+            slots = max(1, slots * 3 // 4)
+            nb = int(lib().scf_batch_work_bytes(arr, n, o.precision, slots))
+    if work is None or work.numel() < nb:
         work = _work(nb)
     dm0_t = None
     dm0_arr = None

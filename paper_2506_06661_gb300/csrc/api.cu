@@ -128,7 +128,7 @@ static Knob g_knobs[] = {
     {"fp64_syrk_split", 0, 0, 4096}, // K-dimension splits of the FP64 exchange SYRK
     {"jpass2_rows", 256, 32, 512},   // auxiliary rows per CTA slice of J's second pass
     {"eig_ctas", 0, 0, 4096},        // CTAs of the multi-SM eigensolver (0 auto, 1 single CTA)
-    {"mixed_planes", 4, 3, 4},       // BF16 planes per operand of the mixed exchange (3: 6 products, 4: 10)
+    {"mixed_planes", 5, 3, 5},       // BF16 planes per operand of the mixed exchange (3, 4, 5: 6, 10, 15 products)
 };
 
 int knob(const char* name) {

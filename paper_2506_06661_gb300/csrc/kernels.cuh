@@ -36,7 +36,7 @@ int transpose(const double* in, int rows, int cols, double* out, cudaStream_t s)
 
 // ---- B layout and J/K (jk.cu, umma.cu) --------------------------------------------------
 // BF16 planes kept of B for the mixed exchange; kernels use the first mixed_planes of them.
-constexpr int kMixedPlanes = 4;
+constexpr int kMixedPlanes = 5;
 
 struct BLayout {
   long ld;       // packed row stride (elements)
@@ -47,7 +47,8 @@ struct BLayout {
 struct MixedKWork {
   void* Cp[kMixedPlanes];  // bf16 [ncpad][npad]  planes of C^T
   void* Xp[kMixedPlanes];  // bf16 [npad][naux * ncpad]  planes of X (row m, column P*ncpad + i)
-  float* X32;              // fp32 [npad][naux * ncpad]  X from the half transform
+  float* X32;              // fp32 [2][npad][naux * ncpad]  X from the half transform as a pair
+                           //   (order-0 accumulator, higher-order accumulator)
   unsigned* xmax;          // [npad] max |X| of row m (FP32 bits)
   float* Kpart;            // fp32 [nsplit][npad][npad] partial K tiles
   int* err;                // device error flag of the tensor-core kernels

@@ -7,6 +7,8 @@
 //   E = 1/2 tr(D (h + F)) + E_nuc,
 //   e = X^T (F D S - S D F) X,  X = U s^-1/2 over eigenvalues s > lindep of S,
 //   Fbar = sum_i c_i F_i with [[B, -1], [-1, 0]] [c, lam] = [0, -1], B_ij = <e_i, e_j>.
+// DIIS works in the orthogonal basis of X: it keeps F' = X^T F X, whose error is
+// F' D' - D' F' for D = X D' X^T, and diagonalises the extrapolated F' directly.
 // One iteration is a fixed sequence of device work with no host decision inside it: the
 // DIIS ring (slot choice, ageing, restart on a singular system) lives in device memory,
 // so the iteration is captured once per precision into a CUDA graph and replayed.  The
@@ -127,14 +129,24 @@ __global__ void diis_select_kernel(DiisState* d) {
   d->slot = slot;
 }
 
+// Keep only the newest vector (a restart of the extrapolation).
+__global__ void diis_reset_kernel(DiisState* d) {
+  if (threadIdx.x != 0) return;
+  for (int k = 0; k < d->space; ++k) d->valid[k] = (k == d->slot);
+  d->nvalid = 1;
+}
+
 // Fhist[slot] = F, Ehist[slot] = E (E holds ne = nmo*nmo entries).
+// Slot stride nn; F and E both hold ne = nmo^2 entries (orthogonal basis).
 __global__ void diis_store_kernel(const DiisState* __restrict__ d, const double* __restrict__ F,
                                   const double* __restrict__ E, double* __restrict__ Fh, double* __restrict__ Eh,
                                   long nn, long ne) {
   long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
   int slot = d->slot;
-  if (i < nn) Fh[(size_t)slot * nn + i] = F[i];
-  if (i < ne) Eh[(size_t)slot * nn + i] = E[i];
+  if (i < ne) {
+    Fh[(size_t)slot * nn + i] = F[i];
+    Eh[(size_t)slot * nn + i] = E[i];
+  }
 }
 
 // G[slot][j] = G[j][slot] = <E[slot], E[j]> for valid slots j.
@@ -229,10 +241,11 @@ __global__ void diis_solve_kernel(DiisState* d, const double* __restrict__ G, do
 }
 
 // out = sum_k coef[k] Fh[k] over valid slots.
-__global__ void diis_combine_kernel(const DiisState* __restrict__ d, const double* __restrict__ Fh, long nn,
+// out[i] = sum_k c_k Fh[k][i] for i < ne (slot stride nn).
+__global__ void diis_combine_kernel(const DiisState* __restrict__ d, const double* __restrict__ Fh, long nn, long ne,
                                     const double* __restrict__ coef, double* __restrict__ out) {
   long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= nn) return;
+  if (i >= ne) return;
   double s = 0.0;
   for (int k = 0; k < d->space; ++k)
     if (d->valid[k]) s += coef[k] * Fh[(size_t)k * nn + i];
@@ -308,7 +321,7 @@ static unsigned blocks_for(long n, int t = 256) { return (unsigned)((n + t - 1) 
 
 // ---- per-molecule workspace --------------------------------------------------------------
 struct ScfWork {
-  double *L, *pair_tab, *S, *h, *V, *X, *F, *Fbar, *J, *K, *D, *Dprev, *Cocc, *Cprev, *Cchunk, *T1, *T2, *E, *Fp,
+  double *L, *pair_tab, *S, *h, *V, *X, *F, *Fo, *Cp, *J, *K, *D, *Dprev, *Cocc, *Cprev, *Cchunk, *T1, *T2, *E, *Fp,
       *ZT, *eps, *Fhist, *Ehist, *G, *coef, *eig_scratch, *enuc, *maxdiag;
   int *eig_status, *chol_status, *idx;
   void* eig_aux;  // p vector and grid barrier of the multi-SM eigensolver
@@ -329,7 +342,8 @@ static void scf_layout(int nao, int naux, int nocc, int precision, Arena* a, Siz
   TAKE(double, w->V, nn);
   TAKE(double, w->X, nn);
   TAKE(double, w->F, nn);
-  TAKE(double, w->Fbar, nn);
+  TAKE(double, w->Fo, nn);
+  TAKE(double, w->Cp, (size_t)nao * std::max(nocc, 1));
   TAKE(double, w->J, nn);
   TAKE(double, w->K, nn);
   TAKE(double, w->D, nn);
@@ -365,10 +379,9 @@ static int eig_rows(double* A, int n, double* w, double* ZT, ScfWork& W, cudaStr
   return eigh_full_rows(A, n, w, ZT, W.eig_scratch, W.eig_status, s, W.eig_aux);
 }
 
-// Occupied coefficients from a Fock-like matrix: C_occ = X C'_occ, D = 2 C C^T.
-static int diagonalize_fock(const double* Fm, int nao, int nmo, int nocc, ScfWork& W, cudaStream_t s) {
-  DF_TRY(dgemm(false, false, nao, nmo, nao, 1.0, Fm, nao, 0, W.X, nmo, 0, 0.0, W.T1, nmo, 0, 1, s, 0, 0));
-  DF_TRY(dgemm(true, false, nmo, nmo, nao, 1.0, W.X, nmo, 0, W.T1, nmo, 0, 0.0, W.Fp, nmo, 0, 1, s, 0, 0));
+// Occupied orbitals of the orthogonal-basis Fock matrix W.Fp [nmo][nmo] (destroyed):
+// C'_occ into W.Cp [nmo][nocc], C_occ = X C'_occ, D = 2 C C^T.
+static int diagonalize_orth(int nao, int nmo, int nocc, ScfWork& W, cudaStream_t s) {
   // only the occupied orbitals and the LUMO are needed: k lowest eigenpairs when k << nmo
   const int k = std::min(nocc + 1, nmo);
   {
@@ -378,11 +391,24 @@ static int diagonalize_fock(const double* Fm, int nao, int nmo, int nocc, ScfWor
     else
       DF_TRY(eig_rows(W.Fp, nmo, W.eps, W.ZT, W, s));
   }
-  occ_columns_kernel<<<blocks_for((long)nmo * nocc), 256, 0, s>>>(W.ZT, nmo, nocc, W.T2);
+  occ_columns_kernel<<<blocks_for((long)nmo * nocc), 256, 0, s>>>(W.ZT, nmo, nocc, W.Cp);
   DF_LAUNCHED("occ_columns_kernel");
-  DF_TRY(dgemm(false, false, nao, nocc, nmo, 1.0, W.X, nmo, 0, W.T2, nocc, 0, 0.0, W.Cocc, nocc, 0, 1, s, 0, 0));
+  DF_TRY(dgemm(false, false, nao, nocc, nmo, 1.0, W.X, nmo, 0, W.Cp, nocc, 0, 0.0, W.Cocc, nocc, 0, 1, s, 0, 0));
   DF_TRY(dgemm(false, true, nao, nao, nocc, 2.0, W.Cocc, nocc, 0, W.Cocc, nocc, 0, 0.0, W.D, nao, 0, 1, s, 0, 0));
   return DF_OK;
+}
+
+// F' = X^T Fm X into `out` [nmo][nmo] (T1 as scratch).
+static int to_orth(const double* Fm, int nao, int nmo, ScfWork& W, double* out, cudaStream_t s) {
+  DF_TRY(dgemm(false, false, nao, nmo, nao, 1.0, Fm, nao, 0, W.X, nmo, 0, 0.0, W.T1, nmo, 0, 1, s, 0, 0));
+  DF_TRY(dgemm(true, false, nmo, nmo, nao, 1.0, W.X, nmo, 0, W.T1, nmo, 0, 0.0, out, nmo, 0, 1, s, 0, 0));
+  return DF_OK;
+}
+
+// Occupied coefficients from an AO-basis Fock-like matrix.
+static int diagonalize_fock(const double* Fm, int nao, int nmo, int nocc, ScfWork& W, cudaStream_t s) {
+  DF_TRY(to_orth(Fm, nao, nmo, W, W.Fp, s));
+  return diagonalize_orth(nao, nmo, nocc, W, s);
 }
 
 // ---- one molecule's SCF state machine ----------------------------------------------------------
@@ -572,28 +598,41 @@ static int iteration_tail(ScfMol& M) {
     DF_LAUNCHED("fock_energy_kernel");
   }
   {
+    // DIIS in the orthogonal basis of X (X^T S X = 1): F' = X^T F X and, for D = X D' X^T,
+    // e = X^T (F D S - S D F) X = F' D' - D' F'.  With D' = 2 C' C'^T (C' the occupied
+    // columns of the last diagonalisation) e = M - M^T, M = 2 (F' C') C'^T: O(nmo^2 nocc)
+    // work instead of four O(nao^3) products; the extrapolated F' is diagonalised as it is.
     ProfScope ps("scf_diis_error", s);
-    DF_TRY(dgemm(false, false, nao, nao, nao, 1.0, W.F, nao, 0, W.D, nao, 0, 0.0, W.T1, nao, 0, 1, s, 0, 0));
-    DF_TRY(dgemm(false, false, nao, nao, nao, 1.0, W.T1, nao, 0, W.S, nao, 0, 0.0, W.T2, nao, 0, 1, s, 0, 0));
-    antisym_kernel<<<blocks_for(nn), 256, 0, s>>>(W.T2, nao, W.T1);
-    DF_LAUNCHED("antisym_kernel");
-    DF_TRY(dgemm(false, false, nao, nmo, nao, 1.0, W.T1, nao, 0, W.X, nmo, 0, 0.0, W.T2, nmo, 0, 1, s, 0, 0));
-    DF_TRY(dgemm(true, false, nmo, nmo, nao, 1.0, W.X, nmo, 0, W.T2, nmo, 0, 0.0, W.E, nmo, 0, 1, s, 0, 0));
+    DF_TRY(to_orth(W.F, nao, nmo, W, W.Fo, s));
+    if (M.first_dm0) {
+      // a starting density need not lie in the span of X C': AO-basis commutator
+      DF_TRY(dgemm(false, false, nao, nao, nao, 1.0, W.F, nao, 0, W.D, nao, 0, 0.0, W.T1, nao, 0, 1, s, 0, 0));
+      DF_TRY(dgemm(false, false, nao, nao, nao, 1.0, W.T1, nao, 0, W.S, nao, 0, 0.0, W.T2, nao, 0, 1, s, 0, 0));
+      antisym_kernel<<<blocks_for(nn), 256, 0, s>>>(W.T2, nao, W.T1);
+      DF_LAUNCHED("antisym_kernel");
+      DF_TRY(dgemm(false, false, nao, nmo, nao, 1.0, W.T1, nao, 0, W.X, nmo, 0, 0.0, W.T2, nmo, 0, 1, s, 0, 0));
+      DF_TRY(dgemm(true, false, nmo, nmo, nao, 1.0, W.X, nmo, 0, W.T2, nmo, 0, 0.0, W.E, nmo, 0, 1, s, 0, 0));
+    } else {
+      DF_TRY(dgemm(false, false, nmo, nocc, nmo, 1.0, W.Fo, nmo, 0, W.Cp, nocc, 0, 0.0, W.T1, nocc, 0, 1, s, 0, 0));
+      DF_TRY(dgemm(false, true, nmo, nmo, nocc, 2.0, W.T1, nocc, 0, W.Cp, nocc, 0, 0.0, W.T2, nmo, 0, 1, s, 0, 0));
+      antisym_kernel<<<blocks_for(ne), 256, 0, s>>>(W.T2, nmo, W.E);
+      DF_LAUNCHED("antisym_kernel");
+    }
     absmax_kernel<<<1, 1024, 0, s>>>(W.E, ne, &W.st->emax);
     DF_LAUNCHED("absmax_kernel");
   }
   ProfScope ps_diis("scf_diis_and_diagonalize", s);
   diis_select_kernel<<<1, 32, 0, s>>>(W.diis);
   DF_LAUNCHED("diis_select_kernel");
-  diis_store_kernel<<<blocks_for(nn), 256, 0, s>>>(W.diis, W.F, W.E, W.Fhist, W.Ehist, nn, ne);
+  diis_store_kernel<<<blocks_for(ne), 256, 0, s>>>(W.diis, W.Fo, W.E, W.Fhist, W.Ehist, nn, ne);
   DF_LAUNCHED("diis_store_kernel");
   diis_gram_kernel<<<DIIS_MAX, 256, 0, s>>>(W.diis, W.Ehist, nn, ne, W.G);
   DF_LAUNCHED("diis_gram_kernel");
   diis_solve_kernel<<<1, 32, 0, s>>>(W.diis, W.G, W.coef, W.st);
   DF_LAUNCHED("diis_solve_kernel");
-  diis_combine_kernel<<<blocks_for(nn), 256, 0, s>>>(W.diis, W.Fhist, nn, W.coef, W.Fbar);
+  diis_combine_kernel<<<blocks_for(ne), 256, 0, s>>>(W.diis, W.Fhist, nn, ne, W.coef, W.Fp);
   DF_LAUNCHED("diis_combine_kernel");
-  DF_TRY(diagonalize_fock(W.Fbar, nao, nmo, nocc, W, s));
+  DF_TRY(diagonalize_orth(nao, nmo, nocc, W, s));
   orbital_status_kernel<<<1, 32, 0, s>>>(W.eps, nmo, nocc, W.eig_status, W.st);
   DF_LAUNCHED("orbital_status_kernel");
   DF_CUDA(cudaMemcpyAsync(M.hst, W.st, sizeof(ScfStatus), cudaMemcpyDeviceToHost, s));
@@ -668,6 +707,17 @@ static bool scf_iter_finish(ScfMol& M) {
     M.res.converged = 1;
     return true;
   }
+  // First FP64 iteration after the switch: when its error jumps well above what the mixed
+  // phase reached, the mixed-precision vectors in the DIIS history no longer describe the
+  // FP64 problem (the mixed floor was high); restart the extrapolation from the new vector.
+  if (M.opt.precision == DF_MIXED && M.prec == DF_FP64 && M.fp64_done == 0 && h.emax > 3.0 * M.best_err) {
+    diis_reset_kernel<<<1, 32, 0, M.s>>>(M.W.diis);
+    if (cudaGetLastError() != cudaSuccess) {
+      M.rc = DF_ERR_CUDA;
+      set_error("scf: DIIS restart launch failed");
+      return true;
+    }
+  }
   if (M.prec == DF_FP64) M.fp64_done++;
   // orbital energies of the diagonalisation that produced the next density
   M.res.homo = h.homo;
@@ -689,7 +739,8 @@ static bool scf_iter_finish(ScfMol& M) {
   }
   if (!M.switched && M.have_old && (de < M.opt.switch_tol || h.emax < M.opt.switch_err || stalled)) {
     // The DIIS history is kept: the mixed-precision Fock matrices are close to the FP64
-    // ones and keep the extrapolation informed; new FP64 vectors replace them as they age.
+    // ones and keep the extrapolation informed; new FP64 vectors replace them as they age
+    // (unless the first FP64 error shows they are not close, see above).
     M.switched = true;
     M.prec = DF_FP64;
   }
@@ -1011,6 +1062,7 @@ static void guess_layout(int nao, int nocc, Arena* a, Sizer* z, ScfWork* w) {
   TAKE(int, w->eig_status, 1);
   TAKE(char, w->eig_aux, eigh_coop_aux_bytes(nao));
   TAKE(double, w->Cocc, (size_t)nao * std::max(nocc, 1));
+  TAKE(double, w->Cp, (size_t)nao * std::max(nocc, 1));
   TAKE(double, w->D, nn);
 #undef TAKE
 }

@@ -6,11 +6,14 @@
 // stored as NP BF16 planes, p0 = x rounded to 8 bits on a power-of-two grid fixed along the
 // row (an integer in [-128, 128] times the row's scale), p1 = RN_bf16(x - p0),
 // p2 = RN_bf16(x - p0 - p1).  A product is formed from the plane products pa*qb with
-// a + b < NP in two FP32 accumulators in tensor memory (TMEM): order 0 (p0*q0) sums
-// integers on one grid and is exact in FP32; the higher orders are at most 2^-8 of it, so
-// their rounding stays near 2^-32 of the result.  With a single accumulator the FP32
-// rounding of long sums with cancellation, not the operand split, limits the accuracy.
-// NP = 3: six products; NP = 4: ten.
+// a + b < NP in FP32 accumulators in tensor memory (TMEM).  p0 and p1 are fixed-point
+// (integers on grids fixed along each row, planes.cuh), so in the exchange SYRK the
+// products (0,0), (0,1)+(1,0) and (1,1) each sum integers on one grid in an accumulator of
+// their own and are exact; every product with a floating plane (the contributions of
+// elements far below their row's max) goes to a fourth.  The half-transform uses two
+// accumulators, (0,0) and the rest.  With a single accumulator, long FP32 sums of many
+// small positive products lose their low bits and K of a 300-centre molecule comes out
+// ~1e-5 low on the diagonal.  NP = 3, 4, 5: 6, 10, 15 products.
 //
 //   half-transform:  X[(P,m), i] = sum_n B[(P,m), n] C^T[i, n]     (A = B planes, B = C^T)
 //   exchange SYRK:   K[m, n]     = sum_(P,i) X[m, (P,i)] X[n, (P,i)] (A = B = X, lower tiles)
@@ -148,11 +151,13 @@ struct Params {
   int stages;
   uint32_t stage_bytes;
   uint32_t b_bytes;  // bytes of one B tile (N x 128)
-  // half-transform epilogue: X in FP32 and the max |X| of every row m
+  // half-transform epilogue: X as the FP32 pair (order 0, higher orders) and the max |X|
+  // of every row m
   int npad;          // rows per P in A
   long ldx;          // X row stride (elements)
   int ncx;           // X columns per P
-  float* X32;
+  float* X32;        // [2][npad][ldx]
+  long xsize;        // npad * ldx
   unsigned* xmax;    // FP32 bit patterns of max |X| per row m (non-negative: integer order)
   // SYRK epilogue
   float* Kpart;      // [split][npad][npad]
@@ -175,8 +180,8 @@ __device__ __forceinline__ void lower_tile(int t, int wide, int& mt, int& nt) {
 
 // Tensor maps of the operand planes (A planes, then B planes); entries >= NP unused.
 struct Maps {
-  CUtensorMap a[4];
-  CUtensorMap b[4];
+  CUtensorMap a[5];
+  CUtensorMap b[5];
 };
 
 template <int NP>
@@ -212,8 +217,9 @@ __global__ void __launch_bounds__(THREADS, 1) split_bf16_gemm_kernel(const __gri
   uint32_t pad = (1024u - (base & 1023u)) & 1023u;
   uint8_t* ring = dyn_smem + pad;
   const uint32_t a_bytes = BM * BK * 2;
+  const int nacc = p.mode == SYRK ? 4 : 2;  // accumulators of N columns
   uint32_t ncols = 32;
-  while ((int)ncols < 2 * p.N) ncols <<= 1;  // accumulators of N columns: order 0, higher orders
+  while ((int)ncols < nacc * p.N) ncols <<= 1;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < p.stages; ++s) {
@@ -281,14 +287,20 @@ __global__ void __launch_bounds__(THREADS, 1) split_bf16_gemm_kernel(const __gri
 #pragma unroll
       for (int kk = 0; kk < BK / 16; ++kk) {
         uint64_t off = (uint64_t)(kk * 32) >> 4;  // 16 bf16 = 32 bytes along K inside the swizzle row
-        // plane products of order t = a + b: (0,0) into accumulator 0; (0,1) (1,0), (0,2) (1,1)
-        // (2,0), ... into accumulator 1
+        // plane products in order t = a + b; accumulator of (a, b): half-transform (0,0) -> 0,
+        // rest -> 1; SYRK (0,0) -> 0, (0,1) (1,0) -> 1, (1,1) -> 2, rest -> 3.  The first
+        // product issued into an accumulator (t = 0; t = 1, a = 0; SYRK t = 2, a <= 1)
+        // overwrites it.
 #pragma unroll
         for (int t = 0; t < NP; ++t)
 #pragma unroll
-          for (int a = 0; a <= t; ++a)
-            umma_bf16(tmem + (uint32_t)(t > 0 ? p.N : 0), ad[a] + off, bd[t - a] + off, idesc,
-                      (i > 0 || kk > 0 || (t > 1 || a > 0)) ? 1u : 0u);
+          for (int a = 0; a <= t; ++a) {
+            const int b = t - a;
+            const int acc = p.mode == SYRK ? ((a <= 1 && b <= 1) ? t : 3) : (t > 0 ? 1 : 0);
+            const bool first = t == 0 || (t == 1 && a == 0) || (p.mode == SYRK && t == 2 && a <= 1);
+            umma_bf16(tmem + (uint32_t)(acc * p.N), ad[a] + off, bd[b] + off, idesc,
+                      (i > 0 || kk > 0 || !first) ? 1u : 0u);
+          }
       }
       umma_commit(&empty_bar[s]);  // slot reusable once these MMAs have read it
     }
@@ -306,19 +318,35 @@ __global__ void __launch_bounds__(THREADS, 1) split_bf16_gemm_kernel(const __gri
       for (int c = 0; c < p.N; c += 16) {
         if (p.mode == HALF_TRANSFORM && col0 + c >= p.ncx) break;  // column tiles past ncpad
         if (p.mode == SYRK && col0 + c >= p.npad) break;            // last wide tile past npad
-        uint32_t v[2][16];
-#pragma unroll
-        for (int t = 0; t < 2; ++t) tmem_ld_x16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(t * p.N + c), v[t]);
+        uint32_t v[4][16];
+        tmem_ld_x16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c, v[0]);
+        tmem_ld_x16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(p.N + c), v[1]);
+        if (nacc == 4) {
+          tmem_ld_x16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(2 * p.N + c), v[2]);
+          tmem_ld_x16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(3 * p.N + c), v[3]);
+        }
         tmem_wait_ld();
         float x[16];
+        if (nacc == 4) {
 #pragma unroll
-        for (int j = 0; j < 16; ++j) x[j] = __uint_as_float(v[0][j]) + __uint_as_float(v[1][j]);
+          for (int j = 0; j < 16; ++j)  // smallest first
+            x[j] = ((__uint_as_float(v[3][j]) + __uint_as_float(v[2][j])) + __uint_as_float(v[1][j])) +
+                   __uint_as_float(v[0][j]);
+        } else {
+#pragma unroll
+          for (int j = 0; j < 16; ++j) x[j] = __uint_as_float(v[0][j]) + __uint_as_float(v[1][j]);
+        }
         if (p.mode == HALF_TRANSFORM) {
           int P = grow / p.npad, m = grow % p.npad;
-          float4* dst = reinterpret_cast<float4*>(p.X32 + (size_t)m * p.ldx + (size_t)P * p.ncx + col0 + c);
+          const size_t o = (size_t)m * p.ldx + (size_t)P * p.ncx + col0 + c;
+          float4* d0 = reinterpret_cast<float4*>(p.X32 + o);
+          float4* d1 = reinterpret_cast<float4*>(p.X32 + p.xsize + o);
 #pragma unroll
           for (int j = 0; j < 4; ++j) {
-            dst[j] = make_float4(x[4 * j], x[4 * j + 1], x[4 * j + 2], x[4 * j + 3]);
+            d0[j] = make_float4(__uint_as_float(v[0][4 * j]), __uint_as_float(v[0][4 * j + 1]),
+                                __uint_as_float(v[0][4 * j + 2]), __uint_as_float(v[0][4 * j + 3]));
+            d1[j] = make_float4(__uint_as_float(v[1][4 * j]), __uint_as_float(v[1][4 * j + 1]),
+                                __uint_as_float(v[1][4 * j + 2]), __uint_as_float(v[1][4 * j + 3]));
             lmax = fmaxf(lmax, fmaxf(fmaxf(fabsf(x[4 * j]), fabsf(x[4 * j + 1])),
                                      fmaxf(fabsf(x[4 * j + 2]), fabsf(x[4 * j + 3]))));
           }
@@ -394,7 +422,7 @@ static int launch_gemm(const umma::Maps& maps, umma::Params p, dim3 grid, cudaSt
 }
 
 struct PlanePtrs {
-  __nv_bfloat16* p[4];
+  __nv_bfloat16* p[5];
 };
 
 // C^T [ncpad][npad] as row-scaled planes (row i = column i of C over n); one CTA per row,
@@ -414,30 +442,34 @@ __global__ void __launch_bounds__(256) pack_ct_kernel(const double* __restrict__
   const double sig = row_scale(t);
   for (int n = threadIdx.x; n < npad; n += blockDim.x) {
     const double x = (i < nocc && n < nao) ? C[(size_t)n * nocc + i] : 0.0;
-    __nv_bfloat16 q[4];
+    __nv_bfloat16 q[kPlanesMax];
     split_row_value(x, sig, q);
     const size_t e = (size_t)i * npad + n;
     for (int j = 0; j < planes; ++j) out.p[j][e] = q[j];
   }
 }
 
-// X [npad][kdim] (FP32) into row-scaled planes, the scale of row m from xmax[m].  Row m is
-// blockIdx.y; four consecutive elements per thread (kdim is a multiple of 16).
+// X [npad][kdim], held as the FP32 pair (X0, X1) = (order-0, higher-order accumulators), into
+// row-scaled planes, the scale of row m from xmax[m].  Row m is blockIdx.y; four consecutive
+// elements per thread (kdim is a multiple of 16).
 template <int NP>
-__global__ void __launch_bounds__(256) x_to_planes_kernel(const float* __restrict__ X,
+__global__ void __launch_bounds__(256) x_to_planes_kernel(const float* __restrict__ X0, const float* __restrict__ X1,
                                                           const unsigned* __restrict__ xmax, long kdim,
                                                           PlanePtrs out) {
   const int m = blockIdx.y;
-  const float sig = row_scale_f(__uint_as_float(xmax[m]));
+  // the row max came from the rounded sum X0 + X1: a power of two above it by at least one
+  // FP32 ulp covers the exact pair
+  const float sig = row_scale_f(__uint_as_float(xmax[m]) * (1.0f + 1.2e-7f));
   const size_t row = (size_t)m * kdim;
   for (long c = ((long)blockIdx.x * blockDim.x + threadIdx.x) * 4; c < kdim; c += (long)gridDim.x * blockDim.x * 4) {
-    const float4 x = *reinterpret_cast<const float4*>(X + row + c);
-    const float xs[4] = {x.x, x.y, x.z, x.w};
+    const float4 a = *reinterpret_cast<const float4*>(X0 + row + c);
+    const float4 b = *reinterpret_cast<const float4*>(X1 + row + c);
+    const float hs[4] = {a.x, a.y, a.z, a.w}, ls[4] = {b.x, b.y, b.z, b.w};
     __align__(8) __nv_bfloat16 q[NP][4];
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       __nv_bfloat16 t[kPlanesMax];
-      split_row_value_f(xs[u], sig, t);
+      split_row_pair(hs[u], ls[u], sig, t);
 #pragma unroll
       for (int j = 0; j < NP; ++j) q[j][u] = t[j];
     }
@@ -461,9 +493,16 @@ __global__ void kmixed_reduce_kernel(const float* __restrict__ Kpart, int nsplit
 
 static int mixed_ncpad(int nocc) { return std::max(16, (nocc + 15) / 16 * 16); }
 
-// Columns of an exchange SYRK tile: 256 for four planes (the 32-element K boxes leave room
-// for two stages of a 128 x 256 tile), else 128.
-static int syrk_n(int planes) { return planes >= 4 ? 256 : 128; }
+// Columns of an exchange SYRK tile: four accumulators of 128 columns fill TMEM.
+static int syrk_n(int) { return 128; }
+
+// Widest half-transform tile (multiple of 16, <= 256) whose stage fits twice in the ring.
+static int ht_max_n(int planes) {
+  const int bk = umma::bk_of(planes);
+  const long budget = 220 * 1024 / 2;
+  long n = (budget / planes - (long)umma::BM * bk * 2) / (bk * 2);
+  return (int)std::min<long>(256, n / 16 * 16);
+}
 
 static int syrk_tiles(int npad, int planes) {
   int t = 0;
@@ -491,13 +530,15 @@ int umma_prepare() {
                                  (int)(220 * 1024 + 1024)));
     DF_CUDA(cudaFuncSetAttribute(umma::split_bf16_gemm_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)(220 * 1024 + 1024)));
+    DF_CUDA(cudaFuncSetAttribute(umma::split_bf16_gemm_kernel<5>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(220 * 1024 + 1024)));
     done = true;
   }
   return DF_OK;
 }
 
-// BF16 planes per operand of the mixed exchange (knob "mixed_planes": 3 or 4).
-int mixed_planes() { return knob("mixed_planes") == 3 ? 3 : 4; }
+// BF16 planes per operand of the mixed exchange (knob "mixed_planes": 3, 4 or 5).
+int mixed_planes() { return std::min(5, std::max(3, knob("mixed_planes"))); }
 
 void mixed_k_work_layout(int nao, int naux, int nocc, Arena* a, Sizer* z, MixedKWork* w) {
   int npad = nao_pad(nao);
@@ -520,10 +561,10 @@ void mixed_k_work_layout(int nao, int naux, int nocc, Arena* a, Sizer* z, MixedK
     else z->take<__nv_bfloat16>(xsize);
   }
   if (a) {
-    w->X32 = a->take<float>(xsize);
+    w->X32 = a->take<float>(2 * xsize);
     w->xmax = a->take<unsigned>((size_t)npad);
   } else {
-    z->take<float>(xsize);
+    z->take<float>(2 * xsize);
     z->take<unsigned>((size_t)npad);
   }
   if (a) {
@@ -540,7 +581,7 @@ int build_K_mixed(const void* B, const BLayout& L, int nao, int naux, const doub
   const int npad = L.npad, ncpad = w.ncpad, NP = w.planes;
   DF_REQUIRE(nocc <= ncpad, DF_ERR_ARG, "mixed K: workspace sized for %d occupied columns, got %d", ncpad, nocc);
   DF_REQUIRE(ncpad <= 256, DF_ERR_ARG, "mixed K: more than 256 occupied orbitals per call is not supported");
-  DF_REQUIRE(NP == 3 || NP == 4, DF_ERR_ARG, "mixed K: %d planes", NP);
+  DF_REQUIRE(NP >= 3 && NP <= 5, DF_ERR_ARG, "mixed K: %d planes", NP);
   DF_CUDA(cudaMemsetAsync(w.err, 0, sizeof(int), s));
   DF_CUDA(cudaMemsetAsync(w.xmax, 0, sizeof(unsigned) * (size_t)npad, s));
   PlanePtrs cpp{}, xpp{};
@@ -550,8 +591,9 @@ int build_K_mixed(const void* B, const BLayout& L, int nao, int naux, const doub
   }
   pack_ct_kernel<<<(unsigned)ncpad, 256, 0, s>>>(C, nao, nocc, npad, NP, cpp);
   DF_LAUNCHED("pack_ct_kernel");
-  // column tiles of the half transform: two accumulators of N columns in 512 TMEM columns
-  const int maxN = 256;
+  // column tiles of the half transform: two stages in the ring and two accumulators of N
+  // columns in 512 TMEM columns
+  const int maxN = ht_max_n(NP);
   const int ntc = (ncpad + maxN - 1) / maxN;
   const int Nht = ((ncpad + ntc - 1) / ntc + 15) / 16 * 16;
   const char* base = (const char*)B;
@@ -571,22 +613,28 @@ int build_K_mixed(const void* B, const BLayout& L, int nao, int naux, const doub
   p.ncx = ncpad;
   p.ldx = (long)naux * ncpad;
   p.X32 = w.X32;
+  p.xsize = (long)npad * naux * ncpad;
   p.xmax = w.xmax;
   p.err = w.err;
   long mtiles = (long)naux * npad / umma::BM;
   DF_REQUIRE(mtiles < (1L << 31), DF_ERR_ARG, "mixed K: too many row tiles");
   {
     ProfScope ps("k_halftransform_tc", s);
-    if (NP == 4) DF_TRY(launch_gemm<4>(maps, p, dim3((unsigned)mtiles, (unsigned)ntc), s));
-    else DF_TRY(launch_gemm<3>(maps, p, dim3((unsigned)mtiles, (unsigned)ntc), s));
+    const dim3 grid((unsigned)mtiles, (unsigned)ntc);
+    if (NP == 5) DF_TRY(launch_gemm<5>(maps, p, grid, s));
+    else if (NP == 4) DF_TRY(launch_gemm<4>(maps, p, grid, s));
+    else DF_TRY(launch_gemm<3>(maps, p, grid, s));
   }
   {
     const long kd = (long)naux * ncpad;
     DF_REQUIRE(npad <= 65535, DF_ERR_ARG, "mixed K: npad %d too large", npad);
     ProfScope ps("k_x_planes", s);
     dim3 grid((unsigned)std::min<long>((kd / 4 + 255) / 256, 64L), (unsigned)npad);
-    if (NP == 4) x_to_planes_kernel<4><<<grid, 256, 0, s>>>(w.X32, w.xmax, kd, xpp);
-    else x_to_planes_kernel<3><<<grid, 256, 0, s>>>(w.X32, w.xmax, kd, xpp);
+    const float* x0 = w.X32;
+    const float* x1 = w.X32 + (size_t)npad * kd;
+    if (NP == 5) x_to_planes_kernel<5><<<grid, 256, 0, s>>>(x0, x1, w.xmax, kd, xpp);
+    else if (NP == 4) x_to_planes_kernel<4><<<grid, 256, 0, s>>>(x0, x1, w.xmax, kd, xpp);
+    else x_to_planes_kernel<3><<<grid, 256, 0, s>>>(x0, x1, w.xmax, kd, xpp);
     DF_LAUNCHED("x_to_planes_kernel");
   }
   // exchange SYRK: A = B = X [m][(P, i)], lower tiles of 128 x syrk_n, split over (P, i)
@@ -609,7 +657,8 @@ int build_K_mixed(const void* B, const BLayout& L, int nao, int naux, const doub
   {
     ProfScope ps("k_syrk_tc", s);
     dim3 grid((unsigned)q.n_lower_tiles, (unsigned)nsplit);
-    if (NP == 4) DF_TRY(launch_gemm<4>(maps, q, grid, s));
+    if (NP == 5) DF_TRY(launch_gemm<5>(maps, q, grid, s));
+    else if (NP == 4) DF_TRY(launch_gemm<4>(maps, q, grid, s));
     else DF_TRY(launch_gemm<3>(maps, q, grid, s));
   }
   long nn = (long)nao * nao;
