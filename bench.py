@@ -3,8 +3,8 @@
 Workload (default): 300 hydrogen-like centres at one per 10 bohr^3 (box 14.42 bohr,
 seed 0), 5 orbital + 15 auxiliary s primitives per centre: nao 1500, naux 4500,
 nocc 150; D and C_occ from the core-Hamiltonian guess, fixed.  One step is one Fock
-build (J[D] and K[C_occ]) in FP64; the mixed-precision (split-BF16 x3 on tcgen05) build
-is timed the same way and reported under "mixed".  B (40.5 GB FP64) is far larger
+build (J[D] and K[C_occ]) in FP64; the mixed-precision build (K from split-BF16 planes on
+tcgen05 tensor cores, J in FP64) is timed the same way and reported under "mixed".  B (40.5 GB FP64) is far larger
 than L2, so no L2 flush is needed between steps.
 
 --impl reference times the CPU oracle (the plain FP64 C loops in oracle/) on a bounded

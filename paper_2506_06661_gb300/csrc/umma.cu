@@ -19,8 +19,8 @@
 //   exchange SYRK:   K[m, n]     = sum_(P,i) X[m, (P,i)] X[n, (P,i)] (A = B = X, lower tiles)
 //
 // Both are "D = A B^T" with A and B K-major in global memory, so one kernel serves both:
-// TMA (128-byte swizzle and 64-element K boxes; 64-byte swizzle and 32-element boxes for
-// four planes, whose stages are twice as wide) fills a multi-stage shared-memory ring, one
+// TMA (128-byte swizzle and 64-element K boxes; 64-byte swizzle and 32-element boxes for four
+// or more planes, whose stages are wider) fills a multi-stage shared-memory ring, one
 // elected lane issues tcgen05.mma (M = 128, N <= 256, K = 16 per instruction, one per
 // plane product and K step), tcgen05.commit releases ring slots, and four epilogue warps read the
 // accumulator with tcgen05.ld.  Every mbarrier wait is bounded; on a timeout the kernel
@@ -38,7 +38,7 @@ namespace dfscf {
 namespace umma {
 
 constexpr int BM = 128;          // rows per tile (TMEM lanes)
-// K elements per stage: one swizzle row of bf16 (128 bytes; 64 bytes for four planes)
+// K elements per stage: one swizzle row of bf16 (128 bytes; 64 bytes for four or more planes)
 __host__ __device__ constexpr int bk_of(int np) { return np >= 4 ? 32 : 64; }
 constexpr int MAX_STAGES = 4;
 constexpr int THREADS = 192;     // warp 0 TMA, warp 1 MMA, warps 2..5 epilogue
