@@ -19,19 +19,26 @@ namespace dfscf {
 struct EigShared {
   double red[32];
   double scal[4];
+  double bsum, bmax;  // broadcast slots of cta_sum / cta_max
   int flag;
 };
 
+// CTA-wide sum, the same value (and the same bits in every CTA of a grid) for every thread:
+// warp sums, then warp 0 reduces the partials and broadcasts through shared memory (FP64
+// issues slowly on this part, so no warp repeats the partials' sum).
 __device__ double cta_sum(double v, EigShared& sh) {
   int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   v = warp_sum(v);
   __syncthreads();
   if (lane == 0) sh.red[wid] = v;
   __syncthreads();
-  double t = 0.0;
-  for (int i = 0; i < nw; ++i) t += sh.red[i];
+  if (wid == 0) {
+    double t = lane < nw ? sh.red[lane] : 0.0;
+    t = warp_sum(t);
+    if (lane == 0) sh.bsum = t;
+  }
   __syncthreads();
-  return t;
+  return sh.bsum;
 }
 
 __device__ double cta_max(double v, EigShared& sh) {
@@ -40,10 +47,13 @@ __device__ double cta_max(double v, EigShared& sh) {
   __syncthreads();
   if (lane == 0) sh.red[wid] = v;
   __syncthreads();
-  double t = -INFINITY;
-  for (int i = 0; i < nw; ++i) t = fmax(t, sh.red[i]);
+  if (wid == 0) {
+    double t = lane < nw ? sh.red[lane] : -INFINITY;
+    for (int o = 16; o; o >>= 1) t = fmax(t, __shfl_xor_sync(0xffffffffu, t, o));
+    if (lane == 0) sh.bmax = t;
+  }
   __syncthreads();
-  return t;
+  return sh.bmax;
 }
 
 // Gershgorin interval [glo, ghi] of tridiag(d, e) and max e^2, reduced over the CTA.
@@ -93,13 +103,21 @@ __device__ void tridiagonalize_cta(double* __restrict__ A, int n, double* __rest
     if (tid == 0) beta[k] = b;
     const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
     if (b != 0.0) {
-      // p = b * A22 v  (one warp per row)
-      for (int i = wid; i < len; i += nw) {
-        const double* row = A + (size_t)(k + 1 + i) * n + k + 1;
-        double s = 0.0;
-        for (int j = lane; j < len; j += 32) s += row[j] * v[j];
-        s = warp_sum(s);
-        if (lane == 0) cs[i] = b * s;
+      // p = b * A22 v, one thread per entry: A22 is symmetric (kept so by the full rank-2
+      // updates), so thread i walks column i, coalesced across the warp and with no
+      // reduction between lanes; four partial sums for independent FMA chains
+      for (int i = tid; i < len; i += nt) {
+        const double* col = A + (size_t)(k + 1) * n + k + 1 + i;
+        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+        int j = 0;
+        for (; j + 3 < len; j += 4) {
+          s0 += col[(size_t)j * n] * v[j];
+          s1 += col[(size_t)(j + 1) * n] * v[j + 1];
+          s2 += col[(size_t)(j + 2) * n] * v[j + 2];
+          s3 += col[(size_t)(j + 3) * n] * v[j + 3];
+        }
+        for (; j < len; ++j) s0 += col[(size_t)j * n] * v[j];
+        cs[i] = b * ((s0 + s1) + (s2 + s3));
       }
       __syncthreads();
       double pv = 0.0;
