@@ -130,7 +130,7 @@ __global__ void diis_select_kernel(DiisState* d) {
 }
 
 // Keep only the newest vector (a restart of the extrapolation).
-__global__ void diis_reset_kernel(DiisState* d) {
+__global__ void diis_keep_newest_kernel(DiisState* d) {
   if (threadIdx.x != 0) return;
   for (int k = 0; k < d->space; ++k) d->valid[k] = (k == d->slot);
   d->nvalid = 1;
@@ -438,9 +438,10 @@ struct ScfMol {
   // Set-up runs as asynchronous phases so that a batch never blocks on one molecule:
   // SETUP (integrals, metric, B, eig(S) enqueued) -> ORTHO (host reads eig(S)) ->
   // GUESS_CHECK (only with dm0) -> READY -> ITER (an iteration is in flight) -> DONE.
-  enum Phase { SETUP, GUESS_CHECK, READY, ITER, DONE } phase = SETUP;
-  double* h_eps = nullptr;  // pinned: eigenvalues of S, then E_nuc (nao + 1 doubles)
+  enum Phase { SETUP, GUESS_CHECK, READY, DM0_EIG, ITER, DONE } phase = SETUP;
+  double* h_eps = nullptr;  // pinned: eigenvalues of S, then E_nuc (nao + 1 doubles); then of dm0
   int* h_ints = nullptr;    // pinned: [0] eigensolver status, [1] Cholesky status
+  std::vector<int> dm0_ids; // eigenvalue indices of the dm0 split (source of an async copy)
 
   ~ScfMol() {
     for (auto& g : graph)
@@ -476,10 +477,56 @@ static int setup_launch(ScfMol& M) {
   return DF_OK;
 }
 
-static int finish_guess(ScfMol& M, bool use_dm0) {
+// use_dm0 with an idempotent dm0 (orbitals): start from its occupied orbitals.  With
+// P = Dx / 2 (Dx = X^T S dm0 S X, left in W.Fp by the guess check) and H = X^T h X, the matrix
+//   A = -2 P + delta (H - P H - H P + 2 P H P),   delta = 1 / (2 ||H||_F),
+// commutes with P; its occupied eigenvalues lie in -2 + delta spec(H) and its virtual ones in
+// delta spec(H), at least 1 apart, so its nocc lowest eigenvectors span range(P) exactly.
+// The core-Hamiltonian term splits the nocc-fold eigenvalue of -Dx (a degenerate cluster
+// that inverse iteration resolves only to ~1e-8) into distinct ones.  The first iteration
+// is then an ordinary one.  A general dm0 keeps the eager first iteration with the exchange
+// of its eigen-decomposition.
+__global__ void frobenius_kernel(const double* __restrict__ A, long n, double* __restrict__ out) {
+  __shared__ double sh[32];
+  double t = 0.0;
+  for (long i = threadIdx.x; i < n; i += blockDim.x) t += A[i] * A[i];
+  t = block_sum(t, sh);
+  if (threadIdx.x == 0) *out = sqrt(t);
+}
+
+// A (in place of Dx) = -Dx + delta (H - PH - (PH)^T + 2 PHP), P = Dx / 2.
+__global__ void shifted_projector_kernel(double* __restrict__ Dx, const double* __restrict__ H,
+                                         const double* __restrict__ PH, const double* __restrict__ PHP, int n,
+                                         const double* __restrict__ hnorm) {
+  long q = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= (long)n * n) return;
+  const int i = (int)(q / n), j = (int)(q % n);
+  const double delta = 0.5 / fmax(*hnorm, 1e-300);
+  Dx[q] = -Dx[q] + delta * (H[q] - PH[q] - PH[(size_t)j * n + i] + 2.0 * PHP[q]);
+}
+
+static int orbitals_from_determinant(ScfMol& M) {
+  ScfWork& W = M.W;
+  cudaStream_t s = M.s;
+  const int nao = M.nao, nmo = M.nmo;
+  const long ne = (long)nmo * nmo;
+  DF_TRY(to_orth(W.h, nao, nmo, W, W.E, s));
+  DF_TRY(dgemm(false, false, nmo, nmo, nmo, 0.5, W.Fp, nmo, 0, W.E, nmo, 0, 0.0, W.J, nmo, 0, 1, s, 0, 0));
+  DF_TRY(dgemm(false, false, nmo, nmo, nmo, 0.5, W.J, nmo, 0, W.Fp, nmo, 0, 0.0, W.K, nmo, 0, 1, s, 0, 0));
+  frobenius_kernel<<<1, 1024, 0, s>>>(W.E, ne, W.coef);
+  DF_LAUNCHED("frobenius_kernel");
+  shifted_projector_kernel<<<blocks_for(ne), 256, 0, s>>>(W.Fp, W.E, W.J, W.K, nmo, W.coef);
+  DF_LAUNCHED("shifted_projector_kernel");
+  return diagonalize_orth(nao, nmo, M.nocc, W, s);
+}
+
+static int finish_guess(ScfMol& M, bool use_dm0, bool orbitals) {
   ScfWork& W = M.W;
   const long nn = (long)M.nao * M.nao;
-  if (use_dm0) {
+  if (use_dm0 && orbitals) {
+    DF_TRY(orbitals_from_determinant(M));
+    use_dm0 = false;
+  } else if (use_dm0) {
     DF_CUDA(cudaMemcpyAsync(W.D, M.dm0, sizeof(double) * nn, cudaMemcpyDeviceToDevice, M.s));
   } else {
     DF_TRY(diagonalize_fock(W.h, M.nao, M.nmo, M.nocc, W, M.s));
@@ -510,7 +557,7 @@ static int setup_orthogonalize(ScfMol& M) {
   M.res.nmo = nmo;
   canonical_x_kernel<<<blocks_for((long)nao * nmo), 256, 0, s>>>(W.ZT, W.eps, nao, nmo, W.X);
   DF_LAUNCHED("canonical_x_kernel");
-  if (!M.dm0) return finish_guess(M, false);
+  if (!M.dm0) return finish_guess(M, false, false);
   // dm0 in the orthonormal basis X: Dx = X^T S dm0 S X; then the checks on Dx and Dx Dx
   DF_TRY(dgemm(false, false, nao, nao, nao, 1.0, W.S, nao, 0, M.dm0, nao, 0, 0.0, W.T1, nao, 0, 1, s, 0, 0));
   DF_TRY(dgemm(false, false, nao, nao, nao, 1.0, W.T1, nao, 0, W.S, nao, 0, 0.0, W.T2, nao, 0, 1, s, 0, 0));
@@ -533,7 +580,8 @@ static int setup_guess(ScfMol& M) {
   int ne = M.mol.nelec;
   bool use = std::isfinite(h.trDS) && fabs(h.trDS - ne) / ne < 0.05 && h.idem < 1.0;
   M.res.guess = use ? 1 : 2;
-  return finish_guess(M, use);
+  // an idempotent dm0 (the learned guess is one): start from its orbitals
+  return finish_guess(M, use, use && h.idem < 1e-6);
 }
 
 // Whole set-up for one molecule, synchronising between the phases.
@@ -549,37 +597,52 @@ static int scf_setup(ScfMol& M) {
 }
 
 // J and K for a general starting density (first iteration with dm0), eager launches.
-static int jk_general_density(ScfMol& M) {
+// First iteration from a non-idempotent dm0, in two halves so that a batch never blocks
+// on it.  dm0_launch enqueues J(dm0) and the eigen-decomposition of dm0 with an asynchronous
+// read-back of its eigenvalues; dm0_finish (once the stream has drained) splits
+// dm0/2 = C+ C+^T - C- C-^T over the non-negligible eigenvalues and enqueues
+// K = K(C+) - K(C-) in chunks of nocc columns, then the rest of the iteration.
+static int dm0_launch(ScfMol& M) {
+  ScfWork& W = M.W;
+  cudaStream_t s = M.s;
+  const int nao = M.nao;
+  const long nn = (long)nao * nao;
+  DF_CUDA(cudaMemcpyAsync(W.Dprev, W.D, sizeof(double) * nn, cudaMemcpyDeviceToDevice, s));
+  DF_TRY(run_jk(W.B, nao, M.naux, M.prec, W.D, nullptr, 0, W.J, nullptr, W.jk, s));
+  DF_CUDA(cudaMemcpyAsync(W.T1, W.D, sizeof(double) * nn, cudaMemcpyDeviceToDevice, s));
+  DF_TRY(eig_rows(W.T1, nao, W.eps, W.ZT, W, s));
+  DF_CUDA(cudaMemcpyAsync(M.h_eps, W.eps, sizeof(double) * nao, cudaMemcpyDeviceToHost, s));
+  DF_CUDA(cudaMemcpyAsync(M.h_ints, W.eig_status, sizeof(int), cudaMemcpyDeviceToHost, s));
+  return DF_OK;
+}
+
+static int dm0_finish(ScfMol& M) {
   ScfWork& W = M.W;
   cudaStream_t s = M.s;
   const int nao = M.nao, naux = M.naux, nocc = M.nocc;
   const long nn = (long)nao * nao;
-  DF_TRY(run_jk(W.B, nao, naux, M.prec, W.D, nullptr, 0, W.J, nullptr, W.jk, s));
-  DF_CUDA(cudaMemcpyAsync(W.T1, W.D, sizeof(double) * nn, cudaMemcpyDeviceToDevice, s));
-  DF_TRY(eig_rows(W.T1, nao, W.eps, W.ZT, W, s));
-  std::vector<double> wv(nao);
-  int eig_bad = 0;
-  DF_CUDA(cudaMemcpyAsync(wv.data(), W.eps, sizeof(double) * nao, cudaMemcpyDeviceToHost, s));
-  DF_CUDA(cudaMemcpyAsync(&eig_bad, W.eig_status, sizeof(int), cudaMemcpyDeviceToHost, s));
-  DF_CUDA(cudaStreamSynchronize(s));
-  DF_REQUIRE(eig_bad == 0, DF_ERR_NOCONV, "scf: eigensolver failed on the starting density");
+  DF_REQUIRE(M.h_ints[0] == 0, DF_ERR_NOCONV, "scf: eigensolver failed on the starting density");
   double wmax = 0.0;
-  for (double x : wv) wmax = fmax(wmax, fabs(x));
+  for (int k = 0; k < nao; ++k) wmax = fmax(wmax, fabs(M.h_eps[k]));
+  // positive eigenvalues first, then negative ones; one copy of all indices to the device
+  M.dm0_ids.clear();
+  for (int k = 0; k < nao; ++k)
+    if (M.h_eps[k] > 1e-12 * wmax) M.dm0_ids.push_back(k);
+  const size_t npos = M.dm0_ids.size();
+  for (int k = 0; k < nao; ++k)
+    if (-M.h_eps[k] > 1e-12 * wmax) M.dm0_ids.push_back(k);
   DF_CUDA(cudaMemsetAsync(W.K, 0, sizeof(double) * nn, s));
-  std::vector<int> ids;
-  for (int sign = 1; sign >= -1; sign -= 2) {
-    ids.clear();
-    for (int k = 0; k < nao; ++k)
-      if (sign * wv[k] > 1e-12 * wmax) ids.push_back(k);
-    for (size_t c0 = 0; c0 < ids.size(); c0 += nocc) {
-      int cnt = (int)std::min((size_t)nocc, ids.size() - c0);
-      DF_CUDA(cudaMemcpyAsync(W.idx, ids.data() + c0, sizeof(int) * cnt, cudaMemcpyHostToDevice, s));
-      split_density_kernel<<<blocks_for((long)nao * cnt), 256, 0, s>>>(W.ZT, W.eps, nao, W.idx, cnt, W.Cchunk);
+  if (!M.dm0_ids.empty())
+    DF_CUDA(cudaMemcpyAsync(W.idx, M.dm0_ids.data(), sizeof(int) * M.dm0_ids.size(), cudaMemcpyHostToDevice, s));
+  for (int part = 0; part < 2; ++part) {
+    const size_t b = part == 0 ? 0 : npos, e = part == 0 ? npos : M.dm0_ids.size();
+    for (size_t c0 = b; c0 < e; c0 += nocc) {
+      int cnt = (int)std::min((size_t)nocc, e - c0);
+      split_density_kernel<<<blocks_for((long)nao * cnt), 256, 0, s>>>(W.ZT, W.eps, nao, W.idx + c0, cnt, W.Cchunk);
       DF_LAUNCHED("split_density_kernel");
       DF_TRY(run_jk(W.B, nao, naux, M.prec, nullptr, W.Cchunk, cnt, nullptr, W.T2, W.jk, s));
-      axpy_kernel<<<blocks_for(nn), 256, 0, s>>>(W.K, W.T2, nn, (double)sign);
+      axpy_kernel<<<blocks_for(nn), 256, 0, s>>>(W.K, W.T2, nn, part == 0 ? 1.0 : -1.0);
       DF_LAUNCHED("axpy_kernel");
-      DF_CUDA(cudaStreamSynchronize(s));  // W.idx is refilled from the host vector
     }
   }
   return DF_OK;
@@ -649,16 +712,18 @@ static int iteration_body(ScfMol& M, int prec) {
   return iteration_tail(M);
 }
 
-// Launch one iteration (asynchronously, except for the eager dm0 iteration).
+// Second half of the first iteration from a non-idempotent dm0 (after dm0_launch drained).
+static int scf_dm0_finish(ScfMol& M) {
+  DF_TRY(dm0_finish(M));
+  DF_TRY(iteration_tail(M));
+  M.first_dm0 = false;
+  return DF_OK;
+}
+
+// Launch one iteration asynchronously.  The first iteration from a non-idempotent dm0 only
+// enqueues its first half here (phase DM0_EIG): scf_dm0_finish completes it.
 static int scf_iter_launch(ScfMol& M, bool use_graphs) {
-  if (M.first_dm0) {
-    const long nn = (long)M.nao * M.nao;
-    DF_CUDA(cudaMemcpyAsync(M.W.Dprev, M.W.D, sizeof(double) * nn, cudaMemcpyDeviceToDevice, M.s));
-    DF_TRY(jk_general_density(M));
-    DF_TRY(iteration_tail(M));
-    M.first_dm0 = false;
-    return DF_OK;
-  }
+  if (M.first_dm0) return dm0_launch(M);
   int gi = M.prec == DF_FP64 ? 0 : 1;
   if (!use_graphs || prof_on()) return iteration_body(M, M.prec);
   if (!M.graph[gi]) {
@@ -711,7 +776,7 @@ static bool scf_iter_finish(ScfMol& M) {
   // phase reached, the mixed-precision vectors in the DIIS history no longer describe the
   // FP64 problem (the mixed floor was high); restart the extrapolation from the new vector.
   if (M.opt.precision == DF_MIXED && M.prec == DF_FP64 && M.fp64_done == 0 && h.emax > 3.0 * M.best_err) {
-    diis_reset_kernel<<<1, 32, 0, M.s>>>(M.W.diis);
+    diis_keep_newest_kernel<<<1, 32, 0, M.s>>>(M.W.diis);
     if (cudaGetLastError() != cudaSuccess) {
       M.rc = DF_ERR_CUDA;
       set_error("scf: DIIS restart launch failed");
@@ -874,7 +939,12 @@ int scf_run_on(const df_molecule* mol, const scf_opts& o, const double* dm0, dou
   M.mo_out = mo_energy;
   int rc = scf_setup(M);
   while (rc == DF_OK && !M.done) {
+    const bool dm0_first = M.first_dm0;
     rc = scf_iter_launch(M, true);
+    if (rc == DF_OK && dm0_first) {
+      rc = cudaStreamSynchronize(s) == cudaSuccess ? scf_dm0_finish(M) : DF_ERR_CUDA;
+      if (rc == DF_ERR_CUDA) set_error("scf_run: %s", cudaGetErrorString(cudaGetLastError()));
+    }
     if (rc != DF_OK) break;
     cudaError_t e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) {
@@ -978,6 +1048,10 @@ extern "C" int scf_run_batch(const df_molecule* mols, int nmol, const scf_opts* 
         break;
       case ScfMol::READY:
         r = scf_iter_launch(*M, true);
+        if (r == DF_OK) M->phase = M->first_dm0 ? ScfMol::DM0_EIG : ScfMol::ITER;
+        break;
+      case ScfMol::DM0_EIG:
+        r = scf_dm0_finish(*M);
         if (r == DF_OK) M->phase = ScfMol::ITER;
         break;
       case ScfMol::ITER:

@@ -203,6 +203,8 @@ def evaluate(model: GuessModel, mols, slots: int = 32, precision: str = "mixed")
     t_core = time.perf_counter() - t0
     t0 = time.perf_counter()
     dm0 = [predict_density(model, m) for m in mols]
+    torch.cuda.synchronize()
+    t_predict = time.perf_counter() - t0
     learned = scf_run_batch(mols, slots=slots, precision=precision, dm0s=dm0, raise_on_noconv=False).results
     torch.cuda.synchronize()
     t_learned = time.perf_counter() - t0
@@ -218,7 +220,7 @@ def evaluate(model: GuessModel, mols, slots: int = 32, precision: str = "mixed")
             "other_state_dE_learned_minus_core": other,
             "mean_iter_core": float(it_core.mean()) if same else None,
             "mean_iter_learned": float(it_learn.mean()) if same else None,
-            "wall_s_core": t_core, "wall_s_learned": t_learned,
+            "wall_s_core": t_core, "wall_s_learned": t_learned, "wall_s_predict": t_predict,
             "guess_used": int(sum(r.guess == 1 for r in learned)), "guess_rejected": int(sum(r.guess == 2 for r in learned)),
             "max_abs_dE_same_state": float(de.max()) if same else None, "converged_core": int(sum(r.converged for r in core)),
             "converged_learned": int(sum(r.converged for r in learned))}

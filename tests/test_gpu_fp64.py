@@ -167,8 +167,16 @@ def test_scf_fp64_matches_oracle(c0, c0_scf):
 
 
 def test_scf_accepts_converged_dm0(c0, c0_scf):
+    # an idempotent dm0 starts from its orbitals; a non-idempotent one (the same density
+    # mixed with half the core-guess density, same electron count) through the eager first
+    # iteration; both reach the oracle's energy
     r = dfscf.scf_run(c0, dm0=c0_scf.D, precision="fp64")
     assert r.guess == 1 and r.converged and r.iterations <= 4
+    assert abs(r.energy - c0_scf.energy) <= 1e-9
+    _, Dc, *_ = dfscf.core_guess(c0)
+    mix = 0.5 * c0_scf.D + 0.5 * Dc.cpu().numpy()
+    r = dfscf.scf_run(c0, dm0=mix, precision="fp64")
+    assert r.guess == 1 and r.converged
     assert abs(r.energy - c0_scf.energy) <= 1e-9
 
 
@@ -255,6 +263,30 @@ def test_eigh_lowest_near_degenerate_spectrum():
     P = Z @ Z.T
     Pref = Q[:, :k] @ Q[:, :k].T
     assert np.max(np.abs(P - Pref)) <= 1e-8
+
+
+@pytest.mark.parametrize("n,nocc,ctas", [(60, 12, 0), (200, 40, 1), (400, 90, 0), (300, 64, 16)])
+def test_eigh_lowest_of_negated_projector(n, nocc, ctas):
+    """-2 V V^T (V orthonormal): an nocc-fold eigenvalue -2 and an (n - nocc)-fold 0.  Inverse
+    iteration from distinct starts plus two Gram-Schmidt passes resolves an exactly degenerate
+    cluster to ~1e-8 in the span (the vectors of the cluster come out nearly parallel before
+    the re-orthogonalisation); eigenvalues and orthonormality stay at rounding level.  One-CTA
+    and cooperative launches alike."""
+    rng = np.random.default_rng(n + nocc)
+    V, _ = np.linalg.qr(rng.standard_normal((n, nocc)))
+    A = -2.0 * V @ V.T
+    lib = dfscf.lib()
+    lib.df_tune_set(b"eig_ctas", ctas)
+    try:
+        w, Z = dfscf.eigh_lowest(A, nocc + 1)
+    finally:
+        lib.df_tune_set(b"eig_ctas", 0)
+    w, Z = w.cpu().numpy(), Z.cpu().numpy()
+    assert np.max(np.abs(w[:nocc] + 2.0)) <= 1e-12 and abs(w[nocc]) <= 1e-12
+    assert np.max(np.abs(Z.T @ Z - np.eye(nocc + 1))) <= 1e-11
+    Zo = Z[:, :nocc]
+    assert np.max(np.abs(Zo @ Zo.T - V @ V.T)) <= 1e-7
+    assert np.max(np.abs(A @ Z - Z * w)) <= 2e-7
 
 
 @pytest.mark.parametrize("n,rank", [(40, 5), (100, 10), (257, 31)])
