@@ -43,6 +43,7 @@ def lib():
         L.oracle_nuclear_repulsion.argtypes = [dp, dp, ctypes.c_int]
         L.oracle_int2c.argtypes = [dp, dp, ctypes.c_int, dp]
         L.oracle_int3c.argtypes = [dp, dp, ctypes.c_int, dp, dp, ctypes.c_int, dp]
+        L.oracle_int3c_rows.argtypes = [dp, dp, ctypes.c_int, dp, dp, ctypes.c_int, ctypes.c_void_p, ctypes.c_int, dp]
         L.oracle_int4c.argtypes = [dp, dp, ctypes.c_int, dp]
         L.oracle_cholesky.restype = ctypes.c_int
         L.oracle_cholesky.argtypes = [dp, ctypes.c_int, dp, ctypes.c_double]
@@ -102,6 +103,19 @@ def int3c(ao_xyz, ao_exp, aux_xyz, aux_exp) -> np.ndarray:
     return R
 
 
+def int3c_rows(ao_xyz, ao_exp, aux_xyz, aux_exp, rows) -> np.ndarray:
+    """(Q|r n) for the orbital rows r in `rows` and every n, as [naux][len(rows)][nao]: the
+    entries of int3c at packed pairs (max(r, n), min(r, n)), for sampling rows of B."""
+    ao_xyz, ao_exp, aux_xyz, aux_exp = map(_f64, (ao_xyz, ao_exp, aux_xyz, aux_exp))
+    nao, naux = ao_exp.size, aux_exp.size
+    r = np.ascontiguousarray(rows, dtype=np.int32)
+    assert r.ndim == 1 and np.all((r >= 0) & (r < nao))
+    out = np.empty((naux, r.size, nao))
+    lib().oracle_int3c_rows(_p(ao_xyz), _p(ao_exp), nao, _p(aux_xyz), _p(aux_exp), naux, r.ctypes.data_as(ctypes.c_void_p),
+                            r.size, _p(out))
+    return out
+
+
 def int4c(ao_xyz, ao_exp) -> np.ndarray:
     ao_xyz, ao_exp = _f64(ao_xyz), _f64(ao_exp)
     n = ao_exp.size
@@ -140,6 +154,17 @@ def whiten(L, R) -> np.ndarray:
     B = np.array(R, dtype=np.float64, order="C", copy=True)
     lib().oracle_whiten(_p(L), L.shape[0], _p(B), B.shape[1])
     return B
+
+
+def df_b_rows(ao_xyz, ao_exp, aux_xyz, aux_exp, L, rows) -> np.ndarray:
+    """Rows of the whitened tensor, B_P[r, n] = sum_Q (L^-1)_PQ (Q|r n) for r in `rows`, as
+    [naux][len(rows)][nao] (the metric / whitening equations after Eq. (eq:df:eri)).  The
+    triangular solve is a library routine (a step, not a restatement), applied to the same
+    columns that `whiten` substitutes one by one."""
+    from scipy.linalg import solve_triangular
+    R = int3c_rows(ao_xyz, ao_exp, aux_xyz, aux_exp, rows)
+    naux, nr, nao = R.shape
+    return solve_triangular(_f64(L), R.reshape(naux, nr * nao), lower=True).reshape(naux, nr, nao)
 
 
 def df_j(B, nao: int, D) -> np.ndarray:

@@ -141,6 +141,33 @@ void oracle_int3c(const double* ao_xyz, const double* ao_ex, int nao, const doub
 }
 
 /* ------------------------------------------------------------------------------------ */
+/* Rows of the three-centre tensor: (Q|r n) for the listed orbital rows r and every n,    */
+/* out [naux][nrows][nao] (unpacked).  The same closed form as oracle_int3c, evaluated    */
+/* with the larger index first so that every value equals the packed one bit for bit;    */
+/* it lets tests sample a few rows of B at sizes where the full tensor is too large.      */
+/* ------------------------------------------------------------------------------------ */
+void oracle_int3c_rows(const double* ao_xyz, const double* ao_ex, int nao, const double* aux_xyz,
+                       const double* aux_ex, int naux, const int* rows, int nrows, double* out) {
+#pragma omp parallel for schedule(dynamic)
+  for (int q = 0; q < naux; ++q) {
+    double ec = aux_ex[q];
+    const double* C = aux_xyz + 3 * q;
+    for (int t = 0; t < nrows; ++t) {
+      for (int n = 0; n < nao; ++n) {
+        int a = rows[t] > n ? rows[t] : n, b = rows[t] > n ? n : rows[t];
+        double ea = ao_ex[a], eb = ao_ex[b];
+        double p = ea + eb, mu = ea * eb / p;
+        double r2 = dist2(ao_xyz + 3 * a, ao_xyz + 3 * b);
+        double P[3];
+        for (int x = 0; x < 3; ++x) P[x] = (ea * ao_xyz[3 * a + x] + eb * ao_xyz[3 * b + x]) / p;
+        double pre = norm_s(ec) * norm_s(ea) * norm_s(eb) * 2.0 * pow(ORACLE_PI, 2.5) / (p * ec * sqrt(p + ec));
+        out[((size_t)q * nrows + t) * nao + n] = pre * exp(-mu * r2) * oracle_boys_f0(p * ec / (p + ec) * dist2(P, C));
+      }
+    }
+  }
+}
+
+/* ------------------------------------------------------------------------------------ */
 /* Four-centre integrals (ab|cd), full nao^4 tensor (brute-force checks only):            */
 /*   (ab|cd) = N_a N_b N_c N_d 2 pi^(5/2) / (p q sqrt(p+q))                               */
 /*             exp(-mu_ab R_AB^2) exp(-mu_cd R_CD^2) F0(p q/(p+q) |P-Q|^2)                */

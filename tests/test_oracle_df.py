@@ -74,6 +74,40 @@ def test_whitening_solves_triangular_system(c0, c0_system):
     assert np.max(np.abs(B - Bref)) <= 1e-9 * np.max(np.abs(Bref))
 
 
+def test_sampled_rows_match_packed_tensor(c0, c0_system):
+    # int3c_rows is int3c read at (max(r, n), min(r, n)): bit for bit, first and last rows
+    # included; df_b_rows gives the same rows of B as the pinned whitening
+    rows = [0, 37, c0.nao - 1]
+    R = oracle.int3c(c0.ao_xyz, c0.ao_exp, c0.aux_xyz, c0.aux_exp)
+    Rr = oracle.int3c_rows(c0.ao_xyz, c0.ao_exp, c0.aux_xyz, c0.aux_exp, rows)
+    n = np.arange(c0.nao)
+    for t, r in enumerate(rows):
+        a, b = np.maximum(r, n), np.minimum(r, n)
+        assert np.array_equal(Rr[:, t, :], R[:, a * (a + 1) // 2 + b])
+    Br = oracle.df_b_rows(c0.ao_xyz, c0.ao_exp, c0.aux_xyz, c0.aux_exp, c0_system.L, rows)
+    for t, r in enumerate(rows):
+        a, b = np.maximum(r, n), np.minimum(r, n)
+        ref = c0_system.B[:, a * (a + 1) // 2 + b]
+        assert np.max(np.abs(Br[:, t, :] - ref)) <= 1e-9 * np.max(np.abs(ref))
+    # the sampled-row J and K formulas of the full-size GPU test, against the oracle's df_j /
+    # df_k on the whole tensor: K among the rows, J of a density supported on the rows
+    rng = np.random.default_rng(5)
+    C = rng.standard_normal((c0.nao, 7)) / np.sqrt(c0.nao)
+    Ds = np.zeros((c0.nao, c0.nao))
+    for r in rows:
+        v = 0.1 * rng.standard_normal(c0.nao)
+        Ds[r, :] += v
+        Ds[:, r] += v
+    X = Br @ C
+    Kref = np.einsum("pai,pbi->ab", X, X)
+    d = sum(2.0 * Br[:, t, :] @ Ds[r, :] - Br[:, t, rows] @ Ds[r, rows] for t, r in enumerate(rows))
+    Jref = np.einsum("p,pab->ab", d, Br[:, :, rows])
+    K = oracle.df_k(c0_system.B, c0.nao, C)[np.ix_(rows, rows)]
+    J = oracle.df_j(c0_system.B, c0.nao, Ds)[np.ix_(rows, rows)]
+    assert np.max(np.abs(K - Kref)) <= 1e-11 * np.max(np.abs(K))
+    assert np.max(np.abs(J - Jref)) <= 1e-11 * np.max(np.abs(J))
+
+
 def test_aux_normalisation_invariance(c0, c0_system):
     """chol(Lam M Lam) = Lam L for positive diagonal Lam, so B does not depend on aux scaling."""
     lam = np.exp(np.random.default_rng(0).uniform(-2, 2, size=c0.naux))
