@@ -63,11 +63,11 @@ __device__ __forceinline__ uint32_t mbar_try_wait(uint64_t* bar, uint32_t parity
   return ok;
 }
 // Bounded wait: false if the phase did not complete within WAIT_LIMIT polls or another
-// role already gave up.
+// role already gave up (abort_flag may be null: no early exit).
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
   for (uint32_t i = 0; i < WAIT_LIMIT; ++i) {
     if (mbar_try_wait(bar, parity)) return true;
-    if ((i & 255u) == 255u && *abort_flag) return false;
+    if ((i & 255u) == 255u && abort_flag && *abort_flag) return false;
   }
   return false;
 }
@@ -245,6 +245,7 @@ __global__ void __launch_bounds__(THREADS, 1) split_bf16_gemm_kernel(const __gri
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tmem_base;
+  int issued = 0;  // k-blocks whose loads the producer has issued
 
   if (warp == 0 && lane == 0 && nkb > 0) {
     // ---- TMA producer ----------------------------------------------------------------
@@ -263,6 +264,7 @@ __global__ void __launch_bounds__(THREADS, 1) split_bf16_gemm_kernel(const __gri
         tma_load_2d(st + j * a_bytes, &maps.a[j], &full_bar[s], kx, row0);
         tma_load_2d(st + NP * a_bytes + j * p.b_bytes, &maps.b[j], &full_bar[s], kx, col0);
       }
+      issued = i + 1;
     }
   } else if (warp == 1 && lane == 0 && nkb > 0) {
     // ---- MMA issuer ------------------------------------------------------------------
@@ -361,7 +363,17 @@ __global__ void __launch_bounds__(THREADS, 1) split_bf16_gemm_kernel(const __gri
   }
   tc_fence_before();
   __syncthreads();
-  if (abort_flag && threadIdx.x == 0) atomicExch(p.err, 1);
+  if (abort_flag && warp == 0 && lane == 0) {
+    atomicExch(p.err, 1);
+    // after a timeout, wait (bounded) for the loads still in flight into each ring slot
+    // before the CTA's shared memory is released: the last k-block issued to slot s
+    // completes phase ((i / stages) & 1) of full_bar[s]
+    for (int s = 0; s < p.stages; ++s) {
+      const int last = issued - 1 - ((issued - 1 - s) % p.stages + p.stages) % p.stages;
+      if (issued > 0 && last >= 0 && last % p.stages == s)
+        mbar_wait(&full_bar[s], (uint32_t)(last / p.stages) & 1u, nullptr);
+    }
+  }
   if (warp == 1) {
     tc_fence_after();
     tmem_dealloc(tmem, ncols);
