@@ -68,3 +68,28 @@ def test_tuning_knobs_host_side():
     finally:
         tune.set_knob("jpass2_rows", 256)
     assert tune.bucket(1500, 4500, 150, "mixed") == "mixed:nao2048:naux8192:nocc256"
+
+
+def test_header_is_plain_c_and_links():
+    """include/dfscf.h is consumable from C99, and a C program calling the core entry points
+    links against the built library (compiled from standard input, linked to /dev/null)."""
+    import shutil
+    import subprocess
+    import paper_2506_06661_gb300 as dfscf
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        import pytest
+        pytest.skip("gcc not available")
+    lib_path = dfscf._build.build()
+    cuda_inc = os.path.join(os.path.dirname(os.path.dirname(os.path.realpath(dfscf._build.nvcc()))), "include")
+    prog = ("#include \"dfscf.h\"\n"
+            "typedef void (*fn)(void);\n"
+            "int main(void) {\n"
+            "  volatile fn used[] = {(fn)df_metric_chol, (fn)df_build_B, (fn)df_jk, (fn)scf_run, (fn)scf_run_batch};\n"
+            "  size_t b = df_B_bytes(100, 300, DF_FP64);\n"
+            "  return (b > 0 && df_version() > 0 && df_last_error() != 0 && used[0] != 0) ? 0 : 1;\n"
+            "}\n")
+    cmd = [gcc, "-x", "c", "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"), "-I", cuda_inc, "-",
+           "-L", os.path.dirname(lib_path), "-l:" + os.path.basename(lib_path), "-o", os.devnull]
+    r = subprocess.run(cmd, input=prog, capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
