@@ -325,7 +325,9 @@ int df_j_noalloc(const void* B, int nao, int naux, const double* D, double* J, c
  * Launch parameters chosen by the autotuner (paper_2506_06661_gb300/tune.py): "umma_max_stages"
  * (2..4, shared-memory ring depth of the tensor-core GEMM), "syrk_split" and "fp64_syrk_split"
  * (K-dimension splits of the exchange SYRK, 0 = built-in heuristic), "jpass2_rows" (32..512,
- * auxiliary rows per CTA slice of J's second pass).  Host-side process-wide state: change
+ * auxiliary rows per CTA slice of J's second pass), "eig_ctas" (CTAs of the multi-SM
+ * eigensolver: 0 automatic, 1 a single CTA) and "mixed_planes" (3..5 BF16 planes per operand of
+ * the mixed exchange: 6, 10 or 15 plane products).  Host-side process-wide state: change
  * knobs only between calls and re-query *_work_bytes afterwards (split counts size the
  * workspaces).  df_tune_set returns DF_ERR_ARG for an unknown name or an out-of-range value;
  * df_tune_get returns -1 for an unknown name.                                              */
