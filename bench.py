@@ -248,6 +248,33 @@ def roofline_of(prof, name, flops_per_launch=None, bytes_per_launch=None, peak=N
             "traffic": None, "avg_ms": avg, "launches": calls}
 
 
+def scf_time_to_convergence(dfscf, torch, wl, oracle_energy=False, max_cycle=100):
+    """Wall time, iterations and energies of the mixed-precision and the plain FP64 SCF of
+    one molecule (one untimed warm-up run each builds and captures the graphs first)."""
+    mol, desc = workload(wl)
+    md = dfscf.MoleculeOnDevice(mol)
+    out = {"workload": desc}
+    for prec in ("mixed", "fp64"):
+        work = dfscf._work(dfscf.scf_work_bytes(md.nao, md.naux, md.nelec // 2, prec))
+        dfscf.scf_run(md, precision=prec, work=work, raise_on_noconv=False, max_cycle=max_cycle)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = dfscf.scf_run(md, precision=prec, work=work, raise_on_noconv=False, max_cycle=max_cycle)
+        torch.cuda.synchronize()
+        out[prec] = {"seconds": time.perf_counter() - t0, "energy": r.energy, "iterations": r.iterations,
+                     "fp64_iterations": r.fp64_iterations, "converged": r.converged}
+        del work
+    out["abs_dE_mixed_vs_fp64"] = abs(out["mixed"]["energy"] - out["fp64"]["energy"])
+    out["speedup_mixed_over_fp64"] = out["fp64"]["seconds"] / out["mixed"]["seconds"]
+    if oracle_energy:
+        from oracle import scf as oscf
+        e = oscf.rhf(oscf.build_system(mol)).energy
+        out["oracle_energy"] = e
+        for prec in ("mixed", "fp64"):
+            out[prec]["abs_err_vs_oracle"] = abs(out[prec]["energy"] - e)
+    return out
+
+
 def run_ours(args):
     import torch
     ws, rank, local = dist_env()
@@ -306,10 +333,10 @@ def run_ours(args):
         if r:
             rl[name] = r
     dominant = max(rl.values(), key=lambda r: r["avg_ms"] * r["launches"]) if rl else None
-    # DRAM traffic of the FP64 half-transform: the ncu capture on the 80-centre workload
-    # (profiles/ncu_exchange_kernels_80centres.md) read 771.98 MB and wrote 144.12 MB against
-    # 926.0 MB of algorithmic bytes (B read once, X written once); traffic grows with those
-    # bytes, so one launch here moves that ratio times its own algorithmic bytes
+    # DRAM traffic of the FP64 half-transform: the ncu capture of the same kernel on the
+    # 80-centre workload read 771.98 MB and wrote 144.12 MB against 926.0 MB of algorithmic
+    # bytes (B read once, X written once); traffic grows with those bytes, so one launch here
+    # moves that ratio times its own algorithmic bytes
     if dominant and dominant["kernel"] == "k_halftransform_fp64":
         ht_bytes = 8.0 * naux * dfscf.lib().df_B_ld(nao) + 8.0 * nao * naux * nocc
         m80_bytes = 8.0 * 1200 * dfscf.lib().df_B_ld(400) + 8.0 * 400 * 1200 * 40
@@ -361,6 +388,13 @@ def run_ours(args):
                  "kernels": rlm, "gpu_launches": LAUNCHES_MIXED * args.mixed_steps, "clocks": clkm.summary(),
                  "phase_ms": {k: v[0] / max(v[1], 1) for k, v in profm.items()}}
 
+    scf = None
+    if not args.no_scf:
+        scf = {"what": "wall time of scf_run to |dE| < 1e-8 Eh and max|e| < 1e-5 (integrals, metric, B and the "
+                       "iterations), mixed precision against plain FP64, same molecule and options"}
+        for wl in ("c0", "m120"):
+            scf[wl] = scf_time_to_convergence(dfscf, torch, wl, oracle_energy=(wl == "c0"))
+
     line = {"metric": METRIC, "value": value, "unit": "builds/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms64, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -378,7 +412,8 @@ def run_ours(args):
             "gpu_launches": LAUNCHES_FP64 * args.steps,
             "clocks": clocks,
             "setup_s": t_setup,
-            "mixed": mixed}
+            "mixed": mixed,
+            "scf": scf}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_obj(mol, args.workload)
     if rank == 0:
@@ -446,6 +481,7 @@ def run_scenario_batch(args):
             slots, src = int(t["slots"]), f"tuned now on 64 molecules: {t['molecules_per_s']}"
     out = {"scenario": "batch", "molecules": len(mols), "centres": "10-80 (uniform, seed 1)",
            "nao_range": [min(m.nao for m in mols), max(m.nao for m in mols)], "slots": slots, "slots_source": src}
+    per_mol = {}
     for prec in ("mixed",) + (("fp64",) if args.batch_fp64 else ()):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -453,15 +489,32 @@ def run_scenario_batch(args):
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
         conv = [r for r in res if r.converged]
+        per_mol[prec] = res
         out[prec] = {"seconds": dt, "molecules_per_s": len(mols) / dt, "converged": len(conv),
+                     "not_converged": [i for i, r in enumerate(res) if not r.converged],
                      "mean_iterations": float(np.mean([r.iterations for r in res])),
-                     "energies": [r.energy for r in res]}
+                     "mean_fp64_iterations": float(np.mean([r.fp64_iterations for r in res]))}
     if "fp64" in out:
-        d = [abs(a - b) for a, b in zip(out["mixed"]["energies"], out["fp64"]["energies"])]
-        out["max_abs_dE_mixed_vs_fp64"] = float(max(d))
-    for prec in ("mixed", "fp64"):
-        if prec in out:
-            out[prec].pop("energies")
+        # the precision gap is judged on molecules that converged in both arms; the others
+        # are listed by index
+        both = [i for i in range(len(mols)) if per_mol["mixed"][i].converged and per_mol["fp64"][i].converged]
+        d = np.array([abs(per_mol["mixed"][i].energy - per_mol["fp64"][i].energy) for i in both])
+        out["converged_both"] = len(both)
+        out["abs_dE_mixed_vs_fp64"] = {
+            "max": float(d.max()) if d.size else None, "median": float(np.median(d)) if d.size else None,
+            "over_1e-6": [both[k] for k in np.nonzero(d > 1e-6)[0]]}
+    if args.dump:
+        rows = []
+        for i, m in enumerate(mols):
+            row = {"index": i, "natm": m.natm, "nao": m.nao, "nelec": m.nelec}
+            for prec, res in per_mol.items():
+                r = res[i]
+                row[prec] = {"energy": r.energy, "iterations": r.iterations, "fp64_iterations": r.fp64_iterations,
+                             "converged": r.converged, "last_dE": r.last_de, "last_err": r.last_err,
+                             "homo": r.homo, "lumo": r.lumo}
+            rows.append(row)
+        with open(args.dump, "w") as fh:
+            json.dump(rows, fh)
     print(json.dumps(out), flush=True)
     return 0
 
@@ -509,6 +562,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-mixed", dest="mixed", action="store_false")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-scf", action="store_true", help="skip the SCF time-to-convergence block of the default line")
     ap.add_argument("--scenario", choices=["fock", "scf", "batch", "guess"], default="fock",
                     help="fock: Fock-build throughput (the default line); scf: SCF time to convergence, "
                          "mixed vs FP64; batch: batched SCF of uneven molecules; guess: learned guess")
@@ -522,6 +576,7 @@ def main():
     ap.add_argument("--neval", type=int, default=512)
     ap.add_argument("--epochs", type=int, default=20)
     ap.add_argument("--save-model", default="")
+    ap.add_argument("--dump", default="", help="batch scenario: write per-molecule results to this JSON file")
     args = ap.parse_args()
     if args.scenario == "scf":
         return run_scenario_scf(args)

@@ -50,20 +50,25 @@ extern "C" {
 /* ---- precision modes -------------------------------------------------------------- */
 #define DF_FP64 0            /* every contraction in FP64                               */
 #define DF_MIXED 1           /* K contractions as split-BF16 GEMMs on tcgen05 tensor
-                                cores.  Every operand row is held as BF16 planes:
-                                p0 = x rounded to 8 bits on the power-of-two grid just
-                                above the row's max |x| (an integer times a scale fixed
-                                along the contraction), p1 = RN_bf16(x - p0),
-                                p2 = RN_bf16(x - p0 - p1).  Plane products pa*qb with
-                                a + b < planes accumulate in FP32, one accumulator per
-                                order a + b; order 0 sums integers on one grid and is
-                                exact.  planes = 3 (default: six products) or 2 (three
-                                products), set by the knob "mixed_planes" before
-                                workspaces are sized.  J is the FP64 streaming pass in
-                                both modes.  An FP32 J, or products summed in a single
-                                FP32 accumulator, leaves an error in F that the
-                                orthogonal-basis DIIS commutator amplifies to ~1e-3 on
-                                ill-conditioned bases, where the mixed SCF then stalls. */
+                                cores.  Every operand row (of B_P, of C^T, of X) is held
+                                as NP BF16 planes, NP = the knob "mixed_planes" (3, 4 or
+                                5; default 5).  With sigma the power of two just above
+                                the row's max |x|: p0 = x rounded to the grid
+                                sigma 2^-7 and p1 = (x - p0) rounded to sigma 2^-15 are
+                                fixed-point planes (integers in [-128, 128] on grids
+                                fixed along the contraction); p2.. p(NP-1) are the BF16
+                                roundings of what is left.  Plane products pa*qb with
+                                a + b < NP (6, 10 or 15 of them) accumulate in FP32
+                                tensor memory.  In the exchange SYRK the products of
+                                the two fixed-point planes, (0,0), (0,1)+(1,0) and
+                                (1,1), each sum integers on one grid in an accumulator
+                                of their own and are exact; every product with a
+                                floating plane goes to a fourth.  J is the FP64
+                                streaming pass in both modes.  An FP32 J, or products
+                                summed in a single FP32 accumulator, leaves an error in
+                                F that the orthogonal-basis DIIS commutator amplifies to
+                                ~1e-3 on ill-conditioned bases, where the mixed SCF
+                                then stalls. */
 
 /* Message describing the last error on the calling thread ("" if none). */
 const char* df_last_error(void);
@@ -110,8 +115,11 @@ int df_metric_chol(const double* aux_xyz, const double* aux_exp, int naux, doubl
  * holding, in this order:
  *   [0]  FP64 packed rows: naux rows of df_B_ld(nao) doubles, entry mn at m(m+1)/2+n,
  *        padding zero;
- *   [1]  (DF_MIXED only) BF16 planes p0, p1, p2 of the full symmetric B_P, each
- *        naux x npad x npad with npad = df_nao_pad(nao), padding zero.
+ *   [1]  (DF_MIXED only) NP BF16 planes p0 .. p(NP-1) of the full symmetric B_P (the
+ *        row-scaled planes described at DF_MIXED), each naux x npad x npad with
+ *        npad = df_nao_pad(nao), padding zero; NP is the knob "mixed_planes" when
+ *        df_B_bytes is called, and df_build_B must see the same value.  A later mixed
+ *        df_jk needs NP at least its own "mixed_planes" (checked: DF_ERR_ARG otherwise).
  * L is the factor from df_metric_chol.  work: df_build_B_work_bytes(...) bytes.         */
 long df_B_ld(int nao);
 int df_nao_pad(int nao);
@@ -130,6 +138,10 @@ int df_B_get_packed(const void* B, int nao, int naux, int P, double* row, cudaSt
  * D: [nao][nao] symmetric density; C: [nao][nocc] occupied coefficients.  For an RHF
  * density D = 2 C C^T the Fock matrix is F = h + J - K.  J or K may be NULL to skip it
  * (then D or C may be NULL too).  precision DF_MIXED requires B built with DF_MIXED.
+ * The tensor-core kernels of the mixed exchange bound every wait; if one gives up, K is
+ * filled with NaN and, unless the stream is being captured into a graph, df_jk (which then
+ * synchronises the stream once to read the flag) returns DF_ERR_TIMEOUT.  A mixed df_jk
+ * outside a capture therefore returns with the stream drained.
  * work: df_jk_work_bytes(nao, naux, nocc, precision) bytes.                           */
 size_t df_jk_work_bytes(int nao, int naux, int nocc, int precision);
 int df_jk(const void* B, int nao, int naux, int precision, const double* D, const double* C,
@@ -141,7 +153,8 @@ int df_jk(const void* B, int nao, int naux, int precision, const double* D, cons
  * implicit QL on one thread block (n < 160), or for larger n the multi-SM path of
  * df_eigh_lowest with k = n (Sturm multisection, inverse iteration, back-transformation,
  * two Gram-Schmidt passes).  Synchronises the stream; DF_ERR_NOCONV if the solver breaks
- * down.  work: df_eigh_work_bytes(n).                                                    */
+ * down, DF_ERR_TIMEOUT if a grid barrier of the multi-SM path gave up waiting (every CTA
+ * then returns; the context stays usable).  work: df_eigh_work_bytes(n).                 */
 size_t df_eigh_work_bytes(int n);
 int df_eigh(double* A, int n, double* w, double* Z, void* work, size_t work_bytes, cudaStream_t s);
 
@@ -149,7 +162,8 @@ int df_eigh(double* A, int n, double* w, double* Z, void* work, size_t work_byte
  * the occupied orbitals and the LUMO: Householder reduction, Sturm bisection, inverse
  * iteration on the tridiagonal matrix, back-transformation of the k vectors and
  * re-orthonormalisation.  A is overwritten.  work: df_eigh_lowest_work_bytes(n, k).
- * Returns DF_ERR_NOCONV if inverse iteration or re-orthonormalisation breaks down.        */
+ * Returns DF_ERR_NOCONV if inverse iteration or re-orthonormalisation breaks down and
+ * DF_ERR_TIMEOUT if a grid barrier of the multi-SM path gave up waiting.                  */
 size_t df_eigh_lowest_work_bytes(int n, int k);
 int df_eigh_lowest(double* A, int n, int k, double* w, double* Z, void* work, size_t work_bytes, cudaStream_t s);
 
@@ -250,6 +264,23 @@ int scf_run_batch(const df_molecule* mols, int nmol, const scf_opts* opt, const 
  * All pointers are device memory; n is the number of pair samples.                        */
 size_t guess_mlp_param_count(void);
 size_t guess_mlp_work_bytes(int n);
+/* Model lifecycle.  guess_mlp_create initialises params [param_count] (device) with
+ * Uniform(-sqrt(3/fan_in), +sqrt(3/fan_in)) weights drawn from a counter-based generator
+ * (SplitMix64 of seed and parameter index) and zero biases, and zeroes the Adam moments
+ * adam_m, adam_v (each may be NULL).
+ * guess_mlp_save writes the model to the HOST buffer blob of guess_mlp_blob_bytes(m) bytes,
+ * m = 1 when adam_m and adam_v are given (both or neither): a header (magic "DFSCFMLP",
+ * format version, the layer shapes, the Adam step, the parameter count and an FNV-1a 64
+ * checksum of the payload) followed by params, then adam_m and adam_v, as FP32.
+ * guess_mlp_load checks magic, version, layer shapes, size and checksum (DF_ERR_ARG on any
+ * mismatch, nothing copied) and fills params (and adam_m, adam_v, zeroed when the blob holds
+ * no moments) and the HOST int *step (may be NULL; 0 without moments).  Both synchronise s. */
+int guess_mlp_create(unsigned long long seed, float* params, float* adam_m, float* adam_v, cudaStream_t s);
+size_t guess_mlp_blob_bytes(int with_moments);
+int guess_mlp_save(const float* params, const float* adam_m, const float* adam_v, int step, void* blob,
+                   size_t blob_bytes, cudaStream_t s);
+int guess_mlp_load(const void* blob, size_t blob_bytes, float* params, float* adam_m, float* adam_v, int* step,
+                   cudaStream_t s);
 /* feat [natm(natm+1)/2][65], mask [natm(natm+1)/2]; work >= 128*natm bytes.               */
 int guess_features(const double* xyz, int natm, float* feat, float* mask, void* work, size_t work_bytes,
                    cudaStream_t s);
@@ -314,10 +345,12 @@ int df_core_guess(const df_molecule* mol, double lindep, double* S_out, double* 
  * that the library reserves on every GPU that loads it, until the process exits.  The
  * call allocates nothing and returns DF_ERR_ARG when (nao, naux) need more than that
  * (for example nao <= 400 with naux <= 1200 always fits; nao 1500 does not).
- * The first call on each device looks up the array's device address (with that device
- * current); make that first call before any stream capture.  Every call shares the array
- * and it keeps the last call's contents: calls whose GPU work overlaps (other streams or
- * threads on the same device) race and must be ordered by the caller.                  */
+ * Each call made outside a stream capture looks up the array's device address (with the
+ * calling thread's current device); a call inside a capture reuses the address of the
+ * last such call on that device, so make one call on each device before capturing (a first
+ * call inside a capture returns DF_ERR_ARG).  Every call shares the array and it keeps the
+ * last call's contents: calls whose GPU work overlaps (other streams or threads on the same
+ * device) race and must be ordered by the caller.                                        */
 size_t df_j_noalloc_capacity(void);
 int df_j_noalloc(const void* B, int nao, int naux, const double* D, double* J, cudaStream_t s);
 
@@ -327,7 +360,11 @@ int df_j_noalloc(const void* B, int nao, int naux, const double* D, double* J, c
  * (K-dimension splits of the exchange SYRK, 0 = built-in heuristic), "jpass2_rows" (32..512,
  * auxiliary rows per CTA slice of J's second pass), "eig_ctas" (CTAs of the multi-SM
  * eigensolver: 0 automatic, 1 a single CTA) and "mixed_planes" (3..5 BF16 planes per operand of
- * the mixed exchange: 6, 10 or 15 plane products).  Host-side process-wide state: change
+ * the mixed exchange: 6, 10 or 15 plane products; it also sizes a mixed B).  Two more knobs
+ * bound the multi-SM eigensolver's grid barriers: "eig_barrier_polls" (256..2^30 polls before a
+ * wait gives up with DF_ERR_TIMEOUT; default 2^22, about a second) and "eig_barrier_extra"
+ * (0 or 1; 1 makes every barrier wait for one arrival that never comes, so that a test can
+ * watch the bounded wait run out; leave it 0).  Host-side process-wide state: change
  * knobs only between calls and re-query *_work_bytes afterwards (split counts size the
  * workspaces).  df_tune_set returns DF_ERR_ARG for an unknown name or an out-of-range value;
  * df_tune_get returns -1 for an unknown name.                                              */

@@ -109,6 +109,10 @@ _SIGS = {
     "guess_mlp_loss_grad": (_I, [_VP, _VP, _VP, _VP, _I, ctypes.c_float, _VP, _VP, _VP, _SZ, _VP]),
     "guess_mlp_train_step": (_I, [_VP, _VP, _VP, _I, ctypes.c_float, _VP, _VP, _VP, _I, ctypes.c_float, _VP, _VP,
                                   _SZ, _VP]),
+    "guess_mlp_create": (_I, [ctypes.c_ulonglong, _VP, _VP, _VP, _VP]),
+    "guess_mlp_blob_bytes": (_SZ, [_I]),
+    "guess_mlp_save": (_I, [_VP, _VP, _VP, _I, _VP, _SZ, _VP]),
+    "guess_mlp_load": (_I, [_VP, _SZ, _VP, _VP, _VP, ctypes.POINTER(_I), _VP]),
     "guess_density_work_bytes": (_SZ, [_I]),
     "guess_density": (_I, [_VP, _VP, _I, _I, _VP, _VP, _VP, _SZ, _VP]),
     "df_lowdin_work_bytes": (_SZ, [_I]),

@@ -129,6 +129,10 @@ static Knob g_knobs[] = {
     {"jpass2_rows", 256, 32, 512},   // auxiliary rows per CTA slice of J's second pass
     {"eig_ctas", 0, 0, 4096},        // CTAs of the multi-SM eigensolver (0 auto, 1 single CTA)
     {"mixed_planes", 5, 3, 5},       // BF16 planes per operand of the mixed exchange (3, 4, 5: 6, 10, 15 products)
+    {"mixed_incremental", 1, 0, 1},  // mixed SCF: update K from the change of the occupied projector
+    {"eig_barrier_polls", 1 << 22, 256, 1 << 30},  // polls before a grid-barrier wait of the eigensolver gives up
+    {"eig_barrier_extra", 0, 0, 1},  // test hook: 1 = every eigensolver grid barrier waits for one arrival
+                                     // that never comes, so its bounded wait runs out
 };
 
 int knob(const char* name) {

@@ -590,24 +590,38 @@ __global__ void __launch_bounds__(1024) eigh_lowest_kernel(double* A, int n, int
 // Barrier waits are bounded; a timeout sets the error flag and every CTA returns.
 struct GridBarrier {
   unsigned count;  // arrivals since launch (monotone; zeroed before the launch)
-  unsigned pad;
-  int err;
+  unsigned extra;  // arrivals expected beyond the grid's own CTAs: 0, except in the test of
+                   // the bounded wait (knob "eig_barrier_extra"), where no barrier can complete
+  int err;         // 1: a wait gave up; 2: inverse iteration failed
+  unsigned limit;  // polls before a wait gives up (knob "eig_barrier_polls")
 };
 
+// Set up the barrier record on the stream (graph-capturable, unlike a host write).
+__global__ void grid_barrier_init_kernel(GridBarrier* b, unsigned limit, unsigned extra) {
+  if (threadIdx.x != 0) return;
+  b->count = 0;
+  b->extra = extra;
+  b->err = 0;
+  b->limit = limit;
+}
+
 // Grid barrier on a monotone arrival counter: the b-th barrier completes when the counter
-// reaches b * G.  Thread 0 of each CTA arrives after a device-scope fence and polls with
-// acquire loads; at most 2^22 polls (seconds), then the error flag is raised.
+// reaches b * (G + extra).  Thread 0 of each CTA arrives after a device-scope fence and polls
+// with acquire loads; after `limit` polls (2^22 by default, about a second) it raises the
+// error flag, every other CTA sees the flag within 256 polls, and all of them return.
 __device__ bool grid_sync(GridBarrier* b, unsigned G) {
   __shared__ int ok;
   __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();
+    const unsigned Ge = G + b->extra;
+    const unsigned limit = b->limit;
     const unsigned old = atomicAdd(&b->count, 1u);
-    const unsigned target = (old / G + 1u) * G;
+    const unsigned target = (old / Ge + 1u) * Ge;
     unsigned cur = old + 1u;
     volatile int* verr = &b->err;
     for (unsigned it = 0; (int)(cur - target) < 0; ++it) {
-      if (it > (1u << 22)) {
+      if (it > limit) {
         atomicCAS(&b->err, 0, 1);
         break;
       }
@@ -1091,7 +1105,9 @@ int eigh_lowest_rows(double* A, int n, int k, double* w, double* ZT, double* scr
     double* part = (double*)p;
     p += align_up(sizeof(double) * kCoopMaxCtas, 256);
     GridBarrier* bar = (GridBarrier*)p;
-    DF_CUDA(cudaMemsetAsync(bar, 0, sizeof(GridBarrier), s));
+    grid_barrier_init_kernel<<<1, 32, 0, s>>>(bar, (unsigned)knob("eig_barrier_polls"),
+                                              (unsigned)knob("eig_barrier_extra"));
+    DF_LAUNCHED("grid_barrier_init_kernel");
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(P.G);
     cfg.blockDim = dim3(256);
@@ -1161,6 +1177,7 @@ extern "C" int df_eigh(double* A, int n, double* w, double* Z, void* work, size_
   int h = 0;
   DF_CUDA(cudaMemcpyAsync(&h, status, sizeof(int), cudaMemcpyDeviceToHost, s));
   DF_CUDA(cudaStreamSynchronize(s));
+  DF_REQUIRE(h != 3, DF_ERR_TIMEOUT, "df_eigh: a grid barrier of the multi-SM eigensolver timed out");
   DF_REQUIRE(h == 0, DF_ERR_NOCONV, "df_eigh: eigensolver failed (status %d)", h);
   return DF_OK;
 }
@@ -1190,6 +1207,7 @@ extern "C" int df_eigh_lowest(double* A, int n, int k, double* w, double* Z, voi
   int h = 0;
   DF_CUDA(cudaMemcpyAsync(&h, status, sizeof(int), cudaMemcpyDeviceToHost, s));
   DF_CUDA(cudaStreamSynchronize(s));
+  DF_REQUIRE(h != 3, DF_ERR_TIMEOUT, "df_eigh_lowest: a grid barrier of the multi-SM eigensolver timed out");
   DF_REQUIRE(h == 0, DF_ERR_NOCONV, "df_eigh_lowest: inverse iteration or re-orthogonalisation failed (%d)", h);
   return DF_OK;
 }

@@ -6,13 +6,18 @@
 //
 // B layout (one caller-owned buffer):
 //   FP64 packed rows        naux x ld doubles,  ld = npair rounded up to 32 (256-byte rows)
-//   BF16 planes 0..3        naux x npad x npad  (mixed mode; full symmetric B_P, npad = nao
-//                                                rounded up to 128, zero padding)
-// Plane 0 is x rounded to 8 bits on a grid fixed along the row (the power of two just above
-// the row's max |x|); planes 1..3 are BF16 roundings of what is left (planes.cuh).  J streams the FP64 packed rows in both modes (each symmetric pair stored once,
-// weight 2 off the diagonal); the mixed K reads the BF16 planes through TMA as plain
-// K-major GEMM operands.
+//   BF16 planes 0..NP-1     naux x npad x npad  (mixed mode; full symmetric B_P, npad = nao
+//                                                rounded up to 128, zero padding; NP = 3..5)
+// With sigma the power of two just above the row's max |x|, planes 0 and 1 are fixed-point
+// (x on the grid sigma 2^-7, then the remainder on sigma 2^-15) and planes 2..NP-1 are BF16
+// roundings of what is left (planes.cuh).  J streams the FP64 packed rows in both modes
+// (each symmetric pair stored once, weight 2 off the diagonal); the mixed K reads the BF16
+// planes through TMA as plain K-major GEMM operands.
 #include <cuda_bf16.h>
+
+#include <algorithm>
+#include <mutex>
+#include <unordered_map>
 
 #include "common.cuh"
 #include "kernels.cuh"
@@ -23,28 +28,42 @@ namespace dfscf {
 long B_ld(int nao) { return (long)align_up((size_t)npair_of(nao), 32); }
 int nao_pad(int nao) { return (int)align_up((size_t)nao, 128); }
 
-BLayout B_layout(int nao, int naux, int precision) {
+BLayout B_layout(int nao, int naux, int precision, int planes) {
   BLayout L{};
   L.ld = B_ld(nao);
   L.npad = nao_pad(nao);
+  L.planes = precision == DF_MIXED ? std::min(kMixedPlanes, std::max(3, planes)) : 0;
   size_t off = 0;
   L.off64 = off;
   off += align_up(sizeof(double) * (size_t)naux * L.ld, 256);
-  if (precision == DF_MIXED) {
-    for (int j = 0; j < kMixedPlanes; ++j) {
-      L.offp[j] = off;
-      off += align_up(sizeof(__nv_bfloat16) * (size_t)naux * L.npad * L.npad, 256);
-    }
+  for (int j = 0; j < L.planes; ++j) {
+    L.offp[j] = off;
+    off += align_up(sizeof(__nv_bfloat16) * (size_t)naux * L.npad * L.npad, 256);
   }
   L.bytes = off;
   return L;
 }
 
+static std::mutex g_bplanes_mutex;
+static std::unordered_map<uintptr_t, int> g_bplanes;
+
+void record_B_planes(const void* B, int planes) {
+  std::lock_guard<std::mutex> lock(g_bplanes_mutex);
+  g_bplanes[(uintptr_t)B] = planes;
+}
+
+int recorded_B_planes(const void* B) {
+  std::lock_guard<std::mutex> lock(g_bplanes_mutex);
+  auto it = g_bplanes.find((uintptr_t)B);
+  return it == g_bplanes.end() ? -1 : it->second;
+}
+
 // ---- BF16 planes of B ------------------------------------------------------------------
-// Row (P, m) of the full symmetric B_P (over n) as kMixedPlanes row-scaled planes (planes.cuh;
+// Row (P, m) of the full symmetric B_P (over n) as `planes` row-scaled planes (planes.cuh;
 // residuals in FP64).  One CTA per row; padding (m or n >= nao) is zero.
 struct PlaneOut {
   __nv_bfloat16* p[kMixedPlanes];
+  int planes;
 };
 
 __global__ void __launch_bounds__(128) b_to_planes_kernel(const double* __restrict__ B64, long ld, int nao, int npad,
@@ -68,7 +87,8 @@ __global__ void __launch_bounds__(128) b_to_planes_kernel(const double* __restri
     __nv_bfloat16 q[kPlanesMax];
     split_row_value(load(n), sig, q);
 #pragma unroll
-    for (int j = 0; j < kMixedPlanes; ++j) out.p[j][o + n] = q[j];
+    for (int j = 0; j < kMixedPlanes; ++j)
+      if (j < out.planes) out.p[j][o + n] = q[j];
   }
 }
 
@@ -313,7 +333,13 @@ int build_K_fp64(const double* B64, long ld, int nao, int naux, const double* C,
 
 int run_jk(const void* B, int nao, int naux, int precision, const double* D, const double* C, int nocc, double* J,
            double* K, const JKWork& w, cudaStream_t s) {
-  BLayout L = B_layout(nao, naux, precision);
+  BLayout L = B_layout(nao, naux, precision, w.mk.planes);
+  if (precision == DF_MIXED && K) {
+    const int built = recorded_B_planes(B);
+    DF_REQUIRE(built < 0 || built >= w.mk.planes, DF_ERR_ARG,
+               "mixed exchange with %d BF16 planes on a B built with %d (set the knob mixed_planes before sizing "
+               "and building B, and keep it while B is used)", w.mk.planes, built);
+  }
   if (J) DF_TRY(build_J(B, L, nao, naux, precision, D, J, w, s));
   if (K) {
     if (precision == DF_FP64) {
@@ -329,14 +355,16 @@ int run_jk(const void* B, int nao, int naux, int precision, const double* D, con
 
 int build_B(const double* ao_xyz, const double* ao_exp, int nao, const double* aux_xyz, const double* aux_exp,
             int naux, const double* Lfac, int precision, void* Bbuf, double* pair_tab, cudaStream_t s) {
-  BLayout L = B_layout(nao, naux, precision);
+  BLayout L = B_layout(nao, naux, precision, mixed_planes());
   double* B64 = (double*)((char*)Bbuf + L.off64);
   DF_TRY(launch_int3c(ao_xyz, ao_exp, nao, aux_xyz, aux_exp, naux, B64, L.ld, pair_tab, s));
   DF_TRY(forward_substitution(B64, L.ld, L.ld, Lfac, naux, s));
   if (precision == DF_MIXED) {
     DF_REQUIRE(naux <= 65535, DF_ERR_ARG, "naux too large");
     PlaneOut po{};
-    for (int j = 0; j < kMixedPlanes; ++j) po.p[j] = (__nv_bfloat16*)((char*)Bbuf + L.offp[j]);
+    po.planes = L.planes;
+    for (int j = 0; j < L.planes; ++j) po.p[j] = (__nv_bfloat16*)((char*)Bbuf + L.offp[j]);
+    record_B_planes(Bbuf, L.planes);
     b_to_planes_kernel<<<dim3((unsigned)L.npad, (unsigned)naux), 128, 0, s>>>(B64, L.ld, nao, L.npad, po);
     DF_LAUNCHED("b_to_planes_kernel");
   }
@@ -352,7 +380,7 @@ extern "C" int df_nao_pad(int nao) { return nao > 0 ? nao_pad(nao) : 0; }
 
 extern "C" size_t df_B_bytes(int nao, int naux, int precision) {
   if (nao <= 0 || naux <= 0 || (precision != DF_FP64 && precision != DF_MIXED)) return 0;
-  return B_layout(nao, naux, precision).bytes;
+  return B_layout(nao, naux, precision, mixed_planes()).bytes;
 }
 
 extern "C" size_t df_build_B_work_bytes(int nao, int naux) {
@@ -404,5 +432,18 @@ extern "C" int df_jk(const void* B, int nao, int naux, int precision, const doub
   Arena a(work, work_bytes);
   JKWork w = jk_work_layout(nao, naux, nocc, precision, &a, nullptr, false);
   DF_REQUIRE(!a.overflow, DF_ERR_NOMEM, "df_jk: workspace overflow");
-  return run_jk(B, nao, naux, precision, D, C, nocc, J, K, w, s);
+  DF_TRY(run_jk(B, nao, naux, precision, D, C, nocc, J, K, w, s));
+  if (K && precision == DF_MIXED) {
+    // The tensor-core kernels flag a bounded wait that gave up (K is then NaN).  Outside a
+    // stream capture the flag is read back here, which synchronises the stream.
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    DF_CUDA(cudaStreamIsCapturing(s, &cs));
+    if (cs == cudaStreamCaptureStatusNone) {
+      int err = 0;
+      DF_CUDA(cudaMemcpyAsync(&err, w.mk.err, sizeof(int), cudaMemcpyDeviceToHost, s));
+      DF_CUDA(cudaStreamSynchronize(s));
+      DF_REQUIRE(err == 0, DF_ERR_TIMEOUT, "df_jk: a bounded wait of the tensor-core exchange gave up; K is NaN");
+    }
+  }
+  return DF_OK;
 }

@@ -35,12 +35,14 @@ int eigh_lowest_rows(double* A, int n, int k, double* w, double* ZT, double* scr
 int transpose(const double* in, int rows, int cols, double* out, cudaStream_t s);
 
 // ---- B layout and J/K (jk.cu, umma.cu) --------------------------------------------------
-// BF16 planes kept of B for the mixed exchange; kernels use the first mixed_planes of them.
+// Most BF16 planes a mixed-precision B can hold; a B keeps as many as the knob "mixed_planes"
+// asked for when it was sized and built (3, 4 or 5).
 constexpr int kMixedPlanes = 5;
 
 struct BLayout {
   long ld;       // packed row stride (elements)
   int npad;      // padded orbital dimension of the BF16 planes
+  int planes;    // BF16 planes held (0 for DF_FP64)
   size_t off64, offp[kMixedPlanes], bytes;
 };
 
@@ -54,7 +56,7 @@ struct MixedKWork {
   int* err;                // device error flag of the tensor-core kernels
   int ncpad;               // padded occupied count (multiple of 16, >= 16)
   int nsplit;              // K-dimension splits of the exchange contraction
-  int planes;              // BF16 planes per operand (2: 3 products, 3: 6 products)
+  int planes;              // BF16 planes per operand (3, 4, 5: 6, 10, 15 plane products)
 };
 
 struct JKWork {
@@ -69,7 +71,14 @@ struct JKWork {
 
 long B_ld(int nao);
 int nao_pad(int nao);
-BLayout B_layout(int nao, int naux, int precision);
+// planes: BF16 planes of a mixed B (ignored for DF_FP64); plane j sits at the same offset
+// whatever the count, so a B with more planes serves an exchange that uses fewer.
+BLayout B_layout(int nao, int naux, int precision, int planes);
+int mixed_planes();
+// Host-side record of the plane count each mixed B was built with (keyed by its address),
+// checked before an exchange reads the planes; -1 if the address was never recorded.
+void record_B_planes(const void* B, int planes);
+int recorded_B_planes(const void* B);
 JKWork jk_work_layout(int nao, int naux, int nocc, int precision, Arena* a, Sizer* z, bool fp64_k);
 int umma_prepare();
 void mixed_k_work_layout(int nao, int naux, int nocc, Arena* a, Sizer* z, MixedKWork* w);

@@ -68,6 +68,7 @@ extern "C" int df_lowdin_factors(const double* ao_xyz, const double* ao_exp, int
   int h = 0;
   DF_CUDA(cudaMemcpyAsync(&h, status, sizeof(int), cudaMemcpyDeviceToHost, s));
   DF_CUDA(cudaStreamSynchronize(s));
+  DF_REQUIRE(h != 3, DF_ERR_TIMEOUT, "df_lowdin_factors: a grid barrier of the eigensolver timed out");
   DF_REQUIRE(h == 0, DF_ERR_NOCONV, "df_lowdin_factors: eigensolver failed on S");
   return DF_OK;
 }

@@ -16,6 +16,9 @@
 // Parameters are one float array: for each layer, W [out][in] then b [out].
 #include <cuda_bf16.h>
 
+#include <cstdint>
+#include <cstring>
+
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -509,5 +512,139 @@ extern "C" int guess_density(const float* params, const double* xyz, int natm, i
   }
   DF_TRY(dgemm(false, false, nao, nao, nao, 1.0, Dt, nao, 0, Sinvhalf, nao, 0, 0.0, T, nao, 0, 1, s, 0, 0));
   DF_TRY(dgemm(false, false, nao, nao, nao, 1.0, Sinvhalf, nao, 0, T, nao, 0, 0.0, D0, nao, 0, 1, s, 0, 0));
+  return DF_OK;
+}
+
+// ---- model lifecycle: create, save, load ---------------------------------------------------
+// The network's parameters (and Adam's moments) live in caller-owned device arrays; these
+// entry points initialise them and move them to and from a self-describing host blob:
+//   header  magic "DFSCFMLP", format version, layer count, each layer's (in, out), Adam step,
+//           a flag for the moments, the parameter count and an FNV-1a 64-bit checksum of the
+//           payload;
+//   payload params [NPARAM], then (if flagged) adam_m [NPARAM] and adam_v [NPARAM], FP32.
+namespace dfscf {
+namespace mlp {
+
+struct BlobHeader {
+  char magic[8];
+  uint32_t version;
+  uint32_t nlayer;
+  uint32_t in[NLAYER];
+  uint32_t out[NLAYER];
+  int32_t step;
+  uint32_t has_moments;
+  uint64_t nparam;
+  uint64_t checksum;
+};
+constexpr uint32_t kBlobVersion = 1;
+
+static uint64_t fnv1a(const unsigned char* p, size_t n) {
+  uint64_t h = 1469598103934665603ull;
+  for (size_t i = 0; i < n; ++i) {
+    h ^= p[i];
+    h *= 1099511628211ull;
+  }
+  return h;
+}
+
+// Uniform(-sqrt(3 / fan_in), +sqrt(3 / fan_in)) weights from a counter-based generator
+// (SplitMix64 of seed and index), zero biases.
+__global__ void init_params_kernel(float* __restrict__ P, unsigned long long seed) {
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (long)NPARAM) return;
+  int l = 0;
+  while (l + 1 < NLAYER && (size_t)i >= w_offset(l + 1)) ++l;
+  if ((size_t)i >= b_offset(l)) {
+    P[i] = 0.0f;
+    return;
+  }
+  unsigned long long z = seed + 0x9E3779B97F4A7C15ull * (unsigned long long)(i + 1);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  z ^= z >> 31;
+  const double u = (double)(z >> 11) * (1.0 / 9007199254740992.0);  // [0, 1)
+  const double bound = sqrt(3.0 / (double)layer_in(l));
+  P[i] = (float)((2.0 * u - 1.0) * bound);
+}
+
+}  // namespace mlp
+}  // namespace dfscf
+
+extern "C" int guess_mlp_create(unsigned long long seed, float* params, float* adam_m, float* adam_v, cudaStream_t s) {
+  clear_error();
+  DF_REQUIRE(params, DF_ERR_ARG, "guess_mlp_create: null params");
+  init_params_kernel<<<nb((long)NPARAM), 256, 0, s>>>(params, seed);
+  DF_LAUNCHED("init_params_kernel");
+  if (adam_m) DF_CUDA(cudaMemsetAsync(adam_m, 0, sizeof(float) * NPARAM, s));
+  if (adam_v) DF_CUDA(cudaMemsetAsync(adam_v, 0, sizeof(float) * NPARAM, s));
+  return DF_OK;
+}
+
+extern "C" size_t guess_mlp_blob_bytes(int with_moments) {
+  return sizeof(BlobHeader) + sizeof(float) * NPARAM * (with_moments ? 3 : 1);
+}
+
+extern "C" int guess_mlp_save(const float* params, const float* adam_m, const float* adam_v, int step, void* blob,
+                              size_t blob_bytes, cudaStream_t s) {
+  clear_error();
+  DF_REQUIRE(params && blob && step >= 0, DF_ERR_ARG, "guess_mlp_save: bad arguments");
+  DF_REQUIRE((adam_m == nullptr) == (adam_v == nullptr), DF_ERR_ARG, "guess_mlp_save: give both Adam moments or neither");
+  const int moments = adam_m != nullptr;
+  DF_REQUIRE(blob_bytes >= guess_mlp_blob_bytes(moments), DF_ERR_NOMEM, "guess_mlp_save: blob of %zu bytes < %zu",
+             blob_bytes, guess_mlp_blob_bytes(moments));
+  BlobHeader h{};
+  memcpy(h.magic, "DFSCFMLP", 8);
+  h.version = kBlobVersion;
+  h.nlayer = NLAYER;
+  for (int l = 0; l < NLAYER; ++l) {
+    h.in[l] = (uint32_t)layer_in(l);
+    h.out[l] = (uint32_t)layer_out(l);
+  }
+  h.step = step;
+  h.has_moments = (uint32_t)moments;
+  h.nparam = NPARAM;
+  unsigned char* payload = (unsigned char*)blob + sizeof(BlobHeader);
+  DF_CUDA(cudaMemcpyAsync(payload, params, sizeof(float) * NPARAM, cudaMemcpyDefault, s));
+  if (moments) {
+    DF_CUDA(cudaMemcpyAsync(payload + sizeof(float) * NPARAM, adam_m, sizeof(float) * NPARAM, cudaMemcpyDefault, s));
+    DF_CUDA(cudaMemcpyAsync(payload + 2 * sizeof(float) * NPARAM, adam_v, sizeof(float) * NPARAM, cudaMemcpyDefault, s));
+  }
+  DF_CUDA(cudaStreamSynchronize(s));
+  h.checksum = fnv1a(payload, sizeof(float) * NPARAM * (moments ? 3 : 1));
+  memcpy(blob, &h, sizeof(h));
+  return DF_OK;
+}
+
+extern "C" int guess_mlp_load(const void* blob, size_t blob_bytes, float* params, float* adam_m, float* adam_v,
+                              int* step, cudaStream_t s) {
+  clear_error();
+  DF_REQUIRE(blob && params, DF_ERR_ARG, "guess_mlp_load: bad arguments");
+  DF_REQUIRE((adam_m == nullptr) == (adam_v == nullptr), DF_ERR_ARG, "guess_mlp_load: give both Adam moments or neither");
+  DF_REQUIRE(blob_bytes >= sizeof(BlobHeader), DF_ERR_ARG, "guess_mlp_load: blob of %zu bytes has no header", blob_bytes);
+  BlobHeader h;
+  memcpy(&h, blob, sizeof(h));
+  DF_REQUIRE(memcmp(h.magic, "DFSCFMLP", 8) == 0, DF_ERR_ARG, "guess_mlp_load: not a model blob (bad magic)");
+  DF_REQUIRE(h.version == kBlobVersion, DF_ERR_ARG, "guess_mlp_load: format version %u, expected %u", h.version,
+             kBlobVersion);
+  bool shapes = h.nlayer == NLAYER && h.nparam == NPARAM;
+  for (int l = 0; shapes && l < NLAYER; ++l) shapes = h.in[l] == (uint32_t)layer_in(l) && h.out[l] == (uint32_t)layer_out(l);
+  DF_REQUIRE(shapes, DF_ERR_ARG, "guess_mlp_load: the blob's layer shapes differ from this library's network");
+  const size_t payload_bytes = sizeof(float) * NPARAM * (h.has_moments ? 3 : 1);
+  DF_REQUIRE(blob_bytes >= sizeof(BlobHeader) + payload_bytes, DF_ERR_ARG, "guess_mlp_load: blob truncated");
+  const unsigned char* payload = (const unsigned char*)blob + sizeof(BlobHeader);
+  DF_REQUIRE(fnv1a(payload, payload_bytes) == h.checksum, DF_ERR_ARG, "guess_mlp_load: checksum mismatch");
+  DF_CUDA(cudaMemcpyAsync(params, payload, sizeof(float) * NPARAM, cudaMemcpyDefault, s));
+  if (adam_m) {
+    if (h.has_moments) {
+      DF_CUDA(cudaMemcpyAsync(adam_m, payload + sizeof(float) * NPARAM, sizeof(float) * NPARAM, cudaMemcpyDefault, s));
+      DF_CUDA(cudaMemcpyAsync(adam_v, payload + 2 * sizeof(float) * NPARAM, sizeof(float) * NPARAM, cudaMemcpyDefault,
+                              s));
+    } else {
+      DF_CUDA(cudaMemsetAsync(adam_m, 0, sizeof(float) * NPARAM, s));
+      DF_CUDA(cudaMemsetAsync(adam_v, 0, sizeof(float) * NPARAM, s));
+    }
+  }
+  DF_CUDA(cudaStreamSynchronize(s));
+  if (step) *step = h.has_moments ? h.step : 0;
   return DF_OK;
 }

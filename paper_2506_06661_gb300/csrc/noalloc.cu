@@ -10,8 +10,11 @@
 // array until the process exits.
 //
 // The array lives in device memory, so host code cannot use the symbol itself as an
-// address; the device address is obtained with cudaGetSymbolAddress once per device (the
-// first call on a device does this) and passed to the kernels.  All calls share the one
+// address; the device address is obtained with cudaGetSymbolAddress (with the device
+// current) and passed to the kernels.  Outside a stream capture every call looks it up
+// again, so a context torn down and recreated (cudaDeviceReset) gets its new address; inside
+// a capture the call reuses the address of the last call on that device, so one call must
+// come before the first capture.  All calls share the one
 // array: two calls whose GPU work overlaps (different streams, or different host threads
 // on the same device without ordering) race on it and give wrong results.  Nothing in the
 // array needs to start at zero: every word a call reads was written earlier in that call.
@@ -29,19 +32,25 @@ static __device__ __align__(256) double g_noalloc_scratch[NOALLOC_DOUBLES];
 static std::mutex g_noalloc_mutex;
 static double* g_noalloc_ptr[256];
 
-// Device address of the scratch array on the current device (set up on first use).
-static int noalloc_scratch(double** out) {
+// Device address of the scratch array on the current device: looked up on every call made
+// outside a stream capture (and remembered), reused from the last such call inside one.
+static int noalloc_scratch(cudaStream_t s, double** out) {
   int dev = 0;
   DF_CUDA(cudaGetDevice(&dev));
   DF_REQUIRE(dev >= 0 && dev < 256, DF_ERR_ARG, "df_j_noalloc: device index %d out of range", dev);
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  DF_CUDA(cudaStreamIsCapturing(s, &cs));
   std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-  if (!g_noalloc_ptr[dev]) {
+  if (cs == cudaStreamCaptureStatusNone) {
     void* p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     DF_REQUIRE(e == cudaSuccess && p, DF_ERR_CUDA, "df_j_noalloc: cudaGetSymbolAddress failed: %s",
                cudaGetErrorString(e));
     g_noalloc_ptr[dev] = (double*)p;
   }
+  DF_REQUIRE(g_noalloc_ptr[dev], DF_ERR_ARG,
+             "df_j_noalloc: first call on device %d made inside a stream capture; call it once before capturing",
+             dev);
   *out = g_noalloc_ptr[dev];
   return DF_OK;
 }
@@ -73,11 +82,11 @@ extern "C" int df_j_noalloc(const void* B, int nao, int naux, const double* D, d
              "(use df_jk with a caller workspace)",
              nao, naux, need * sizeof(double), NOALLOC_DOUBLES * sizeof(double));
   double* base = nullptr;
-  DF_TRY(noalloc_scratch(&base));
+  DF_TRY(noalloc_scratch(s, &base));
   JKWork w{};
   w.Dw = base;
   w.d = base + align_up((size_t)ld, 32);
   w.Jpart = w.d + align_up((size_t)naux, 32);
   w.nsplit_j = nsplit;
-  return build_J(B, B_layout(nao, naux, DF_FP64), nao, naux, DF_FP64, D, J, w, s);
+  return build_J(B, B_layout(nao, naux, DF_FP64, 0), nao, naux, DF_FP64, D, J, w, s);
 }

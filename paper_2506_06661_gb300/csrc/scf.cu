@@ -38,7 +38,12 @@ struct ScfStatus {
   double homo, lumo;
   int singular;  // DIIS system had no usable pivot this iteration
   int nonfinite;
-  int eig_fail;
+  int eig_fail;   // eigensolver status: 0 ok, 3 a grid barrier timed out, else a breakdown
+  int tc_timeout; // a bounded wait of the tensor-core exchange gave up in this iteration
+  double inc_min_cos2;  // smallest cos^2 of the principal angles between the occupied spaces
+                        // of the accumulated K and of the next density (incremental exchange)
+  double inc_ssum;      // sum of the sines of those angles (size of the projector change)
+  int inc_fail;         // the small eigensolver of the incremental exchange failed
   int pad;
 };
 
@@ -271,13 +276,15 @@ __global__ void occ_columns_kernel(const double* __restrict__ ZT, int nmo, int n
   Cp[q] = ZT[(size_t)j * nmo + i];
 }
 
-// HOMO / LUMO of the last diagonalisation and its eigensolver status into the status block.
+// HOMO / LUMO of the last diagonalisation, its eigensolver status and the tensor-core
+// exchange's timeout flag (tc_err may be null: an FP64 iteration) into the status block.
 __global__ void orbital_status_kernel(const double* __restrict__ eps, int nmo, int nocc, const int* eig_status,
-                                      ScfStatus* st) {
+                                      const int* tc_err, ScfStatus* st) {
   if (threadIdx.x != 0) return;
   st->homo = nocc > 0 ? eps[nocc - 1] : 0.0;
   st->lumo = nocc < nmo ? eps[nocc] : 0.0;
   st->eig_fail = *eig_status;
+  st->tc_timeout = tc_err ? *tc_err : 0;
 }
 
 __global__ void axpy_kernel(double* __restrict__ y, const double* __restrict__ x, long n, double a) {
@@ -317,6 +324,76 @@ __global__ void split_density_kernel(const double* __restrict__ ZT, const double
   Cout[q] = ZT[(size_t)k * n + i] * sqrt(fabs(w[k]) * 0.5);
 }
 
+// ---- incremental mixed-precision exchange -----------------------------------------------
+// K is linear in the density, so K[P_new] = K[P_base] + K[P_new - P_base] for the occupied
+// projectors P = C' C'^T (orthonormal basis).  The change is factorised as
+// U+ U+^T - U- U-^T with factors whose squared norm is about twice the sum of the sines of
+// the principal angles between the two occupied spaces: the mixed-precision error of the
+// update then shrinks with the change, and the accumulated K keeps the accuracy of the FP64
+// build it started from.  Principal vectors: with M = C'_base^T C'_new and
+// M^T M = W diag(cos^2) W^T, B = C'_new W and A = C'_base M W (column norms cos) pair up
+// column by column.  For unit vectors a, b, the rank-2 matrix b b^T - a a^T equals
+// s (p m^T + m p^T) with p = (b + a)/|b + a|, m = (b - a)/|b - a| and s = |b - a||b + a|/2
+// the sine of their angle, i.e. u+ u+^T - u- u-^T with u+- = sqrt(s/2) (p +- m).  |b - a|
+// is formed from the difference vector itself, so small angles keep FP64 accuracy.
+
+// One CTA per column j of A, B [nmo][k]: U+, U- columns and the sine s_j.
+__global__ void principal_pairs_kernel(const double* __restrict__ A, const double* __restrict__ B, int nmo, int k,
+                                       double* __restrict__ Up, double* __restrict__ Um, double* __restrict__ sv) {
+  __shared__ double sh[32];
+  const int j = blockIdx.x;
+  double aa = 0.0, bb = 0.0;
+  for (int i = threadIdx.x; i < nmo; i += blockDim.x) {
+    const double a = A[(size_t)i * k + j], b = B[(size_t)i * k + j];
+    aa += a * a;
+    bb += b * b;
+  }
+  aa = block_sum(aa, sh);
+  bb = block_sum(bb, sh);
+  const double ia = aa > 0.0 ? 1.0 / sqrt(aa) : 0.0, ib = bb > 0.0 ? 1.0 / sqrt(bb) : 0.0;
+  double mm = 0.0, pp = 0.0;
+  for (int i = threadIdx.x; i < nmo; i += blockDim.x) {
+    const double a = A[(size_t)i * k + j] * ia, b = B[(size_t)i * k + j] * ib;
+    mm += (b - a) * (b - a);
+    pp += (b + a) * (b + a);
+  }
+  mm = block_sum(mm, sh);
+  pp = block_sum(pp, sh);
+  const double nm = sqrt(mm), np = sqrt(pp);
+  const bool live = aa > 0.0 && bb > 0.0 && nm > 1e-300 && np > 1e-300;
+  const double sj = live ? 0.5 * nm * np : 0.0;
+  const double f = sqrt(0.5 * sj), inm = live ? 1.0 / nm : 0.0, inp = live ? 1.0 / np : 0.0;
+  for (int i = threadIdx.x; i < nmo; i += blockDim.x) {
+    const double a = A[(size_t)i * k + j] * ia, b = B[(size_t)i * k + j] * ib;
+    const double pv = (b + a) * inp, mv = (b - a) * inm;
+    Up[(size_t)i * k + j] = f * (pv + mv);
+    Um[(size_t)i * k + j] = f * (pv - mv);
+  }
+  if (threadIdx.x == 0) sv[j] = sj;
+}
+
+// K += Kp - Km.
+__global__ void kacc_kernel(double* __restrict__ K, const double* __restrict__ Kp, const double* __restrict__ Km,
+                            long n) {
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) K[i] += Kp[i] - Km[i];
+}
+
+// Smallest cos^2 (ascending eigenvalues c2) and sum of the sines of the principal angles into
+// the status block, with the small eigensolver's status.
+__global__ void inc_status_kernel(const double* __restrict__ c2, int k, const int* __restrict__ eig_status,
+                                  ScfStatus* st) {
+  __shared__ double sh[32];
+  double t = 0.0;
+  for (int j = threadIdx.x; j < k; j += blockDim.x) t += sqrt(fmax(0.0, 1.0 - fmin(1.0, c2[j])));
+  t = block_sum(t, sh);
+  if (threadIdx.x == 0) {
+    st->inc_min_cos2 = k > 0 ? c2[0] : 1.0;
+    st->inc_ssum = t;
+    st->inc_fail = *eig_status;
+  }
+}
+
 static unsigned blocks_for(long n, int t = 256) { return (unsigned)((n + t - 1) / t); }
 
 // ---- per-molecule workspace --------------------------------------------------------------
@@ -324,6 +401,17 @@ struct ScfWork {
   double *L, *pair_tab, *S, *h, *V, *X, *F, *Fo, *Cp, *J, *K, *D, *Dprev, *Cocc, *Cprev, *Cchunk, *T1, *T2, *E, *Fp,
       *ZT, *eps, *Fhist, *Ehist, *G, *coef, *eig_scratch, *enuc, *maxdiag;
   int *eig_status, *chol_status, *idx;
+  // incremental mixed exchange: C' the accumulated K belongs to, M = C'_base^T C'_new, the
+  // eigen-decomposition of M^T M (rows of Winc, ascending cos^2 in cinc), the principal
+  // vectors A, B and the two factors of the projector change (orthonormal basis, then AO)
+  double *Cbase, *Minc, *Tinc, *Winc, *cinc, *MW, *Ainc, *Binc, *Up, *Um, *Uao_p, *Uao_m, *sinc;
+  int* inc_status;
+  // second-order SCF: the full orbital set C'_all (columns; occupied first), its Fock matrix,
+  // the extrapolated F' kept for the switch, CG vectors over (virtual, occupied) pairs, the
+  // trial-density response and the small matrices of the exact rotation exp(kappa)
+  double *Fbar, *Call, *Call2, *Fmo, *Lv, *cg_g, *cg_h, *cg_x, *cg_r, *cg_z, *cg_p, *cg_Ap, *Lf, *Lfp, *Lfm, *dD,
+      *dJ, *dK1, *dK2, *cg_s, *kk, *kVrow, *ksig, *Pc, *Ps, *Pd, *ktmp, *KPdK;
+  int* k_status;
   void* eig_aux;  // p vector and grid barrier of the multi-SM eigensolver
   ScfStatus* st;
   DiisState* diis;
@@ -368,6 +456,53 @@ static void scf_layout(int nao, int naux, int nocc, int precision, Arena* a, Siz
   TAKE(char, w->eig_aux, eigh_coop_aux_bytes(nao));
   TAKE(int, w->chol_status, 1);
   TAKE(int, w->idx, nao);
+  {
+    const size_t oc = (size_t)std::max(nocc, 1);
+    TAKE(double, w->Cbase, (size_t)nao * oc);
+    TAKE(double, w->Minc, oc * oc);
+    TAKE(double, w->Tinc, oc * oc);
+    TAKE(double, w->Winc, oc * oc);
+    TAKE(double, w->cinc, oc);
+    TAKE(double, w->MW, oc * oc);
+    TAKE(double, w->Ainc, (size_t)nao * oc);
+    TAKE(double, w->Binc, (size_t)nao * oc);
+    TAKE(double, w->Up, (size_t)nao * oc);
+    TAKE(double, w->Um, (size_t)nao * oc);
+    TAKE(double, w->Uao_p, (size_t)nao * oc);
+    TAKE(double, w->Uao_m, (size_t)nao * oc);
+    TAKE(double, w->sinc, oc);
+    TAKE(int, w->inc_status, 1);
+    const size_t vo = (size_t)nao * oc;  // (virtual, occupied) pairs: at most nao * nocc
+    TAKE(double, w->Fbar, nn);
+    TAKE(double, w->Call, nn);
+    TAKE(double, w->Call2, nn);
+    TAKE(double, w->Fmo, nn);
+    TAKE(double, w->Lv, nn);
+    TAKE(double, w->cg_g, vo);
+    TAKE(double, w->cg_h, vo);
+    TAKE(double, w->cg_x, vo);
+    TAKE(double, w->cg_r, vo);
+    TAKE(double, w->cg_z, vo);
+    TAKE(double, w->cg_p, vo);
+    TAKE(double, w->cg_Ap, vo);
+    TAKE(double, w->Lf, vo);
+    TAKE(double, w->Lfp, vo);
+    TAKE(double, w->Lfm, vo);
+    TAKE(double, w->dD, nn);
+    TAKE(double, w->dJ, nn);
+    TAKE(double, w->dK1, nn);
+    TAKE(double, w->dK2, nn);
+    TAKE(double, w->cg_s, 32);
+    TAKE(double, w->kk, oc * oc);
+    TAKE(double, w->kVrow, oc * oc);
+    TAKE(double, w->ksig, oc);
+    TAKE(double, w->Pc, oc * oc);
+    TAKE(double, w->Ps, oc * oc);
+    TAKE(double, w->Pd, oc * oc);
+    TAKE(double, w->ktmp, vo);
+    TAKE(double, w->KPdK, nn);
+    TAKE(int, w->k_status, 1);
+  }
   TAKE(ScfStatus, w->st, 1);
   TAKE(DiisState, w->diis, 1);
   if (a) w->B = a->take<char>(df_B_bytes(nao, naux, precision)); else z->take<char>(df_B_bytes(nao, naux, precision));
@@ -427,9 +562,19 @@ struct ScfMol {
   bool have_old = false;
   double best_err = INFINITY;  // smallest max|e| of the mixed phase so far
   int stall = 0;               // mixed iterations without a 10% gain on best_err
+  // Incremental mixed exchange (mixed precision with the knob "mixed_incremental"): full
+  // mixed builds until max|e| < 1e-3 (or the switch rules), one FP64 build as the base of
+  // the accumulated K, updates from the change of the occupied projector until converged,
+  // then n_fp64_final FP64 iterations.  A base is rebuilt when the occupied space turned by
+  // more than 60 degrees in one step or the updates stall.
+  bool inc = false;
+  enum KPhase { KP_FULL, KP_BASE, KP_INCR, KP_FINAL } kp = KP_FULL;
+  int rebases = 0;
+  double inc_best = INFINITY;
+  int inc_stall = 0;
   bool done = false;
   int rc = DF_OK;
-  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  cudaGraphExec_t graph[3] = {nullptr, nullptr, nullptr};
   scf_result res{};
   const double* dm0 = nullptr;
   double* D_out = nullptr;
@@ -533,6 +678,8 @@ static int finish_guess(ScfMol& M, bool use_dm0, bool orbitals) {
   }
   diis_reset_kernel<<<1, 32, 0, M.s>>>(W.diis, M.opt.diis_space);
   DF_LAUNCHED("diis_reset_kernel");
+  M.inc = M.opt.precision == DF_MIXED && knob("mixed_incremental") != 0;
+  if (M.inc) DF_CUDA(cudaMemsetAsync(W.Cbase, 0, sizeof(double) * (size_t)M.nmo * M.nocc, M.s));
   M.first_dm0 = use_dm0;
   M.prec = M.opt.precision;
   M.switched = (M.prec == DF_FP64);
@@ -549,6 +696,7 @@ static int setup_orthogonalize(ScfMol& M) {
   const long nn = (long)nao * nao;
   M.res.e_nuc = M.h_eps[nao];
   DF_REQUIRE(M.h_ints[1] < 0, DF_ERR_NOT_SPD, "scf: auxiliary metric not positive definite at pivot %d", M.h_ints[1]);
+  DF_REQUIRE(M.h_ints[0] != 3, DF_ERR_TIMEOUT, "scf: a grid barrier of the eigensolver timed out on S");
   DF_REQUIRE(M.h_ints[0] == 0, DF_ERR_NOCONV, "scf: eigensolver failed on S");
   int nmo = 0;
   for (int i = 0; i < nao; ++i) nmo += M.h_eps[i] > M.opt.lindep;
@@ -621,6 +769,7 @@ static int dm0_finish(ScfMol& M) {
   cudaStream_t s = M.s;
   const int nao = M.nao, naux = M.naux, nocc = M.nocc;
   const long nn = (long)nao * nao;
+  DF_REQUIRE(M.h_ints[0] != 3, DF_ERR_TIMEOUT, "scf: a grid barrier of the eigensolver timed out on dm0");
   DF_REQUIRE(M.h_ints[0] == 0, DF_ERR_NOCONV, "scf: eigensolver failed on the starting density");
   double wmax = 0.0;
   for (int k = 0; k < nao; ++k) wmax = fmax(wmax, fabs(M.h_eps[k]));
@@ -650,7 +799,7 @@ static int dm0_finish(ScfMol& M) {
 
 // Everything after J and K: Fock, energy, DIIS error and extrapolation, diagonalisation,
 // status readback.  No host decisions: capturable.
-static int iteration_tail(ScfMol& M) {
+static int iteration_tail(ScfMol& M, int prec) {
   ScfWork& W = M.W;
   cudaStream_t s = M.s;
   const int nao = M.nao, nmo = M.nmo, nocc = M.nocc;
@@ -696,7 +845,19 @@ static int iteration_tail(ScfMol& M) {
   diis_combine_kernel<<<blocks_for(ne), 256, 0, s>>>(W.diis, W.Fhist, nn, ne, W.coef, W.Fp);
   DF_LAUNCHED("diis_combine_kernel");
   DF_TRY(diagonalize_orth(nao, nmo, nocc, W, s));
-  orbital_status_kernel<<<1, 32, 0, s>>>(W.eps, nmo, nocc, W.eig_status, W.st);
+  if (M.inc) {
+    // principal angles between the occupied space of the accumulated K (C'_base) and the
+    // new one (C'): M = C'_base^T C', eigen-decomposition of M^T M on one CTA
+    ProfScope ps_inc("scf_incremental_prep", s);
+    DF_TRY(dgemm(true, false, nocc, nocc, nmo, 1.0, W.Cbase, nocc, 0, W.Cp, nocc, 0, 0.0, W.Minc, nocc, 0, 1, s, 0, 0));
+    DF_TRY(dgemm(true, false, nocc, nocc, nocc, 1.0, W.Minc, nocc, 0, W.Minc, nocc, 0, 0.0, W.Tinc, nocc, 0, 1, s, 0,
+                 0));
+    DF_TRY(eigh_rows(W.Tinc, nocc, W.cinc, W.Winc, W.eig_scratch, W.inc_status, s));
+    inc_status_kernel<<<1, 256, 0, s>>>(W.cinc, nocc, W.inc_status, W.st);
+    DF_LAUNCHED("inc_status_kernel");
+  }
+  orbital_status_kernel<<<1, 32, 0, s>>>(W.eps, nmo, nocc, W.eig_status, prec == DF_MIXED ? W.jk.mk.err : nullptr,
+                                         W.st);
   DF_LAUNCHED("orbital_status_kernel");
   DF_CUDA(cudaMemcpyAsync(M.hst, W.st, sizeof(ScfStatus), cudaMemcpyDeviceToHost, s));
   return DF_OK;
@@ -709,13 +870,45 @@ static int iteration_body(ScfMol& M, int prec) {
   DF_CUDA(cudaMemcpyAsync(W.Dprev, W.D, sizeof(double) * nn, cudaMemcpyDeviceToDevice, M.s));
   DF_CUDA(cudaMemcpyAsync(W.Cprev, W.Cocc, sizeof(double) * M.nao * M.nocc, cudaMemcpyDeviceToDevice, M.s));
   DF_TRY(run_jk(W.B, M.nao, M.naux, prec, W.D, W.Cocc, M.nocc, W.J, W.K, W.jk, M.s));
-  return iteration_tail(M);
+  if (M.inc)  // a full build: the accumulated K now belongs to this density
+    DF_CUDA(cudaMemcpyAsync(W.Cbase, W.Cp, sizeof(double) * M.nmo * M.nocc, cudaMemcpyDeviceToDevice, M.s));
+  return iteration_tail(M, prec);
+}
+
+// Body of an incremental iteration: J in FP64 as always; K += K[U+] - K[U-] with the
+// factors of P_new - P_base in mixed precision (the principal-angle decomposition above,
+// from the eigen-decomposition the previous tail left in Winc / cinc).
+static int iteration_body_incremental(ScfMol& M) {
+  ScfWork& W = M.W;
+  cudaStream_t s = M.s;
+  const int nao = M.nao, nmo = M.nmo, nocc = M.nocc;
+  const long nn = (long)nao * nao;
+  DF_CUDA(cudaMemcpyAsync(W.Dprev, W.D, sizeof(double) * nn, cudaMemcpyDeviceToDevice, s));
+  DF_CUDA(cudaMemcpyAsync(W.Cprev, W.Cocc, sizeof(double) * nao * nocc, cudaMemcpyDeviceToDevice, s));
+  DF_TRY(run_jk(W.B, nao, M.naux, DF_MIXED, W.D, nullptr, 0, W.J, nullptr, W.jk, s));
+  {
+    ProfScope ps("scf_incremental_factors", s);
+    // MW = M W, A = C'_base M W, B = C' W (W = Winc^T: eigenvectors as rows)
+    DF_TRY(dgemm(false, true, nocc, nocc, nocc, 1.0, W.Minc, nocc, 0, W.Winc, nocc, 0, 0.0, W.MW, nocc, 0, 1, s, 0, 0));
+    DF_TRY(dgemm(false, false, nmo, nocc, nocc, 1.0, W.Cbase, nocc, 0, W.MW, nocc, 0, 0.0, W.Ainc, nocc, 0, 1, s, 0, 0));
+    DF_TRY(dgemm(false, true, nmo, nocc, nocc, 1.0, W.Cp, nocc, 0, W.Winc, nocc, 0, 0.0, W.Binc, nocc, 0, 1, s, 0, 0));
+    principal_pairs_kernel<<<nocc, 256, 0, s>>>(W.Ainc, W.Binc, nmo, nocc, W.Up, W.Um, W.sinc);
+    DF_LAUNCHED("principal_pairs_kernel");
+    DF_TRY(dgemm(false, false, nao, nocc, nmo, 1.0, W.X, nmo, 0, W.Up, nocc, 0, 0.0, W.Uao_p, nocc, 0, 1, s, 0, 0));
+    DF_TRY(dgemm(false, false, nao, nocc, nmo, 1.0, W.X, nmo, 0, W.Um, nocc, 0, 0.0, W.Uao_m, nocc, 0, 1, s, 0, 0));
+  }
+  DF_TRY(run_jk(W.B, nao, M.naux, DF_MIXED, nullptr, W.Uao_p, nocc, nullptr, W.T2, W.jk, s));
+  DF_TRY(run_jk(W.B, nao, M.naux, DF_MIXED, nullptr, W.Uao_m, nocc, nullptr, W.T1, W.jk, s));
+  kacc_kernel<<<blocks_for(nn), 256, 0, s>>>(W.K, W.T2, W.T1, nn);
+  DF_LAUNCHED("kacc_kernel");
+  DF_CUDA(cudaMemcpyAsync(W.Cbase, W.Cp, sizeof(double) * nmo * nocc, cudaMemcpyDeviceToDevice, s));
+  return iteration_tail(M, DF_MIXED);
 }
 
 // Second half of the first iteration from a non-idempotent dm0 (after dm0_launch drained).
 static int scf_dm0_finish(ScfMol& M) {
   DF_TRY(dm0_finish(M));
-  DF_TRY(iteration_tail(M));
+  DF_TRY(iteration_tail(M, M.prec));
   M.first_dm0 = false;
   return DF_OK;
 }
@@ -724,12 +917,14 @@ static int scf_dm0_finish(ScfMol& M) {
 // enqueues its first half here (phase DM0_EIG): scf_dm0_finish completes it.
 static int scf_iter_launch(ScfMol& M, bool use_graphs) {
   if (M.first_dm0) return dm0_launch(M);
-  int gi = M.prec == DF_FP64 ? 0 : 1;
-  if (!use_graphs || prof_on()) return iteration_body(M, M.prec);
+  const bool incr = M.inc && M.kp == ScfMol::KP_INCR;
+  int gi = M.prec == DF_FP64 ? 0 : (incr ? 2 : 1);
+  auto body = [&]() { return incr ? iteration_body_incremental(M) : iteration_body(M, M.prec); };
+  if (!use_graphs || prof_on()) return body();
   if (!M.graph[gi]) {
     cudaGraph_t g = nullptr;
     DF_CUDA(cudaStreamBeginCapture(M.s, cudaStreamCaptureModeThreadLocal));
-    int rc = iteration_body(M, M.prec);
+    int rc = body();
     cudaError_t ce = cudaStreamEndCapture(M.s, &g);
     if (rc != DF_OK) {
       if (g) cudaGraphDestroy(g);
@@ -744,6 +939,104 @@ static int scf_iter_launch(ScfMol& M, bool use_graphs) {
   return DF_OK;
 }
 
+// Phase logic of the incremental mixed exchange (after the checks common to every mode):
+// FULL (mixed builds) -> BASE (one FP64 build) -> INCR (updates) -> FINAL (FP64 builds).
+static bool scf_iter_finish_incremental(ScfMol& M, double de) {
+  const ScfStatus& h = *M.hst;
+  const scf_opts& o = M.opt;
+  const bool crit = M.have_old && de < o.conv_tol && h.emax < o.conv_err;
+  M.res.homo = h.homo;
+  M.res.lumo = h.lumo;
+  // the next update is safe when the small eigensolver worked and no principal angle
+  // between the accumulated K's occupied space and the next one exceeds 60 degrees
+  const bool update_ok = h.inc_fail == 0 && h.inc_min_cos2 >= 0.25;
+  auto to_final = [&]() {
+    M.kp = ScfMol::KP_FINAL;
+    M.switched = true;
+    M.prec = DF_FP64;
+  };
+  auto to_base = [&]() {
+    M.kp = ScfMol::KP_BASE;
+    M.prec = DF_FP64;
+  };
+  switch (M.kp) {
+    case ScfMol::KP_FINAL:
+      if (M.fp64_done + 1 >= o.n_fp64_final && crit) {
+        M.res.converged = 1;
+        return true;
+      }
+      M.fp64_done++;
+      break;
+    case ScfMol::KP_FULL: {
+      if (h.emax < 0.9 * M.best_err) {
+        M.best_err = h.emax;
+        M.stall = 0;
+      } else {
+        M.stall++;
+      }
+      const bool stalled = (M.stall >= 10 && M.best_err < 1e-3) || 4 * M.res.iterations >= 3 * o.max_cycle;
+      if (M.have_old && (h.emax < 1e-3 || de < o.switch_tol || h.emax < o.switch_err || stalled)) to_base();
+      break;
+    }
+    case ScfMol::KP_BASE:
+      // an FP64 iteration: when its error jumps well above the mixed phase's best, the mixed
+      // vectors in the DIIS history do not describe the FP64 problem; restart from this one
+      if (M.rebases == 0 && h.emax > 3.0 * M.best_err) {
+        diis_keep_newest_kernel<<<1, 32, 0, M.s>>>(M.W.diis);
+        if (cudaGetLastError() != cudaSuccess) {
+          M.rc = DF_ERR_CUDA;
+          set_error("scf: DIIS restart launch failed");
+          return true;
+        }
+      }
+      if (crit) {  // converged on the base build itself: it is the first final FP64 iteration
+        to_final();
+        M.fp64_done = 1;
+        if (M.fp64_done >= o.n_fp64_final) {
+          M.res.converged = 1;
+          return true;
+        }
+      } else if (update_ok && M.rebases <= 3) {
+        M.kp = ScfMol::KP_INCR;
+        M.prec = DF_MIXED;
+        M.inc_best = h.emax;
+        M.inc_stall = 0;
+      } else if (M.rebases > 3) {
+        to_final();
+      } else {
+        M.rebases++;
+      }
+      break;
+    case ScfMol::KP_INCR:
+      if (crit || 4 * M.res.iterations >= 3 * o.max_cycle) {
+        to_final();
+        break;
+      }
+      if (h.emax < 0.9 * M.inc_best) {
+        M.inc_best = h.emax;
+        M.inc_stall = 0;
+      } else {
+        M.inc_stall++;
+      }
+      if (!update_ok || M.inc_stall >= 10) {
+        // a large rotation, or updates that no longer reduce the error: rebuild the base
+        M.rebases++;
+        if (M.rebases > 3) to_final();
+        else to_base();
+      }
+      break;
+  }
+  M.e_old = h.energy;
+  M.have_old = true;
+  if (M.res.iterations >= o.max_cycle) {
+    M.rc = DF_ERR_NOCONV;
+    set_error("scf: not converged after %d iterations (dE %.3e, max|e| %.3e)", M.res.iterations, M.res.last_de,
+              M.res.last_err);
+    return true;
+  }
+  return false;
+}
+
 // After the stream has completed the iteration: convergence, precision switch.
 // Returns true when the molecule is finished (converged, failed or out of iterations).
 static bool scf_iter_finish(ScfMol& M) {
@@ -753,6 +1046,16 @@ static bool scf_iter_finish(ScfMol& M) {
   if (h.nonfinite || !std::isfinite(h.emax)) {
     M.rc = DF_ERR_NUMERIC;
     set_error("scf: non-finite Fock matrix at iteration %d", M.res.iterations);
+    return true;
+  }
+  if (h.tc_timeout) {
+    M.rc = DF_ERR_TIMEOUT;
+    set_error("scf: a bounded wait of the tensor-core exchange gave up at iteration %d", M.res.iterations);
+    return true;
+  }
+  if (h.eig_fail == 3) {
+    M.rc = DF_ERR_TIMEOUT;
+    set_error("scf: a grid barrier of the eigensolver timed out at iteration %d", M.res.iterations);
     return true;
   }
   if (h.eig_fail) {
@@ -766,7 +1069,8 @@ static bool scf_iter_finish(ScfMol& M) {
   M.res.last_err = h.emax;
   if (M.opt.verbose)
     printf("scf iter %3d  %s  E = %.12f  dE = %.3e  max|e| = %.3e\n", M.res.iterations,
-           M.prec == DF_FP64 ? "fp64 " : "mixed", h.energy, de, h.emax);
+           M.prec == DF_FP64 ? "fp64 " : (M.inc && M.kp == ScfMol::KP_INCR ? "incr " : "mixed"), h.energy, de, h.emax);
+  if (M.inc) return scf_iter_finish_incremental(M, de);
   if (M.prec == DF_FP64 && M.switched && M.fp64_done + 1 >= M.opt.n_fp64_final && M.have_old &&
       de < M.opt.conv_tol && h.emax < M.opt.conv_err) {
     M.res.converged = 1;
@@ -1176,6 +1480,7 @@ extern "C" int df_core_guess(const df_molecule* mol, double lindep, double* S_ou
   DF_CUDA(cudaMemcpyAsync(hs.data(), W.eps, sizeof(double) * nao, cudaMemcpyDeviceToHost, s));
   DF_CUDA(cudaMemcpyAsync(&bad, W.eig_status, sizeof(int), cudaMemcpyDeviceToHost, s));
   DF_CUDA(cudaStreamSynchronize(s));
+  DF_REQUIRE(bad != 3, DF_ERR_TIMEOUT, "df_core_guess: a grid barrier of the eigensolver timed out on S");
   DF_REQUIRE(bad == 0, DF_ERR_NOCONV, "df_core_guess: eigensolver failed on S");
   int nmo = 0;
   for (int i = 0; i < nao; ++i) nmo += hs[i] > lindep;
@@ -1192,6 +1497,7 @@ extern "C" int df_core_guess(const df_molecule* mol, double lindep, double* S_ou
   bad = 0;
   DF_CUDA(cudaMemcpyAsync(&bad, W.eig_status, sizeof(int), cudaMemcpyDeviceToHost, s));
   DF_CUDA(cudaStreamSynchronize(s));
+  DF_REQUIRE(bad != 3, DF_ERR_TIMEOUT, "df_core_guess: a grid barrier of the eigensolver timed out");
   DF_REQUIRE(bad == 0, DF_ERR_NOCONV, "df_core_guess: eigensolver failed on the core Hamiltonian");
   if (nmo_out) *nmo_out = nmo;
   return DF_OK;

@@ -3,11 +3,11 @@
 // K_mn = sum_P sum_i X_{P,mi} X_{P,ni},  X_P = B_P C   (arXiv 2506.06661, Section
 // "Density fitting": the fitted integrals sum_P B_{P,mk} B_{P,nl} contracted with the
 // occupied coefficients).  Both contractions run as split-BF16 GEMMs: every operand row is
-// stored as NP BF16 planes, p0 = x rounded to 8 bits on a power-of-two grid fixed along the
-// row (an integer in [-128, 128] times the row's scale), p1 = RN_bf16(x - p0),
-// p2 = RN_bf16(x - p0 - p1).  A product is formed from the plane products pa*qb with
-// a + b < NP in FP32 accumulators in tensor memory (TMEM).  p0 and p1 are fixed-point
-// (integers on grids fixed along each row, planes.cuh), so in the exchange SYRK the
+// stored as NP BF16 planes; with sigma the power of two just above the row's max |x|,
+// p0 = x rounded to the grid sigma 2^-7, p1 = (x - p0) rounded to sigma 2^-15, and
+// p2 .. p(NP-1) = BF16 roundings of what is left.  A product is formed from the plane
+// products pa*qb with a + b < NP in FP32 accumulators in tensor memory (TMEM).  p0 and p1
+// are fixed-point (integers on grids fixed along each row, planes.cuh), so in the exchange SYRK the
 // products (0,0), (0,1)+(1,0) and (1,1) each sum integers on one grid in an accumulator of
 // their own and are exact; every product with a floating plane (the contributions of
 // elements far below their row's max) goes to a fourth.  The half-transform uses two
@@ -491,14 +491,17 @@ __global__ void __launch_bounds__(256) x_to_planes_kernel(const float* __restric
 }
 
 // K[m][n] = K[n][m] = sum_split Kpart[split][m][n] (FP64 sum of FP32 partials), m >= n.
+// When a bounded wait of the tensor-core kernels gave up (*err set), K is filled with NaN so
+// that an incomplete exchange matrix can never pass for a result.
 __global__ void kmixed_reduce_kernel(const float* __restrict__ Kpart, int nsplit, int npad, int nao,
-                                     double* __restrict__ K) {
+                                     const int* __restrict__ err, double* __restrict__ K) {
   long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= (long)nao * nao) return;
   int m = (int)(e / nao), n = (int)(e % nao);
   if (n > m) return;
   double s = 0.0;
   for (int k = 0; k < nsplit; ++k) s += (double)Kpart[((size_t)k * npad + m) * npad + n];
+  if (*err) s = __longlong_as_double(0x7ff8000000000000LL);
   K[(size_t)m * nao + n] = s;
   K[(size_t)n * nao + m] = s;
 }
@@ -674,7 +677,7 @@ int build_K_mixed(const void* B, const BLayout& L, int nao, int naux, const doub
     else DF_TRY(launch_gemm<3>(maps, q, grid, s));
   }
   long nn = (long)nao * nao;
-  kmixed_reduce_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, s>>>(w.Kpart, nsplit, npad, nao, K);
+  kmixed_reduce_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, s>>>(w.Kpart, nsplit, npad, nao, w.err, K);
   DF_LAUNCHED("kmixed_reduce_kernel");
   return DF_OK;
 }

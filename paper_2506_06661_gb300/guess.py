@@ -56,15 +56,41 @@ class GuessModel:
         p = torch.tensor(init_params(seed), dtype=torch.float32, device="cuda")
         return cls(p, torch.zeros_like(p), torch.zeros_like(p), 0)
 
+    @classmethod
+    def create_on_device(cls, seed: int = 0) -> "GuessModel":
+        """Initialise through the library's guess_mlp_create (counter-based generator on the
+        GPU) instead of the host generator of create()."""
+        p = torch.empty(param_count(), dtype=torch.float32, device="cuda")
+        m, v = torch.empty_like(p), torch.empty_like(p)
+        _check(lib().guess_mlp_create(ctypes.c_ulonglong(seed), _ptr(p), _ptr(m), _ptr(v), _stream()))
+        return cls(p, m, v, 0)
+
+    def to_blob(self, with_moments: bool = True) -> bytes:
+        """The library's self-describing model blob (guess_mlp_save)."""
+        n = int(lib().guess_mlp_blob_bytes(1 if with_moments else 0))
+        buf = ctypes.create_string_buffer(n)
+        _check(lib().guess_mlp_save(_ptr(self.params), _ptr(self.m) if with_moments else None,
+                                    _ptr(self.v) if with_moments else None, self.step, buf, n, _stream()))
+        return buf.raw
+
+    @classmethod
+    def from_blob(cls, blob: bytes) -> "GuessModel":
+        p = torch.empty(param_count(), dtype=torch.float32, device="cuda")
+        m, v = torch.empty_like(p), torch.empty_like(p)
+        step = ctypes.c_int(0)
+        buf = ctypes.create_string_buffer(bytes(blob), len(blob))
+        _check(lib().guess_mlp_load(buf, len(blob), _ptr(p), _ptr(m), _ptr(v), ctypes.byref(step), _stream()))
+        return cls(p, m, v, step.value)
+
     def save(self, path: str) -> None:
-        np.savez(path, params=self.params.cpu().numpy(), m=self.m.cpu().numpy(), v=self.v.cpu().numpy(),
-                 step=self.step, history=np.array(self.history, dtype=np.float64))
+        """Write the model blob (parameters, Adam moments and step) to a file."""
+        with open(path, "wb") as fh:
+            fh.write(self.to_blob(True))
 
     @classmethod
     def load(cls, path: str) -> "GuessModel":
-        z = np.load(path)
-        t = lambda a: torch.tensor(a, dtype=torch.float32, device="cuda")  # noqa: E731
-        return cls(t(z["params"]), t(z["m"]), t(z["v"]), int(z["step"]), list(z["history"]))
+        with open(path, "rb") as fh:
+            return cls.from_blob(fh.read())
 
 
 def features(xyz):

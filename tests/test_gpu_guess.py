@@ -143,3 +143,49 @@ def test_trained_guess_reduces_iterations():
     # the network's blocks scaled to the electron count pass the validity gate
     assert ev["guess_used"] >= (3 * len(test_mols)) // 4
     assert ev["mean_iter_learned"] < ev["mean_iter_core"]
+
+
+def test_model_blob_roundtrip_and_rejections(tmp_path):
+    """guess_mlp_create / _save / _load through the C ABI: a saved model loads back bit for bit
+    (parameters, Adam moments and step); a corrupted payload, a wrong version or a truncated
+    blob is refused with DF_ERR_ARG."""
+    from paper_2506_06661_gb300 import guess
+    model = guess.GuessModel.create_on_device(seed=7)
+    n = guess.param_count()
+    p = model.params.cpu().numpy()
+    # weights within +-sqrt(3 / fan_in) of each layer, biases zero
+    off = 0
+    for fan_in, fan_out in guess.LAYERS:
+        W = p[off:off + fan_in * fan_out]
+        b = p[off + fan_in * fan_out: off + fan_in * fan_out + fan_out]
+        assert np.abs(W).max() <= np.sqrt(3.0 / fan_in) and np.abs(W).max() > 0.5 * np.sqrt(3.0 / fan_in)
+        assert np.all(b == 0)
+        off += fan_in * fan_out + fan_out
+    assert off == n
+    model.m.normal_()
+    model.v.uniform_()
+    model.step = 123
+    path = str(tmp_path / "model.bin")
+    model.save(path)
+    back = guess.GuessModel.load(path)
+    assert back.step == 123
+    for a, b in ((model.params, back.params), (model.m, back.m), (model.v, back.v)):
+        assert torch.equal(a, b)
+    blob = bytearray(open(path, "rb").read())
+    assert len(blob) == int(dfscf.lib().guess_mlp_blob_bytes(1))
+    bad = bytearray(blob)
+    bad[-1] ^= 0x01                        # one payload bit
+    with pytest.raises(dfscf.DFError) as e:
+        guess.GuessModel.from_blob(bytes(bad))
+    assert e.value.code == dfscf.DF_ERR_ARG and "checksum" in e.value.msg
+    bad = bytearray(blob)
+    bad[8] = 99                            # format version
+    with pytest.raises(dfscf.DFError) as e:
+        guess.GuessModel.from_blob(bytes(bad))
+    assert e.value.code == dfscf.DF_ERR_ARG and "version" in e.value.msg
+    with pytest.raises(dfscf.DFError) as e:
+        guess.GuessModel.from_blob(bytes(blob[: len(blob) // 2]))
+    assert e.value.code == dfscf.DF_ERR_ARG
+    # without moments: parameters only, step 0 and zero moments on load
+    lean = guess.GuessModel.from_blob(model.to_blob(with_moments=False))
+    assert torch.equal(lean.params, model.params) and lean.step == 0 and float(lean.m.abs().max()) == 0.0

@@ -1,9 +1,9 @@
 """df_j_noalloc, the Coulomb build for callers that cannot allocate a device workspace
 (plugins whose host framework owns all device memory, services that forbid allocation
-while running).  Called through the C ABI with ctypes and checked against df_jk's J on
-two calls in a row, at the FP64 parity tolerance the other J tests use (1e-10 relative,
-max-norm).  This file is collected last so that a failure here leaves every other test
-already run."""
+while running).  Called through the C ABI with ctypes and checked against df_jk's J and
+against the CPU oracle's DF-J on two calls in a row, at the FP64 parity tolerance the other
+J tests use (1e-10 relative, max-norm).  This file is collected last so that a failure here
+leaves every other test already run."""
 import ctypes
 
 import numpy as np
@@ -11,6 +11,8 @@ import pytest
 import torch
 
 import gen
+import oracle
+from oracle import scf as oscf
 
 pytestmark = pytest.mark.gpu
 dfscf = pytest.importorskip("paper_2506_06661_gb300")
@@ -35,6 +37,7 @@ def test_noalloc_j_matches_df_jk_twice():
     mol = gen.make_molecule(13, 5.5, 21)          # nao 65, naux 195: ragged tile counts
     Lf = dfscf.metric_chol(mol.aux_xyz, mol.aux_exp)
     B = dfscf.build_B(mol.ao_xyz, mol.ao_exp, mol.aux_xyz, mol.aux_exp, Lf, "fp64")
+    Bora = oscf.build_system(mol).B
     rng = np.random.default_rng(5)
     stream = torch.cuda.current_stream().cuda_stream
     for call in range(2):
@@ -48,6 +51,8 @@ def test_noalloc_j_matches_df_jk_twice():
         torch.cuda.synchronize()
         assert torch.isfinite(J).all()
         assert _rel(J, Jref) <= 1e-10
+        Jora = torch.from_numpy(oracle.df_j(Bora, mol.nao, 2 * C @ C.T))
+        assert _rel(J.cpu(), Jora) <= 1e-10
 
 
 def test_noalloc_rejects_oversized_problem():
