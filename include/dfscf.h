@@ -174,10 +174,23 @@ int df_eigh_lowest(double* A, int n, int k, double* w, double* Z, void* work, si
  *   e = X^T (F D S - S D F) X with canonical orthogonalisation X = U s^-1/2 (s > lindep),
  *   extrapolation over <= diis_space vectors, aufbau occupation of nocc = nelec/2.
  * Converged when |dE| < conv_tol and max|e| < conv_err.  In DF_MIXED mode the loop runs
- * with mixed-precision K until |dE| < switch_tol or max|e| < switch_err, or until max|e|,
- * once below 1e-3, has not improved by 10% for 10 iterations (the mixed-precision floor), or
- * for three quarters of max_cycle; then at least n_fp64_final FP64 iterations follow and the
- * reported energy is the FP64 one.
+ * with mixed-precision K until max|e| < 1e-3, |dE| < switch_tol or max|e| < switch_err, or
+ * until max|e|, once below 1e-3, has not improved by 10% for 10 iterations (the
+ * mixed-precision floor), or for three quarters of max_cycle.  With the knob
+ * "mixed_incremental" (default 1) one FP64 Fock build then becomes the base of K, and later
+ * iterations update K += K[U+] - K[U-] in mixed precision, U+ U+^T - U- U-^T being the change
+ * of the occupied projector (factorised over the principal angles between the two occupied
+ * spaces, so the mixed error shrinks with the change); a new base is built when the occupied
+ * space turns by more than 60 degrees in one step or the updates stall.  With the knob at 0
+ * the iterations switch to FP64 instead.  Either way at least n_fp64_final FP64 iterations
+ * end the run and the reported energy is the FP64 one.
+ * Newton steps (knob "soscf", default 1; the paper's Section "Second-Order Self-Consistent
+ * Field"): once max|e| has not improved by 10% for 12 iterations with an accurate Fock
+ * matrix, each later iteration replaces the DIIS extrapolation and diagonalisation by a
+ * Newton step on the orbital rotation, solved by "soscf_cg" preconditioned conjugate-
+ * gradient iterations whose Hessian products use the exchange of the SCF's precision (mixed
+ * in DF_MIXED mode: an approximate Hessian with the exact gradient, so the converged result
+ * is unchanged).
  * dm0 (device [nao][nao], may be NULL): initial density; it need not be idempotent nor
  * have the right electron count (paper, Section "Initial Guess for Mean-field Methods").
  * If dm0 fails the checks |tr(dm0 S) - nelec| / nelec < 0.05 and
@@ -235,14 +248,20 @@ int scf_run(const df_molecule* mol, const scf_opts* opt, const double* dm0, doub
             cudaStream_t s);
 
 /* ---- a13: batched SCF -------------------------------------------------------------------
- * Runs scf_run's algorithm for nmol molecules of uneven size.  `slots` molecules are in
- * flight at once, each with its own stream (created by the library, ordered after `s`)
- * and its own slice of the workspace; a slot that finishes takes the next molecule.  Each
- * molecule's iteration is captured once per precision into a CUDA graph and replayed.
- * dm0s (may be NULL; entries may be NULL): device starting densities; D_outs (may be
- * NULL; entries may be NULL): device [nao][nao] outputs; results: HOST array of nmol.
- * Returns DF_ERR_NOCONV if any molecule did not converge (all results are still filled).
- * work: scf_batch_work_bytes(mols, nmol, precision, slots) bytes.  Blocks until done.  */
+ * Runs scf_run's algorithm for nmol molecules of uneven size.  At most `slots` molecules
+ * are in flight at once, each with its own stream (created by the library, ordered after
+ * `s`) and a region of the workspace of its own size (scf_work_bytes of that molecule),
+ * handed out first-fit: many small molecules run beside a few large ones.  Molecules start
+ * largest first; a molecule that finishes returns its region and stream to the next one.
+ * The workspace may have any size that holds the largest molecule; more bytes allow more
+ * molecules in flight.  scf_batch_work_bytes(mols, nmol, precision, slots) is the size that
+ * holds `slots` copies of the largest molecule (always enough for `slots` in flight).
+ * Each molecule's iteration is captured once per precision into a CUDA graph and replayed
+ * (Newton iterations run eagerly).  dm0s (may be NULL; entries may be NULL): device starting
+ * densities; D_outs (may be NULL; entries may be NULL): device [nao][nao] outputs; results:
+ * HOST array of nmol.  Returns DF_ERR_NOCONV if any molecule did not converge (all results
+ * are still filled), DF_ERR_NOMEM if the workspace cannot hold the largest molecule.
+ * Blocks until done.                                                                     */
 size_t scf_batch_work_bytes(const df_molecule* mols, int nmol, int precision, int slots);
 int scf_run_batch(const df_molecule* mols, int nmol, const scf_opts* opt, const double* const* dm0s,
                   double* const* D_outs, scf_result* results, int slots, void* work, size_t work_bytes,
@@ -321,6 +340,48 @@ size_t df_congruence_work_bytes(int n);
 int df_congruence(const double* M, const double* A, int n, double* out, void* work, size_t work_bytes,
                   cudaStream_t s);
 
+/* ---- density-fitting error diagnostics (NEXT-3) ------------------------------------------
+ * Lehtola's diagonal error of the paper's Section "Density fitting",
+ *     Delta = sum_mn [(mn|mn) - sum_P T_{P,mn}^2]   (ordered pairs: packed pairs off the
+ *                                                    diagonal count twice),
+ * and the residual of the auxiliary-basis fit of Section "Automatic Differentiation",
+ *     sigma_mn = (mn|mn) - sum_PQ (P|mn) (M^-1)_PQ (Q|mn)   (>= 0 for the Coulomb metric),
+ * for every packed pair mn (sigma [npair], device).  With jac (device [npair][ntheta], may be
+ * NULL) the Jacobian is also formed, contracted with dalpha (device [naux][ntheta],
+ * d alpha_P / d theta_t, 1 <= ntheta <= 8): jac[mn][t] = sum_P (d sigma_mn / d alpha_P)
+ * dalpha[P][t], from the closed-form exponent derivatives of the s-type integrals (the paper
+ * differentiates automatically).  For an even-tempered set alpha_P = a beta^k_P on every
+ * centre, theta = (ln a, ln beta) gives dalpha[P] = (alpha_P, k_P alpha_P).  *delta (HOST,
+ * may be NULL) receives Delta.  Synchronises the stream (pivot check of the metric's
+ * Cholesky factor: DF_ERR_NOT_SPD).  The Jacobian needs O(naux^2 npair) work and
+ * 4 naux npair doubles of workspace: meant for small molecules or single atoms, as in the
+ * paper's basis optimisation.  work: df_fit_residual_work_bytes(nao, naux, jac != NULL).   */
+size_t df_fit_residual_work_bytes(int nao, int naux, int with_jacobian);
+int df_fit_residual(const double* ao_xyz, const double* ao_exp, int nao, const double* aux_xyz,
+                    const double* aux_exp, int naux, const double* dalpha, int ntheta, double* sigma, double* jac,
+                    double* delta, void* work, size_t work_bytes, cudaStream_t s);
+
+/* ---- long-range density fitting (NEXT-1) -----------------------------------------------
+ * The LRDF scheme of the paper's Section "Density fitting": 1/r = erf(w r)/r + erfc(w r)/r,
+ * the long-range part density fitted with the long-range metric M^LR = L L^T and
+ * T = L^-1 (Q|mn)^LR, the short-range part computed exactly:
+ *     (mn|kl) ~ (mn|kl)^SR + sum_P T_{P,mn} T_{P,kl}.
+ * df_lrdf_build writes T (omega > 0) into B in the DF_FP64 layout of df_build_B
+ * (df_B_bytes(nao, naux, DF_FP64) bytes), synchronising once for the metric's pivot check
+ * (DF_ERR_NOT_SPD).  df_lrdf_jk returns J[D] and K[C C^T] (either may be NULL) as the
+ * long-range DF part (df_jk on T) plus the short-range four-centre part, summed directly over
+ * orbital pairs (quartets whose pair factors multiply to less than 1e-16 of the largest are
+ * skipped).  The short-range sums cost O(npair^2) for J and O(nao^4) for K: meant for
+ * molecules of up to a few hundred basis functions.  Both synchronise the stream once.
+ * works: df_lrdf_build_work_bytes(nao, naux), df_lrdf_jk_work_bytes(nao, naux, nocc).       */
+size_t df_lrdf_build_work_bytes(int nao, int naux);
+int df_lrdf_build(const double* ao_xyz, const double* ao_exp, int nao, const double* aux_xyz, const double* aux_exp,
+                  int naux, double omega, void* B, size_t B_bytes, void* work, size_t work_bytes, cudaStream_t s);
+size_t df_lrdf_jk_work_bytes(int nao, int naux, int nocc);
+int df_lrdf_jk(const void* B_lr, const double* ao_xyz, const double* ao_exp, int nao, int naux, double omega,
+               const double* D, const double* C, int nocc, double* J, double* K, void* work, size_t work_bytes,
+               cudaStream_t s);
+
 /* ---- core-Hamiltonian guess ------------------------------------------------------------
  * S, h = T + V, canonical orthogonalisation X (eigenvalues of S above lindep), the
  * nocc = nelec/2 lowest eigenvectors C_occ = X C' of X^T h X and D = 2 C_occ C_occ^T: the
@@ -360,9 +421,10 @@ int df_j_noalloc(const void* B, int nao, int naux, const double* D, double* J, c
  * (K-dimension splits of the exchange SYRK, 0 = built-in heuristic), "jpass2_rows" (32..512,
  * auxiliary rows per CTA slice of J's second pass), "eig_ctas" (CTAs of the multi-SM
  * eigensolver: 0 automatic, 1 a single CTA) and "mixed_planes" (3..5 BF16 planes per operand of
- * the mixed exchange: 6, 10 or 15 plane products; it also sizes a mixed B).  Two more knobs
- * bound the multi-SM eigensolver's grid barriers: "eig_barrier_polls" (256..2^30 polls before a
- * wait gives up with DF_ERR_TIMEOUT; default 2^22, about a second) and "eig_barrier_extra"
+ * the mixed exchange: 6, 10 or 15 plane products; it also sizes a mixed B).
+ * "mixed_incremental" (0 or 1), "soscf" (0 or 1) and "soscf_cg" (1..64) shape the SCF as
+ * described at scf_run.  Two more knobs bound the multi-SM eigensolver's grid barriers:
+ * "eig_barrier_polls" (256..2^30 polls before a wait gives up with DF_ERR_TIMEOUT; default 2^22, about a second) and "eig_barrier_extra"
  * (0 or 1; 1 makes every barrier wait for one arrival that never comes, so that a test can
  * watch the bounded wait run out; leave it 0).  Host-side process-wide state: change
  * knobs only between calls and re-query *_work_bytes afterwards (split counts size the
@@ -370,6 +432,18 @@ int df_j_noalloc(const void* B, int nao, int naux, const double* D, double* J, c
  * df_tune_get returns -1 for an unknown name.                                              */
 int df_tune_set(const char* name, int value);
 int df_tune_get(const char* name);
+
+/* ---- bounds-checking build -------------------------------------------------------------
+ * A build of this library with -DDFSCF_BOUNDS_CHECK (libdfscf_bounds.so) checks the global
+ * index of the kernels' computed accesses against their buffer's extent; a bad index is
+ * counted, the first one is recorded with its bound and source line, and the access is
+ * redirected to element 0 so that the run continues without a fault (it stands in for a
+ * memory checker).  df_bounds_checked() is 1 in that build, 0 otherwise.
+ * df_bounds_violations synchronises the device, writes the number of bad indices since the
+ * last call to the HOST *count and the first one's location to where (HOST, may be NULL),
+ * and clears the records (always 0 in the normal build).                                   */
+int df_bounds_checked(void);
+int df_bounds_violations(unsigned long long* count, char* where, size_t where_bytes);
 
 /* ---- phase profiler ------------------------------------------------------------------
  * When enabled, the J/K builds bracket each kernel phase with CUDA events on the

@@ -119,6 +119,14 @@ _SIGS = {
     "df_lowdin_factors": (_I, [_VP, _VP, _I, _D, _VP, _VP, _VP, _SZ, _VP]),
     "df_congruence_work_bytes": (_SZ, [_I]),
     "df_congruence": (_I, [_VP, _VP, _I, _VP, _VP, _SZ, _VP]),
+    "df_fit_residual_work_bytes": (_SZ, [_I, _I, _I]),
+    "df_fit_residual": (_I, [_VP, _VP, _I, _VP, _VP, _I, _VP, _I, _VP, _VP, ctypes.POINTER(_D), _VP, _SZ, _VP]),
+    "df_lrdf_build_work_bytes": (_SZ, [_I, _I]),
+    "df_lrdf_build": (_I, [_VP, _VP, _I, _VP, _VP, _I, _D, _VP, _SZ, _VP, _SZ, _VP]),
+    "df_lrdf_jk_work_bytes": (_SZ, [_I, _I, _I]),
+    "df_lrdf_jk": (_I, [_VP, _VP, _VP, _I, _I, _D, _VP, _VP, _I, _VP, _VP, _VP, _SZ, _VP]),
+    "df_bounds_checked": (_I, []),
+    "df_bounds_violations": (_I, [ctypes.POINTER(ctypes.c_ulonglong), ctypes.c_char_p, _SZ]),
     "df_j_noalloc_capacity": (_SZ, []),
     "df_j_noalloc": (_I, [_VP, _I, _I, _VP, _VP, _VP]),
     "scf_batch_work_bytes": (_SZ, [ctypes.POINTER(DFMolecule), _I, _I, _I]),
@@ -128,10 +136,11 @@ _SIGS = {
 
 
 def lib():
-    """Load libdfscf.so (building it with nvcc first if it is missing or stale)."""
+    """Load libdfscf.so (building it with nvcc first if it is missing or stale); with the
+    environment variable DFSCF_VARIANT=bounds, the bounds-checking build instead."""
     global _lib
     if _lib is None:
-        path = _build.build()
+        path = _build.build(variant=os.environ.get("DFSCF_VARIANT", ""))
         if not os.path.exists(path):
             raise RuntimeError("libdfscf.so is missing and could not be built")
         L = ctypes.CDLL(path)
@@ -144,7 +153,15 @@ def lib():
 
 
 def library_path() -> str:
-    return _build.LIB
+    return _build.variant_path(os.environ.get("DFSCF_VARIANT", ""))
+
+
+def bounds_violations():
+    """(count, first location) of out-of-range indices since the last call (checking build)."""
+    n = ctypes.c_ulonglong(0)
+    where = ctypes.create_string_buffer(256)
+    _check(lib().df_bounds_violations(ctypes.byref(n), where, 256))
+    return int(n.value), where.value.decode()
 
 
 def _check(rc: int):
@@ -270,6 +287,52 @@ def jk(B: DFTensor, D=None, C=None, precision=None, want_j=True, want_k=True, wo
     _check(lib().df_jk(_ptr(B.buf), nao, B.naux, p, _ptr(D), _ptr(C), nocc, _ptr(J), _ptr(K), _ptr(work.buf),
                        work.buf.numel(), _stream()))
     return J, K
+
+
+def lrdf_build(ao_xyz, ao_exp, aux_xyz, aux_exp, omega: float) -> DFTensor:
+    """Long-range whitened tensor T (FP64 B layout) of the LRDF scheme (df_lrdf_build)."""
+    ao_xyz, ao_exp, aux_xyz, aux_exp = map(_dev, (ao_xyz, ao_exp, aux_xyz, aux_exp))
+    nao, naux = ao_exp.numel(), aux_exp.numel()
+    nb = B_bytes(nao, naux, "fp64")
+    buf = torch.empty(nb, dtype=torch.uint8, device="cuda")
+    w = _work(lib().df_lrdf_build_work_bytes(nao, naux))
+    _check(lib().df_lrdf_build(_ptr(ao_xyz), _ptr(ao_exp), nao, _ptr(aux_xyz), _ptr(aux_exp), naux, float(omega),
+                               _ptr(buf), nb, _ptr(w), w.numel(), _stream()))
+    return DFTensor(buf, nao, naux, DF_FP64)
+
+
+def lrdf_jk(T: DFTensor, ao_xyz, ao_exp, omega: float, D=None, C=None):
+    """J[D] and K[C C^T] with long-range DF plus exact short-range four-centre terms."""
+    ao_xyz, ao_exp = _dev(ao_xyz), _dev(ao_exp)
+    nao = T.nao
+    D = _dev(D) if D is not None else None
+    C = _dev(C) if C is not None else None
+    nocc = C.shape[1] if C is not None else 0
+    J = torch.empty(nao, nao, dtype=torch.float64, device="cuda") if D is not None else None
+    K = torch.empty(nao, nao, dtype=torch.float64, device="cuda") if C is not None else None
+    w = _work(lib().df_lrdf_jk_work_bytes(nao, T.naux, nocc))
+    _check(lib().df_lrdf_jk(_ptr(T.buf), _ptr(ao_xyz), _ptr(ao_exp), nao, T.naux, float(omega), _ptr(D), _ptr(C), nocc,
+                            _ptr(J), _ptr(K), _ptr(w), w.numel(), _stream()))
+    return J, K
+
+
+def fit_residual(ao_xyz, ao_exp, aux_xyz, aux_exp, dalpha=None):
+    """(sigma [npair], jac [npair][ntheta] or None, Delta) of the density fit (df_fit_residual)."""
+    ao_xyz, ao_exp, aux_xyz, aux_exp = map(_dev, (ao_xyz, ao_exp, aux_xyz, aux_exp))
+    nao, naux = ao_exp.numel(), aux_exp.numel()
+    sigma = torch.empty(nao * (nao + 1) // 2, dtype=torch.float64, device="cuda")
+    jac, nt, da = None, 0, None
+    if dalpha is not None:
+        da = _dev(dalpha)
+        if da.dim() == 1:
+            da = da.reshape(-1, 1).contiguous()
+        nt = da.shape[1]
+        jac = torch.empty(sigma.numel(), nt, dtype=torch.float64, device="cuda")
+    w = _work(lib().df_fit_residual_work_bytes(nao, naux, 1 if jac is not None else 0))
+    delta = ctypes.c_double(0.0)
+    _check(lib().df_fit_residual(_ptr(ao_xyz), _ptr(ao_exp), nao, _ptr(aux_xyz), _ptr(aux_exp), naux, _ptr(da), nt,
+                                 _ptr(sigma), _ptr(jac), ctypes.byref(delta), _ptr(w), w.numel(), _stream()))
+    return sigma, jac, delta.value
 
 
 def eigh(A):
@@ -407,16 +470,13 @@ def scf_run_batch(mols, opts: ScfOpts | None = None, dm0s=None, slots: int = 16,
     arr = (DFMolecule * n)(*[d.c for d in devs])
     o = opts if opts is not None else default_opts(**kw)
     slots = max(1, min(slots, n))
-    nb = int(lib().scf_batch_work_bytes(arr, n, o.precision, slots))
-    if work is None or work.numel() < nb:
-        # every slot is sized for the largest molecule: fewer slots when they do not fit in
-        # 85% of the free device memory
-        free = torch.cuda.mem_get_info()[0] + (work.numel() if work is not None else 0)
-        while slots > 1 and nb > 0.85 * free:
-            slots = max(1, slots * 3 // 4)
-            nb = int(lib().scf_batch_work_bytes(arr, n, o.precision, slots))
-    if work is None or work.numel() < nb:
-        work = _work(nb)
+    if work is None:
+        # molecules take regions of their own size: give the library up to `slots` copies of
+        # the largest molecule, capped at 85% of the free device memory (it needs one)
+        nb = int(lib().scf_batch_work_bytes(arr, n, o.precision, slots))
+        largest = int(lib().scf_batch_work_bytes(arr, n, o.precision, 1))
+        free = torch.cuda.mem_get_info()[0]
+        work = _work(max(largest, min(nb, int(0.85 * free))))
     dm0_t = None
     dm0_arr = None
     if dm0s is not None:

@@ -3,6 +3,7 @@
 #include <cstdio>
 
 #include "common.cuh"
+#include "kernels.cuh"
 
 namespace dfscf {
 
@@ -127,9 +128,13 @@ static Knob g_knobs[] = {
     {"syrk_split", 0, 0, 4096},      // K-dimension splits of the tcgen05 exchange SYRK
     {"fp64_syrk_split", 0, 0, 4096}, // K-dimension splits of the FP64 exchange SYRK
     {"jpass2_rows", 256, 32, 512},   // auxiliary rows per CTA slice of J's second pass
+    {"j_fp64_fma", 0, 0, 1},         // J passes: 0 double-float products on FP32 units, 1 FP64 FMAs
+    {"jpass1_rows", 1, 1, 8},        // auxiliary rows per CTA of J's first pass (1, 2, 4 or 8)
     {"eig_ctas", 0, 0, 4096},        // CTAs of the multi-SM eigensolver (0 auto, 1 single CTA)
     {"mixed_planes", 5, 3, 5},       // BF16 planes per operand of the mixed exchange (3, 4, 5: 6, 10, 15 products)
     {"mixed_incremental", 1, 0, 1},  // mixed SCF: update K from the change of the occupied projector
+    {"soscf", 1, 0, 1},              // switch from DIIS to Newton steps when DIIS stalls
+    {"soscf_cg", 6, 1, 64},          // conjugate-gradient iterations per Newton step
     {"eig_barrier_polls", 1 << 22, 256, 1 << 30},  // polls before a grid-barrier wait of the eigensolver gives up
     {"eig_barrier_extra", 0, 0, 1},  // test hook: 1 = every eigensolver grid barrier waits for one arrival
                                      // that never comes, so its bounded wait runs out
@@ -164,4 +169,38 @@ extern "C" int df_tune_get(const char* name) {
   for (auto& k : dfscf::g_knobs)
     if (strcmp(k.name, name) == 0) return k.value;
   return -1;
+}
+
+// ---- bounds-check records -------------------------------------------------------------
+extern "C" int df_bounds_checked(void) {
+#ifdef DFSCF_BOUNDS_CHECK
+  return 1;
+#else
+  return 0;
+#endif
+}
+
+extern "C" int df_bounds_violations(unsigned long long* count, char* where, size_t where_bytes) {
+  dfscf::clear_error();
+  DF_REQUIRE(count, DF_ERR_ARG, "df_bounds_violations: null count");
+  struct Unit {
+    const char* name;
+    dfscf::BoundsReader read;
+  };
+  const Unit units[] = {{"dferr.cu", dfscf::bounds_read_dferr},   {"eig.cu", dfscf::bounds_read_eig},
+                        {"integrals.cu", dfscf::bounds_read_integrals}, {"jk.cu", dfscf::bounds_read_jk},
+                        {"linalg.cu", dfscf::bounds_read_linalg}, {"lowdin.cu", dfscf::bounds_read_lowdin},
+                        {"lrdf.cu", dfscf::bounds_read_lrdf},     {"mlp.cu", dfscf::bounds_read_mlp},
+                        {"scf.cu", dfscf::bounds_read_scf},       {"umma.cu", dfscf::bounds_read_umma}};
+  DF_CUDA(cudaDeviceSynchronize());
+  *count = 0;
+  if (where && where_bytes) where[0] = '\0';
+  for (const Unit& u : units) {
+    dfscf::BoundsRecord r{};
+    DF_TRY(u.read(&r));
+    if (r.count && *count == 0 && where && where_bytes)
+      snprintf(where, where_bytes, "%s:%d index %lld outside [0, %lld)", u.name, r.line, r.index, r.bound);
+    *count += r.count;
+  }
+  return DF_OK;
 }

@@ -95,6 +95,56 @@ struct Sizer {
     if (rc_ != DF_OK) return rc_; \
   } while (0)
 
+// ---- bounds-checked indexing (checking build) -------------------------------------------
+// Built with -DDFSCF_BOUNDS_CHECK, DF_IX(i, n) checks 0 <= i < n.  A bad index is counted in
+// this translation unit's record (the first one with its bound and source line is kept)
+// and replaced by 0, so the access stays inside the buffer and the run goes on; the host
+// reads the records with df_bounds_violations().  In the normal build DF_IX(i, n) is i.
+namespace dfscf {
+struct BoundsRecord {
+  unsigned long long count;
+  long long index, bound;
+  int line, pad;
+};
+// Reads and clears this translation unit's record (all zero in the normal build).
+typedef int (*BoundsReader)(BoundsRecord* out);
+}  // namespace dfscf
+
+#ifdef DFSCF_BOUNDS_CHECK
+static __device__ dfscf::BoundsRecord g_df_bounds;
+// An access of w consecutive elements starting at i: 0 <= i and i + w <= n.
+__device__ __forceinline__ long long df_ixw(long long i, long long w, long long n, int line) {
+  if (i >= 0 && i + w <= n) return i;
+  if (atomicAdd(&g_df_bounds.count, 1ull) == 0ull) {
+    g_df_bounds.index = i;
+    g_df_bounds.bound = n;
+    g_df_bounds.line = line;
+  }
+  return 0;
+}
+#define DF_IX(i, n) df_ixw((long long)(i), 1, (long long)(n), __LINE__)
+#define DF_IXW(i, w, n) df_ixw((long long)(i), (long long)(w), (long long)(n), __LINE__)
+#define DF_BOUNDS_READER(name)                                                            \
+  namespace dfscf {                                                                       \
+  int name(BoundsRecord* out) {                                                           \
+    if (cudaMemcpyFromSymbol(out, g_df_bounds, sizeof(BoundsRecord)) != cudaSuccess) return DF_ERR_CUDA; \
+    BoundsRecord zero{};                                                                  \
+    if (cudaMemcpyToSymbol(g_df_bounds, &zero, sizeof(BoundsRecord)) != cudaSuccess) return DF_ERR_CUDA; \
+    return DF_OK;                                                                         \
+  }                                                                                       \
+  }
+#else
+#define DF_IX(i, n) (i)
+#define DF_IXW(i, w, n) (i)
+#define DF_BOUNDS_READER(name)            \
+  namespace dfscf {                       \
+  int name(BoundsRecord* out) {           \
+    *out = BoundsRecord{};                \
+    return DF_OK;                         \
+  }                                       \
+  }
+#endif
+
 // ---- device helpers ----------------------------------------------------------------
 __device__ __forceinline__ double warp_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

@@ -1211,3 +1211,5 @@ extern "C" int df_eigh_lowest(double* A, int n, int k, double* w, double* Z, voi
   DF_REQUIRE(h == 0, DF_ERR_NOCONV, "df_eigh_lowest: inverse iteration or re-orthogonalisation failed (%d)", h);
   return DF_OK;
 }
+
+DF_BOUNDS_READER(bounds_read_eig)

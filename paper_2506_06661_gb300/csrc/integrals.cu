@@ -65,8 +65,11 @@ __global__ void int1e_kernel(const double* __restrict__ xyz, const double* __res
   if (V) V[o] = v;
 }
 
-// (c|d) = N_c N_d 2 pi^{5/2} / (c d sqrt(c + d)) F0(cd/(c+d) R^2)
-__global__ void int2c_kernel(const double* __restrict__ xyz, const double* __restrict__ ex, int naux,
+// (c|d) = N_c N_d 2 pi^{5/2} / (c d sqrt(c + d)) F0(cd/(c+d) R^2).  With omega > 0 the
+// long-range operator erf(omega r)/r of the paper's LRDF split: the reduced exponent
+// rho = cd/(c+d) becomes rho f in the Boys argument and the prefactor gains sqrt(f),
+// f = omega^2 / (rho + omega^2).
+__global__ void int2c_kernel(const double* __restrict__ xyz, const double* __restrict__ ex, int naux, double omega,
                              double* __restrict__ M) {
   int c = blockIdx.y;
   int d = blockIdx.x * blockDim.x + threadIdx.x;
@@ -75,7 +78,13 @@ __global__ void int2c_kernel(const double* __restrict__ xyz, const double* __res
   double dx = xyz[3 * c] - xyz[3 * d], dy = xyz[3 * c + 1] - xyz[3 * d + 1], dz = xyz[3 * c + 2] - xyz[3 * d + 2];
   double r2 = dx * dx + dy * dy + dz * dz;
   double pre = norm_s(ec) * norm_s(ed) * 2.0 * kPi * kPi * sqrt(kPi) / (ec * ed * sqrt(ec + ed));
-  M[(size_t)c * naux + d] = pre * boys_f0(ec * ed / (ec + ed) * r2);
+  double rho = ec * ed / (ec + ed);
+  if (omega > 0.0) {
+    const double f = omega * omega / (rho + omega * omega);
+    pre *= sqrt(f);
+    rho *= f;
+  }
+  M[(size_t)c * naux + d] = pre * boys_f0(rho * r2);
 }
 
 // Per packed pair mn: product exponent p, centre P and K_mn = N_m N_n e^{-mu R^2} 2 pi^{5/2} / p.
@@ -101,7 +110,7 @@ __global__ void pair_table_kernel(const double* __restrict__ xyz, const double* 
 __global__ void int3c_kernel(const double* __restrict__ pp, const double* __restrict__ px,
                              const double* __restrict__ py, const double* __restrict__ pz,
                              const double* __restrict__ pk, long npair, long ld,
-                             const double* __restrict__ axyz, const double* __restrict__ aex, int q0,
+                             const double* __restrict__ axyz, const double* __restrict__ aex, int q0, double omega,
                              double* __restrict__ R) {
   int q = q0 + blockIdx.y;
   long ij = (long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -116,9 +125,14 @@ __global__ void int3c_kernel(const double* __restrict__ pp, const double* __rest
   double p = pp[ij];
   double dx = px[ij] - cx, dy = py[ij] - cy, dz = pz[ij] - cz;
   double inv = 1.0 / (p + c);
-  double t = p * c * inv * (dx * dx + dy * dy + dz * dz);
+  double rho = p * c * inv;
   double pre = pk[ij] * norm_s(c) / c * sqrt(inv);
-  row[ij] = pre * boys_f0(t);
+  if (omega > 0.0) {  // long-range operator, as in int2c_kernel
+    const double f = omega * omega / (rho + omega * omega);
+    pre *= sqrt(f);
+    rho *= f;
+  }
+  row[ij] = pre * boys_f0(rho * (dx * dx + dy * dy + dz * dz));
 }
 
 __global__ void enuc_kernel(const double* __restrict__ xyz, const double* __restrict__ z, int natm,
@@ -144,26 +158,34 @@ int launch_int1e(const double* ao_xyz, const double* ao_exp, int nao, const doub
   return DF_OK;
 }
 
-int launch_int2c(const double* xyz, const double* ex, int naux, double* M, cudaStream_t s) {
+int launch_int2c(const double* xyz, const double* ex, int naux, double* M, cudaStream_t s, double omega) {
   dim3 grid((naux + 127) / 128, naux);
-  int2c_kernel<<<grid, 128, 0, s>>>(xyz, ex, naux, M);
+  int2c_kernel<<<grid, 128, 0, s>>>(xyz, ex, naux, omega, M);
   DF_LAUNCHED("int2c_kernel");
   return DF_OK;
 }
 
+int launch_pair_table(const double* ao_xyz, const double* ao_exp, int nao, double* pair_tab, cudaStream_t s) {
+  long npair = npair_of(nao);
+  double* pp = pair_tab;
+  pair_table_kernel<<<(unsigned)((npair + 255) / 256), 256, 0, s>>>(ao_xyz, ao_exp, npair, pp, pp + npair,
+                                                                    pp + 2 * npair, pp + 3 * npair, pp + 4 * npair);
+  DF_LAUNCHED("pair_table_kernel");
+  return DF_OK;
+}
+
 int launch_int3c(const double* ao_xyz, const double* ao_exp, int nao, const double* aux_xyz, const double* aux_exp,
-                 int naux, double* R, long ld, double* pair_tab, cudaStream_t s) {
+                 int naux, double* R, long ld, double* pair_tab, cudaStream_t s, double omega) {
   long npair = npair_of(nao);
   double* pp = pair_tab;
   double* px = pp + npair;
   double* py = px + npair;
   double* pz = py + npair;
   double* pk = pz + npair;
-  pair_table_kernel<<<(unsigned)((npair + 255) / 256), 256, 0, s>>>(ao_xyz, ao_exp, npair, pp, px, py, pz, pk);
-  DF_LAUNCHED("pair_table_kernel");
+  DF_TRY(launch_pair_table(ao_xyz, ao_exp, nao, pair_tab, s));
   for (int q0 = 0; q0 < naux; q0 += 32768) {
     dim3 grid((unsigned)((ld + 255) / 256), (unsigned)min(32768, naux - q0));
-    int3c_kernel<<<grid, 256, 0, s>>>(pp, px, py, pz, pk, npair, ld, aux_xyz, aux_exp, q0, R);
+    int3c_kernel<<<grid, 256, 0, s>>>(pp, px, py, pz, pk, npair, ld, aux_xyz, aux_exp, q0, omega, R);
     DF_LAUNCHED("int3c_kernel");
   }
   return DF_OK;
@@ -205,3 +227,5 @@ extern "C" int df_nuclear_repulsion(const double* nuc_xyz, const double* nuc_z, 
   DF_REQUIRE(natm == 0 || (nuc_xyz && nuc_z), DF_ERR_ARG, "df_nuclear_repulsion: null pointer");
   return launch_enuc(nuc_xyz, nuc_z, natm, e_nuc, s);
 }
+
+DF_BOUNDS_READER(bounds_read_integrals)

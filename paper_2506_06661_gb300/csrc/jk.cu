@@ -74,7 +74,7 @@ __global__ void __launch_bounds__(128) b_to_planes_kernel(const double* __restri
   auto load = [&](int n) -> double {
     if (m >= nao || n >= nao) return 0.0;
     int a = max(m, n), b = min(m, n);
-    return row[(size_t)a * (a + 1) / 2 + b];
+    return row[DF_IX((size_t)a * (a + 1) / 2 + b, ld)];
   };
   double amax = 0.0;
   for (int n = threadIdx.x; n < npad; n += blockDim.x) amax = fmax(amax, fabs(load(n)));
@@ -88,7 +88,7 @@ __global__ void __launch_bounds__(128) b_to_planes_kernel(const double* __restri
     split_row_value(load(n), sig, q);
 #pragma unroll
     for (int j = 0; j < kMixedPlanes; ++j)
-      if (j < out.planes) out.p[j][o + n] = q[j];
+      if (j < out.planes) out.p[j][DF_IX(o + n, (size_t)gridDim.y * npad * npad)] = q[j];
   }
 }
 
@@ -133,7 +133,172 @@ __global__ void __launch_bounds__(512) jpass1_fp64_kernel(const double* __restri
   if (threadIdx.x == 0) d[blockIdx.x] = t;
 }
 
+// ---- J in double-float arithmetic -------------------------------------------------------
+// FP64 issues at about 0.6e12 FMA/s on this GPU, below the one FMA per 8-byte element that
+// J's two passes would need at full HBM speed, so the passes below keep FP64 out of their
+// inner loops.  Each FP64 element x of B is split with integer operations into an unevaluated
+// pair of floats x = hi + lo: hi holds the sign, exponent and top 23 fraction bits (x
+// truncated to 24 significant bits), lo the remaining 29 fraction bits rounded to 24 (so the
+// pair is x to 2^-48 relative; |x| below 2^-126 counts as zero).  Products with the density
+// (or fitting coefficient) pair (h, l) keep h*hi exactly as p + e (e = fma(h, hi, -p)) and add
+// the cross terms h*lo + l*hi to e; sums accumulate as float pairs with Knuth's TwoSum and are
+// combined in FP64 once per thread.  The result matches the FP64 passes to ~1e-13 relative.
+__device__ __forceinline__ void split_f64_bits(double x, float& hi, float& lo) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  const unsigned int uh = (unsigned int)(u >> 32), ul = (unsigned int)u;
+  const unsigned int sign = uh & 0x80000000u;
+  const int e11 = (int)((uh >> 20) & 0x7FFu);
+  const int e8 = e11 - 1023 + 127;                  // biased float exponent of x
+  const bool normal = e8 > 0 && e8 < 255;
+  const unsigned int frac23 = ((uh & 0xFFFFFu) << 3) | (ul >> 29);
+  hi = normal ? __uint_as_float(sign | ((unsigned int)e8 << 23) | frac23) : (e11 == 0x7FF ? __int_as_float(0x7fc00000) : 0.0f);
+  const int es = e11 - 1075 + 127;                  // biased exponent of 2^(e - 52)
+  const float scale = (normal && es > 0) ? __uint_as_float((unsigned int)es << 23) : 0.0f;
+  const float r = __uint2float_rn(ul & 0x1FFFFFFFu) * scale;
+  lo = __uint_as_float(__float_as_uint(r) | sign);
+}
+
+__device__ __forceinline__ void split_f64_arith(double x, float& hi, float& lo) {
+  hi = __double2float_rn(x);
+  lo = __double2float_rn(x - (double)hi);
+}
+
+// (sh, sl) += x * (h + l), x = xh + xl.
+__device__ __forceinline__ void df_madd(float xh, float xl, float h, float l, float& sh, float& sl) {
+  const float p = xh * h;
+  float e = fmaf(xh, h, -p);
+  e = fmaf(xh, l, e);
+  e = fmaf(xl, h, e);
+  const float s = sh + p;
+  const float bp = s - sh;
+  const float t = (sh - (s - bp)) + (p - bp);
+  sl += t + e;
+  sh = s;
+}
+
+// Dw2[ij] = (hi, lo) of w_mn D_mn (packed, padding zero).
+__global__ void weighted_packed_density_df_kernel(const double* __restrict__ D, int nao, long npair, long ld,
+                                                  float2* __restrict__ Dw2) {
+  long ij = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (ij >= ld) return;
+  if (ij >= npair) {
+    Dw2[ij] = make_float2(0.0f, 0.0f);
+    return;
+  }
+  int m, n;
+  unpack_pair(ij, m, n);
+  const double w = (m == n) ? 1.0 : 2.0;
+  float h, l;
+  split_f64_arith(w * 0.5 * (D[DF_IX((size_t)m * nao + n, (size_t)nao * nao)] + D[DF_IX((size_t)n * nao + m, (size_t)nao * nao)]),
+                  h, l);
+  Dw2[ij] = make_float2(h, l);
+}
+
+// d_P = sum_ij B[P][ij] Dw[ij] for R rows per CTA: every load of the density pair (from L2)
+// serves R rows of B (from HBM), so the density is re-read naux / R times instead of naux
+// times.  128-bit loads, double-float products, one FP64 block sum per row.
+template <int R, int NT>
+__global__ void __launch_bounds__(NT) jpass1_df_kernel(const double* __restrict__ B, long ld, int naux,
+                                                       const float4* __restrict__ Dw4, double* __restrict__ d) {
+  __shared__ double sh[NT / 32];
+  const int p0 = blockIdx.x * R;
+  const long n2 = ld / 2;
+  const double2* rows[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r)
+    rows[r] = reinterpret_cast<const double2*>(B) + DF_IX((size_t)min(p0 + r, naux - 1) * n2, (size_t)naux * n2);
+  float ah[R], al[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) ah[r] = al[r] = 0.0f;
+  long i = threadIdx.x;
+  for (; i + NT < n2; i += 2 * NT) {
+    const float4 w0 = Dw4[DF_IX(i, n2)], w1 = Dw4[DF_IX(i + NT, n2)];
+    double2 b0[R], b1[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      b0[r] = __ldcs(rows[r] + DF_IX(i, n2));
+      b1[r] = __ldcs(rows[r] + DF_IX(i + NT, n2));
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      float xh, xl, yh, yl;
+      split_f64_bits(b0[r].x, xh, xl);
+      split_f64_bits(b0[r].y, yh, yl);
+      df_madd(xh, xl, w0.x, w0.y, ah[r], al[r]);
+      df_madd(yh, yl, w0.z, w0.w, ah[r], al[r]);
+      split_f64_bits(b1[r].x, xh, xl);
+      split_f64_bits(b1[r].y, yh, yl);
+      df_madd(xh, xl, w1.x, w1.y, ah[r], al[r]);
+      df_madd(yh, yl, w1.z, w1.w, ah[r], al[r]);
+    }
+  }
+  for (; i < n2; i += NT) {
+    const float4 w0 = Dw4[i];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const double2 b0 = __ldcs(rows[r] + i);
+      float xh, xl, yh, yl;
+      split_f64_bits(b0.x, xh, xl);
+      split_f64_bits(b0.y, yh, yl);
+      df_madd(xh, xl, w0.x, w0.y, ah[r], al[r]);
+      df_madd(yh, yl, w0.z, w0.w, ah[r], al[r]);
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const double t = block_sum((double)ah[r] + (double)al[r], sh);
+    if (threadIdx.x == 0 && p0 + r < naux) d[p0 + r] = t;
+  }
+}
+
 constexpr int JP2_MAX_ROWS = 512;  // largest P slice of pass 2 (shared-memory copy of d)
+
+// Jpart[split][ij] = sum_{P in split} d_P B[P][ij]; one lane per two packed columns,
+// double-float products and sums.
+__global__ void __launch_bounds__(256) jpass2_df_kernel(const double* __restrict__ B, long ld, int naux, int rows,
+                                                        const double* __restrict__ d, double* __restrict__ Jpart) {
+  __shared__ float2 sd[JP2_MAX_ROWS];
+  const int p0 = blockIdx.y * rows;
+  const int np = min(rows, naux - p0);
+  for (int i = threadIdx.x; i < np; i += blockDim.x) {
+    float h, l;
+    split_f64_arith(d[p0 + i], h, l);
+    sd[i] = make_float2(h, l);
+  }
+  __syncthreads();
+  const long c2 = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c2 * 2 >= ld) return;
+  const long st = ld / 2;
+  const double2* col = reinterpret_cast<const double2*>(B) + (size_t)p0 * st + c2;
+  float xh = 0.0f, xl = 0.0f, yh = 0.0f, yl = 0.0f;
+  int p = 0;
+  for (; p + 3 < np; p += 4) {
+    double2 v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      v[u] = __ldcs(col + DF_IX((size_t)(p0 + p + u) * st + c2, (size_t)naux * st) - (size_t)p0 * st - c2);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const float2 w = sd[p + u];
+      float ah, al, bh, bl;
+      split_f64_bits(v[u].x, ah, al);
+      split_f64_bits(v[u].y, bh, bl);
+      df_madd(ah, al, w.x, w.y, xh, xl);
+      df_madd(bh, bl, w.x, w.y, yh, yl);
+    }
+  }
+  for (; p < np; ++p) {
+    const double2 v0 = __ldcs(col + (size_t)p * st);
+    const float2 w = sd[p];
+    float ah, al, bh, bl;
+    split_f64_bits(v0.x, ah, al);
+    split_f64_bits(v0.y, bh, bl);
+    df_madd(ah, al, w.x, w.y, xh, xl);
+    df_madd(bh, bl, w.x, w.y, yh, yl);
+  }
+  reinterpret_cast<double2*>(Jpart)[DF_IX((size_t)blockIdx.y * st + c2, (size_t)gridDim.y * st)] =
+      make_double2((double)xh + (double)xl, (double)yh + (double)yl);
+}
 
 // Jpart[split][ij] = sum_{P in split} d_P B[P][ij]; one lane per two packed columns.
 __global__ void __launch_bounds__(256) jpass2_fp64_kernel(const double* __restrict__ B, long ld, int naux, int rows,
@@ -167,11 +332,11 @@ __global__ void jreduce_unpack_kernel(const double* __restrict__ Jpart, int nspl
   long ij = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (ij >= (long)nao * (nao + 1) / 2) return;
   double s = 0.0;
-  for (int k = 0; k < nsplit; ++k) s += Jpart[(size_t)k * ld + ij];
+  for (int k = 0; k < nsplit; ++k) s += Jpart[DF_IX((size_t)k * ld + ij, (size_t)nsplit * ld)];
   int m, n;
   unpack_pair(ij, m, n);
-  J[(size_t)m * nao + n] = s;
-  J[(size_t)n * nao + m] = s;
+  J[DF_IX((size_t)m * nao + n, (size_t)nao * nao)] = s;
+  J[DF_IX((size_t)n * nao + m, (size_t)nao * nao)] = s;
 }
 
 // ---- FP64 K ---------------------------------------------------------------------------
@@ -196,7 +361,7 @@ __global__ void __launch_bounds__(256) k_halftransform_fp64_kernel(const double*
       double v = 0.0;
       if (gm < nao && gn < nao) {
         int a = max(gm, gn), b = min(gm, gn);
-        v = row[(size_t)a * (a + 1) / 2 + b];
+        v = row[DF_IX((size_t)a * (a + 1) / 2 + b, ld)];
       }
       As[nn][mm] = v;
     }
@@ -205,7 +370,7 @@ __global__ void __launch_bounds__(256) k_halftransform_fp64_kernel(const double*
       int idx = threadIdx.x + 256 * r;
       int nn = idx >> 5, ii = idx & 31;
       int gn = n0 + nn, gi = i0 + ii;
-      Cs[nn][ii] = (gn < nao && gi < nocc) ? C[(size_t)gn * nocc + gi] : 0.0;
+      Cs[nn][ii] = (gn < nao && gi < nocc) ? C[DF_IX((size_t)gn * nocc + gi, (size_t)nao * nocc)] : 0.0;
     }
     __syncthreads();
 #pragma unroll
@@ -230,7 +395,7 @@ __global__ void __launch_bounds__(256) k_halftransform_fp64_kernel(const double*
 #pragma unroll
     for (int v = 0; v < 2; ++v) {
       int gi = i0 + tx + 16 * v;
-      if (gi < nocc) X[((size_t)gm * naux + P) * nocc + gi] = acc[u][v];
+      if (gi < nocc) X[DF_IX(((size_t)gm * naux + P) * nocc + gi, (size_t)nao * naux * nocc)] = acc[u][v];
     }
   }
 }
@@ -242,7 +407,7 @@ __global__ void ksum_mirror_kernel(const double* __restrict__ Kpart, int nsplit,
   int m = (int)(e / nao), n = (int)(e % nao);
   if (n > m) return;
   double s = 0.0;
-  for (int k = 0; k < nsplit; ++k) s += Kpart[(size_t)k * nao * nao + e];
+  for (int k = 0; k < nsplit; ++k) s += Kpart[DF_IX((size_t)k * nao * nao + e, (size_t)nsplit * nao * nao)];
   K[(size_t)m * nao + n] = s;
   K[(size_t)n * nao + m] = s;
 }
@@ -290,18 +455,45 @@ int build_J(const void* Bbuf, const BLayout& L, int nao, int naux, int precision
   unsigned g = (unsigned)((ld + 255) / 256);
   unsigned gp = (unsigned)((npair + 255) / 256);
   (void)precision;  // J streams the FP64 rows in both modes
-  weighted_packed_density_kernel<<<g, 256, 0, s>>>(D, nao, npair, ld, w.Dw);
-  DF_LAUNCHED("weighted_packed_density_kernel");
-  {
-    ProfScope ps("j_pass1_fp64", s);
-    jpass1_fp64_kernel<<<naux, 512, 0, s>>>((const double*)(base + L.off64), ld, w.Dw, w.d);
-    DF_LAUNCHED("jpass1_fp64_kernel");
-  }
-  {
-    ProfScope ps("j_pass2_fp64", s);
-    dim3 grid2((unsigned)((ld / 2 + 255) / 256), (unsigned)w.nsplit_j);
-    jpass2_fp64_kernel<<<grid2, 256, 0, s>>>((const double*)(base + L.off64), ld, naux, rows, w.d, w.Jpart);
-    DF_LAUNCHED("jpass2_fp64_kernel");
+  const double* B64 = (const double*)(base + L.off64);
+  const dim3 grid2((unsigned)((ld / 2 + 255) / 256), (unsigned)w.nsplit_j);
+  if (knob("j_fp64_fma") == 0) {
+    // double-float passes (the Dw buffer holds ld float pairs: the same bytes as ld doubles)
+    weighted_packed_density_df_kernel<<<g, 256, 0, s>>>(D, nao, npair, ld, (float2*)w.Dw);
+    DF_LAUNCHED("weighted_packed_density_df_kernel");
+    {
+      ProfScope ps("j_pass1", s);
+      // rows per CTA: each density load from L2 serves R rows of B (knob "jpass1_rows")
+      const int R = knob("jpass1_rows");
+      const float4* Dw4 = (const float4*)w.Dw;
+      if (R >= 8)
+        jpass1_df_kernel<8, 512><<<(unsigned)((naux + 7) / 8), 512, 0, s>>>(B64, ld, naux, Dw4, w.d);
+      else if (R >= 4)
+        jpass1_df_kernel<4, 256><<<(unsigned)((naux + 3) / 4), 256, 0, s>>>(B64, ld, naux, Dw4, w.d);
+      else if (R >= 2)
+        jpass1_df_kernel<2, 256><<<(unsigned)((naux + 1) / 2), 256, 0, s>>>(B64, ld, naux, Dw4, w.d);
+      else
+        jpass1_df_kernel<1, 512><<<(unsigned)naux, 512, 0, s>>>(B64, ld, naux, Dw4, w.d);
+      DF_LAUNCHED("jpass1_df_kernel");
+    }
+    {
+      ProfScope ps("j_pass2", s);
+      jpass2_df_kernel<<<grid2, 256, 0, s>>>(B64, ld, naux, rows, w.d, w.Jpart);
+      DF_LAUNCHED("jpass2_df_kernel");
+    }
+  } else {
+    weighted_packed_density_kernel<<<g, 256, 0, s>>>(D, nao, npair, ld, w.Dw);
+    DF_LAUNCHED("weighted_packed_density_kernel");
+    {
+      ProfScope ps("j_pass1", s);
+      jpass1_fp64_kernel<<<naux, 512, 0, s>>>(B64, ld, w.Dw, w.d);
+      DF_LAUNCHED("jpass1_fp64_kernel");
+    }
+    {
+      ProfScope ps("j_pass2", s);
+      jpass2_fp64_kernel<<<grid2, 256, 0, s>>>(B64, ld, naux, rows, w.d, w.Jpart);
+      DF_LAUNCHED("jpass2_fp64_kernel");
+    }
   }
   jreduce_unpack_kernel<<<gp, 256, 0, s>>>(w.Jpart, w.nsplit_j, ld, nao, J);
   DF_LAUNCHED("jreduce_unpack_kernel");
@@ -447,3 +639,5 @@ extern "C" int df_jk(const void* B, int nao, int naux, int precision, const doub
   }
   return DF_OK;
 }
+
+DF_BOUNDS_READER(bounds_read_jk)

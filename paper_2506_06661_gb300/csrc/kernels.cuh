@@ -11,9 +11,13 @@ namespace dfscf {
 // ---- integrals (integrals.cu) ------------------------------------------------------
 int launch_int1e(const double* ao_xyz, const double* ao_exp, int nao, const double* nuc_xyz, const double* nuc_z,
                  int natm, double* S, double* T, double* V, cudaStream_t s);
-int launch_int2c(const double* xyz, const double* ex, int naux, double* M, cudaStream_t s);
+// Per packed orbital pair: exponent p, centre (x, y, z) and factor K_ab = N_a N_b e^{-mu R^2}
+// 2 pi^{5/2} / p, as five arrays of npair doubles in pair_tab.
+int launch_pair_table(const double* ao_xyz, const double* ao_exp, int nao, double* pair_tab, cudaStream_t s);
+// omega > 0: the long-range operator erf(omega r)/r instead of 1/r (LRDF)
+int launch_int2c(const double* xyz, const double* ex, int naux, double* M, cudaStream_t s, double omega = 0.0);
 int launch_int3c(const double* ao_xyz, const double* ao_exp, int nao, const double* aux_xyz, const double* aux_exp,
-                 int naux, double* R, long ld, double* pair_tab, cudaStream_t s);
+                 int naux, double* R, long ld, double* pair_tab, cudaStream_t s, double omega = 0.0);
 int launch_enuc(const double* xyz, const double* z, int natm, double* out, cudaStream_t s);
 
 // ---- FP64 linear algebra (linalg.cu) -----------------------------------------------
@@ -90,5 +94,18 @@ int run_jk(const void* B, int nao, int naux, int precision, const double* D, con
            double* K, const JKWork& w, cudaStream_t s);
 int build_B(const double* ao_xyz, const double* ao_exp, int nao, const double* aux_xyz, const double* aux_exp,
             int naux, const double* Lfac, int precision, void* Bbuf, double* pair_tab, cudaStream_t s);
+
+// Bounds-check records of the translation units with kernels (checking build; all zero
+// otherwise).
+int bounds_read_dferr(BoundsRecord*);
+int bounds_read_eig(BoundsRecord*);
+int bounds_read_integrals(BoundsRecord*);
+int bounds_read_jk(BoundsRecord*);
+int bounds_read_linalg(BoundsRecord*);
+int bounds_read_lowdin(BoundsRecord*);
+int bounds_read_lrdf(BoundsRecord*);
+int bounds_read_mlp(BoundsRecord*);
+int bounds_read_scf(BoundsRecord*);
+int bounds_read_umma(BoundsRecord*);
 
 }  // namespace dfscf

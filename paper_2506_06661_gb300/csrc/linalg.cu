@@ -304,3 +304,5 @@ extern "C" int df_metric_chol(const double* aux_xyz, const double* aux_exp, int 
   }
   return DF_OK;
 }
+
+DF_BOUNDS_READER(bounds_read_linalg)

@@ -85,3 +85,5 @@ extern "C" int df_congruence(const double* M, const double* A, int n, double* ou
   DF_TRY(dgemm(false, false, n, n, n, 1.0, M, n, 0, T, n, 0, 0.0, out, n, 0, 1, s, 0, 0));
   return DF_OK;
 }
+
+DF_BOUNDS_READER(bounds_read_lowdin)

@@ -648,3 +648,5 @@ extern "C" int guess_mlp_load(const void* blob, size_t blob_bytes, float* params
   if (step) *step = h.has_moments ? h.step : 0;
   return DF_OK;
 }
+
+DF_BOUNDS_READER(bounds_read_mlp)

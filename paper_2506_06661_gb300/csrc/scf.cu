@@ -18,6 +18,7 @@
 // decomposition dm0 = sum_k n_k u_k u_k^T as K[C+] - K[C-] in an eager first iteration.
 #include <algorithm>
 #include <chrono>
+#include <cstdint>
 #include <cmath>
 #include <cstring>
 #include <thread>
@@ -149,8 +150,8 @@ __global__ void diis_store_kernel(const DiisState* __restrict__ d, const double*
   long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
   int slot = d->slot;
   if (i < ne) {
-    Fh[(size_t)slot * nn + i] = F[i];
-    Eh[(size_t)slot * nn + i] = E[i];
+    Fh[DF_IX((size_t)slot * nn + i, (size_t)DIIS_MAX * nn)] = F[i];
+    Eh[DF_IX((size_t)slot * nn + i, (size_t)DIIS_MAX * nn)] = E[i];
   }
 }
 
@@ -253,7 +254,7 @@ __global__ void diis_combine_kernel(const DiisState* __restrict__ d, const doubl
   if (i >= ne) return;
   double s = 0.0;
   for (int k = 0; k < d->space; ++k)
-    if (d->valid[k]) s += coef[k] * Fh[(size_t)k * nn + i];
+    if (d->valid[k]) s += coef[k] * Fh[DF_IX((size_t)k * nn + i, (size_t)DIIS_MAX * nn)];
   out[i] = s;
 }
 
@@ -344,7 +345,7 @@ __global__ void principal_pairs_kernel(const double* __restrict__ A, const doubl
   const int j = blockIdx.x;
   double aa = 0.0, bb = 0.0;
   for (int i = threadIdx.x; i < nmo; i += blockDim.x) {
-    const double a = A[(size_t)i * k + j], b = B[(size_t)i * k + j];
+    const double a = A[DF_IX((size_t)i * k + j, (size_t)nmo * k)], b = B[DF_IX((size_t)i * k + j, (size_t)nmo * k)];
     aa += a * a;
     bb += b * b;
   }
@@ -366,8 +367,8 @@ __global__ void principal_pairs_kernel(const double* __restrict__ A, const doubl
   for (int i = threadIdx.x; i < nmo; i += blockDim.x) {
     const double a = A[(size_t)i * k + j] * ia, b = B[(size_t)i * k + j] * ib;
     const double pv = (b + a) * inp, mv = (b - a) * inm;
-    Up[(size_t)i * k + j] = f * (pv + mv);
-    Um[(size_t)i * k + j] = f * (pv - mv);
+    Up[DF_IX((size_t)i * k + j, (size_t)nmo * k)] = f * (pv + mv);
+    Um[DF_IX((size_t)i * k + j, (size_t)nmo * k)] = f * (pv - mv);
   }
   if (threadIdx.x == 0) sv[j] = sj;
 }
@@ -392,6 +393,195 @@ __global__ void inc_status_kernel(const double* __restrict__ c2, int k, const in
     st->inc_ssum = t;
     st->inc_fail = *eig_status;
   }
+}
+
+// ---- second-order SCF (Newton steps on the orbital rotation) ----------------------------
+// The paper's SOSCF section: after DIIS has stalled, an exact-gradient Newton solver with an
+// approximate orbital Hessian converges where DIIS oscillates.  Closed-shell form in the
+// orthonormal basis of X, with the full orbital set C' = [C'_o, C'_v] and the Fock matrix
+// F_mo = C'^T F' C': gradient F_vo (the energy gradient divided by 4), Hessian product
+//   (H v)_ai = (F_vv v - v F_oo)_ai + (C_v^T dF[v] C_o)_ai,  dF = J[dD] - 1/2 K[dD],
+//   dD = 2 (L R^T + R L^T),  L = X C'_v v,  R = X C'_o = C_occ,
+// solved for H kappa = -F_vo by preconditioned conjugate gradients (diagonal
+// F_aa - F_ii, floored at 0.05) from kappa = 0 with device-side scalars, truncated as in
+// Steihaug's method at a trust radius |kappa| <= 0.5 or at non-positive curvature (near a
+// saddle point the step then follows the downhill direction).  K[dD] comes from
+// two ordinary exchange builds: F+- = L/t +- t R, F+ F+^T - F- F-^T = 2 (L R^T + R L^T), with
+// t = (|L| / |R|)^(1/2) so that both factors are of the size of the change.  The step is
+// capped at 0.3 rad per element, and the orbitals rotate exactly by exp([[0, -k^T], [k, 0]]):
+// with k^T k = V diag(s^2) V^T,
+//   C'_o <- C'_o V cos(s) V^T + C'_v k V sinc(s) V^T,
+//   C'_v <- C'_v (1 + k V ((cos(s) - 1)/s^2) V^T k^T) - C'_o V sinc(s) V^T k^T.
+
+// g = F_vo and the preconditioner h_ai = max(F_aa - F_ii, 0.05), both [nvir][nocc].
+__global__ void soscf_grad_kernel(const double* __restrict__ Fmo, int nmo, int nocc, double* __restrict__ g,
+                                  double* __restrict__ h) {
+  const long q = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int nvir = nmo - nocc;
+  if (q >= (long)nvir * nocc) return;
+  const int a = (int)(q / nocc), i = (int)(q % nocc);
+  g[q] = Fmo[DF_IX((size_t)(nocc + a) * nmo + i, (size_t)nmo * nmo)];
+  h[q] = fmax(Fmo[DF_IX((size_t)(nocc + a) * nmo + nocc + a, (size_t)nmo * nmo)] -
+                  Fmo[DF_IX((size_t)i * nmo + i, (size_t)nmo * nmo)], 0.05);
+}
+
+// *out = <a, b> over n entries (one CTA).
+__global__ void dot_kernel(const double* __restrict__ a, const double* __restrict__ b, long n,
+                           double* __restrict__ out) {
+  __shared__ double sh[32];
+  double t = 0.0;
+  for (long i = threadIdx.x; i < n; i += blockDim.x) t += a[i] * b[i];
+  t = block_sum(t, sh);
+  if (threadIdx.x == 0) *out = t;
+}
+
+// CG start from x = 0: r = -g, z = r / h, p = z.
+__global__ void cg_start_kernel(double* __restrict__ x, double* __restrict__ r, double* __restrict__ z,
+                                double* __restrict__ p, const double* __restrict__ g, const double* __restrict__ h,
+                                long n) {
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  x[i] = 0.0;
+  r[i] = -g[i];
+  z[i] = -g[i] / h[i];
+  p[i] = z[i];
+}
+
+// Steihaug's truncated CG inside the trust region |x| <= Delta (2-norm): the step length is
+// alpha = rz / pAp, unless the curvature along p is not positive or the step would leave the
+// region; then x moves along p to the boundary and the iteration stops (later steps add
+// nothing).  sc: [0] rz, [1] pAp, [6] x.x, [7] x.p, [8] p.p, [9] stopped, [10] Delta,
+// [11] the step length used.
+__global__ void cg_decide_kernel(double* __restrict__ sc) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  if (sc[9] != 0.0) {
+    sc[11] = 0.0;
+    return;
+  }
+  const double rz = sc[0], pAp = sc[1], xx = sc[6], xp = sc[7], pp = sc[8], D = sc[10];
+  const double alpha = pAp > 0.0 ? rz / pAp : 0.0;
+  if (pAp > 0.0 && xx + 2.0 * alpha * xp + alpha * alpha * pp <= D * D) {
+    sc[11] = alpha;
+    return;
+  }
+  // boundary: |x + tau p| = Delta, tau >= 0
+  double tau = 0.0;
+  if (pp > 0.0) tau = (-xp + sqrt(fmax(xp * xp - pp * (xx - D * D), 0.0))) / pp;
+  sc[11] = tau;
+  sc[9] = 1.0;
+}
+
+// x += a p; r -= a Ap; z = r / h with a = sc[11].
+__global__ void cg_step_kernel(double* __restrict__ x, double* __restrict__ r, double* __restrict__ z,
+                               const double* __restrict__ p, const double* __restrict__ Ap,
+                               const double* __restrict__ h, long n, const double* __restrict__ sc) {
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double alpha = sc[11];
+  x[i] += alpha * p[i];
+  const double ri = r[i] - alpha * Ap[i];
+  r[i] = ri;
+  z[i] = ri / h[i];
+}
+
+// Start of a Newton step's CG: not stopped, trust radius Delta.
+__global__ void cg_reset_kernel(double* __restrict__ sc, double Delta) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  sc[9] = 0.0;
+  sc[10] = Delta;
+}
+
+// p = z + beta p, beta = rz_new / rz (sc[2] / sc[0]).
+__global__ void cg_dir_kernel(double* __restrict__ p, const double* __restrict__ z, long n,
+                              const double* __restrict__ sc) {
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double beta = sc[0] > 0.0 ? sc[2] / sc[0] : 0.0;
+  p[i] = z[i] + beta * p[i];
+}
+
+__global__ void copy_scalar_kernel(double* __restrict__ dst, const double* __restrict__ src) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) *dst = *src;
+}
+
+// F+- = L / t +- t R with t = (|L|^2 / |R|^2)^(1/4) (sc[3] = |L|^2, sc[4] = |R|^2).
+__global__ void pm_factors_kernel(const double* __restrict__ L, const double* __restrict__ R, long n,
+                                  const double* __restrict__ sc, double* __restrict__ Fp, double* __restrict__ Fm) {
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double t = (sc[3] > 0.0 && sc[4] > 0.0) ? sqrt(sqrt(sc[3] / sc[4])) : 1.0;
+  const double a = L[i] / t, b = t * R[i];
+  Fp[i] = a + b;
+  Fm[i] = a - b;
+}
+
+// out = 2 (T + T^T) for n x n T.
+__global__ void sym2_kernel(const double* __restrict__ T, int n, double* __restrict__ out) {
+  const long q = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= (long)n * n) return;
+  const int i = (int)(q / n), j = (int)(q % n);
+  out[q] = 2.0 * (T[q] + T[(size_t)j * n + i]);
+}
+
+// dF = dJ - 1/2 (dK+ - dK-), in place of dJ.
+__global__ void response_fock_kernel(double* __restrict__ dJ, const double* __restrict__ dKp,
+                                     const double* __restrict__ dKm, long n) {
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dJ[i] -= 0.5 * (dKp[i] - dKm[i]);
+}
+
+// Cap the step: x *= cap / max|x| when max|x| (sc[5]) exceeds cap.
+__global__ void cap_step_kernel(double* __restrict__ x, long n, const double* __restrict__ sc, double cap) {
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n && sc[5] > cap) x[i] *= cap / sc[5];
+}
+
+// Pc = V cos(s) V^T, Ps = V sinc(s) V^T, Pd = V ((cos(s) - 1)/s^2) V^T from the eigenvector
+// rows Vrow [k][k] and eigenvalues s^2 of k^T k (series below s = 1e-4).
+__global__ void rotation_mats_kernel(const double* __restrict__ Vrow, const double* __restrict__ s2, int k,
+                                     double* __restrict__ Pc, double* __restrict__ Ps, double* __restrict__ Pd) {
+  const long q = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= (long)k * k) return;
+  const int a = (int)(q / k), b = (int)(q % k);
+  double c = 0.0, sn = 0.0, d = 0.0;
+  for (int j = 0; j < k; ++j) {
+    const double sq = fmax(s2[j], 0.0), sg = sqrt(sq);
+    double fc, fs, fd;
+    if (sg < 1e-4) {
+      fc = 1.0 - 0.5 * sq;
+      fs = 1.0 - sq / 6.0;
+      fd = -0.5 + sq / 24.0;
+    } else {
+      fc = cos(sg);
+      fs = sin(sg) / sg;
+      fd = (fc - 1.0) / sq;
+    }
+    const double vv = Vrow[DF_IX((size_t)j * k + a, (size_t)k * k)] * Vrow[DF_IX((size_t)j * k + b, (size_t)k * k)];
+    c += vv * fc;
+    sn += vv * fs;
+    d += vv * fd;
+  }
+  Pc[q] = c;
+  Ps[q] = sn;
+  Pd[q] = d;
+}
+
+__global__ void add_identity_kernel(double* __restrict__ A, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) A[(size_t)i * n + i] += 1.0;
+}
+
+// HOMO / LUMO estimates (diagonal of F_mo) and statuses after a Newton step.
+__global__ void soscf_status_kernel(const double* __restrict__ Fmo, int nmo, int nocc, const int* k_status,
+                                    const int* tc_err, ScfStatus* st) {
+  if (threadIdx.x != 0) return;
+  double homo = -INFINITY, lumo = INFINITY;
+  for (int i = 0; i < nocc; ++i) homo = fmax(homo, Fmo[(size_t)i * nmo + i]);
+  for (int a = nocc; a < nmo; ++a) lumo = fmin(lumo, Fmo[(size_t)a * nmo + a]);
+  st->homo = homo;
+  st->lumo = nocc < nmo ? lumo : 0.0;
+  st->eig_fail = *k_status;
+  st->tc_timeout = tc_err ? *tc_err : 0;
 }
 
 static unsigned blocks_for(long n, int t = 256) { return (unsigned)((n + t - 1) / t); }
@@ -568,6 +758,14 @@ struct ScfMol {
   // then n_fp64_final FP64 iterations.  A base is rebuilt when the occupied space turned by
   // more than 60 degrees in one step or the updates stall.
   bool inc = false;
+  // Second-order steps (knob "soscf"): once the DIIS error has not improved by 10% for 12
+  // iterations with an accurate Fock matrix, every later iteration takes a Newton step
+  // instead of the DIIS extrapolation and diagonalisation.
+  bool soscf_on = false;      // enabled for this molecule (F' is kept for the switch)
+  bool soscf = false;         // Newton steps active
+  bool soscf_pending = false; // switch before the next launch
+  double d_best = INFINITY;
+  int d_stall = 0;
   enum KPhase { KP_FULL, KP_BASE, KP_INCR, KP_FINAL } kp = KP_FULL;
   int rebases = 0;
   double inc_best = INFINITY;
@@ -679,6 +877,7 @@ static int finish_guess(ScfMol& M, bool use_dm0, bool orbitals) {
   diis_reset_kernel<<<1, 32, 0, M.s>>>(W.diis, M.opt.diis_space);
   DF_LAUNCHED("diis_reset_kernel");
   M.inc = M.opt.precision == DF_MIXED && knob("mixed_incremental") != 0;
+  M.soscf_on = knob("soscf") != 0 && M.nocc < M.nmo;
   if (M.inc) DF_CUDA(cudaMemsetAsync(W.Cbase, 0, sizeof(double) * (size_t)M.nmo * M.nocc, M.s));
   M.first_dm0 = use_dm0;
   M.prec = M.opt.precision;
@@ -797,6 +996,156 @@ static int dm0_finish(ScfMol& M) {
   return DF_OK;
 }
 
+// Principal angles between the occupied space of the accumulated K (C'_base) and the new
+// one (C'): M = C'_base^T C', eigen-decomposition of M^T M on one CTA, summary into the status.
+static int incremental_prep(ScfMol& M) {
+  ScfWork& W = M.W;
+  cudaStream_t s = M.s;
+  const int nmo = M.nmo, nocc = M.nocc;
+  ProfScope ps_inc("scf_incremental_prep", s);
+  DF_TRY(dgemm(true, false, nocc, nocc, nmo, 1.0, W.Cbase, nocc, 0, W.Cp, nocc, 0, 0.0, W.Minc, nocc, 0, 1, s, 0, 0));
+  DF_TRY(dgemm(true, false, nocc, nocc, nocc, 1.0, W.Minc, nocc, 0, W.Minc, nocc, 0, 0.0, W.Tinc, nocc, 0, 1, s, 0, 0));
+  DF_TRY(eigh_rows(W.Tinc, nocc, W.cinc, W.Winc, W.eig_scratch, W.inc_status, s));
+  inc_status_kernel<<<1, 256, 0, s>>>(W.cinc, nocc, W.inc_status, W.st);
+  DF_LAUNCHED("inc_status_kernel");
+  return DF_OK;
+}
+
+// C_occ = X C'_o, D = 2 C_occ C_occ^T from the occupied columns of C'_all.
+static int occupied_from_all(ScfMol& M) {
+  ScfWork& W = M.W;
+  cudaStream_t s = M.s;
+  const int nao = M.nao, nmo = M.nmo, nocc = M.nocc;
+  DF_CUDA(cudaMemcpy2DAsync(W.Cp, sizeof(double) * nocc, W.Call, sizeof(double) * nmo, sizeof(double) * nocc, nmo,
+                            cudaMemcpyDeviceToDevice, s));
+  DF_TRY(dgemm(false, false, nao, nocc, nmo, 1.0, W.X, nmo, 0, W.Cp, nocc, 0, 0.0, W.Cocc, nocc, 0, 1, s, 0, 0));
+  DF_TRY(dgemm(false, true, nao, nao, nocc, 2.0, W.Cocc, nocc, 0, W.Cocc, nocc, 0, 0.0, W.D, nao, 0, 1, s, 0, 0));
+  return DF_OK;
+}
+
+// Switch to Newton steps: the full orbital set from the extrapolated F' that produced the
+// current occupied orbitals (kept in Fbar by the last DIIS step), so that the occupied
+// space is unchanged.
+static int soscf_init(ScfMol& M) {
+  ScfWork& W = M.W;
+  cudaStream_t s = M.s;
+  const int nmo = M.nmo;
+  const long ne = (long)nmo * nmo;
+  DF_CUDA(cudaMemcpyAsync(W.Fp, W.Fbar, sizeof(double) * ne, cudaMemcpyDeviceToDevice, s));
+  DF_TRY(eigh_full_rows(W.Fp, nmo, W.eps, W.ZT, W.eig_scratch, W.eig_status, s, W.eig_aux));
+  DF_TRY(transpose(W.ZT, nmo, nmo, W.Call, s));
+  DF_TRY(occupied_from_all(M));
+  if (M.inc) DF_TRY(incremental_prep(M));
+  return DF_OK;
+}
+
+// Av = H v for v [nvir][nocc] (see the head of the Newton-step kernels).
+static int soscf_hessian(ScfMol& M, const double* v, double* Av, int hprec) {
+  ScfWork& W = M.W;
+  cudaStream_t s = M.s;
+  const int nao = M.nao, nmo = M.nmo, nocc = M.nocc, nvir = nmo - nocc;
+  const long nn = (long)nao * nao, no = (long)nao * nocc;
+  DF_TRY(dgemm(false, false, nvir, nocc, nvir, 1.0, W.Fmo + (size_t)nocc * nmo + nocc, nmo, 0, v, nocc, 0, 0.0, Av,
+               nocc, 0, 1, s, 0, 0));
+  DF_TRY(dgemm(false, false, nvir, nocc, nocc, -1.0, v, nocc, 0, W.Fmo, nmo, 0, 1.0, Av, nocc, 0, 1, s, 0, 0));
+  // L = X C'_v v, dD = 2 (L R^T + R L^T)
+  DF_TRY(dgemm(false, false, nao, nocc, nvir, 1.0, W.Lv, nvir, 0, v, nocc, 0, 0.0, W.Lf, nocc, 0, 1, s, 0, 0));
+  DF_TRY(dgemm(false, true, nao, nao, nocc, 1.0, W.Lf, nocc, 0, W.Cocc, nocc, 0, 0.0, W.dK1, nao, 0, 1, s, 0, 0));
+  sym2_kernel<<<blocks_for(nn), 256, 0, s>>>(W.dK1, nao, W.dD);
+  DF_LAUNCHED("sym2_kernel");
+  DF_TRY(run_jk(W.B, nao, M.naux, hprec, W.dD, nullptr, 0, W.dJ, nullptr, W.jk, s));
+  dot_kernel<<<1, 1024, 0, s>>>(W.Lf, W.Lf, no, W.cg_s + 3);
+  DF_LAUNCHED("dot_kernel");
+  dot_kernel<<<1, 1024, 0, s>>>(W.Cocc, W.Cocc, no, W.cg_s + 4);
+  DF_LAUNCHED("dot_kernel");
+  pm_factors_kernel<<<blocks_for(no), 256, 0, s>>>(W.Lf, W.Cocc, no, W.cg_s, W.Lfp, W.Lfm);
+  DF_LAUNCHED("pm_factors_kernel");
+  DF_TRY(run_jk(W.B, nao, M.naux, hprec, nullptr, W.Lfp, nocc, nullptr, W.dK1, W.jk, s));
+  DF_TRY(run_jk(W.B, nao, M.naux, hprec, nullptr, W.Lfm, nocc, nullptr, W.dK2, W.jk, s));
+  response_fock_kernel<<<blocks_for(nn), 256, 0, s>>>(W.dJ, W.dK1, W.dK2, nn);
+  DF_LAUNCHED("response_fock_kernel");
+  // Av += (X C'_v)^T dF C_occ
+  DF_TRY(dgemm(false, false, nao, nocc, nao, 1.0, W.dJ, nao, 0, W.Cocc, nocc, 0, 0.0, W.Lf, nocc, 0, 1, s, 0, 0));
+  DF_TRY(dgemm(true, false, nvir, nocc, nao, 1.0, W.Lv, nvir, 0, W.Lf, nocc, 0, 1.0, Av, nocc, 0, 1, s, 0, 0));
+  return DF_OK;
+}
+
+// One Newton step from the Fock matrix F' (W.Fo) of the current orbitals C'_all: CG on
+// H kappa = -F_vo, capped step, exact rotation of C'_all, new C_occ and D.
+static int soscf_step(ScfMol& M) {
+  ScfWork& W = M.W;
+  cudaStream_t s = M.s;
+  const int nao = M.nao, nmo = M.nmo, nocc = M.nocc, nvir = nmo - nocc;
+  const long ne = (long)nmo * nmo, nvo = (long)nvir * nocc;
+  const int hprec = M.opt.precision;  // the approximate Hessian uses the mixed exchange when B has its planes
+  ProfScope ps("scf_newton_step", s);
+  DF_TRY(dgemm(false, false, nmo, nmo, nmo, 1.0, W.Fo, nmo, 0, W.Call, nmo, 0, 0.0, W.T1, nmo, 0, 1, s, 0, 0));
+  DF_TRY(dgemm(true, false, nmo, nmo, nmo, 1.0, W.Call, nmo, 0, W.T1, nmo, 0, 0.0, W.Fmo, nmo, 0, 1, s, 0, 0));
+  soscf_grad_kernel<<<blocks_for(nvo), 256, 0, s>>>(W.Fmo, nmo, nocc, W.cg_g, W.cg_h);
+  DF_LAUNCHED("soscf_grad_kernel");
+  DF_TRY(dgemm(false, false, nao, nvir, nmo, 1.0, W.X, nmo, 0, W.Call + nocc, nmo, 0, 0.0, W.Lv, nvir, 0, 1, s, 0, 0));
+  cg_start_kernel<<<blocks_for(nvo), 256, 0, s>>>(W.cg_x, W.cg_r, W.cg_z, W.cg_p, W.cg_g, W.cg_h, nvo);
+  DF_LAUNCHED("cg_start_kernel");
+  cg_reset_kernel<<<1, 32, 0, s>>>(W.cg_s, 0.5);
+  DF_LAUNCHED("cg_reset_kernel");
+  dot_kernel<<<1, 1024, 0, s>>>(W.cg_r, W.cg_z, nvo, W.cg_s + 0);
+  DF_LAUNCHED("dot_kernel");
+  const int ncg = std::max(1, knob("soscf_cg"));
+  for (int it = 0; it < ncg; ++it) {
+    DF_TRY(soscf_hessian(M, W.cg_p, W.cg_Ap, hprec));
+    dot_kernel<<<1, 1024, 0, s>>>(W.cg_p, W.cg_Ap, nvo, W.cg_s + 1);
+    DF_LAUNCHED("dot_kernel");
+    dot_kernel<<<1, 1024, 0, s>>>(W.cg_x, W.cg_x, nvo, W.cg_s + 6);
+    DF_LAUNCHED("dot_kernel");
+    dot_kernel<<<1, 1024, 0, s>>>(W.cg_x, W.cg_p, nvo, W.cg_s + 7);
+    DF_LAUNCHED("dot_kernel");
+    dot_kernel<<<1, 1024, 0, s>>>(W.cg_p, W.cg_p, nvo, W.cg_s + 8);
+    DF_LAUNCHED("dot_kernel");
+    cg_decide_kernel<<<1, 32, 0, s>>>(W.cg_s);
+    DF_LAUNCHED("cg_decide_kernel");
+    cg_step_kernel<<<blocks_for(nvo), 256, 0, s>>>(W.cg_x, W.cg_r, W.cg_z, W.cg_p, W.cg_Ap, W.cg_h, nvo, W.cg_s);
+    DF_LAUNCHED("cg_step_kernel");
+    if (it + 1 == ncg) break;
+    dot_kernel<<<1, 1024, 0, s>>>(W.cg_r, W.cg_z, nvo, W.cg_s + 2);
+    DF_LAUNCHED("dot_kernel");
+    cg_dir_kernel<<<blocks_for(nvo), 256, 0, s>>>(W.cg_p, W.cg_z, nvo, W.cg_s);
+    DF_LAUNCHED("cg_dir_kernel");
+    copy_scalar_kernel<<<1, 32, 0, s>>>(W.cg_s + 0, W.cg_s + 2);
+    DF_LAUNCHED("copy_scalar_kernel");
+  }
+  absmax_kernel<<<1, 1024, 0, s>>>(W.cg_x, nvo, W.cg_s + 5);
+  DF_LAUNCHED("absmax_kernel");
+  cap_step_kernel<<<blocks_for(nvo), 256, 0, s>>>(W.cg_x, nvo, W.cg_s, 0.3);
+  DF_LAUNCHED("cap_step_kernel");
+  // exact rotation by exp(kappa)
+  DF_TRY(dgemm(true, false, nocc, nocc, nvir, 1.0, W.cg_x, nocc, 0, W.cg_x, nocc, 0, 0.0, W.kk, nocc, 0, 1, s, 0, 0));
+  DF_TRY(eigh_rows(W.kk, nocc, W.ksig, W.kVrow, W.eig_scratch, W.k_status, s));
+  rotation_mats_kernel<<<blocks_for((long)nocc * nocc), 256, 0, s>>>(W.kVrow, W.ksig, nocc, W.Pc, W.Ps, W.Pd);
+  DF_LAUNCHED("rotation_mats_kernel");
+  // occupied: C'_o Pc + C'_v (k Ps)
+  DF_TRY(dgemm(false, false, nvir, nocc, nocc, 1.0, W.cg_x, nocc, 0, W.Ps, nocc, 0, 0.0, W.ktmp, nocc, 0, 1, s, 0, 0));
+  DF_TRY(dgemm(false, false, nmo, nocc, nocc, 1.0, W.Call, nmo, 0, W.Pc, nocc, 0, 0.0, W.Call2, nmo, 0, 1, s, 0, 0));
+  DF_TRY(dgemm(false, false, nmo, nocc, nvir, 1.0, W.Call + nocc, nmo, 0, W.ktmp, nocc, 0, 1.0, W.Call2, nmo, 0, 1, s,
+               0, 0));
+  // virtual: C'_v (1 + k Pd k^T) - C'_o (Ps k^T)
+  if (nvir > 0) {
+    DF_TRY(dgemm(false, false, nvir, nocc, nocc, 1.0, W.cg_x, nocc, 0, W.Pd, nocc, 0, 0.0, W.ktmp, nocc, 0, 1, s, 0,
+                 0));
+    DF_TRY(dgemm(false, true, nvir, nvir, nocc, 1.0, W.ktmp, nocc, 0, W.cg_x, nocc, 0, 0.0, W.KPdK, nvir, 0, 1, s, 0,
+                 0));
+    add_identity_kernel<<<blocks_for(nvir), 256, 0, s>>>(W.KPdK, nvir);
+    DF_LAUNCHED("add_identity_kernel");
+    DF_TRY(dgemm(false, false, nmo, nvir, nvir, 1.0, W.Call + nocc, nmo, 0, W.KPdK, nvir, 0, 0.0, W.Call2 + nocc, nmo,
+                 0, 1, s, 0, 0));
+    DF_TRY(dgemm(false, true, nocc, nvir, nocc, 1.0, W.Ps, nocc, 0, W.cg_x, nocc, 0, 0.0, W.ktmp, nvir, 0, 1, s, 0,
+                 0));
+    DF_TRY(dgemm(false, false, nmo, nvir, nocc, -1.0, W.Call, nmo, 0, W.ktmp, nvir, 0, 1.0, W.Call2 + nocc, nmo, 0, 1,
+                 s, 0, 0));
+  }
+  DF_CUDA(cudaMemcpyAsync(W.Call, W.Call2, sizeof(double) * ne, cudaMemcpyDeviceToDevice, s));
+  return occupied_from_all(M);
+}
+
 // Everything after J and K: Fock, energy, DIIS error and extrapolation, diagonalisation,
 // status readback.  No host decisions: capturable.
 static int iteration_tail(ScfMol& M, int prec) {
@@ -844,21 +1193,37 @@ static int iteration_tail(ScfMol& M, int prec) {
   DF_LAUNCHED("diis_solve_kernel");
   diis_combine_kernel<<<blocks_for(ne), 256, 0, s>>>(W.diis, W.Fhist, nn, ne, W.coef, W.Fp);
   DF_LAUNCHED("diis_combine_kernel");
+  if (M.soscf_on) DF_CUDA(cudaMemcpyAsync(W.Fbar, W.Fp, sizeof(double) * ne, cudaMemcpyDeviceToDevice, s));
   DF_TRY(diagonalize_orth(nao, nmo, nocc, W, s));
-  if (M.inc) {
-    // principal angles between the occupied space of the accumulated K (C'_base) and the
-    // new one (C'): M = C'_base^T C', eigen-decomposition of M^T M on one CTA
-    ProfScope ps_inc("scf_incremental_prep", s);
-    DF_TRY(dgemm(true, false, nocc, nocc, nmo, 1.0, W.Cbase, nocc, 0, W.Cp, nocc, 0, 0.0, W.Minc, nocc, 0, 1, s, 0, 0));
-    DF_TRY(dgemm(true, false, nocc, nocc, nocc, 1.0, W.Minc, nocc, 0, W.Minc, nocc, 0, 0.0, W.Tinc, nocc, 0, 1, s, 0,
-                 0));
-    DF_TRY(eigh_rows(W.Tinc, nocc, W.cinc, W.Winc, W.eig_scratch, W.inc_status, s));
-    inc_status_kernel<<<1, 256, 0, s>>>(W.cinc, nocc, W.inc_status, W.st);
-    DF_LAUNCHED("inc_status_kernel");
-  }
+  if (M.inc) DF_TRY(incremental_prep(M));
   orbital_status_kernel<<<1, 32, 0, s>>>(W.eps, nmo, nocc, W.eig_status, prec == DF_MIXED ? W.jk.mk.err : nullptr,
                                          W.st);
   DF_LAUNCHED("orbital_status_kernel");
+  DF_CUDA(cudaMemcpyAsync(M.hst, W.st, sizeof(ScfStatus), cudaMemcpyDeviceToHost, s));
+  return DF_OK;
+}
+
+// Tail of a Newton iteration: Fock and energy, the orthogonal-basis error of the density
+// that was built (for the convergence test), then a Newton step instead of DIIS and the
+// diagonalisation.
+static int iteration_tail_soscf(ScfMol& M, int prec) {
+  ScfWork& W = M.W;
+  cudaStream_t s = M.s;
+  const int nao = M.nao, nmo = M.nmo, nocc = M.nocc;
+  const long nn = (long)nao * nao, ne = (long)nmo * nmo;
+  fock_energy_kernel<<<1, 1024, 0, s>>>(W.h, W.J, W.K, W.D, nn, W.enuc, W.F, W.st);
+  DF_LAUNCHED("fock_energy_kernel");
+  DF_TRY(to_orth(W.F, nao, nmo, W, W.Fo, s));
+  DF_TRY(dgemm(false, false, nmo, nocc, nmo, 1.0, W.Fo, nmo, 0, W.Cp, nocc, 0, 0.0, W.T1, nocc, 0, 1, s, 0, 0));
+  DF_TRY(dgemm(false, true, nmo, nmo, nocc, 2.0, W.T1, nocc, 0, W.Cp, nocc, 0, 0.0, W.T2, nmo, 0, 1, s, 0, 0));
+  antisym_kernel<<<blocks_for(ne), 256, 0, s>>>(W.T2, nmo, W.E);
+  DF_LAUNCHED("antisym_kernel");
+  absmax_kernel<<<1, 1024, 0, s>>>(W.E, ne, &W.st->emax);
+  DF_LAUNCHED("absmax_kernel");
+  DF_TRY(soscf_step(M));
+  if (M.inc) DF_TRY(incremental_prep(M));
+  soscf_status_kernel<<<1, 32, 0, s>>>(W.Fmo, nmo, nocc, W.k_status, prec == DF_MIXED ? W.jk.mk.err : nullptr, W.st);
+  DF_LAUNCHED("soscf_status_kernel");
   DF_CUDA(cudaMemcpyAsync(M.hst, W.st, sizeof(ScfStatus), cudaMemcpyDeviceToHost, s));
   return DF_OK;
 }
@@ -872,7 +1237,7 @@ static int iteration_body(ScfMol& M, int prec) {
   DF_TRY(run_jk(W.B, M.nao, M.naux, prec, W.D, W.Cocc, M.nocc, W.J, W.K, W.jk, M.s));
   if (M.inc)  // a full build: the accumulated K now belongs to this density
     DF_CUDA(cudaMemcpyAsync(W.Cbase, W.Cp, sizeof(double) * M.nmo * M.nocc, cudaMemcpyDeviceToDevice, M.s));
-  return iteration_tail(M, prec);
+  return M.soscf ? iteration_tail_soscf(M, prec) : iteration_tail(M, prec);
 }
 
 // Body of an incremental iteration: J in FP64 as always; K += K[U+] - K[U-] with the
@@ -902,7 +1267,7 @@ static int iteration_body_incremental(ScfMol& M) {
   kacc_kernel<<<blocks_for(nn), 256, 0, s>>>(W.K, W.T2, W.T1, nn);
   DF_LAUNCHED("kacc_kernel");
   DF_CUDA(cudaMemcpyAsync(W.Cbase, W.Cp, sizeof(double) * nmo * nocc, cudaMemcpyDeviceToDevice, s));
-  return iteration_tail(M, DF_MIXED);
+  return M.soscf ? iteration_tail_soscf(M, DF_MIXED) : iteration_tail(M, DF_MIXED);
 }
 
 // Second half of the first iteration from a non-idempotent dm0 (after dm0_launch drained).
@@ -917,10 +1282,16 @@ static int scf_dm0_finish(ScfMol& M) {
 // enqueues its first half here (phase DM0_EIG): scf_dm0_finish completes it.
 static int scf_iter_launch(ScfMol& M, bool use_graphs) {
   if (M.first_dm0) return dm0_launch(M);
+  if (M.soscf_pending) {
+    DF_TRY(soscf_init(M));
+    M.soscf = true;
+    M.soscf_pending = false;
+  }
   const bool incr = M.inc && M.kp == ScfMol::KP_INCR;
   int gi = M.prec == DF_FP64 ? 0 : (incr ? 2 : 1);
   auto body = [&]() { return incr ? iteration_body_incremental(M) : iteration_body(M, M.prec); };
-  if (!use_graphs || prof_on()) return body();
+  // Newton iterations run eagerly (their launch count varies with the CG length knob)
+  if (!use_graphs || prof_on() || M.soscf) return body();
   if (!M.graph[gi]) {
     cudaGraph_t g = nullptr;
     DF_CUDA(cudaStreamBeginCapture(M.s, cudaStreamCaptureModeThreadLocal));
@@ -1018,9 +1389,14 @@ static bool scf_iter_finish_incremental(ScfMol& M, double de) {
       } else {
         M.inc_stall++;
       }
-      if (!update_ok || M.inc_stall >= 10) {
+      if (M.inc_stall >= 10 && update_ok && M.soscf_on && !M.soscf && M.rebases >= 1) {
+        // still stalled after a fresh base: DIIS itself is stuck, take Newton steps
+        M.soscf_pending = true;
+        M.inc_stall = 0;
+      } else if (!update_ok || (M.inc_stall >= 10 && !M.soscf_pending)) {
         // a large rotation, or updates that no longer reduce the error: rebuild the base
         M.rebases++;
+        M.inc_stall = 0;
         if (M.rebases > 3) to_final();
         else to_base();
       }
@@ -1070,6 +1446,19 @@ static bool scf_iter_finish(ScfMol& M) {
   if (M.opt.verbose)
     printf("scf iter %3d  %s  E = %.12f  dE = %.3e  max|e| = %.3e\n", M.res.iterations,
            M.prec == DF_FP64 ? "fp64 " : (M.inc && M.kp == ScfMol::KP_INCR ? "incr " : "mixed"), h.energy, de, h.emax);
+  // DIIS progress, for the switch to Newton steps: with an accurate Fock matrix (FP64, or
+  // the incremental updates) and no 10% gain on the best error for 12 iterations
+  if (h.emax < 0.9 * M.d_best) {
+    M.d_best = h.emax;
+    M.d_stall = 0;
+  } else {
+    M.d_stall++;
+  }
+  const bool accurate_fock = M.prec == DF_FP64 || (M.inc && M.kp == ScfMol::KP_INCR);
+  if (M.soscf_on && !M.soscf && !M.soscf_pending && accurate_fock && M.d_stall >= 12 && M.d_best < 0.1) {
+    M.soscf_pending = true;
+    M.inc_stall = 0;
+  }
   if (M.inc) return scf_iter_finish_incremental(M, de);
   if (M.prec == DF_FP64 && M.switched && M.fp64_done + 1 >= M.opt.n_fp64_final && M.have_old &&
       de < M.opt.conv_tol && h.emax < M.opt.conv_err) {
@@ -1278,6 +1667,49 @@ extern "C" size_t scf_batch_work_bytes(const df_molecule* mols, int nmol, int pr
   return align_up(mx, 256) * (size_t)std::min(slots, nmol);
 }
 
+// First-fit allocator over the batch workspace: molecules of uneven size take regions of
+// their own size, so many small molecules run beside a few large ones.  Free regions are
+// kept sorted by offset and merged with their neighbours when a region is released.
+namespace dfscf {
+class RegionPool {
+ public:
+  explicit RegionPool(size_t bytes) { free_.push_back({0, bytes}); }
+  // offset of a region of `bytes` (256-byte aligned), or SIZE_MAX when none fits
+  size_t take(size_t bytes) {
+    bytes = align_up(bytes, 256);
+    for (size_t i = 0; i < free_.size(); ++i)
+      if (free_[i].size >= bytes) {
+        const size_t off = free_[i].off;
+        free_[i].off += bytes;
+        free_[i].size -= bytes;
+        if (free_[i].size == 0) free_.erase(free_.begin() + (long)i);
+        return off;
+      }
+    return SIZE_MAX;
+  }
+  void give(size_t off, size_t bytes) {
+    bytes = align_up(bytes, 256);
+    size_t i = 0;
+    while (i < free_.size() && free_[i].off < off) ++i;
+    free_.insert(free_.begin() + (long)i, {off, bytes});
+    if (i + 1 < free_.size() && free_[i].off + free_[i].size == free_[i + 1].off) {
+      free_[i].size += free_[i + 1].size;
+      free_.erase(free_.begin() + (long)i + 1);
+    }
+    if (i > 0 && free_[i - 1].off + free_[i - 1].size == free_[i].off) {
+      free_[i - 1].size += free_[i].size;
+      free_.erase(free_.begin() + (long)i);
+    }
+  }
+
+ private:
+  struct Region {
+    size_t off, size;
+  };
+  std::vector<Region> free_;
+};
+}  // namespace dfscf
+
 extern "C" int scf_run_batch(const df_molecule* mols, int nmol, const scf_opts* opt, const double* const* dm0s,
                              double* const* D_outs, scf_result* results, int slots, void* work, size_t work_bytes,
                              cudaStream_t s) {
@@ -1288,11 +1720,20 @@ extern "C" int scf_run_batch(const df_molecule* mols, int nmol, const scf_opts* 
   o.verbose = 0;
   for (int i = 0; i < nmol; ++i) DF_TRY(check_molecule(&mols[i], o));
   slots = std::min(slots, nmol);
-  size_t need = scf_batch_work_bytes(mols, nmol, o.precision, slots);
-  DF_REQUIRE(work && work_bytes >= need, DF_ERR_NOMEM, "scf_run_batch: workspace of %zu bytes < %zu", work_bytes,
-             need);
-  const size_t per_slot = need / slots;
+  std::vector<size_t> bytes(nmol);
+  size_t largest = 0;
+  for (int i = 0; i < nmol; ++i) {
+    bytes[i] = align_up(scf_work_bytes(mols[i].nao, mols[i].naux, mols[i].nelec / 2, o.precision), 256);
+    largest = std::max(largest, bytes[i]);
+  }
+  DF_REQUIRE(work && work_bytes >= largest, DF_ERR_NOMEM,
+             "scf_run_batch: workspace of %zu bytes cannot hold the largest molecule (%zu bytes)", work_bytes, largest);
   memset(results, 0, sizeof(scf_result) * nmol);
+  // largest molecules first: the long runs start early and small ones fill the gaps
+  std::vector<int> order(nmol);
+  for (int i = 0; i < nmol; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return bytes[a] > bytes[b]; });
+  RegionPool pool(work_bytes);
   // stream pool, ordered after the caller's stream
   std::vector<cudaStream_t> streams(slots, nullptr);
   cudaEvent_t start;
@@ -1312,20 +1753,27 @@ extern "C" int scf_run_batch(const df_molecule* mols, int nmol, const scf_opts* 
   DF_CUDA(cudaMallocHost(&hints, sizeof(int) * 2 * slots));
   std::vector<ScfMol*> slot_mol(slots, nullptr);
   std::vector<int> slot_index(slots, -1);
-  int next = 0, finished = 0, rc = DF_OK;
-  // Each molecule holds a slot (workspace + stream) until it finishes; a freed slot takes
-  // the next molecule, so molecules of uneven size keep every stream busy.  The host polls
-  // the streams and advances whichever slot's stream has drained: it never blocks on one
-  // molecule while others could run.
-  auto start_molecule = [&](int k) -> int {
-    int i = next++;
+  std::vector<size_t> slot_off(slots, 0);
+  int next = 0, finished = 0, running = 0, rc = DF_OK;
+  // Each running molecule holds a stream and a region of the workspace until it finishes.
+  // The host polls the streams and advances whichever molecule's stream has drained: it
+  // never blocks on one molecule while others could run.  A stream slot that frees up takes
+  // the next molecule (in the size order above) as soon as its region fits.
+  auto try_start = [&](int k) -> int {
+    if (next >= nmol) return DF_OK;
+    const int i = order[next];
+    const size_t off = pool.take(bytes[i]);
+    if (off == SIZE_MAX) return DF_OK;  // wait until a running molecule returns its region
+    next++;
     ScfMol* M = new ScfMol();
     slot_mol[k] = M;
     slot_index[k] = i;
-    DF_TRY(init_mol(*M, &mols[i], o, (char*)work + per_slot * k, per_slot, streams[k]));
-    // With several slots each molecule diagonalises on one CTA: many one-CTA eigensolvers
-    // fill the SMs in parallel, while cooperative grids from different streams (one CTA per
-    // SM each) would contend for co-residency.
+    slot_off[k] = off;
+    running++;
+    DF_TRY(init_mol(*M, &mols[i], o, (char*)work + off, bytes[i], streams[k]));
+    // With several molecules in flight each diagonalises on one CTA: many one-CTA
+    // eigensolvers fill the SMs in parallel, while cooperative grids from different streams
+    // (one CTA per SM each) would contend for co-residency.
     if (slots > 1) M->W.eig_aux = nullptr;
     M->hst = hst + k;
     M->h_eps = heps + (size_t)(max_nao + 1) * k;
@@ -1339,7 +1787,7 @@ extern "C" int scf_run_batch(const df_molecule* mols, int nmol, const scf_opts* 
     }
     return DF_OK;
   };
-  // Advance one slot whose stream is idle; returns a fatal status.
+  // Advance one molecule whose stream is idle; returns a fatal status.
   auto advance = [&](int k) -> int {
     ScfMol* M = slot_mol[k];
     int r = DF_OK;
@@ -1375,21 +1823,29 @@ extern "C" int scf_run_batch(const df_molecule* mols, int nmol, const scf_opts* 
       M->phase = ScfMol::DONE;
     }
     if (M->phase == ScfMol::DONE) {
-      int i = slot_index[k];
+      const int i = slot_index[k];
       if (M->rc == DF_OK || M->rc == DF_ERR_NOCONV) DF_TRY(scf_outputs(*M));
       results[i] = M->res;
-      delete M;  // the outputs are ordered before the next molecule's work on this stream
+      // the region goes back to the pool only once this stream has finished with it: the
+      // outputs above are its last work, so wait for them
+      DF_CUDA(cudaStreamSynchronize(streams[k]));
+      delete M;
       slot_mol[k] = nullptr;
+      pool.give(slot_off[k], bytes[i]);
       finished++;
-      if (next < nmol) DF_TRY(start_molecule(k));
+      running--;
     }
     return DF_OK;
   };
-  for (int k = 0; k < slots && rc == DF_OK; ++k) rc = start_molecule(k);
   while (rc == DF_OK && finished < nmol) {
     bool progressed = false;
     for (int k = 0; k < slots && rc == DF_OK; ++k) {
-      if (!slot_mol[k]) continue;
+      if (!slot_mol[k]) {
+        const int before = next;
+        rc = try_start(k);
+        if (next != before) progressed = true;
+        continue;
+      }
       cudaError_t q = cudaStreamQuery(streams[k]);
       if (q == cudaErrorNotReady) continue;
       if (q != cudaSuccess) {
@@ -1399,6 +1855,12 @@ extern "C" int scf_run_batch(const df_molecule* mols, int nmol, const scf_opts* 
       }
       progressed = true;
       rc = advance(k);
+    }
+    if (rc == DF_OK && running == 0 && next < nmol) {
+      // nothing runs and the next molecule still does not fit: cannot happen while the
+      // workspace holds the largest molecule, but never spin on it
+      set_error("scf_run_batch: molecule %d does not fit in the workspace", order[next]);
+      rc = DF_ERR_NOMEM;
     }
     if (!progressed && rc == DF_OK) std::this_thread::sleep_for(std::chrono::microseconds(20));
   }
@@ -1502,3 +1964,5 @@ extern "C" int df_core_guess(const df_molecule* mol, double lindep, double* S_ou
   if (nmo_out) *nmo_out = nmo;
   return DF_OK;
 }
+
+DF_BOUNDS_READER(bounds_read_scf)

