@@ -406,6 +406,8 @@ def run_ours(args):
         import gen
         mols = gen.batch_molecules(args.nmol, 10, 80, 1)
         devs = [dfscf.MoleculeOnDevice(m) for m in mols]
+        from paper_2506_06661_gb300 import tune
+        batch_knobs = tune.apply_for_molecules(mols, "mixed")
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         res = dfscf.scf_run_batch(devs, slots=args.batch_slots, precision="mixed", raise_on_noconv=False).results
@@ -416,7 +418,7 @@ def run_ours(args):
                  "seconds": dt, "molecules_per_s": len(mols) / dt, "converged": int(sum(r.converged for r in res)),
                  "mean_iterations": float(np.mean([r.iterations for r in res])),
                  "mean_fp64_iterations": float(np.mean([r.fp64_iterations for r in res])),
-                 "max_in_flight": args.batch_slots}
+                 "max_in_flight": args.batch_slots, "knobs": batch_knobs or "library defaults"}
         del devs
 
     line = {"metric": METRIC, "value": value, "unit": "builds/s", "n_gpus": ws, "steps": args.steps,
@@ -568,13 +570,70 @@ def run_scenario_guess(args):
         model.save(args.save_model)
     test = gen.batch_molecules(args.neval, 40, 120, 3)
     ev = guess.evaluate(model, test, slots=slots, precision="mixed")
+    core_run = ev.pop("_core_run")
     for key in ("energy_core", "energy_learned", "iterations_core", "iterations_learned"):
         ev.pop(key, None)
+    # the learned start's first exchange with coarser cuts of dm0's natural occupations
+    from paper_2506_06661_gb300 import tune
+    cuts = {}
+    for cut in [int(c) for c in args.dm0_cuts.split(",") if c]:
+        old = tune.get_knob("dm0_eig_cut")
+        tune.set_knob("dm0_eig_cut", cut)
+        e2 = guess.evaluate(model, test, slots=slots, precision="mixed", core_run=core_run)
+        tune.set_knob("dm0_eig_cut", old)
+        cuts[f"1e-{cut}"] = {k: e2[k] for k in ("mean_iter_core", "mean_iter_learned", "same_state", "both_converged",
+                                                "wall_s_core", "wall_s_learned", "guess_used")}
+    ev["dm0_cuts"] = cuts
     out = {"scenario": "guess", "train_molecules": len(train), "train_converged": len(ok),
            "train_samples": int(M.sum().item()), "data_seconds": t_data, "train_seconds": t_train,
            "epochs": args.epochs, "mse_first_last": [hist[0], hist[-1]], "eval_molecules": len(test),
            "eval_centres": "40-120 (uniform, seed 3)", "eval": ev}
     print(json.dumps(out), flush=True)
+    return 0
+
+
+def run_scenario_states(args):
+    """SCF solutions reached by the FP64 and the mixed-precision runs of selected molecules of
+    the batched workload, each tested by perturbation: the converged occupied orbitals are
+    rotated by a small random angle into the virtual space (in the orthonormal basis of the
+    overlap) and the FP64 SCF restarts from that determinant.  A local minimum comes back to
+    its energy; a saddle point falls to a lower one."""
+    import torch
+    import gen
+    import paper_2506_06661_gb300 as dfscf
+    idx = [int(i) for i in args.indices.split(",") if i]
+    sizes = gen.molecules.batch_sizes(256, 10, 80, 1)
+    rng = np.random.default_rng(7)
+    out = []
+    for i in idx:
+        n = int(sizes[i])
+        mol = gen.make_molecule(n, gen.molecules.box_for(n), (1, i))
+        md = dfscf.MoleculeOnDevice(mol)
+        S, _, _ = dfscf.int1e(mol.ao_xyz, mol.ao_exp, mol.xyz, mol.charges)
+        S = S.cpu().numpy()
+        s, U = np.linalg.eigh(S)
+        X = U[:, s > 1e-8] / np.sqrt(s[s > 1e-8])
+        row = {"index": i, "centres": n}
+        for prec in ("fp64", "mixed"):
+            r = dfscf.scf_run(md, precision=prec, raise_on_noconv=False)
+            C = r.C.cpu().numpy()
+            # orthonormal-basis occupied orbitals and their complement
+            Cp = np.linalg.lstsq(X, C, rcond=None)[0]
+            Q, _ = np.linalg.qr(np.hstack([Cp, rng.standard_normal((Cp.shape[0], Cp.shape[0] - Cp.shape[1]))]))
+            Vp = Q[:, Cp.shape[1]:]
+            probes = []
+            for _ in range(args.probes):
+                kappa = args.angle * rng.standard_normal((Vp.shape[1], Cp.shape[1])) / np.sqrt(Cp.shape[1])
+                Cn, _ = np.linalg.qr(Cp + Vp @ kappa)
+                Cao = X @ Cn[:, :Cp.shape[1]]
+                rp = dfscf.scf_run(md, precision="fp64", dm0=2 * Cao @ Cao.T, raise_on_noconv=False)
+                probes.append({"energy": rp.energy, "converged": rp.converged, "iterations": rp.iterations})
+            lower = [p["energy"] for p in probes if p["converged"] and p["energy"] < r.energy - 1e-6]
+            row[prec] = {"energy": r.energy, "converged": r.converged, "iterations": r.iterations,
+                         "probes": probes, "minimum": not lower, "lowest_probe": min([p["energy"] for p in probes])}
+        row["dE_mixed_minus_fp64"] = row["mixed"]["energy"] - row["fp64"]["energy"]
+        out.append(row)
+        print(json.dumps(row), flush=True)
     return 0
 
 
@@ -594,7 +653,7 @@ def main():
     ap.add_argument("--kcols", type=int, default=0,
                     help="exchange over this many seeded columns instead of the occupied orbitals (profiling)")
     ap.add_argument("--batch-slots", type=int, default=128, help="molecules in flight in the batched-SCF block")
-    ap.add_argument("--scenario", choices=["fock", "scf", "batch", "guess"], default="fock",
+    ap.add_argument("--scenario", choices=["fock", "scf", "batch", "guess", "states"], default="fock",
                     help="fock: Fock-build throughput (the default line); scf: SCF time to convergence, "
                          "mixed vs FP64; batch: batched SCF of uneven molecules; guess: learned guess")
     ap.add_argument("--max-cycle", type=int, default=200, help="SCF iteration budget (scf, batch scenarios)")
@@ -607,6 +666,10 @@ def main():
     ap.add_argument("--neval", type=int, default=512)
     ap.add_argument("--epochs", type=int, default=20)
     ap.add_argument("--save-model", default="")
+    ap.add_argument("--indices", default="2,6,156,214,246", help="states scenario: batch molecules to probe")
+    ap.add_argument("--probes", type=int, default=4, help="states scenario: perturbed restarts per state")
+    ap.add_argument("--angle", type=float, default=0.05, help="states scenario: rotation size (rad)")
+    ap.add_argument("--dm0-cuts", default="", help="guess scenario: also evaluate these dm0_eig_cut exponents (e.g. 3,2)")
     ap.add_argument("--dump", default="", help="batch scenario: write per-molecule results to this JSON file")
     args = ap.parse_args()
     if args.scenario == "scf":
@@ -615,6 +678,8 @@ def main():
         return run_scenario_batch(args)
     if args.scenario == "guess":
         return run_scenario_guess(args)
+    if args.scenario == "states":
+        return run_scenario_states(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -417,13 +417,20 @@ int df_j_noalloc(const void* B, int nao, int naux, const double* D, double* J, c
 
 /* ---- tuning knobs ------------------------------------------------------------------------
  * Launch parameters chosen by the autotuner (paper_2506_06661_gb300/tune.py): "umma_max_stages"
- * (2..4, shared-memory ring depth of the tensor-core GEMM), "syrk_split" and "fp64_syrk_split"
+ * (2..8, the largest shared-memory ring depth of the tensor-core GEMM; as many stages as fit
+ * up to that), "syrk_bk" (32, or 16: K boxes of 16 elements in the exchange SYRK, so that
+ * twice as many narrower stages are in flight), "syrk_split" and "fp64_syrk_split"
  * (K-dimension splits of the exchange SYRK, 0 = built-in heuristic), "jpass2_rows" (32..512,
  * auxiliary rows per CTA slice of J's second pass), "eig_ctas" (CTAs of the multi-SM
  * eigensolver: 0 automatic, 1 a single CTA) and "mixed_planes" (3..5 BF16 planes per operand of
  * the mixed exchange: 6, 10 or 15 plane products; it also sizes a mixed B).
+ * Tile shapes: "fp64_ht_cols" (0 automatic, 16 or 32 occupied columns per FP64 half-transform
+ * CTA), "ht_n" (0: the widest tcgen05 half-transform tile that fits; else a cap, a multiple
+ * of 16), "jpass1_rows" (1, 2, 4 or 8 auxiliary rows per CTA of J's first pass) and
+ * "j_fp64_fma" (1: J's passes with FP64 FMAs instead of double-float products).
  * "mixed_incremental" (0 or 1), "soscf" (0 or 1) and "soscf_cg" (1..64) shape the SCF as
- * described at scf_run.  Two more knobs bound the multi-SM eigensolver's grid barriers:
+ * described at scf_run; "dm0_eig_cut" (1..16, default 12) drops natural occupations of a
+ * non-idempotent dm0 below 10^-cut of the largest from its first exchange.  Two more knobs bound the multi-SM eigensolver's grid barriers:
  * "eig_barrier_polls" (256..2^30 polls before a wait gives up with DF_ERR_TIMEOUT; default 2^22, about a second) and "eig_barrier_extra"
  * (0 or 1; 1 makes every barrier wait for one arrival that never comes, so that a test can
  * watch the bounded wait run out; leave it 0).  Host-side process-wide state: change

@@ -124,12 +124,16 @@ struct Knob {
   int value, lo, hi;
 };
 static Knob g_knobs[] = {
-    {"umma_max_stages", 4, 2, 4},    // shared-memory ring depth of the tcgen05 GEMM
+    {"umma_max_stages", 8, 2, 8},    // largest shared-memory ring depth of the tcgen05 GEMM (as many as fit)
+    {"syrk_bk", 32, 16, 32},         // K box of the tcgen05 exchange SYRK: 32, or 16 for a deeper ring
     {"syrk_split", 0, 0, 4096},      // K-dimension splits of the tcgen05 exchange SYRK
     {"fp64_syrk_split", 0, 0, 4096}, // K-dimension splits of the FP64 exchange SYRK
     {"jpass2_rows", 256, 32, 512},   // auxiliary rows per CTA slice of J's second pass
     {"j_fp64_fma", 0, 0, 1},         // J passes: 0 double-float products on FP32 units, 1 FP64 FMAs
     {"jpass1_rows", 1, 1, 8},        // auxiliary rows per CTA of J's first pass (1, 2, 4 or 8)
+    {"fp64_ht_cols", 0, 0, 32},      // FP64 half-transform tile columns: 0 auto, 16 or 32
+    {"dm0_eig_cut", 12, 1, 16},      // first exchange of a fractional dm0: occupations below 10^-cut dropped
+    {"ht_n", 0, 0, 256},             // tcgen05 half-transform tile columns: 0 widest that fits, else a cap
     {"eig_ctas", 0, 0, 4096},        // CTAs of the multi-SM eigensolver (0 auto, 1 single CTA)
     {"mixed_planes", 5, 3, 5},       // BF16 planes per operand of the mixed exchange (3, 4, 5: 6, 10, 15 products)
     {"mixed_incremental", 1, 0, 1},  // mixed SCF: update K from the change of the occupied projector

@@ -341,17 +341,25 @@ __global__ void jreduce_unpack_kernel(const double* __restrict__ Jpart, int nspl
 
 // ---- FP64 K ---------------------------------------------------------------------------
 // X[m][P][i] = sum_n B_P[m][n] C[n][i]; B_P gathered from the packed row.
-// CTA tile 64 (m) x 32 (i), 256 lanes with 4 x 2 outputs each.
+// CTA tile 64 (m) x 16 CI (i), 256 lanes with 4 x CI outputs each (CI = 2: 32 columns, for
+// wide occupied spaces; CI = 1: 16 columns, less padding for small ones; knob
+// "fp64_ht_cols").
+template <int CI>
 __global__ void __launch_bounds__(256) k_halftransform_fp64_kernel(const double* __restrict__ B, long ld, int nao,
                                                                    int naux, const double* __restrict__ C, int nocc,
                                                                    double* __restrict__ X) {
+  constexpr int TN = 16 * CI;
   __shared__ double As[16][65];
-  __shared__ double Cs[16][33];
+  __shared__ double Cs[16][TN + 1];
   int P = blockIdx.z;
-  int m0 = blockIdx.y * 64, i0 = blockIdx.x * 32;
+  int m0 = blockIdx.y * 64, i0 = blockIdx.x * TN;
   const double* row = B + (size_t)P * ld;
-  int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;  // tx -> i (2 each, stride 16), ty -> m (4 each, stride 16)
-  double acc[4][2] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
+  int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;  // tx -> i (CI each, stride 16), ty -> m (4 each, stride 16)
+  double acc[4][CI];
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < CI; ++v) acc[u][v] = 0.0;
   for (int n0 = 0; n0 < nao; n0 += 16) {
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
@@ -366,25 +374,24 @@ __global__ void __launch_bounds__(256) k_halftransform_fp64_kernel(const double*
       As[nn][mm] = v;
     }
 #pragma unroll
-    for (int r = 0; r < 2; ++r) {
+    for (int r = 0; r < CI; ++r) {
       int idx = threadIdx.x + 256 * r;
-      int nn = idx >> 5, ii = idx & 31;
+      int nn = idx / TN, ii = idx % TN;
       int gn = n0 + nn, gi = i0 + ii;
       Cs[nn][ii] = (gn < nao && gi < nocc) ? C[DF_IX((size_t)gn * nocc + gi, (size_t)nao * nocc)] : 0.0;
     }
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < 16; ++k) {
-      double a[4], c[2];
+      double a[4], c[CI];
 #pragma unroll
       for (int u = 0; u < 4; ++u) a[u] = As[k][ty + 16 * u];
-      c[0] = Cs[k][tx];
-      c[1] = Cs[k][tx + 16];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        acc[u][0] = fma(a[u], c[0], acc[u][0]);
-        acc[u][1] = fma(a[u], c[1], acc[u][1]);
-      }
+      for (int v = 0; v < CI; ++v) c[v] = Cs[k][tx + 16 * v];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < CI; ++v) acc[u][v] = fma(a[u], c[v], acc[u][v]);
     }
     __syncthreads();
   }
@@ -393,7 +400,7 @@ __global__ void __launch_bounds__(256) k_halftransform_fp64_kernel(const double*
     int gm = m0 + ty + 16 * u;
     if (gm >= nao) continue;
 #pragma unroll
-    for (int v = 0; v < 2; ++v) {
+    for (int v = 0; v < CI; ++v) {
       int gi = i0 + tx + 16 * v;
       if (gi < nocc) X[DF_IX(((size_t)gm * naux + P) * nocc + gi, (size_t)nao * naux * nocc)] = acc[u][v];
     }
@@ -504,8 +511,15 @@ int build_K_fp64(const double* B64, long ld, int nao, int naux, const double* C,
                  cudaStream_t s) {
   {
     ProfScope ps("k_halftransform_fp64", s);
-    dim3 grid((nocc + 31) / 32, (nao + 63) / 64, naux);
-    k_halftransform_fp64_kernel<<<grid, 256, 0, s>>>(B64, ld, nao, naux, C, nocc, w.X);
+    const int forced = knob("fp64_ht_cols");
+    const int cols = forced == 16 || forced == 32 ? forced : (nocc <= 16 ? 16 : 32);
+    if (cols == 16) {
+      dim3 grid((nocc + 15) / 16, (nao + 63) / 64, naux);
+      k_halftransform_fp64_kernel<1><<<grid, 256, 0, s>>>(B64, ld, nao, naux, C, nocc, w.X);
+    } else {
+      dim3 grid((nocc + 31) / 32, (nao + 63) / 64, naux);
+      k_halftransform_fp64_kernel<2><<<grid, 256, 0, s>>>(B64, ld, nao, naux, C, nocc, w.X);
+    }
     DF_LAUNCHED("k_halftransform_fp64_kernel");
   }
   long kdim = (long)naux * nocc;

@@ -972,13 +972,17 @@ static int dm0_finish(ScfMol& M) {
   DF_REQUIRE(M.h_ints[0] == 0, DF_ERR_NOCONV, "scf: eigensolver failed on the starting density");
   double wmax = 0.0;
   for (int k = 0; k < nao; ++k) wmax = fmax(wmax, fabs(M.h_eps[k]));
+  // natural occupations below 10^-dm0_eig_cut of the largest are dropped (default 10^-12:
+  // the exact exchange of dm0; a coarser cut trades exactness of the first exchange for
+  // fewer columns)
+  const double cut = pow(10.0, -(double)std::max(1, knob("dm0_eig_cut"))) * wmax;
   // positive eigenvalues first, then negative ones; one copy of all indices to the device
   M.dm0_ids.clear();
   for (int k = 0; k < nao; ++k)
-    if (M.h_eps[k] > 1e-12 * wmax) M.dm0_ids.push_back(k);
+    if (M.h_eps[k] > cut) M.dm0_ids.push_back(k);
   const size_t npos = M.dm0_ids.size();
   for (int k = 0; k < nao; ++k)
-    if (-M.h_eps[k] > 1e-12 * wmax) M.dm0_ids.push_back(k);
+    if (-M.h_eps[k] > cut) M.dm0_ids.push_back(k);
   DF_CUDA(cudaMemsetAsync(W.K, 0, sizeof(double) * nn, s));
   if (!M.dm0_ids.empty())
     DF_CUDA(cudaMemcpyAsync(W.idx, M.dm0_ids.data(), sizeof(int) * M.dm0_ids.size(), cudaMemcpyHostToDevice, s));

@@ -40,7 +40,7 @@ namespace umma {
 constexpr int BM = 128;          // rows per tile (TMEM lanes)
 // K elements per stage: one swizzle row of bf16 (128 bytes; 64 bytes for four or more planes)
 __host__ __device__ constexpr int bk_of(int np) { return np >= 4 ? 32 : 64; }
-constexpr int MAX_STAGES = 4;
+constexpr int MAX_STAGES = 8;
 constexpr int THREADS = 192;     // warp 0 TMA, warp 1 MMA, warps 2..5 epilogue
 constexpr uint32_t WAIT_LIMIT = 1u << 27;
 
@@ -123,13 +123,13 @@ __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.
 // BK-element rows (2 BK bytes) swizzled at that width: 8-row groups 16 BK bytes apart.
 template <int BK>
 __device__ __forceinline__ uint64_t desc_sw(uint32_t saddr) {
-  static_assert(BK == 64 || BK == 32, "swizzle width");
+  static_assert(BK == 64 || BK == 32 || BK == 16, "swizzle width");
   uint64_t d = 0;
   d |= (uint64_t)((saddr >> 4) & 0x3FFFu);     // start address
   d |= (uint64_t)1 << 16;                      // leading byte offset (unused for swizzled K-major)
   d |= (uint64_t)((8 * 2 * BK) >> 4) << 32;    // stride byte offset: 8 rows
   d |= (uint64_t)1 << 46;                      // descriptor version for tcgen05
-  d |= (uint64_t)(BK == 64 ? 2 : 4) << 61;     // 128-byte or 64-byte swizzle
+  d |= (uint64_t)(BK == 64 ? 2 : (BK == 32 ? 4 : 6)) << 61;  // 128-, 64- or 32-byte swizzle
   return d;
 }
 
@@ -184,10 +184,9 @@ struct Maps {
   CUtensorMap b[5];
 };
 
-template <int NP>
+template <int NP, int BK>
 __global__ void __launch_bounds__(THREADS, 1) split_bf16_gemm_kernel(const __grid_constant__ Maps maps,
                                                                       const Params p) {
-  constexpr int BK = bk_of(NP);
   extern __shared__ uint8_t dyn_smem[];
   __shared__ uint64_t full_bar[MAX_STAGES];
   __shared__ uint64_t empty_bar[MAX_STAGES];
@@ -399,8 +398,8 @@ static PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
 }
 
 // 2-D bf16 tensor map: inner dimension `cols` (K, contiguous), `rows` rows of `ld` elements,
-// box of bk x box_rows swizzled at the box width (bk = 64: 128 bytes; 32: 64 bytes), zero
-// fill out of bounds.
+// box of bk x box_rows swizzled at the box width (bk = 64: 128 bytes; 32: 64 bytes; 16: 32
+// bytes), zero fill out of bounds.
 static int make_map(CUtensorMap* map, const void* base, uint64_t cols, uint64_t rows, uint64_t ld, uint32_t box_rows,
                     int bk) {
   auto enc = get_encode();
@@ -411,16 +410,16 @@ static int make_map(CUtensorMap* map, const void* base, uint64_t cols, uint64_t 
   cuuint32_t box[2] = {(cuuint32_t)bk, box_rows};
   cuuint32_t estr[2] = {1, 1};
   CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
-                   CU_TENSOR_MAP_INTERLEAVE_NONE, bk == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   bk == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : (bk == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B),
                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   DF_REQUIRE(r == CUDA_SUCCESS, DF_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
   return DF_OK;
 }
 
-template <int NP>
+template <int NP, int BK>
 static int launch_gemm(const umma::Maps& maps, umma::Params p, dim3 grid, cudaStream_t s) {
-  constexpr int BK = umma::bk_of(NP);
   p.b_bytes = (uint32_t)p.N * BK * 2;
   p.stage_bytes = NP * (umma::BM * BK * 2 + p.b_bytes);
   const uint32_t budget = 220 * 1024;
@@ -430,7 +429,7 @@ static int launch_gemm(const umma::Maps& maps, umma::Params p, dim3 grid, cudaSt
   size_t smem = (size_t)p.stages * p.stage_bytes + 1024;
   DF_REQUIRE(smem <= 220 * 1024 + 1024, DF_ERR_ARG, "split-bf16 GEMM: %zu bytes of shared memory requested", smem);
   DF_TRY(umma_prepare());
-  umma::split_bf16_gemm_kernel<NP><<<grid, umma::THREADS, smem, s>>>(maps, p);
+  umma::split_bf16_gemm_kernel<NP, BK><<<grid, umma::THREADS, smem, s>>>(maps, p);
   DF_LAUNCHED("split_bf16_gemm_kernel");
   return DF_OK;
 }
@@ -544,12 +543,13 @@ static int mixed_nsplit(int npad, int naux, int ncpad, int planes) {
 int umma_prepare() {
   static bool done = false;
   if (!done) {
-    DF_CUDA(cudaFuncSetAttribute(umma::split_bf16_gemm_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)(220 * 1024 + 1024)));
-    DF_CUDA(cudaFuncSetAttribute(umma::split_bf16_gemm_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)(220 * 1024 + 1024)));
-    DF_CUDA(cudaFuncSetAttribute(umma::split_bf16_gemm_kernel<5>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)(220 * 1024 + 1024)));
+    const int lim = 220 * 1024 + 1024;
+    DF_CUDA(cudaFuncSetAttribute(umma::split_bf16_gemm_kernel<3, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+    DF_CUDA(cudaFuncSetAttribute(umma::split_bf16_gemm_kernel<4, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+    DF_CUDA(cudaFuncSetAttribute(umma::split_bf16_gemm_kernel<5, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+    DF_CUDA(cudaFuncSetAttribute(umma::split_bf16_gemm_kernel<3, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+    DF_CUDA(cudaFuncSetAttribute(umma::split_bf16_gemm_kernel<4, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+    DF_CUDA(cudaFuncSetAttribute(umma::split_bf16_gemm_kernel<5, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
     done = true;
   }
   return DF_OK;
@@ -611,7 +611,9 @@ int build_K_mixed(const void* B, const BLayout& L, int nao, int naux, const doub
   DF_LAUNCHED("pack_ct_kernel");
   // column tiles of the half transform: two stages in the ring and two accumulators of N
   // columns in 512 TMEM columns
-  const int maxN = ht_max_n(NP);
+  // knob "ht_n" (a multiple of 16) caps the tile width below the widest that fits
+  const int forced = knob("ht_n");
+  const int maxN = forced >= 16 ? std::min(ht_max_n(NP), forced / 16 * 16) : ht_max_n(NP);
   const int ntc = (ncpad + maxN - 1) / maxN;
   const int Nht = ((ncpad + ntc - 1) / ntc + 15) / 16 * 16;
   const char* base = (const char*)B;
@@ -639,9 +641,9 @@ int build_K_mixed(const void* B, const BLayout& L, int nao, int naux, const doub
   {
     ProfScope ps("k_halftransform_tc", s);
     const dim3 grid((unsigned)mtiles, (unsigned)ntc);
-    if (NP == 5) DF_TRY(launch_gemm<5>(maps, p, grid, s));
-    else if (NP == 4) DF_TRY(launch_gemm<4>(maps, p, grid, s));
-    else DF_TRY(launch_gemm<3>(maps, p, grid, s));
+    if (NP == 5) DF_TRY((launch_gemm<5, 32>(maps, p, grid, s)));
+    else if (NP == 4) DF_TRY((launch_gemm<4, 32>(maps, p, grid, s)));
+    else DF_TRY((launch_gemm<3, 64>(maps, p, grid, s)));
   }
   {
     const long kd = (long)naux * ncpad;
@@ -655,17 +657,20 @@ int build_K_mixed(const void* B, const BLayout& L, int nao, int naux, const doub
     else x_to_planes_kernel<3><<<grid, 256, 0, s>>>(x0, x1, w.xmax, kd, xpp);
     DF_LAUNCHED("x_to_planes_kernel");
   }
-  // exchange SYRK: A = B = X [m][(P, i)], lower tiles of 128 x syrk_n, split over (P, i)
+  // exchange SYRK: A = B = X [m][(P, i)], lower tiles of 128 x syrk_n, split over (P, i).
+  // Knob "syrk_bk" = 16: K boxes of 16 elements (32-byte swizzle), stages half as wide, so
+  // twice as many k-blocks are in flight to hide the refills from L2.
   long kdim = (long)naux * ncpad;
   const int ns = syrk_n(NP);
+  const int sbk = knob("syrk_bk") == 16 ? 16 : bk;
   for (int j = 0; j < NP; ++j) {
-    DF_TRY(make_map(&maps.a[j], w.Xp[j], kdim, npad, kdim, umma::BM, bk));
-    DF_TRY(make_map(&maps.b[j], w.Xp[j], kdim, npad, kdim, ns, bk));
+    DF_TRY(make_map(&maps.a[j], w.Xp[j], kdim, npad, kdim, umma::BM, sbk));
+    DF_TRY(make_map(&maps.b[j], w.Xp[j], kdim, npad, kdim, ns, sbk));
   }
   umma::Params q{};
   q.mode = umma::SYRK;
   q.N = ns;
-  q.num_kb = (int)((kdim + bk - 1) / bk);
+  q.num_kb = (int)((kdim + sbk - 1) / sbk);
   q.kb_per_split = (q.num_kb + w.nsplit - 1) / w.nsplit;
   int nsplit = (q.num_kb + q.kb_per_split - 1) / q.kb_per_split;
   q.npad = npad;
@@ -675,9 +680,15 @@ int build_K_mixed(const void* B, const BLayout& L, int nao, int naux, const doub
   {
     ProfScope ps("k_syrk_tc", s);
     dim3 grid((unsigned)q.n_lower_tiles, (unsigned)nsplit);
-    if (NP == 5) DF_TRY(launch_gemm<5>(maps, q, grid, s));
-    else if (NP == 4) DF_TRY(launch_gemm<4>(maps, q, grid, s));
-    else DF_TRY(launch_gemm<3>(maps, q, grid, s));
+    if (sbk == 16) {
+      if (NP == 5) DF_TRY((launch_gemm<5, 16>(maps, q, grid, s)));
+      else if (NP == 4) DF_TRY((launch_gemm<4, 16>(maps, q, grid, s)));
+      else DF_TRY((launch_gemm<3, 16>(maps, q, grid, s)));
+    } else {
+      if (NP == 5) DF_TRY((launch_gemm<5, 32>(maps, q, grid, s)));
+      else if (NP == 4) DF_TRY((launch_gemm<4, 32>(maps, q, grid, s)));
+      else DF_TRY((launch_gemm<3, 64>(maps, q, grid, s)));
+    }
   }
   long nn = (long)nao * nao;
   kmixed_reduce_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, s>>>(w.Kpart, nsplit, npad, nao, w.err, K);

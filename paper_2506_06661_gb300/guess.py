@@ -220,16 +220,21 @@ def converged_densities(mols, slots: int = 32, precision: str = "fp64", chunk: i
     return res, Ds
 
 
-def evaluate(model: GuessModel, mols, slots: int = 32, precision: str = "mixed", want_D: bool = False):
+def evaluate(model: GuessModel, mols, slots: int = 32, precision: str = "mixed", want_D: bool = False,
+             core_run=None):
     """Batched SCF from the core guess and from the learned guess on the same molecules.
     With want_D the converged densities of both runs are returned too (keys D_core,
-    D_learned), and per-molecule energies and iterations always are."""
+    D_learned), and per-molecule energies and iterations always are.  core_run = (batch
+    result, seconds) of an earlier core-guess run on the same molecules skips that run."""
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    out_core = scf_run_batch(mols, slots=slots, precision=precision, raise_on_noconv=False, want_D=want_D)
+    if core_run is None:
+        out_core = scf_run_batch(mols, slots=slots, precision=precision, raise_on_noconv=False, want_D=want_D)
+        torch.cuda.synchronize()
+        t_core = time.perf_counter() - t0
+    else:
+        out_core, t_core = core_run
     core = out_core.results
-    torch.cuda.synchronize()
-    t_core = time.perf_counter() - t0
     t0 = time.perf_counter()
     dm0 = [predict_density(model, m) for m in mols]
     torch.cuda.synchronize()
@@ -260,4 +265,5 @@ def evaluate(model: GuessModel, mols, slots: int = 32, precision: str = "mixed",
             "converged_learned": int(sum(r.converged for r in learned))}
     if want_D:
         ev["D_core"], ev["D_learned"] = out_core.D, out_learned.D
+    ev["_core_run"] = (out_core, t_core)
     return ev

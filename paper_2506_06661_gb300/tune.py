@@ -1,11 +1,15 @@
-"""Autotuner for the Fock-build launch parameters and the batched-SCF slot count.
+"""Autotuner for the Fock-build tile shapes and launch parameters, and the batched-SCF slot
+count.
 
-The library exposes its launch choices as named knobs (df_tune_set / df_tune_get):
-the tcgen05 GEMM's shared-memory ring depth, the K-dimension splits of the exchange
-SYRK (tensor-core and FP64), and the auxiliary-row slice of J's second pass.  This module
-times df_jk with CUDA events on the caller's stream for candidate values (coordinate
-descent: one knob at a time, keeping the best), and stores the winners in a JSON cache
-keyed by a problem-size bucket, so later runs of the same size class reuse them.
+The library exposes its launch choices as named knobs (df_tune_set / df_tune_get): tile
+shapes (the FP64 half-transform's column tile, the tcgen05 half-transform's tile width, the
+auxiliary rows per CTA of J's first pass and per slice of its second), the tcgen05 GEMM's
+shared-memory ring depth and the K-dimension splits of the exchange SYRK (tensor-core and
+FP64).  This module times df_jk with CUDA events on the caller's stream for candidate
+values (coordinate descent: one knob at a time, keeping the best), and stores the winners in
+a JSON cache keyed by a problem-size bucket, so later runs of the same size class reuse
+them.  `python -m paper_2506_06661_gb300.tune` fills the buckets of the batched workload's
+size range (nao 50-400) in both precisions.
 """
 from __future__ import annotations
 
@@ -20,10 +24,19 @@ from . import _check, lib
 
 CACHE = os.environ.get("DFSCF_TUNE_CACHE", os.path.join(os.path.dirname(os.path.abspath(__file__)), "tune_cache.json"))
 
+# Launch parameters and tile shapes searched per precision: FP64 half-transform tile columns,
+# tcgen05 half-transform tile width (0 = widest that fits) and ring depth, K-dimension splits
+# of the exchange SYRK, auxiliary rows per slice / per CTA of J's passes.
 CANDIDATES = {
-    "fp64": {"fp64_syrk_split": [0, 4, 9, 18, 36], "jpass2_rows": [128, 256, 512]},
-    "mixed": {"umma_max_stages": [2, 3, 4], "syrk_split": [0, 16, 44, 88, 176], "jpass2_rows": [128, 256, 512]},
+    "fp64": {"fp64_ht_cols": [16, 32], "fp64_syrk_split": [0, 4, 9, 18, 36], "jpass2_rows": [128, 256, 512],
+             "jpass1_rows": [1, 2]},
+    "mixed": {"ht_n": [0, 64, 128], "syrk_bk": [32, 16], "umma_max_stages": [2, 4, 8], "syrk_split": [0, 16, 44, 88, 176],
+              "jpass2_rows": [128, 256, 512], "jpass1_rows": [1, 2]},
 }
+
+# Representative molecules of the batched workload's size range (nao 50-400): one per
+# power-of-two bucket of nao.
+BUCKET_CENTRES = (10, 20, 40, 80)
 
 
 def set_knob(name: str, value: int) -> None:
@@ -130,3 +143,36 @@ def tune_batch_slots(mols, precision: str = "mixed", candidates=(16, 32, 64), sa
     cache[f"batch:{precision}"] = {"slots": best, "molecules_per_s": out}
     save_cache(cache)
     return {"slots": best, "molecules_per_s": out}
+
+
+def tune_buckets(precision: str = "mixed", centres=BUCKET_CENTRES, reps: int = 3, log=None) -> dict:
+    """Tune the knobs for one representative molecule per size bucket (seed 0, one centre per
+    10 bohr^3, core-guess density) and store each bucket's winners in the cache."""
+    import gen
+    import paper_2506_06661_gb300 as dfscf
+    out = {}
+    for n in centres:
+        mol = gen.make_molecule(n, gen.molecules.box_for(n), 0)
+        md = dfscf.MoleculeOnDevice(mol)
+        L = dfscf.metric_chol(mol.aux_xyz, mol.aux_exp)
+        B = dfscf.build_B(mol.ao_xyz, mol.ao_exp, mol.aux_xyz, mol.aux_exp, L, precision)
+        C, D, *_ = dfscf.core_guess(md)
+        res = tune_and_store(B, D, C, mol.nocc, precision, reps, log)
+        out[res["key"]] = res
+        del B
+    return out
+
+
+def apply_for_molecules(mols, precision: str) -> dict:
+    """Apply the cached knobs of the bucket of the largest molecule (it dominates the work of
+    a batch); returns them ({} when that bucket is not cached)."""
+    big = max(mols, key=lambda m: m.nao)
+    return apply(bucket(big.nao, big.naux, big.nelec // 2, precision))
+
+
+if __name__ == "__main__":
+    import sys
+    for prec in ("mixed", "fp64"):
+        for k, v in tune_buckets(prec, log=print).items():
+            print(k, v["knobs"], f"{v['baseline_ms']:.3f} -> {v['ms']:.3f} ms", flush=True)
+    sys.exit(0)

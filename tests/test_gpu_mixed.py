@@ -107,3 +107,27 @@ def test_mixed_scf_energy_within_1e6(c0, c0_scf):
     r = dfscf.scf_run(c0, precision="mixed")
     assert r.converged and r.fp64_iterations >= 2
     assert abs(r.energy - c0_scf.energy) <= 1e-6
+
+
+@pytest.mark.parametrize("n", [13, 27])
+def test_syrk_k_box_16_matches_default(n):
+    """The exchange SYRK with 16-element K boxes (32-byte swizzle, a deeper ring; knob
+    syrk_bk) issues the same plane products in the same order as the 32-element boxes: K must
+    agree to FP32-partial rounding and stay within the mixed tolerance of the FP64 oracle."""
+    m = gen.make_molecule(n, gen.molecules.box_for(n), 31)
+    sysm = oscf.build_system(m)
+    rng = np.random.default_rng(n)
+    C = 0.3 * rng.standard_normal((m.nao, max(2, m.nocc)))
+    L = dfscf.metric_chol(m.aux_xyz, m.aux_exp)
+    B = dfscf.build_B(m.ao_xyz, m.ao_exp, m.aux_xyz, m.aux_exp, L, "mixed")
+    old = dfscf.lib().df_tune_get(b"syrk_bk")
+    try:
+        assert dfscf.lib().df_tune_set(b"syrk_bk", 32) == 0
+        _, K32 = dfscf.jk(B, None, C, precision="mixed", want_j=False)
+        assert dfscf.lib().df_tune_set(b"syrk_bk", 16) == 0
+        _, K16 = dfscf.jk(B, None, C, precision="mixed", want_j=False)
+    finally:
+        dfscf.lib().df_tune_set(b"syrk_bk", old)
+    Ko = oracle.df_k(sysm.B, m.nao, C)
+    assert rel(K16, K32.cpu().numpy()) <= 1e-6
+    assert rel(K16, Ko) <= 2e-6 and rel(K32, Ko) <= 2e-6
