@@ -317,6 +317,10 @@ def run_ours(args):
         else:
             got = tune.apply(key)
             knobs[prec] = {"bucket": key, "source": "tune cache" if got else "defaults", **got}
+    for kv in args.knob:
+        name, val = kv.split("=")
+        tune.set_knob(name, int(val))
+        knobs.setdefault("forced", {})[name] = int(val)
     work64 = dfscf.JKWorkspace(nao, naux, nocc, "fp64")
 
     with ClockSampler(local) as clk:
@@ -340,14 +344,15 @@ def run_ours(args):
         if r:
             rl[name] = r
     dominant = max(rl.values(), key=lambda r: r["avg_ms"] * r["launches"]) if rl else None
-    # DRAM traffic of the FP64 half-transform: the ncu capture of the same kernel on the
-    # 80-centre workload read 771.98 MB and wrote 144.12 MB against 926.0 MB of algorithmic
-    # bytes (B read once, X written once); traffic grows with those bytes, so one launch here
-    # moves that ratio times its own algorithmic bytes
+    # DRAM traffic of the FP64 half-transform: the ncu capture of the same kernel (32
+    # occupied columns per CTA, the variant this workload runs) on the 80-centre workload
+    # read 772.81 MB and wrote 144.74 MB against 926.0 MB of algorithmic bytes (B read once,
+    # X written once); traffic grows with those bytes, so one launch here moves that ratio
+    # times its own algorithmic bytes
     if dominant and dominant["kernel"] == "k_halftransform_fp64":
         ht_bytes = 8.0 * naux * dfscf.lib().df_B_ld(nao) + 8.0 * nao * naux * nocc
         m80_bytes = 8.0 * 1200 * dfscf.lib().df_B_ld(400) + 8.0 * 400 * 1200 * 40
-        dominant["traffic"] = (771.981056e6 + 144.117504e6) / m80_bytes * ht_bytes
+        dominant["traffic"] = (772.808448e6 + 144.741120e6) / m80_bytes * ht_bytes
         dominant["traffic_source"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of the 80-centre capture, "
                                       "scaled by the algorithmic bytes of this launch")
 
@@ -396,6 +401,7 @@ def run_ours(args):
                  "phase_ms": {k: v[0] / max(v[1], 1) for k, v in profm.items()}}
 
     scf = None
+    tune.reset()  # the SCF and batch blocks do not inherit this workload's launch knobs
     if not args.no_scf:
         scf = {"what": "wall time of scf_run to |dE| < 1e-8 Eh and max|e| < 1e-5 (integrals, metric, B and the "
                        "iterations), mixed precision against plain FP64, same molecule and options"}
@@ -407,7 +413,7 @@ def run_ours(args):
         mols = gen.batch_molecules(args.nmol, 10, 80, 1)
         devs = [dfscf.MoleculeOnDevice(m) for m in mols]
         from paper_2506_06661_gb300 import tune
-        batch_knobs = tune.apply_for_molecules(mols, "mixed")
+        batch_knobs = tune.apply_batch("mixed")
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         res = dfscf.scf_run_batch(devs, slots=args.batch_slots, precision="mixed", raise_on_noconv=False).results
@@ -506,9 +512,18 @@ def run_scenario_batch(args):
         else:
             t = tune.tune_batch_slots(mols, precision="mixed", candidates=(16, 32, 64), sample=64)
             slots, src = int(t["slots"]), f"tuned now on 64 molecules: {t['molecules_per_s']}"
+    if args.tune:
+        tune.tune_batch_knobs(mols, "mixed", slots=slots, log=print)
+    knobs = tune.apply_batch("mixed")
     out = {"scenario": "batch", "molecules": len(mols), "centres": "10-80 (uniform, seed 1)",
-           "nao_range": [min(m.nao for m in mols), max(m.nao for m in mols)], "slots": slots, "slots_source": src}
+           "nao_range": [min(m.nao for m in mols), max(m.nao for m in mols)], "slots": slots, "slots_source": src,
+           "knobs": knobs or "library defaults"}
     per_mol = {}
+    if args.stability:
+        # lowest orbital-Hessian eigenvalue of every converged solution (Davidson), in the dump
+        dfscf.lib().df_tune_set(b"stability", args.stability)
+        out["stability"] = (f"{args.stability}: the times include the Davidson Hessian products"
+                            + (" and the iterations after each saddle escape" if args.stability == 2 else ""))
     for prec in ("mixed",) + (("fp64",) if args.batch_fp64 else ()):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -538,7 +553,8 @@ def run_scenario_batch(args):
                 r = res[i]
                 row[prec] = {"energy": r.energy, "iterations": r.iterations, "fp64_iterations": r.fp64_iterations,
                              "converged": r.converged, "last_dE": r.last_de, "last_err": r.last_err,
-                             "homo": r.homo, "lumo": r.lumo}
+                             "homo": r.homo, "lumo": r.lumo, "hess_min": r.hess_min,
+                             "stability_restarts": r.stability_restarts}
             rows.append(row)
         with open(args.dump, "w") as fh:
             json.dump(rows, fh)
@@ -597,7 +613,10 @@ def run_scenario_states(args):
     the batched workload, each tested by perturbation: the converged occupied orbitals are
     rotated by a small random angle into the virtual space (in the orthonormal basis of the
     overlap) and the FP64 SCF restarts from that determinant.  A local minimum comes back to
-    its energy; a saddle point falls to a lower one."""
+    its energy; a saddle point falls to a lower one.  The lowest orbital-Hessian eigenvalue of
+    each solution (Davidson, knob "stability") is reported beside it: a small positive value is
+    a soft mode, along which a loosely converged gradient leaves an energy error of about
+    |g|^2 / (2 hess_min)."""
     import torch
     import gen
     import paper_2506_06661_gb300 as dfscf
@@ -605,6 +624,7 @@ def run_scenario_states(args):
     sizes = gen.molecules.batch_sizes(256, 10, 80, 1)
     rng = np.random.default_rng(7)
     out = []
+    dfscf.lib().df_tune_set(b"stability", 1)
     for i in idx:
         n = int(sizes[i])
         mol = gen.make_molecule(n, gen.molecules.box_for(n), (1, i))
@@ -630,10 +650,11 @@ def run_scenario_states(args):
                 probes.append({"energy": rp.energy, "converged": rp.converged, "iterations": rp.iterations})
             lower = [p["energy"] for p in probes if p["converged"] and p["energy"] < r.energy - 1e-6]
             row[prec] = {"energy": r.energy, "converged": r.converged, "iterations": r.iterations,
-                         "probes": probes, "minimum": not lower, "lowest_probe": min([p["energy"] for p in probes])}
+                         "hess_min": r.hess_min, "last_err": r.last_err, "probes": probes, "minimum": not lower, "lowest_probe": min([p["energy"] for p in probes])}
         row["dE_mixed_minus_fp64"] = row["mixed"]["energy"] - row["fp64"]["energy"]
         out.append(row)
         print(json.dumps(row), flush=True)
+    dfscf.lib().df_tune_set(b"stability", 0)
     return 0
 
 
@@ -661,6 +682,10 @@ def main():
     ap.add_argument("--nmol", type=int, default=256)
     ap.add_argument("--slots", type=int, default=0, help="molecules in flight (0: the autotuner's choice)")
     ap.add_argument("--tune", action="store_true", help="run the autotuner and store its winners in the cache")
+    ap.add_argument("--knob", action="append", default=[], metavar="NAME=VALUE",
+                    help="set a launch knob after the cached ones (repeatable)")
+    ap.add_argument("--stability", type=int, default=0, choices=[0, 1, 2],
+                    help="batch scenario: stability analysis of every converged solution (2: also leave saddles)")
     ap.add_argument("--batch-fp64", action="store_true")
     ap.add_argument("--ntrain", type=int, default=20000)
     ap.add_argument("--neval", type=int, default=512)

@@ -239,6 +239,11 @@ typedef struct {
   int converged;        /* 1 if both thresholds were met                          */
   int guess;            /* 0 core guess, 1 dm0 used, 2 dm0 rejected -> core guess */
   int nmo;              /* orbitals kept by canonical orthogonalisation           */
+  double hess_min;      /* lowest orbital-Hessian eigenvalue at the solution (knob
+                           "stability" >= 1; NaN otherwise): > 0 a local minimum over
+                           closed-shell determinants, < 0 a saddle point          */
+  int stability_restarts; /* saddle points left along their negative mode (knob
+                           "stability" = 2)                                       */
 } scf_result;
 
 void scf_default_opts(scf_opts* opt);
@@ -429,16 +434,25 @@ int df_j_noalloc(const void* B, int nao, int naux, const double* D, double* J, c
  * of 16), "jpass1_rows" (1, 2, 4 or 8 auxiliary rows per CTA of J's first pass) and
  * "j_fp64_fma" (1: J's passes with FP64 FMAs instead of double-float products).
  * "mixed_incremental" (0 or 1), "soscf" (0 or 1) and "soscf_cg" (1..64) shape the SCF as
- * described at scf_run; "dm0_eig_cut" (1..16, default 12) drops natural occupations of a
+ * described at scf_run; "stability" (0, 1 or 2) finds the lowest eigenvalue of
+ * the orbital Hessian of every converged solution by Davidson's method with the
+ * eps_a - eps_i preconditioner, to a residual below 1e-6 or at most "stability_steps"
+ * (2..400, default 60) Hessian products (scf_result.hess_min; the products use the SCF's
+ * precision, one J and two exchange builds each); with 2, a solution whose
+ * hess_min is below -1e-4 (a saddle point) is turned by 0.3 rad along the Ritz vector of that
+ * eigenvalue and the SCF goes on from there in FP64 (Newton steps when "soscf" is on) with a
+ * fresh max_cycle budget, at most three times (scf_result.stability_restarts); "dm0_eig_cut" (1..16, default 12) drops natural occupations of a
  * non-idempotent dm0 below 10^-cut of the largest from its first exchange.  Two more knobs bound the multi-SM eigensolver's grid barriers:
  * "eig_barrier_polls" (256..2^30 polls before a wait gives up with DF_ERR_TIMEOUT; default 2^22, about a second) and "eig_barrier_extra"
  * (0 or 1; 1 makes every barrier wait for one arrival that never comes, so that a test can
  * watch the bounded wait run out; leave it 0).  Host-side process-wide state: change
  * knobs only between calls and re-query *_work_bytes afterwards (split counts size the
  * workspaces).  df_tune_set returns DF_ERR_ARG for an unknown name or an out-of-range value;
- * df_tune_get returns -1 for an unknown name.                                              */
+ * df_tune_get returns -1 for an unknown name; df_tune_reset puts every knob back to its
+ * built-in value.                                                                           */
 int df_tune_set(const char* name, int value);
 int df_tune_get(const char* name);
+void df_tune_reset(void);
 
 /* ---- bounds-checking build -------------------------------------------------------------
  * A build of this library with -DDFSCF_BOUNDS_CHECK (libdfscf_bounds.so) checks the global

@@ -56,7 +56,8 @@ class ScfResultC(ctypes.Structure):
     _fields_ = [("energy", ctypes.c_double), ("e_nuc", ctypes.c_double), ("homo", ctypes.c_double),
                 ("lumo", ctypes.c_double), ("last_de", ctypes.c_double), ("last_err", ctypes.c_double),
                 ("iterations", ctypes.c_int), ("fp64_iterations", ctypes.c_int), ("converged", ctypes.c_int),
-                ("guess", ctypes.c_int), ("nmo", ctypes.c_int)]
+                ("guess", ctypes.c_int), ("nmo", ctypes.c_int), ("hess_min", ctypes.c_double),
+                ("stability_restarts", ctypes.c_int)]
 
 
 _lib = None
@@ -86,6 +87,7 @@ _SIGS = {
     "df_eigh": (_I, [_VP, _I, _VP, _VP, _VP, _SZ, _VP]),
     "df_tune_set": (_I, [ctypes.c_char_p, _I]),
     "df_tune_get": (_I, [ctypes.c_char_p]),
+    "df_tune_reset": (None, []),
     "df_eigh_lowest_work_bytes": (_SZ, [_I, _I]),
     "df_eigh_lowest": (_I, [_VP, _I, _I, _VP, _VP, _VP, _SZ, _VP]),
     "scf_default_opts": (None, [ctypes.POINTER(ScfOpts)]),
@@ -382,6 +384,8 @@ class SCFResult:
     D: torch.Tensor
     C: torch.Tensor
     mo_energy: torch.Tensor
+    hess_min: float = float("nan")
+    stability_restarts: int = 0
 
 
 class MoleculeOnDevice:
@@ -422,7 +426,7 @@ def scf_run(mol, opts: ScfOpts | None = None, dm0=None, work: torch.Tensor | Non
     if rc != DF_OK and not (rc == DF_ERR_NOCONV and not raise_on_noconv):
         raise DFError(rc, lib().df_last_error().decode())
     return SCFResult(r.energy, r.e_nuc, r.homo, r.lumo, r.last_de, r.last_err, r.iterations, r.fp64_iterations,
-                     bool(r.converged), r.guess, r.nmo, D, C, eps)
+                     bool(r.converged), r.guess, r.nmo, D, C, eps, r.hess_min, r.stability_restarts)
 
 
 def core_guess(mol, lindep: float = 1e-8):
@@ -493,5 +497,6 @@ def scf_run_batch(mols, opts: ScfOpts | None = None, dm0s=None, slots: int = 16,
     if rc != DF_OK and not (rc == DF_ERR_NOCONV and not raise_on_noconv):
         raise DFError(rc, lib().df_last_error().decode())
     out = [SCFResult(r.energy, r.e_nuc, r.homo, r.lumo, r.last_de, r.last_err, r.iterations, r.fp64_iterations,
-                     bool(r.converged), r.guess, r.nmo, None, None, None) for r in res]
+                     bool(r.converged), r.guess, r.nmo, None, None, None, r.hess_min, r.stability_restarts)
+           for r in res]
     return BatchResult(out, Ds)

@@ -122,6 +122,7 @@ namespace dfscf {
 struct Knob {
   const char* name;
   int value, lo, hi;
+  int def = -1;  // the built-in value, recorded at the first df_tune_set / df_tune_reset
 };
 static Knob g_knobs[] = {
     {"umma_max_stages", 8, 2, 8},    // largest shared-memory ring depth of the tcgen05 GEMM (as many as fit)
@@ -139,6 +140,8 @@ static Knob g_knobs[] = {
     {"mixed_incremental", 1, 0, 1},  // mixed SCF: update K from the change of the occupied projector
     {"soscf", 1, 0, 1},              // switch from DIIS to Newton steps when DIIS stalls
     {"soscf_cg", 6, 1, 64},          // conjugate-gradient iterations per Newton step
+    {"stability", 0, 0, 2},          // lowest orbital-Hessian eigenvalue of every converged solution (2: leave saddles)
+    {"stability_steps", 60, 2, 400}, // Hessian products allowed to that analysis (Davidson)
     {"eig_barrier_polls", 1 << 22, 256, 1 << 30},  // polls before a grid-barrier wait of the eigensolver gives up
     {"eig_barrier_extra", 0, 0, 1},  // test hook: 1 = every eigensolver grid barrier waits for one arrival
                                      // that never comes, so its bounded wait runs out
@@ -152,9 +155,24 @@ int knob(const char* name) {
 
 }  // namespace dfscf
 
+namespace dfscf {
+static void record_defaults() {
+  static bool done = false;
+  if (done) return;
+  for (auto& k : g_knobs) k.def = k.value;
+  done = true;
+}
+}  // namespace dfscf
+
+extern "C" void df_tune_reset(void) {
+  dfscf::record_defaults();
+  for (auto& k : dfscf::g_knobs) k.value = k.def;
+}
+
 extern "C" int df_tune_set(const char* name, int value) {
   dfscf::clear_error();
   if (!name) return DF_ERR_ARG;
+  dfscf::record_defaults();
   for (auto& k : dfscf::g_knobs)
     if (strcmp(k.name, name) == 0) {
       if (value < k.lo || value > k.hi) {

@@ -30,6 +30,7 @@
 namespace dfscf {
 
 constexpr int DIIS_MAX = 16;
+constexpr int kDavidsonMax = 24;  // subspace of the stability analysis (vectors)
 
 struct ScfStatus {
   double energy;
@@ -602,6 +603,7 @@ struct ScfWork {
   double *Fbar, *Call, *Call2, *Fmo, *Lv, *cg_g, *cg_h, *cg_x, *cg_r, *cg_z, *cg_p, *cg_Ap, *Lf, *Lfp, *Lfm, *dD,
       *dJ, *dK1, *dK2, *cg_s, *kk, *kVrow, *ksig, *Pc, *Ps, *Pd, *ktmp, *KPdK;
   int* k_status;
+  double* dav;  // Davidson subspace of the stability analysis: V, H V [kDavidsonMax][nvir * nocc], dots
   void* eig_aux;  // p vector and grid barrier of the multi-SM eigensolver
   ScfStatus* st;
   DiisState* diis;
@@ -692,6 +694,7 @@ static void scf_layout(int nao, int naux, int nocc, int precision, Arena* a, Siz
     TAKE(double, w->ktmp, vo);
     TAKE(double, w->KPdK, nn);
     TAKE(int, w->k_status, 1);
+    TAKE(double, w->dav, (size_t)2 * kDavidsonMax * vo + kDavidsonMax);
   }
   TAKE(ScfStatus, w->st, 1);
   TAKE(DiisState, w->diis, 1);
@@ -771,6 +774,7 @@ struct ScfMol {
   double inc_best = INFINITY;
   int inc_stall = 0;
   bool done = false;
+  int iter_limit = 0;         // iterations allowed so far (max_cycle, renewed by a saddle escape)
   int rc = DF_OK;
   cudaGraphExec_t graph[3] = {nullptr, nullptr, nullptr};
   scf_result res{};
@@ -1074,6 +1078,8 @@ static int soscf_hessian(ScfMol& M, const double* v, double* Av, int hprec) {
   return DF_OK;
 }
 
+static int rotate_orbitals(ScfMol& M);
+
 // One Newton step from the Fock matrix F' (W.Fo) of the current orbitals C'_all: CG on
 // H kappa = -F_vo, capped step, exact rotation of C'_all, new C_occ and D.
 static int soscf_step(ScfMol& M) {
@@ -1121,7 +1127,16 @@ static int soscf_step(ScfMol& M) {
   DF_LAUNCHED("absmax_kernel");
   cap_step_kernel<<<blocks_for(nvo), 256, 0, s>>>(W.cg_x, nvo, W.cg_s, 0.3);
   DF_LAUNCHED("cap_step_kernel");
-  // exact rotation by exp(kappa)
+  return rotate_orbitals(M);
+}
+
+// C'_all <- C'_all exp(A) with A = [[0, -k^T], [k, 0]] and k = W.cg_x [nvir][nocc] (exact, from
+// the eigen-decomposition of k^T k), then the new C_occ and D.
+static int rotate_orbitals(ScfMol& M) {
+  ScfWork& W = M.W;
+  cudaStream_t s = M.s;
+  const int nmo = M.nmo, nocc = M.nocc, nvir = nmo - nocc;
+  const long ne = (long)nmo * nmo;
   DF_TRY(dgemm(true, false, nocc, nocc, nvir, 1.0, W.cg_x, nocc, 0, W.cg_x, nocc, 0, 0.0, W.kk, nocc, 0, 1, s, 0, 0));
   DF_TRY(eigh_rows(W.kk, nocc, W.ksig, W.kVrow, W.eig_scratch, W.k_status, s));
   rotation_mats_kernel<<<blocks_for((long)nocc * nocc), 256, 0, s>>>(W.kVrow, W.ksig, nocc, W.Pc, W.Ps, W.Pd);
@@ -1148,6 +1163,267 @@ static int soscf_step(ScfMol& M) {
   }
   DF_CUDA(cudaMemcpyAsync(W.Call, W.Call2, sizeof(double) * ne, cudaMemcpyDeviceToDevice, s));
   return occupied_from_all(M);
+}
+
+// ---- stability analysis ---------------------------------------------------------------------
+// The lowest eigenvalue of the orbital Hessian at a converged solution (the operator of the
+// Newton steps, in units of the gradient F_vo): positive at a local minimum of the energy over
+// closed-shell determinants, negative at a saddle point.  Davidson's method on the canonical
+// orbitals of the last Fock matrix (the converged ones: F and D commute there): the subspace
+// holds the search vectors V and their products H V; the Rayleigh-Ritz matrix V^T H V is
+// diagonalised on the host (cyclic Jacobi, at most kDavidsonMax rows); the correction is the
+// residual divided by (eps_a - eps_i - theta), the diagonal of the Hessian's one-electron part.
+// The start block is the unit vectors of the smallest eps_a - eps_i and one fixed
+// pseudo-random vector (so that a mode of another symmetry than the lowest excitations is
+// still reached).  A full subspace collapses onto the current Ritz vector.
+
+constexpr int kDavidsonStart = 3; // start block: two lowest excitations + one pseudo-random
+
+__global__ void scale_copy_kernel(const double* __restrict__ x, double* __restrict__ y, long n,
+                                  const double* __restrict__ nrm2) {
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = *nrm2 > 0.0 ? x[i] / sqrt(*nrm2) : 0.0;
+}
+
+// w -= c v with c = *cp (device scalar).
+__global__ void axpy_dev_kernel(double* __restrict__ w, const double* __restrict__ v, long n,
+                                const double* __restrict__ cp) {
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) w[i] -= (*cp) * v[i];
+}
+
+// t = r / (eps_a - eps_i - theta), the denominator kept at least 1e-3 away from zero.
+__global__ void davidson_precond_kernel(const double* __restrict__ Fmo, int nmo, int nocc,
+                                        const double* __restrict__ r, double theta, double* __restrict__ t) {
+  const long q = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int nvir = nmo - nocc;
+  if (q >= (long)nvir * nocc) return;
+  const int a = (int)(q / nocc), i = (int)(q % nocc);
+  double d = Fmo[DF_IX((size_t)(nocc + a) * nmo + nocc + a, (size_t)nmo * nmo)] -
+             Fmo[DF_IX((size_t)i * nmo + i, (size_t)nmo * nmo)] - theta;
+  if (fabs(d) < 1e-3) d = d < 0.0 ? -1e-3 : 1e-3;
+  t[q] = r[q] / d;
+}
+
+// eps_a - eps_i for every (virtual, occupied) pair.
+__global__ void excitation_diag_kernel(const double* __restrict__ Fmo, int nmo, int nocc, double* __restrict__ d) {
+  const long q = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int nvir = nmo - nocc;
+  if (q >= (long)nvir * nocc) return;
+  const int a = (int)(q / nocc), i = (int)(q % nocc);
+  d[q] = Fmo[DF_IX((size_t)(nocc + a) * nmo + nocc + a, (size_t)nmo * nmo)] -
+         Fmo[DF_IX((size_t)i * nmo + i, (size_t)nmo * nmo)];
+}
+
+// Lowest eigenpair of a symmetric k x k matrix (row-major, k <= kDavidsonMax) by cyclic
+// Jacobi rotations.
+static double sym_lowest(std::vector<double> T, int k, std::vector<double>& vec) {
+  std::vector<double> V((size_t)k * k, 0.0);
+  for (int i = 0; i < k; ++i) V[(size_t)i * k + i] = 1.0;
+  for (int sweep = 0; sweep < 60; ++sweep) {
+    double off = 0.0, diag = 0.0;
+    for (int p = 0; p < k; ++p) {
+      diag += T[(size_t)p * k + p] * T[(size_t)p * k + p];
+      for (int q = p + 1; q < k; ++q) off += T[(size_t)p * k + q] * T[(size_t)p * k + q];
+    }
+    if (off <= 1e-30 * std::max(diag, 1e-300)) break;
+    for (int p = 0; p < k; ++p)
+      for (int q = p + 1; q < k; ++q) {
+        const double apq = T[(size_t)p * k + q];
+        if (apq == 0.0) continue;
+        const double theta = (T[(size_t)q * k + q] - T[(size_t)p * k + p]) / (2.0 * apq);
+        const double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+        const double c = 1.0 / sqrt(t * t + 1.0), sn = t * c;
+        for (int r = 0; r < k; ++r) {  // T <- T G (columns p, q)
+          const double tp = T[(size_t)r * k + p], tq = T[(size_t)r * k + q];
+          T[(size_t)r * k + p] = c * tp - sn * tq;
+          T[(size_t)r * k + q] = sn * tp + c * tq;
+        }
+        for (int r = 0; r < k; ++r) {  // T <- G^T T (rows p, q)
+          const double tp = T[(size_t)p * k + r], tq = T[(size_t)q * k + r];
+          T[(size_t)p * k + r] = c * tp - sn * tq;
+          T[(size_t)q * k + r] = sn * tp + c * tq;
+        }
+        for (int r = 0; r < k; ++r) {  // V <- V G
+          const double vp = V[(size_t)r * k + p], vq = V[(size_t)r * k + q];
+          V[(size_t)r * k + p] = c * vp - sn * vq;
+          V[(size_t)r * k + q] = sn * vp + c * vq;
+        }
+      }
+  }
+  int lo = 0;
+  for (int i = 1; i < k; ++i)
+    if (T[(size_t)i * k + i] < T[(size_t)lo * k + lo]) lo = i;
+  vec.resize(k);
+  for (int r = 0; r < k; ++r) vec[r] = V[(size_t)r * k + lo];
+  return T[(size_t)lo * k + lo];
+}
+
+// Orthonormalise w against V[0..m) (classical Gram-Schmidt, two passes, device scalars) and
+// store it normalised as V[m]; *n2 gets its squared norm before the normalisation.
+static int davidson_store(ScfMol& M, double* w, double* V, int m, long nvo, double* n2) {
+  cudaStream_t s = M.s;
+  double* sc = M.W.cg_s;
+  for (int pass = 0; pass < 2; ++pass)
+    for (int i = 0; i < m; ++i) {
+      dot_kernel<<<1, 1024, 0, s>>>(V + (size_t)i * nvo, w, nvo, sc + 14);
+      DF_LAUNCHED("dot_kernel");
+      axpy_dev_kernel<<<blocks_for(nvo), 256, 0, s>>>(w, V + (size_t)i * nvo, nvo, sc + 14);
+      DF_LAUNCHED("axpy_dev_kernel");
+    }
+  dot_kernel<<<1, 1024, 0, s>>>(w, w, nvo, sc + 12);
+  DF_LAUNCHED("dot_kernel");
+  DF_CUDA(cudaMemcpyAsync(n2, sc + 12, sizeof(double), cudaMemcpyDeviceToHost, s));
+  scale_copy_kernel<<<blocks_for(nvo), 256, 0, s>>>(w, V + (size_t)m * nvo, nvo, sc + 12);
+  DF_LAUNCHED("scale_copy_kernel");
+  DF_CUDA(cudaStreamSynchronize(s));
+  return DF_OK;
+}
+
+// mode_scale > 0: also leave mode_scale times the unit Ritz vector of the lowest eigenvalue
+// in W.cg_x, in the (virtual, occupied) basis of the canonical orbitals left in C'_all.
+static int stability_analysis(ScfMol& M, double* hess_min, double mode_scale = 0.0) {
+  ScfWork& W = M.W;
+  cudaStream_t s = M.s;
+  const int nao = M.nao, nmo = M.nmo, nocc = M.nocc, nvir = nmo - nocc;
+  const long ne = (long)nmo * nmo, nvo = (long)nvir * nocc;
+  *hess_min = NAN;
+  if (nvir <= 0) return DF_OK;
+  // canonical orbitals of the last Fock matrix F' (W.Fo)
+  DF_CUDA(cudaMemcpyAsync(W.Fp, W.Fo, sizeof(double) * ne, cudaMemcpyDeviceToDevice, s));
+  DF_TRY(eigh_full_rows(W.Fp, nmo, W.eps, W.ZT, W.eig_scratch, W.eig_status, s, W.eig_aux));
+  DF_TRY(transpose(W.ZT, nmo, nmo, W.Call, s));
+  DF_TRY(occupied_from_all(M));
+  DF_TRY(dgemm(false, false, nmo, nmo, nmo, 1.0, W.Fo, nmo, 0, W.Call, nmo, 0, 0.0, W.T1, nmo, 0, 1, s, 0, 0));
+  DF_TRY(dgemm(true, false, nmo, nmo, nmo, 1.0, W.Call, nmo, 0, W.T1, nmo, 0, 0.0, W.Fmo, nmo, 0, 1, s, 0, 0));
+  DF_TRY(dgemm(false, false, nao, nvir, nmo, 1.0, W.X, nmo, 0, W.Call + nocc, nmo, 0, 0.0, W.Lv, nvir, 0, 1, s, 0, 0));
+  const int kmax = (int)std::min<long>(kDavidsonMax, nvo);
+  const int max_products = std::max(2, knob("stability_steps"));
+  const int hprec = M.opt.precision;
+  double* V = W.dav;                                    // [kDavidsonMax][nvo]
+  double* AV = W.dav + (size_t)kDavidsonMax * nvo;      // [kDavidsonMax][nvo]
+  double* dots = AV + (size_t)kDavidsonMax * nvo;       // [kDavidsonMax]
+  double* x = W.cg_x;
+  double* r = W.cg_r;
+  double* wv = W.cg_Ap;
+  // start block: the two smallest eps_a - eps_i, then a SplitMix64 vector of the index
+  std::vector<double> dia(nvo);
+  excitation_diag_kernel<<<blocks_for(nvo), 256, 0, s>>>(W.Fmo, nmo, nocc, W.cg_h);
+  DF_LAUNCHED("excitation_diag_kernel");
+  DF_CUDA(cudaMemcpyAsync(dia.data(), W.cg_h, sizeof(double) * nvo, cudaMemcpyDeviceToHost, s));
+  DF_CUDA(cudaStreamSynchronize(s));
+  std::vector<long> order(nvo);
+  for (long q = 0; q < nvo; ++q) order[q] = q;
+  const int nlow = (int)std::min<long>(kDavidsonStart - 1, nvo);
+  std::partial_sort(order.begin(), order.begin() + nlow, order.end(),
+                    [&](long p, long q) { return dia[p] < dia[q]; });
+  std::vector<double> h0(nvo);
+  int m = 0;
+  double n2 = 0.0;
+  for (int b = 0; b < kDavidsonStart && m < kmax; ++b) {
+    if (b < nlow) {
+      std::fill(h0.begin(), h0.end(), 0.0);
+      h0[order[b]] = 1.0;
+    } else {
+      for (long i = 0; i < nvo; ++i) {
+        unsigned long long z = 0x9E3779B97F4A7C15ull * (unsigned long long)(i + 1);
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        z ^= z >> 31;
+        h0[i] = (double)(z >> 11) * (1.0 / 9007199254740992.0) - 0.5;
+      }
+    }
+    DF_CUDA(cudaMemcpyAsync(wv, h0.data(), sizeof(double) * nvo, cudaMemcpyHostToDevice, s));
+    DF_TRY(davidson_store(M, wv, V, m, nvo, &n2));
+    if (n2 > 1e-20) m++;
+  }
+  std::vector<double> Hs((size_t)kDavidsonMax * kDavidsonMax, 0.0), hd(kDavidsonMax), y;
+  int have = 0, products = 0;
+  double theta = NAN;
+  for (;;) {
+    for (; have < m; ++have) {  // products and Rayleigh-Ritz entries of the new vectors
+      DF_TRY(soscf_hessian(M, V + (size_t)have * nvo, AV + (size_t)have * nvo, hprec));
+      products++;
+      for (int i = 0; i <= have; ++i) {
+        dot_kernel<<<1, 1024, 0, s>>>(V + (size_t)i * nvo, AV + (size_t)have * nvo, nvo, dots + i);
+        DF_LAUNCHED("dot_kernel");
+      }
+      DF_CUDA(cudaMemcpyAsync(hd.data(), dots, sizeof(double) * (have + 1), cudaMemcpyDeviceToHost, s));
+      DF_CUDA(cudaStreamSynchronize(s));
+      for (int i = 0; i <= have; ++i) Hs[(size_t)i * kDavidsonMax + have] = Hs[(size_t)have * kDavidsonMax + i] = hd[i];
+    }
+    std::vector<double> T((size_t)m * m);
+    for (int i = 0; i < m; ++i)
+      for (int j = 0; j < m; ++j) T[(size_t)i * m + j] = Hs[(size_t)i * kDavidsonMax + j];
+    theta = sym_lowest(T, m, y);
+    // Ritz vector x = V y and residual r = H x - theta x = AV y - theta x
+    DF_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * nvo, s));
+    DF_CUDA(cudaMemsetAsync(r, 0, sizeof(double) * nvo, s));
+    for (int i = 0; i < m; ++i) {
+      axpy_kernel<<<blocks_for(nvo), 256, 0, s>>>(x, V + (size_t)i * nvo, nvo, y[i]);
+      DF_LAUNCHED("axpy_kernel");
+      axpy_kernel<<<blocks_for(nvo), 256, 0, s>>>(r, AV + (size_t)i * nvo, nvo, y[i]);
+      DF_LAUNCHED("axpy_kernel");
+    }
+    axpy_kernel<<<blocks_for(nvo), 256, 0, s>>>(r, x, nvo, -theta);
+    DF_LAUNCHED("axpy_kernel");
+    dot_kernel<<<1, 1024, 0, s>>>(r, r, nvo, W.cg_s + 13);
+    DF_LAUNCHED("dot_kernel");
+    double rr = 0.0;
+    DF_CUDA(cudaMemcpyAsync(&rr, W.cg_s + 13, sizeof(double), cudaMemcpyDeviceToHost, s));
+    DF_CUDA(cudaStreamSynchronize(s));
+    if (M.opt.verbose) printf("stability: %d products, theta %.10f, |r| %.3e\n", products, theta, sqrt(rr));
+    if (sqrt(rr) < 1e-6 * std::max(1.0, fabs(theta)) || products >= max_products || m == nvo) break;
+    if (m == kmax) {  // collapse the subspace onto the Ritz vector and its product
+      DF_CUDA(cudaMemcpyAsync(V, x, sizeof(double) * nvo, cudaMemcpyDeviceToDevice, s));
+      DF_CUDA(cudaMemcpyAsync(wv, r, sizeof(double) * nvo, cudaMemcpyDeviceToDevice, s));
+      axpy_kernel<<<blocks_for(nvo), 256, 0, s>>>(wv, x, nvo, theta);  // H x = r + theta x
+      DF_LAUNCHED("axpy_kernel");
+      DF_CUDA(cudaMemcpyAsync(AV, wv, sizeof(double) * nvo, cudaMemcpyDeviceToDevice, s));
+      Hs[0] = theta;
+      m = have = 1;
+    }
+    davidson_precond_kernel<<<blocks_for(nvo), 256, 0, s>>>(W.Fmo, nmo, nocc, r, theta, wv);
+    DF_LAUNCHED("davidson_precond_kernel");
+    DF_TRY(davidson_store(M, wv, V, m, nvo, &n2));
+    if (!(n2 > 1e-24)) break;  // the correction lies in the subspace: nothing new to add
+    m++;
+  }
+  *hess_min = theta;
+  if (mode_scale > 0.0) {  // x is a unit vector (orthonormal V, unit y)
+    DF_CUDA(cudaMemcpyAsync(wv, x, sizeof(double) * nvo, cudaMemcpyDeviceToDevice, s));
+    DF_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * nvo, s));
+    axpy_kernel<<<blocks_for(nvo), 256, 0, s>>>(x, wv, nvo, mode_scale);
+    DF_LAUNCHED("axpy_kernel");
+  }
+  return DF_OK;
+}
+
+// Escape from a saddle point (knob "stability" = 2): with the Ritz vector u of the negative
+// Hessian eigenvalue in W.cg_x (scaled to the rotation angle), turn the canonical orbitals by
+// exp(u) (the energy falls as 2 hess_min |u|^2 to second order, in Eh) and restart the
+// iterations there with Newton steps (or DIIS from an empty history when they are switched
+// off), in FP64, with a fresh iteration budget.
+constexpr double kSaddleTol = -1e-4;  // hess_min below this is a saddle, not noise
+constexpr double kEscapeAngle = 0.3;  // |u| of the escape rotation (radians)
+constexpr int kMaxEscapes = 3;
+
+static int escape_saddle(ScfMol& M) {
+  DF_TRY(rotate_orbitals(M));
+  diis_reset_kernel<<<1, 32, 0, M.s>>>(M.W.diis, M.opt.diis_space);
+  DF_LAUNCHED("diis_reset_kernel");
+  M.res.converged = 0;
+  M.res.stability_restarts++;
+  M.done = false;
+  M.have_old = false;
+  M.fp64_done = 0;
+  M.prec = DF_FP64;
+  M.switched = true;
+  if (M.inc) M.kp = ScfMol::KP_FINAL;
+  M.soscf = M.soscf_on;
+  M.soscf_pending = false;
+  M.iter_limit = M.res.iterations + M.opt.max_cycle;
+  return DF_OK;
 }
 
 // Everything after J and K: Fock, energy, DIIS error and extrapolation, diagonalisation,
@@ -1408,7 +1684,7 @@ static bool scf_iter_finish_incremental(ScfMol& M, double de) {
   }
   M.e_old = h.energy;
   M.have_old = true;
-  if (M.res.iterations >= o.max_cycle) {
+  if (M.res.iterations >= M.iter_limit) {
     M.rc = DF_ERR_NOCONV;
     set_error("scf: not converged after %d iterations (dE %.3e, max|e| %.3e)", M.res.iterations, M.res.last_de,
               M.res.last_err);
@@ -1508,7 +1784,7 @@ static bool scf_iter_finish(ScfMol& M) {
   }
   M.e_old = h.energy;
   M.have_old = true;
-  if (M.res.iterations >= M.opt.max_cycle) {
+  if (M.res.iterations >= M.iter_limit) {
     M.rc = DF_ERR_NOCONV;
     set_error("scf: not converged after %d iterations (dE %.3e, max|e| %.3e)", M.res.iterations, M.res.last_de,
               M.res.last_err);
@@ -1553,6 +1829,7 @@ static int init_mol(ScfMol& M, const df_molecule* mol, const scf_opts& o, void* 
                     cudaStream_t s) {
   M.mol = *mol;
   M.opt = o;
+  M.iter_limit = o.max_cycle;
   M.nao = mol->nao;
   M.naux = mol->naux;
   M.nocc = mol->nelec / 2;
@@ -1635,24 +1912,32 @@ int scf_run_on(const df_molecule* mol, const scf_opts& o, const double* dm0, dou
   M.C_out = C_out;
   M.mo_out = mo_energy;
   int rc = scf_setup(M);
-  while (rc == DF_OK && !M.done) {
-    const bool dm0_first = M.first_dm0;
-    rc = scf_iter_launch(M, true);
-    if (rc == DF_OK && dm0_first) {
-      rc = cudaStreamSynchronize(s) == cudaSuccess ? scf_dm0_finish(M) : DF_ERR_CUDA;
-      if (rc == DF_ERR_CUDA) set_error("scf_run: %s", cudaGetErrorString(cudaGetLastError()));
+  for (;;) {
+    while (rc == DF_OK && !M.done) {
+      const bool dm0_first = M.first_dm0;
+      rc = scf_iter_launch(M, true);
+      if (rc == DF_OK && dm0_first) {
+        rc = cudaStreamSynchronize(s) == cudaSuccess ? scf_dm0_finish(M) : DF_ERR_CUDA;
+        if (rc == DF_ERR_CUDA) set_error("scf_run: %s", cudaGetErrorString(cudaGetLastError()));
+      }
+      if (rc != DF_OK) break;
+      cudaError_t e = cudaStreamSynchronize(s);
+      if (e != cudaSuccess) {
+        set_error("scf_run: %s", cudaGetErrorString(e));
+        rc = DF_ERR_CUDA;
+        break;
+      }
+      M.done = scf_iter_finish(M);
     }
-    if (rc != DF_OK) break;
-    cudaError_t e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) {
-      set_error("scf_run: %s", cudaGetErrorString(e));
-      rc = DF_ERR_CUDA;
-      break;
-    }
-    M.done = scf_iter_finish(M);
+    if (rc == DF_OK) rc = scf_outputs(M);
+    if (rc == DF_OK && cudaStreamSynchronize(s) != cudaSuccess) rc = DF_ERR_CUDA;
+    M.res.hess_min = NAN;
+    if (!(rc == DF_OK && M.rc == DF_OK && M.res.converged && knob("stability"))) break;
+    const bool follow = knob("stability") >= 2 && M.res.stability_restarts < kMaxEscapes;
+    rc = stability_analysis(M, &M.res.hess_min, follow ? kEscapeAngle : 0.0);
+    if (rc != DF_OK || !follow || !(M.res.hess_min < kSaddleTol)) break;
+    rc = escape_saddle(M);
   }
-  if (rc == DF_OK) rc = scf_outputs(M);
-  if (rc == DF_OK && cudaStreamSynchronize(s) != cudaSuccess) rc = DF_ERR_CUDA;
   *res = M.res;
   cudaFreeHost(hst);
   cudaFreeHost(heps);
@@ -1829,6 +2114,24 @@ extern "C" int scf_run_batch(const df_molecule* mols, int nmol, const scf_opts* 
     if (M->phase == ScfMol::DONE) {
       const int i = slot_index[k];
       if (M->rc == DF_OK || M->rc == DF_ERR_NOCONV) DF_TRY(scf_outputs(*M));
+      M->res.hess_min = NAN;
+      if (M->rc == DF_OK && M->res.converged && knob("stability")) {
+        // the outputs are ordered before the analysis, which only uses the workspace
+        const bool follow = knob("stability") >= 2 && M->res.stability_restarts < kMaxEscapes;
+        int sr = stability_analysis(*M, &M->res.hess_min, follow ? kEscapeAngle : 0.0);
+        if (sr == DF_OK && follow && M->res.hess_min < kSaddleTol) {
+          // a saddle point: turn along its mode and iterate on (the outputs are rewritten
+          // when the molecule finishes again)
+          sr = escape_saddle(*M);
+          if (sr == DF_OK) sr = scf_iter_launch(*M, true);
+          if (sr == DF_OK) {
+            M->phase = ScfMol::ITER;
+            return DF_OK;
+          }
+        }
+        if (sr == DF_ERR_CUDA) return sr;
+        if (sr != DF_OK) M->rc = sr;
+      }
       results[i] = M->res;
       // the region goes back to the pool only once this stream has finished with it: the
       // outputs above are its last work, so wait for them

@@ -8,8 +8,9 @@ shared-memory ring depth and the K-dimension splits of the exchange SYRK (tensor
 FP64).  This module times df_jk with CUDA events on the caller's stream for candidate
 values (coordinate descent: one knob at a time, keeping the best), and stores the winners in
 a JSON cache keyed by a problem-size bucket, so later runs of the same size class reuse
-them.  `python -m paper_2506_06661_gb300.tune` fills the buckets of the batched workload's
-size range (nao 50-400) in both precisions.
+them.  Batched SCF has its own entry, tuned on molecules/s with many molecules in flight.
+`python -m paper_2506_06661_gb300.tune` fills the buckets of the batched workload's size
+range (nao 50-400) in both precisions and the batched-SCF entry.
 """
 from __future__ import annotations
 
@@ -37,6 +38,16 @@ CANDIDATES = {
 # Representative molecules of the batched workload's size range (nao 50-400): one per
 # power-of-two bucket of nao.
 BUCKET_CENTRES = (10, 20, 40, 80)
+
+
+# Knobs searched for batched-SCF throughput (many molecules in flight share the SMs, so the
+# best single-molecule launch shapes are not the best here).
+BATCH_CANDIDATES = {"syrk_split": [0, 44], "umma_max_stages": [8, 2], "ht_n": [0, 128], "jpass1_rows": [1, 2]}
+
+
+def reset() -> None:
+    """Every knob back to its built-in value."""
+    lib().df_tune_reset()
 
 
 def set_knob(name: str, value: int) -> None:
@@ -140,9 +151,56 @@ def tune_batch_slots(mols, precision: str = "mixed", candidates=(16, 32, 64), sa
         out[s] = len(devs) / (time.perf_counter() - t0)
     best = max(out, key=out.get)
     cache = load_cache()
-    cache[f"batch:{precision}"] = {"slots": best, "molecules_per_s": out}
+    entry = cache.get(f"batch:{precision}", {})
+    entry.update({"slots": best, "molecules_per_s": out})
+    cache[f"batch:{precision}"] = entry
     save_cache(cache)
     return {"slots": best, "molecules_per_s": out}
+
+
+def tune_batch_knobs(mols, precision: str = "mixed", slots: int = 128, sample: int = 64, log=None) -> dict:
+    """Coordinate descent over BATCH_CANDIDATES on the molecules/s of scf_run_batch over a
+    sample (from the built-in values; a change must gain 3%); stored as the "knobs" of the
+    cache entry "batch:<precision>"."""
+    import time
+    import paper_2506_06661_gb300 as dfscf
+    devs = [dfscf.MoleculeOnDevice(m) for m in mols[:sample]]
+    reset()
+
+    def rate():
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        dfscf.scf_run_batch(devs, slots=slots, precision=precision, raise_on_noconv=False)
+        torch.cuda.synchronize()
+        return len(devs) / (time.perf_counter() - t0)
+
+    rate()  # first run: graph capture and lazy module loads
+    best = {k: get_knob(k) for k in BATCH_CANDIDATES}
+    base = best_rate = rate()
+    for name, values in BATCH_CANDIDATES.items():
+        for v in values:
+            if v == best[name]:
+                continue
+            set_knob(name, v)
+            r = rate()
+            if log:
+                log(f"  batch {name}={v}: {r:.3f} molecules/s")
+            if r > best_rate * 1.03:
+                best_rate, best[name] = r, v
+            set_knob(name, best[name])
+    cache = load_cache()
+    entry = cache.get(f"batch:{precision}", {})
+    entry.update({"knobs": best, "molecules_per_s_sample": best_rate, "baseline_per_s_sample": base,
+                  "sample": len(devs), "slots_tuned_with": slots})
+    cache[f"batch:{precision}"] = entry
+    save_cache(cache)
+    return entry
+
+
+def apply_batch(precision: str = "mixed") -> dict:
+    """Built-in knob values, then those stored for batched SCF ({} when none are cached)."""
+    reset()
+    return apply(f"batch:{precision}")
 
 
 def tune_buckets(precision: str = "mixed", centres=BUCKET_CENTRES, reps: int = 3, log=None) -> dict:
@@ -172,7 +230,11 @@ def apply_for_molecules(mols, precision: str) -> dict:
 
 if __name__ == "__main__":
     import sys
+    import gen
     for prec in ("mixed", "fp64"):
         for k, v in tune_buckets(prec, log=print).items():
             print(k, v["knobs"], f"{v['baseline_ms']:.3f} -> {v['ms']:.3f} ms", flush=True)
+    e = tune_batch_knobs(gen.batch_molecules(256, 10, 80, 1), "mixed", log=print)
+    print("batch:mixed", e["knobs"], f"{e['baseline_per_s_sample']:.3f} -> {e['molecules_per_s_sample']:.3f} "
+          "molecules/s", flush=True)
     sys.exit(0)

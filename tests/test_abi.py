@@ -68,6 +68,14 @@ def test_tuning_knobs_host_side():
     finally:
         tune.set_knob("jpass2_rows", 256)
     assert tune.bucket(1500, 4500, 150, "mixed") == "mixed:nao2048:naux8192:nocc256"
+    # df_tune_reset restores every knob's built-in value
+    defaults = {k: L.df_tune_get(k.encode()) for k in ("syrk_split", "umma_max_stages", "stability")}
+    tune.set_knob("syrk_split", 44)
+    tune.set_knob("umma_max_stages", 2)
+    tune.set_knob("stability", 2)
+    tune.reset()
+    assert {k: L.df_tune_get(k.encode()) for k in defaults} == defaults == {
+        "syrk_split": 0, "umma_max_stages": 8, "stability": 0}
 
 
 def test_header_is_plain_c_and_links():
