@@ -402,6 +402,10 @@ def run_ours(args):
 
     scf = None
     tune.reset()  # the SCF and batch blocks do not inherit this workload's launch knobs
+    # nor its device memory: B alone holds 40.5 GB (FP64) plus the BF16 planes
+    B = work64 = workm = Jm = Km = J6 = K6 = None
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
     if not args.no_scf:
         scf = {"what": "wall time of scf_run to |dE| < 1e-8 Eh and max|e| < 1e-5 (integrals, metric, B and the "
                        "iterations), mixed precision against plain FP64, same molecule and options"}

@@ -479,6 +479,8 @@ def scf_run_batch(mols, opts: ScfOpts | None = None, dm0s=None, slots: int = 16,
         # the largest molecule, capped at 85% of the free device memory (it needs one)
         nb = int(lib().scf_batch_work_bytes(arr, n, o.precision, slots))
         largest = int(lib().scf_batch_work_bytes(arr, n, o.precision, 1))
+        # blocks torch still caches (an earlier batch's workspace) count as free
+        torch.cuda.empty_cache()
         free = torch.cuda.mem_get_info()[0]
         work = _work(max(largest, min(nb, int(0.85 * free))))
     dm0_t = None

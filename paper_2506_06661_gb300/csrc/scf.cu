@@ -694,7 +694,7 @@ static void scf_layout(int nao, int naux, int nocc, int precision, Arena* a, Siz
     TAKE(double, w->ktmp, vo);
     TAKE(double, w->KPdK, nn);
     TAKE(int, w->k_status, 1);
-    TAKE(double, w->dav, (size_t)2 * kDavidsonMax * vo + kDavidsonMax);
+    TAKE(double, w->dav, (size_t)2 * kDavidsonMax * vo + (size_t)kDavidsonMax * kDavidsonMax + 8);
   }
   TAKE(ScfStatus, w->st, 1);
   TAKE(DiisState, w->diis, 1);
@@ -740,6 +740,14 @@ static int diagonalize_fock(const double* Fm, int nao, int nmo, int nocc, ScfWor
 }
 
 // ---- one molecule's SCF state machine ----------------------------------------------------------
+// Host state of the stability analysis (Davidson; see dav_begin / dav_advance).
+struct DavState {
+  enum Stage { OFF, RITZ, CHECK, NORM } stage = OFF;
+  int m = 0, have = 0, row0 = 0, products = 0, kmax = 0, max_products = 0;
+  double theta = NAN, mode_scale = 0.0;
+  std::vector<double> Hs, y;
+};
+
 struct ScfMol {
   df_molecule mol{};
   scf_opts opt{};
@@ -784,10 +792,14 @@ struct ScfMol {
   double* mo_out = nullptr;
   // Set-up runs as asynchronous phases so that a batch never blocks on one molecule:
   // SETUP (integrals, metric, B, eig(S) enqueued) -> ORTHO (host reads eig(S)) ->
-  // GUESS_CHECK (only with dm0) -> READY -> ITER (an iteration is in flight) -> DONE.
-  enum Phase { SETUP, GUESS_CHECK, READY, DM0_EIG, ITER, DONE } phase = SETUP;
+  // GUESS_CHECK (only with dm0) -> READY -> ITER (an iteration is in flight) -> [STAB (the
+  // stability analysis, knob "stability"; back to ITER after a saddle escape)] -> DONE.
+  enum Phase { SETUP, GUESS_CHECK, READY, DM0_EIG, ITER, STAB, DONE } phase = SETUP;
+  bool outputs_done = false;  // outputs already written for the current solution
   double* h_eps = nullptr;  // pinned: eigenvalues of S, then E_nuc (nao + 1 doubles); then of dm0
   int* h_ints = nullptr;    // pinned: [0] eigensolver status, [1] Cholesky status
+  double* h_dav = nullptr;  // pinned: read-backs of the stability analysis
+  DavState dav;
   std::vector<int> dm0_ids; // eigenvalue indices of the dm0 split (source of an async copy)
 
   ~ScfMol() {
@@ -1086,7 +1098,7 @@ static int soscf_step(ScfMol& M) {
   ScfWork& W = M.W;
   cudaStream_t s = M.s;
   const int nao = M.nao, nmo = M.nmo, nocc = M.nocc, nvir = nmo - nocc;
-  const long ne = (long)nmo * nmo, nvo = (long)nvir * nocc;
+  const long nvo = (long)nvir * nocc;
   const int hprec = M.opt.precision;  // the approximate Hessian uses the mixed exchange when B has its planes
   ProfScope ps("scf_newton_step", s);
   DF_TRY(dgemm(false, false, nmo, nmo, nmo, 1.0, W.Fo, nmo, 0, W.Call, nmo, 0, 0.0, W.T1, nmo, 0, 1, s, 0, 0));
@@ -1177,7 +1189,6 @@ static int rotate_orbitals(ScfMol& M) {
 // pseudo-random vector (so that a mode of another symmetry than the lowest excitations is
 // still reached).  A full subspace collapses onto the current Ritz vector.
 
-constexpr int kDavidsonStart = 3; // start block: two lowest excitations + one pseudo-random
 
 __global__ void scale_copy_kernel(const double* __restrict__ x, double* __restrict__ y, long n,
                                   const double* __restrict__ nrm2) {
@@ -1259,36 +1270,149 @@ static double sym_lowest(std::vector<double> T, int k, std::vector<double>& vec)
   return T[(size_t)lo * k + lo];
 }
 
+// Index of the smallest d[i] (ties: the smaller index), skipping i == *skip when skip is set;
+// written as a double to *out (one CTA).
+__global__ void dav_argmin_kernel(const double* __restrict__ d, long n, const double* __restrict__ skip,
+                                  double* __restrict__ out) {
+  __shared__ double sv[1024];
+  __shared__ long si[1024];
+  const long excl = skip ? (long)*skip : -1;
+  double bv = INFINITY;
+  long bi = -1;
+  for (long i = threadIdx.x; i < n; i += blockDim.x)
+    if (i != excl && (d[i] < bv || (d[i] == bv && (bi < 0 || i < bi)))) {
+      bv = d[i];
+      bi = i;
+    }
+  sv[threadIdx.x] = bv;
+  si[threadIdx.x] = bi;
+  __syncthreads();
+  for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+    if ((int)threadIdx.x < h) {
+      const double ov = sv[threadIdx.x + h];
+      const long oi = si[threadIdx.x + h];
+      if (oi >= 0 && (si[threadIdx.x] < 0 || ov < sv[threadIdx.x] || (ov == sv[threadIdx.x] && oi < si[threadIdx.x]))) {
+        sv[threadIdx.x] = ov;
+        si[threadIdx.x] = oi;
+      }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = (double)(si[0] < 0 ? 0 : si[0]);
+}
+
+// v = unit vector at index *at.
+__global__ void dav_unit_kernel(double* __restrict__ v, long n, const double* __restrict__ at) {
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) v[i] = i == (long)*at ? 1.0 : 0.0;
+}
+
+// SplitMix64 of i + 1 mapped to [-1/2, 1/2): the fixed pseudo-random direction of the start
+// block and of the sign convention of the Ritz vector.
+__device__ __forceinline__ double splitmix_unit(long i) {
+  unsigned long long z = 0x9E3779B97F4A7C15ull * (unsigned long long)(i + 1);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  z ^= z >> 31;
+  return (double)(z >> 11) * (1.0 / 9007199254740992.0) - 0.5;
+}
+
+__global__ void dav_splitmix_kernel(double* __restrict__ v, long n) {
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) v[i] = splitmix_unit(i);
+}
+
+// *out = sum_i x[i] h(i) with h the SplitMix direction (one CTA).
+__global__ void dav_dot_splitmix_kernel(const double* __restrict__ x, long n, double* __restrict__ out) {
+  __shared__ double sh[32];
+  double acc = 0.0;
+  for (long i = threadIdx.x; i < n; i += blockDim.x) acc += x[i] * splitmix_unit(i);
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    acc = (int)threadIdx.x < (int)(blockDim.x >> 5) ? sh[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if (threadIdx.x == 0) *out = acc;
+  }
+}
+
+// x *= a * sign(*sdot) (a zero dot counts as positive).
+__global__ void dav_scale_signed_kernel(double* __restrict__ x, long n, double a, const double* __restrict__ sdot) {
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) x[i] *= (*sdot < 0.0 ? -a : a);
+}
+
 // Orthonormalise w against V[0..m) (classical Gram-Schmidt, two passes, device scalars) and
-// store it normalised as V[m]; *n2 gets its squared norm before the normalisation.
-static int davidson_store(ScfMol& M, double* w, double* V, int m, long nvo, double* n2) {
+// store it normalised as V[m]; its squared norm before the normalisation stays in *n2.
+static int davidson_store(ScfMol& M, double* w, double* V, int m, long nvo, double* n2, double* scratch) {
   cudaStream_t s = M.s;
-  double* sc = M.W.cg_s;
   for (int pass = 0; pass < 2; ++pass)
     for (int i = 0; i < m; ++i) {
-      dot_kernel<<<1, 1024, 0, s>>>(V + (size_t)i * nvo, w, nvo, sc + 14);
+      dot_kernel<<<1, 1024, 0, s>>>(V + (size_t)i * nvo, w, nvo, scratch);
       DF_LAUNCHED("dot_kernel");
-      axpy_dev_kernel<<<blocks_for(nvo), 256, 0, s>>>(w, V + (size_t)i * nvo, nvo, sc + 14);
+      axpy_dev_kernel<<<blocks_for(nvo), 256, 0, s>>>(w, V + (size_t)i * nvo, nvo, scratch);
       DF_LAUNCHED("axpy_dev_kernel");
     }
-  dot_kernel<<<1, 1024, 0, s>>>(w, w, nvo, sc + 12);
+  dot_kernel<<<1, 1024, 0, s>>>(w, w, nvo, n2);
   DF_LAUNCHED("dot_kernel");
-  DF_CUDA(cudaMemcpyAsync(n2, sc + 12, sizeof(double), cudaMemcpyDeviceToHost, s));
-  scale_copy_kernel<<<blocks_for(nvo), 256, 0, s>>>(w, V + (size_t)m * nvo, nvo, sc + 12);
+  scale_copy_kernel<<<blocks_for(nvo), 256, 0, s>>>(w, V + (size_t)m * nvo, nvo, n2);
   DF_LAUNCHED("scale_copy_kernel");
-  DF_CUDA(cudaStreamSynchronize(s));
   return DF_OK;
 }
 
-// mode_scale > 0: also leave mode_scale times the unit Ritz vector of the lowest eigenvalue
-// in W.cg_x, in the (virtual, occupied) basis of the canonical orbitals left in C'_all.
-static int stability_analysis(ScfMol& M, double* hess_min, double mode_scale = 0.0) {
+// Device layout of the Davidson workspace W.dav: V, H V, the Rayleigh-Ritz entries G (row j
+// holds V_i . H V_j, i <= j) and scalars (|r|^2, |t|^2, sign dot, two start indices, scratch).
+struct DavPtrs {
+  double *V, *AV, *G, *misc;
+};
+static DavPtrs dav_ptrs(ScfMol& M) {
+  const long nvo = (long)(M.nmo - M.nocc) * M.nocc;
+  DavPtrs p;
+  p.V = M.W.dav;
+  p.AV = p.V + (size_t)kDavidsonMax * nvo;
+  p.G = p.AV + (size_t)kDavidsonMax * nvo;
+  p.misc = p.G + (size_t)kDavidsonMax * kDavidsonMax;
+  return p;
+}
+constexpr int kDavHost = kDavidsonMax * kDavidsonMax + 8;  // pinned doubles per molecule
+
+// Products H V_j for the vectors without one, their Rayleigh-Ritz entries, and an
+// asynchronous read-back of the new rows of G.
+static int dav_products(ScfMol& M) {
+  DavState& d = M.dav;
+  const long nvo = (long)(M.nmo - M.nocc) * M.nocc;
+  DavPtrs p = dav_ptrs(M);
+  d.row0 = d.have;
+  for (; d.have < d.m; ++d.have) {
+    DF_TRY(soscf_hessian(M, p.V + (size_t)d.have * nvo, p.AV + (size_t)d.have * nvo, M.opt.precision));
+    d.products++;
+    for (int i = 0; i <= d.have; ++i) {
+      dot_kernel<<<1, 1024, 0, M.s>>>(p.V + (size_t)i * nvo, p.AV + (size_t)d.have * nvo, nvo,
+                                      p.G + (size_t)d.have * kDavidsonMax + i);
+      DF_LAUNCHED("dot_kernel");
+    }
+  }
+  DF_CUDA(cudaMemcpyAsync(M.h_dav + (size_t)d.row0 * kDavidsonMax, p.G + (size_t)d.row0 * kDavidsonMax,
+                          sizeof(double) * kDavidsonMax * (d.have - d.row0), cudaMemcpyDeviceToHost, M.s));
+  d.stage = DavState::RITZ;
+  return DF_OK;
+}
+
+// Start of the stability analysis of a converged solution (enqueued only; the host continues
+// with dav_advance once the stream has drained).  mode_scale > 0: the finished analysis
+// leaves mode_scale times the unit Ritz vector of the lowest eigenvalue in W.cg_x, in the
+// (virtual, occupied) basis of the canonical orbitals left in C'_all, with the sign that makes
+// its dot with the SplitMix direction non-negative (so that both precisions turn the same way).
+static int dav_begin(ScfMol& M, double mode_scale) {
   ScfWork& W = M.W;
   cudaStream_t s = M.s;
   const int nao = M.nao, nmo = M.nmo, nocc = M.nocc, nvir = nmo - nocc;
   const long ne = (long)nmo * nmo, nvo = (long)nvir * nocc;
-  *hess_min = NAN;
-  if (nvir <= 0) return DF_OK;
+  DavState& d = M.dav;
+  d = DavState();
+  M.res.hess_min = NAN;
+  if (nvo <= 0) return DF_OK;  // stage stays OFF: nothing to analyse
   // canonical orbitals of the last Fock matrix F' (W.Fo)
   DF_CUDA(cudaMemcpyAsync(W.Fp, W.Fo, sizeof(double) * ne, cudaMemcpyDeviceToDevice, s));
   DF_TRY(eigh_full_rows(W.Fp, nmo, W.eps, W.ZT, W.eig_scratch, W.eig_status, s, W.eig_aux));
@@ -1297,104 +1421,130 @@ static int stability_analysis(ScfMol& M, double* hess_min, double mode_scale = 0
   DF_TRY(dgemm(false, false, nmo, nmo, nmo, 1.0, W.Fo, nmo, 0, W.Call, nmo, 0, 0.0, W.T1, nmo, 0, 1, s, 0, 0));
   DF_TRY(dgemm(true, false, nmo, nmo, nmo, 1.0, W.Call, nmo, 0, W.T1, nmo, 0, 0.0, W.Fmo, nmo, 0, 1, s, 0, 0));
   DF_TRY(dgemm(false, false, nao, nvir, nmo, 1.0, W.X, nmo, 0, W.Call + nocc, nmo, 0, 0.0, W.Lv, nvir, 0, 1, s, 0, 0));
-  const int kmax = (int)std::min<long>(kDavidsonMax, nvo);
-  const int max_products = std::max(2, knob("stability_steps"));
-  const int hprec = M.opt.precision;
-  double* V = W.dav;                                    // [kDavidsonMax][nvo]
-  double* AV = W.dav + (size_t)kDavidsonMax * nvo;      // [kDavidsonMax][nvo]
-  double* dots = AV + (size_t)kDavidsonMax * nvo;       // [kDavidsonMax]
+  d.kmax = (int)std::min<long>(kDavidsonMax, nvo);
+  d.max_products = std::max(2, knob("stability_steps"));
+  d.mode_scale = mode_scale;
+  d.Hs.assign((size_t)kDavidsonMax * kDavidsonMax, 0.0);
+  DavPtrs p = dav_ptrs(M);
+  // start block: the unit vectors of the two smallest eps_a - eps_i, then the SplitMix
+  // direction orthonormalised against them
+  excitation_diag_kernel<<<blocks_for(nvo), 256, 0, s>>>(W.Fmo, nmo, nocc, W.cg_h);
+  DF_LAUNCHED("excitation_diag_kernel");
+  dav_argmin_kernel<<<1, 1024, 0, s>>>(W.cg_h, nvo, nullptr, p.misc + 3);
+  DF_LAUNCHED("dav_argmin_kernel");
+  dav_unit_kernel<<<blocks_for(nvo), 256, 0, s>>>(p.V, nvo, p.misc + 3);
+  DF_LAUNCHED("dav_unit_kernel");
+  d.m = 1;
+  if (nvo >= 2) {
+    dav_argmin_kernel<<<1, 1024, 0, s>>>(W.cg_h, nvo, p.misc + 3, p.misc + 4);
+    DF_LAUNCHED("dav_argmin_kernel");
+    dav_unit_kernel<<<blocks_for(nvo), 256, 0, s>>>(p.V + nvo, nvo, p.misc + 4);
+    DF_LAUNCHED("dav_unit_kernel");
+    d.m = 2;
+  }
+  if (nvo >= 3 && d.kmax >= 3) {
+    dav_splitmix_kernel<<<blocks_for(nvo), 256, 0, s>>>(W.cg_Ap, nvo);
+    DF_LAUNCHED("dav_splitmix_kernel");
+    DF_TRY(davidson_store(M, W.cg_Ap, p.V, 2, nvo, p.misc + 1, p.misc + 5));
+    d.m = 3;
+  }
+  return dav_products(M);
+}
+
+// One host step of the analysis after the stream has drained; *finished once hess_min is set
+// (and, with a mode scale, the scaled Ritz vector is enqueued into W.cg_x).
+static int dav_advance(ScfMol& M, bool* finished) {
+  ScfWork& W = M.W;
+  cudaStream_t s = M.s;
+  DavState& d = M.dav;
+  const int nmo = M.nmo, nocc = M.nocc;
+  const long nvo = (long)(nmo - nocc) * nocc;
+  DavPtrs p = dav_ptrs(M);
   double* x = W.cg_x;
   double* r = W.cg_r;
   double* wv = W.cg_Ap;
-  // start block: the two smallest eps_a - eps_i, then a SplitMix64 vector of the index
-  std::vector<double> dia(nvo);
-  excitation_diag_kernel<<<blocks_for(nvo), 256, 0, s>>>(W.Fmo, nmo, nocc, W.cg_h);
-  DF_LAUNCHED("excitation_diag_kernel");
-  DF_CUDA(cudaMemcpyAsync(dia.data(), W.cg_h, sizeof(double) * nvo, cudaMemcpyDeviceToHost, s));
-  DF_CUDA(cudaStreamSynchronize(s));
-  std::vector<long> order(nvo);
-  for (long q = 0; q < nvo; ++q) order[q] = q;
-  const int nlow = (int)std::min<long>(kDavidsonStart - 1, nvo);
-  std::partial_sort(order.begin(), order.begin() + nlow, order.end(),
-                    [&](long p, long q) { return dia[p] < dia[q]; });
-  std::vector<double> h0(nvo);
-  int m = 0;
-  double n2 = 0.0;
-  for (int b = 0; b < kDavidsonStart && m < kmax; ++b) {
-    if (b < nlow) {
-      std::fill(h0.begin(), h0.end(), 0.0);
-      h0[order[b]] = 1.0;
-    } else {
-      for (long i = 0; i < nvo; ++i) {
-        unsigned long long z = 0x9E3779B97F4A7C15ull * (unsigned long long)(i + 1);
-        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-        z ^= z >> 31;
-        h0[i] = (double)(z >> 11) * (1.0 / 9007199254740992.0) - 0.5;
+  *finished = false;
+  auto finish = [&]() -> int {
+    M.res.hess_min = d.theta;
+    d.stage = DavState::OFF;
+    *finished = true;
+    if (d.mode_scale > 0.0) {  // x is a unit vector (orthonormal V, unit y)
+      dav_dot_splitmix_kernel<<<1, 1024, 0, s>>>(x, nvo, p.misc + 2);
+      DF_LAUNCHED("dav_dot_splitmix_kernel");
+      dav_scale_signed_kernel<<<blocks_for(nvo), 256, 0, s>>>(x, nvo, d.mode_scale, p.misc + 2);
+      DF_LAUNCHED("dav_scale_signed_kernel");
+    }
+    return DF_OK;
+  };
+  switch (d.stage) {
+    case DavState::OFF:
+      *finished = true;
+      return DF_OK;
+    case DavState::RITZ: {
+      for (int j = d.row0; j < d.have; ++j)
+        for (int i = 0; i <= j; ++i)
+          d.Hs[(size_t)i * kDavidsonMax + j] = d.Hs[(size_t)j * kDavidsonMax + i] =
+              M.h_dav[(size_t)j * kDavidsonMax + i];
+      std::vector<double> T((size_t)d.m * d.m);
+      for (int i = 0; i < d.m; ++i)
+        for (int j = 0; j < d.m; ++j) T[(size_t)i * d.m + j] = d.Hs[(size_t)i * kDavidsonMax + j];
+      d.theta = sym_lowest(T, d.m, d.y);
+      // Ritz vector x = V y and residual r = H x - theta x = AV y - theta x
+      DF_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * nvo, s));
+      DF_CUDA(cudaMemsetAsync(r, 0, sizeof(double) * nvo, s));
+      for (int i = 0; i < d.m; ++i) {
+        axpy_kernel<<<blocks_for(nvo), 256, 0, s>>>(x, p.V + (size_t)i * nvo, nvo, d.y[i]);
+        DF_LAUNCHED("axpy_kernel");
+        axpy_kernel<<<blocks_for(nvo), 256, 0, s>>>(r, p.AV + (size_t)i * nvo, nvo, d.y[i]);
+        DF_LAUNCHED("axpy_kernel");
       }
+      axpy_kernel<<<blocks_for(nvo), 256, 0, s>>>(r, x, nvo, -d.theta);
+      DF_LAUNCHED("axpy_kernel");
+      dot_kernel<<<1, 1024, 0, s>>>(r, r, nvo, p.misc + 0);
+      DF_LAUNCHED("dot_kernel");
+      DF_CUDA(cudaMemcpyAsync(M.h_dav + kDavidsonMax * kDavidsonMax, p.misc, sizeof(double), cudaMemcpyDeviceToHost,
+                              s));
+      d.stage = DavState::CHECK;
+      return DF_OK;
     }
-    DF_CUDA(cudaMemcpyAsync(wv, h0.data(), sizeof(double) * nvo, cudaMemcpyHostToDevice, s));
-    DF_TRY(davidson_store(M, wv, V, m, nvo, &n2));
-    if (n2 > 1e-20) m++;
-  }
-  std::vector<double> Hs((size_t)kDavidsonMax * kDavidsonMax, 0.0), hd(kDavidsonMax), y;
-  int have = 0, products = 0;
-  double theta = NAN;
-  for (;;) {
-    for (; have < m; ++have) {  // products and Rayleigh-Ritz entries of the new vectors
-      DF_TRY(soscf_hessian(M, V + (size_t)have * nvo, AV + (size_t)have * nvo, hprec));
-      products++;
-      for (int i = 0; i <= have; ++i) {
-        dot_kernel<<<1, 1024, 0, s>>>(V + (size_t)i * nvo, AV + (size_t)have * nvo, nvo, dots + i);
-        DF_LAUNCHED("dot_kernel");
+    case DavState::CHECK: {
+      const double rn = sqrt(std::max(0.0, M.h_dav[kDavidsonMax * kDavidsonMax]));
+      if (M.opt.verbose) printf("stability: %d products, theta %.10f, |r| %.3e\n", d.products, d.theta, rn);
+      if (rn < 1e-6 * std::max(1.0, fabs(d.theta)) || d.products >= d.max_products || d.m == nvo) return finish();
+      if (d.m == d.kmax) {  // collapse the subspace onto the Ritz vector and its product
+        DF_CUDA(cudaMemcpyAsync(p.V, x, sizeof(double) * nvo, cudaMemcpyDeviceToDevice, s));
+        DF_CUDA(cudaMemcpyAsync(wv, r, sizeof(double) * nvo, cudaMemcpyDeviceToDevice, s));
+        axpy_kernel<<<blocks_for(nvo), 256, 0, s>>>(wv, x, nvo, d.theta);  // H x = r + theta x
+        DF_LAUNCHED("axpy_kernel");
+        DF_CUDA(cudaMemcpyAsync(p.AV, wv, sizeof(double) * nvo, cudaMemcpyDeviceToDevice, s));
+        d.Hs[0] = d.theta;
+        d.m = d.have = 1;
       }
-      DF_CUDA(cudaMemcpyAsync(hd.data(), dots, sizeof(double) * (have + 1), cudaMemcpyDeviceToHost, s));
-      DF_CUDA(cudaStreamSynchronize(s));
-      for (int i = 0; i <= have; ++i) Hs[(size_t)i * kDavidsonMax + have] = Hs[(size_t)have * kDavidsonMax + i] = hd[i];
+      davidson_precond_kernel<<<blocks_for(nvo), 256, 0, s>>>(W.Fmo, nmo, nocc, r, d.theta, wv);
+      DF_LAUNCHED("davidson_precond_kernel");
+      DF_TRY(davidson_store(M, wv, p.V, d.m, nvo, p.misc + 1, p.misc + 5));
+      DF_CUDA(cudaMemcpyAsync(M.h_dav + kDavidsonMax * kDavidsonMax + 1, p.misc + 1, sizeof(double),
+                              cudaMemcpyDeviceToHost, s));
+      d.stage = DavState::NORM;
+      return DF_OK;
     }
-    std::vector<double> T((size_t)m * m);
-    for (int i = 0; i < m; ++i)
-      for (int j = 0; j < m; ++j) T[(size_t)i * m + j] = Hs[(size_t)i * kDavidsonMax + j];
-    theta = sym_lowest(T, m, y);
-    // Ritz vector x = V y and residual r = H x - theta x = AV y - theta x
-    DF_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * nvo, s));
-    DF_CUDA(cudaMemsetAsync(r, 0, sizeof(double) * nvo, s));
-    for (int i = 0; i < m; ++i) {
-      axpy_kernel<<<blocks_for(nvo), 256, 0, s>>>(x, V + (size_t)i * nvo, nvo, y[i]);
-      DF_LAUNCHED("axpy_kernel");
-      axpy_kernel<<<blocks_for(nvo), 256, 0, s>>>(r, AV + (size_t)i * nvo, nvo, y[i]);
-      DF_LAUNCHED("axpy_kernel");
+    case DavState::NORM: {
+      const double n2 = M.h_dav[kDavidsonMax * kDavidsonMax + 1];
+      if (!(n2 > 1e-24)) return finish();  // the correction lies in the subspace
+      d.m++;
+      return dav_products(M);
     }
-    axpy_kernel<<<blocks_for(nvo), 256, 0, s>>>(r, x, nvo, -theta);
-    DF_LAUNCHED("axpy_kernel");
-    dot_kernel<<<1, 1024, 0, s>>>(r, r, nvo, W.cg_s + 13);
-    DF_LAUNCHED("dot_kernel");
-    double rr = 0.0;
-    DF_CUDA(cudaMemcpyAsync(&rr, W.cg_s + 13, sizeof(double), cudaMemcpyDeviceToHost, s));
-    DF_CUDA(cudaStreamSynchronize(s));
-    if (M.opt.verbose) printf("stability: %d products, theta %.10f, |r| %.3e\n", products, theta, sqrt(rr));
-    if (sqrt(rr) < 1e-6 * std::max(1.0, fabs(theta)) || products >= max_products || m == nvo) break;
-    if (m == kmax) {  // collapse the subspace onto the Ritz vector and its product
-      DF_CUDA(cudaMemcpyAsync(V, x, sizeof(double) * nvo, cudaMemcpyDeviceToDevice, s));
-      DF_CUDA(cudaMemcpyAsync(wv, r, sizeof(double) * nvo, cudaMemcpyDeviceToDevice, s));
-      axpy_kernel<<<blocks_for(nvo), 256, 0, s>>>(wv, x, nvo, theta);  // H x = r + theta x
-      DF_LAUNCHED("axpy_kernel");
-      DF_CUDA(cudaMemcpyAsync(AV, wv, sizeof(double) * nvo, cudaMemcpyDeviceToDevice, s));
-      Hs[0] = theta;
-      m = have = 1;
-    }
-    davidson_precond_kernel<<<blocks_for(nvo), 256, 0, s>>>(W.Fmo, nmo, nocc, r, theta, wv);
-    DF_LAUNCHED("davidson_precond_kernel");
-    DF_TRY(davidson_store(M, wv, V, m, nvo, &n2));
-    if (!(n2 > 1e-24)) break;  // the correction lies in the subspace: nothing new to add
-    m++;
   }
-  *hess_min = theta;
-  if (mode_scale > 0.0) {  // x is a unit vector (orthonormal V, unit y)
-    DF_CUDA(cudaMemcpyAsync(wv, x, sizeof(double) * nvo, cudaMemcpyDeviceToDevice, s));
-    DF_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * nvo, s));
-    axpy_kernel<<<blocks_for(nvo), 256, 0, s>>>(x, wv, nvo, mode_scale);
-    DF_LAUNCHED("axpy_kernel");
+  return DF_OK;
+}
+
+// The whole analysis for one molecule, waiting on its stream between the host steps.
+static int stability_analysis(ScfMol& M, double mode_scale) {
+  DF_TRY(dav_begin(M, mode_scale));
+  bool fin = false;
+  while (!fin) {
+    DF_CUDA(cudaStreamSynchronize(M.s));
+    DF_TRY(dav_advance(M, &fin));
   }
   return DF_OK;
 }
@@ -1830,6 +1980,7 @@ static int init_mol(ScfMol& M, const df_molecule* mol, const scf_opts& o, void* 
   M.mol = *mol;
   M.opt = o;
   M.iter_limit = o.max_cycle;
+  M.res.hess_min = NAN;
   M.nao = mol->nao;
   M.naux = mol->naux;
   M.nocc = mol->nelec / 2;
@@ -1904,6 +2055,9 @@ int scf_run_on(const df_molecule* mol, const scf_opts& o, const double* dm0, dou
   DF_CUDA(cudaMallocHost(&hst, sizeof(ScfStatus)));
   DF_CUDA(cudaMallocHost(&heps, sizeof(double) * (mol->nao + 1)));
   DF_CUDA(cudaMallocHost(&hints, sizeof(int) * 2));
+  double* hdav = nullptr;
+  DF_CUDA(cudaMallocHost(&hdav, sizeof(double) * kDavHost));
+  M.h_dav = hdav;
   M.hst = hst;
   M.h_eps = heps;
   M.h_ints = hints;
@@ -1934,11 +2088,12 @@ int scf_run_on(const df_molecule* mol, const scf_opts& o, const double* dm0, dou
     M.res.hess_min = NAN;
     if (!(rc == DF_OK && M.rc == DF_OK && M.res.converged && knob("stability"))) break;
     const bool follow = knob("stability") >= 2 && M.res.stability_restarts < kMaxEscapes;
-    rc = stability_analysis(M, &M.res.hess_min, follow ? kEscapeAngle : 0.0);
+    rc = stability_analysis(M, follow ? kEscapeAngle : 0.0);
     if (rc != DF_OK || !follow || !(M.res.hess_min < kSaddleTol)) break;
     rc = escape_saddle(M);
   }
   *res = M.res;
+  cudaFreeHost(hdav);
   cudaFreeHost(hst);
   cudaFreeHost(heps);
   cudaFreeHost(hints);
@@ -2040,6 +2195,8 @@ extern "C" int scf_run_batch(const df_molecule* mols, int nmol, const scf_opts* 
   DF_CUDA(cudaMallocHost(&hst, sizeof(ScfStatus) * slots));
   DF_CUDA(cudaMallocHost(&heps, sizeof(double) * (size_t)(max_nao + 1) * slots));
   DF_CUDA(cudaMallocHost(&hints, sizeof(int) * 2 * slots));
+  double* hdav = nullptr;
+  DF_CUDA(cudaMallocHost(&hdav, sizeof(double) * kDavHost * slots));
   std::vector<ScfMol*> slot_mol(slots, nullptr);
   std::vector<int> slot_index(slots, -1);
   std::vector<size_t> slot_off(slots, 0);
@@ -2067,6 +2224,7 @@ extern "C" int scf_run_batch(const df_molecule* mols, int nmol, const scf_opts* 
     M->hst = hst + k;
     M->h_eps = heps + (size_t)(max_nao + 1) * k;
     M->h_ints = hints + 2 * k;
+    M->h_dav = hdav + (size_t)kDavHost * k;
     M->dm0 = dm0s ? dm0s[i] : nullptr;
     M->D_out = D_outs ? D_outs[i] : nullptr;
     int r = setup_launch(*M);
@@ -2098,10 +2256,36 @@ extern "C" int scf_run_batch(const df_molecule* mols, int nmol, const scf_opts* 
       case ScfMol::ITER:
         if (scf_iter_finish(*M)) {
           M->phase = ScfMol::DONE;
+          if (M->rc == DF_OK && M->res.converged && knob("stability")) {
+            // outputs of this solution first (the analysis overwrites the orbitals), then the
+            // analysis, advanced like the iterations whenever this stream is idle
+            r = scf_outputs(*M);
+            M->outputs_done = true;
+            const bool follow = knob("stability") >= 2 && M->res.stability_restarts < kMaxEscapes;
+            if (r == DF_OK) r = dav_begin(*M, follow ? kEscapeAngle : 0.0);
+            if (r == DF_OK) M->phase = ScfMol::STAB;
+          }
         } else {
           r = scf_iter_launch(*M, true);
         }
         break;
+      case ScfMol::STAB: {
+        bool fin = false;
+        r = dav_advance(*M, &fin);
+        if (r == DF_OK && fin) {
+          const bool follow = knob("stability") >= 2 && M->res.stability_restarts < kMaxEscapes;
+          if (follow && M->res.hess_min < kSaddleTol) {
+            // a saddle point: turn along its mode and iterate on
+            r = escape_saddle(*M);
+            if (r == DF_OK) r = scf_iter_launch(*M, true);
+            M->outputs_done = false;
+            M->phase = ScfMol::ITER;
+          } else {
+            M->phase = ScfMol::DONE;
+          }
+        }
+        break;
+      }
       case ScfMol::DONE:
         break;
     }
@@ -2113,25 +2297,7 @@ extern "C" int scf_run_batch(const df_molecule* mols, int nmol, const scf_opts* 
     }
     if (M->phase == ScfMol::DONE) {
       const int i = slot_index[k];
-      if (M->rc == DF_OK || M->rc == DF_ERR_NOCONV) DF_TRY(scf_outputs(*M));
-      M->res.hess_min = NAN;
-      if (M->rc == DF_OK && M->res.converged && knob("stability")) {
-        // the outputs are ordered before the analysis, which only uses the workspace
-        const bool follow = knob("stability") >= 2 && M->res.stability_restarts < kMaxEscapes;
-        int sr = stability_analysis(*M, &M->res.hess_min, follow ? kEscapeAngle : 0.0);
-        if (sr == DF_OK && follow && M->res.hess_min < kSaddleTol) {
-          // a saddle point: turn along its mode and iterate on (the outputs are rewritten
-          // when the molecule finishes again)
-          sr = escape_saddle(*M);
-          if (sr == DF_OK) sr = scf_iter_launch(*M, true);
-          if (sr == DF_OK) {
-            M->phase = ScfMol::ITER;
-            return DF_OK;
-          }
-        }
-        if (sr == DF_ERR_CUDA) return sr;
-        if (sr != DF_OK) M->rc = sr;
-      }
+      if ((M->rc == DF_OK || M->rc == DF_ERR_NOCONV) && !M->outputs_done) DF_TRY(scf_outputs(*M));
       results[i] = M->res;
       // the region goes back to the pool only once this stream has finished with it: the
       // outputs above are its last work, so wait for them
@@ -2177,6 +2343,7 @@ extern "C" int scf_run_batch(const df_molecule* mols, int nmol, const scf_opts* 
     cudaStreamDestroy(streams[k]);
   }
   cudaEventDestroy(start);
+  cudaFreeHost(hdav);
   cudaFreeHost(hst);
   cudaFreeHost(heps);
   cudaFreeHost(hints);

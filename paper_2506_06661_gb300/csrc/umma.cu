@@ -141,6 +141,59 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
          | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
+// ---- CTA-pair forms (cta_group::2): two CTAs of a cluster share one M = 256 MMA ---------
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+// Shared::cluster address of the same shared-memory offset in CTA `rank` of this cluster.
+__device__ __forceinline__ uint32_t mapa_rank(uint32_t saddr, uint32_t rank) {
+  uint32_t d;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(d) : "r"(saddr), "r"(rank));
+  return d;
+}
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// TMA load into this CTA's shared memory that completes its bytes on an mbarrier of either
+// CTA of the pair (bar_cluster: shared::cluster address).
+__device__ __forceinline__ void tma_load_2d_pair(void* dst, const CUtensorMap* map, uint32_t bar_cluster, int x,
+                                                 int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, "
+      "%4}], [%2];" ::"r"(smem_u32(dst)),
+      "l"((uint64_t)map), "r"(bar_cluster), "r"(x), "r"(y)
+      : "memory");
+}
+__device__ __forceinline__ void tmem_alloc_pair(uint32_t* dst, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)), "r"(ncols)
+               : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish_pair() {
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc_pair(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void umma_bf16_pair(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                               uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\ttcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(
+          d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+// Arrive on the mbarrier at this shared-memory offset in both CTAs of the pair once the
+// MMAs issued so far have completed.
+__device__ __forceinline__ void umma_commit_pair(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+          smem_u32(bar)),
+      "h"((uint16_t)3)
+      : "memory");
+}
+
 enum Mode { HALF_TRANSFORM = 0, SYRK = 1 };
 
 struct Params {
@@ -381,6 +434,196 @@ __global__ void __launch_bounds__(THREADS, 1) split_bf16_gemm_kernel(const __gri
   }
 }
 
+// ---- exchange SYRK on CTA pairs ------------------------------------------------------------
+// One cluster of two CTAs computes a 256 x 128 block of K (rows row_pair .. +255, columns
+// col0 .. +127) with tcgen05.mma.cta_group::2 (M = 256, N = 128): each CTA stages its own 128
+// rows of the A operand and 64 of the 128 rows of the shared B operand, and the leader CTA
+// (rank 0) issues every MMA, which reads both CTAs' shared memory and writes rows 0..127 of the
+// block into the leader's TMEM and rows 128..255 into the peer's.  Per MMA a CTA reads 4 KB of
+// A and 2 KB of B from its shared memory instead of 4 + 4 KB for a one-CTA 128 x 128 tile, and
+// a stage is 60 KB instead of 80 KB (three stages in flight instead of two).  The plane
+// products and their four accumulators are those of split_bf16_gemm_kernel's SYRK mode.
+//
+// Blocks: double rows of 256 (row blocks 2 mp and 2 mp + 1) times column blocks of 128 up to
+// and including the double row's diagonal, nt <= 2 mp + 1 (the block above the diagonal of
+// row block 2 mp is formed too; the reduction reads m >= n only).  A double row past npad
+// (odd npad / 128) loads zeros (TMA fill) and writes nothing.
+//
+// Barriers: full_bar[s] of the leader counts the bytes of both CTAs' loads of stage s (the
+// peer's loads complete on it through their cluster address); the leader's commits arrive on
+// empty_bar[s] and accum_bar of both CTAs.  Waits are bounded as in the one-CTA kernel.
+
+__host__ __device__ __forceinline__ int pair_col_blocks(int mp, int nblk) { return min(2 * mp + 2, nblk); }
+
+__device__ __forceinline__ void pair_block(int t, int nblk, int& mp, int& nt) {
+  int m = 0;
+  while (t >= pair_col_blocks(m, nblk)) {
+    t -= pair_col_blocks(m, nblk);
+    ++m;
+  }
+  mp = m;
+  nt = t;
+}
+
+template <int NP, int BK>
+__global__ void __launch_bounds__(THREADS, 1) syrk_pair_kernel(const __grid_constant__ Maps maps, const Params p) {
+  extern __shared__ uint8_t dyn_smem[];
+  __shared__ uint64_t full_bar[MAX_STAGES];
+  __shared__ uint64_t empty_bar[MAX_STAGES];
+  __shared__ uint64_t accum_bar;
+  __shared__ uint32_t tmem_base;
+  __shared__ int abort_flag;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t rank = cluster_rank();
+  const int nblk = p.npad / BM;
+  int mp, nt;
+  pair_block((int)(blockIdx.x >> 1), nblk, mp, nt);
+  const int row0 = mp * 2 * BM + (int)rank * BM;  // this CTA's rows of the block
+  const int col0 = nt * BM;                       // the block's columns
+  const int bcol = col0 + (int)rank * (BM / 2);   // this CTA's half of the B rows
+  const int split = blockIdx.y;
+  const int kb0 = split * p.kb_per_split;
+  const int nkb = min(p.kb_per_split, p.num_kb - kb0);
+
+  uint32_t base = smem_u32(dyn_smem);
+  uint32_t pad = (1024u - (base & 1023u)) & 1023u;
+  uint8_t* ring = dyn_smem + pad;
+  constexpr uint32_t a_bytes = BM * BK * 2;        // 128 rows
+  constexpr uint32_t bh_bytes = (BM / 2) * BK * 2; // 64 rows
+  constexpr uint32_t cta_stage = NP * (a_bytes + bh_bytes);
+  constexpr uint32_t ncols = 4 * BM;               // four accumulators of 128 columns
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < p.stages; ++s) {
+      mbar_init(&full_bar[s], 1);
+      mbar_init(&empty_bar[s], 1);
+    }
+    mbar_init(&accum_bar, 1);
+    abort_flag = 0;
+    mbar_fence_init();
+  }
+  if (warp == 0 && lane == 0) {
+#pragma unroll
+    for (int j = 0; j < NP; ++j) {
+      tma_prefetch(&maps.a[j]);
+      tma_prefetch(&maps.b[j]);
+    }
+  }
+  if (warp == 1) {
+    tmem_alloc_pair(&tmem_base, ncols);
+    tmem_relinquish_pair();
+  }
+  tc_fence_before();
+  cluster_sync();  // both CTAs' barriers initialised and TMEM allocated before any remote use
+  tc_fence_after();
+  const uint32_t tmem = tmem_base;
+  int issued = 0;
+
+  if (warp == 0 && lane == 0 && nkb > 0) {
+    // ---- TMA producer (both CTAs) --------------------------------------------------------
+    for (int i = 0; i < nkb; ++i) {
+      const int s = i % p.stages;
+      const uint32_t ph = (uint32_t)(i / p.stages) & 1u;
+      if (!mbar_wait(&empty_bar[s], ph ^ 1u, &abort_flag)) {
+        abort_flag = 1;
+        break;
+      }
+      uint8_t* st = ring + (size_t)s * cta_stage;
+      if (rank == 0) mbar_arrive_expect_tx(&full_bar[s], 2 * cta_stage);
+      const uint32_t bar = mapa_rank(smem_u32(&full_bar[s]), 0);
+      const int kx = (kb0 + i) * BK;
+#pragma unroll
+      for (int j = 0; j < NP; ++j) {
+        tma_load_2d_pair(st + j * a_bytes, &maps.a[j], bar, kx, row0);
+        tma_load_2d_pair(st + NP * a_bytes + j * bh_bytes, &maps.b[j], bar, kx, bcol);
+      }
+      issued = i + 1;
+    }
+  } else if (warp == 1 && lane == 0 && rank == 0 && nkb > 0) {
+    // ---- MMA issuer (leader only) -------------------------------------------------------
+    const uint32_t idesc = idesc_bf16(2 * BM, BM);
+    bool ok = true;
+    for (int i = 0; i < nkb; ++i) {
+      const int s = i % p.stages;
+      const uint32_t ph = (uint32_t)(i / p.stages) & 1u;
+      if (!mbar_wait(&full_bar[s], ph, &abort_flag)) {
+        abort_flag = 1;
+        ok = false;
+        break;
+      }
+      tc_fence_after();
+      const uint32_t st = smem_u32(ring + (size_t)s * cta_stage);
+      uint64_t ad[NP], bd[NP];
+#pragma unroll
+      for (int j = 0; j < NP; ++j) {
+        ad[j] = desc_sw<BK>(st + j * a_bytes);
+        bd[j] = desc_sw<BK>(st + NP * a_bytes + j * bh_bytes);
+      }
+#pragma unroll
+      for (int kk = 0; kk < BK / 16; ++kk) {
+        const uint64_t off = (uint64_t)(kk * 32) >> 4;
+#pragma unroll
+        for (int t = 0; t < NP; ++t)
+#pragma unroll
+          for (int a = 0; a <= t; ++a) {
+            const int b = t - a;
+            const int acc = (a <= 1 && b <= 1) ? t : 3;
+            const bool first = t == 0 || (t == 1 && a == 0) || (t == 2 && a <= 1);
+            umma_bf16_pair(tmem + (uint32_t)(acc * BM), ad[a] + off, bd[b] + off, idesc,
+                           (i > 0 || kk > 0 || !first) ? 1u : 0u);
+          }
+      }
+      umma_commit_pair(&empty_bar[s]);
+    }
+    if (ok) umma_commit_pair(&accum_bar);
+  } else if (warp >= 2) {
+    // ---- epilogue (both CTAs): this CTA's 128 rows from its own TMEM --------------------
+    const int q = warp & 3;
+    const int r = q * 32 + lane;
+    bool ok = (nkb > 0) && mbar_wait(&accum_bar, 0, &abort_flag);
+    if (!ok && nkb > 0) abort_flag = 1;
+    tc_fence_after();
+    const int grow = row0 + r;
+    if (ok && row0 < p.npad) {
+      for (int c = 0; c < BM; c += 16) {
+        uint32_t v[4][16];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) tmem_ld_x16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(k * BM + c), v[k]);
+        tmem_wait_ld();
+        float x[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j)  // smallest first
+          x[j] = ((__uint_as_float(v[3][j]) + __uint_as_float(v[2][j])) + __uint_as_float(v[1][j])) +
+                 __uint_as_float(v[0][j]);
+        float4* dst = reinterpret_cast<float4*>(
+            p.Kpart + DF_IXW(((size_t)split * p.npad + grow) * p.npad + col0 + c, 16,
+                             (size_t)gridDim.y * p.npad * p.npad));
+#pragma unroll
+        for (int j = 0; j < 4; ++j) dst[j] = make_float4(x[4 * j], x[4 * j + 1], x[4 * j + 2], x[4 * j + 3]);
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (abort_flag && warp == 0 && lane == 0) {
+    atomicExch(p.err, 1);
+    // loads still in flight complete on the leader's full barriers: the leader waits
+    // (bounded) for the last phase of every slot it armed
+    if (rank == 0)
+      for (int s = 0; s < p.stages; ++s) {
+        const int last = issued - 1 - ((issued - 1 - s) % p.stages + p.stages) % p.stages;
+        if (issued > 0 && last >= 0 && last % p.stages == s)
+          mbar_wait(&full_bar[s], (uint32_t)(last / p.stages) & 1u, nullptr);
+      }
+  }
+  cluster_sync();  // no CTA leaves while its peer may still signal its barriers or read its TMEM
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc_pair(tmem, ncols);
+  }
+}
+
 }  // namespace umma
 
 // ---- host side -------------------------------------------------------------------------
@@ -431,6 +674,43 @@ static int launch_gemm(const umma::Maps& maps, umma::Params p, dim3 grid, cudaSt
   DF_TRY(umma_prepare());
   umma::split_bf16_gemm_kernel<NP, BK><<<grid, umma::THREADS, smem, s>>>(maps, p);
   DF_LAUNCHED("split_bf16_gemm_kernel");
+  return DF_OK;
+}
+
+// Double-row blocks of the CTA-pair SYRK for npad rows.
+static int pair_blocks(int npad) {
+  const int nblk = npad / umma::BM;
+  int t = 0;
+  for (int mp = 0; 2 * mp < nblk; ++mp) t += umma::pair_col_blocks(mp, nblk);
+  return t;
+}
+
+// CTA-pair exchange SYRK: clusters of two CTAs along x (grid.x = 2 x double-row blocks).
+template <int NP, int BK>
+static int launch_syrk_pair(const umma::Maps& maps, umma::Params p, dim3 grid, cudaStream_t s) {
+  p.b_bytes = (uint32_t)(umma::BM / 2) * BK * 2;
+  p.stage_bytes = NP * (umma::BM * BK * 2 + p.b_bytes);
+  const uint32_t budget = 220 * 1024;
+  p.stages = (int)std::min<uint32_t>(std::min(umma::MAX_STAGES, std::max(2, knob("umma_max_stages"))),
+                                     budget / p.stage_bytes);
+  DF_REQUIRE(p.stages >= 2, DF_ERR_ARG, "pair SYRK: stage too large for shared memory");
+  DF_REQUIRE(grid.x % 2 == 0, DF_ERR_ARG, "pair SYRK: odd grid");
+  const size_t smem = (size_t)p.stages * p.stage_bytes + 1024;
+  DF_TRY(umma_prepare());
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = dim3(umma::THREADS);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 2;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  DF_CUDA(cudaLaunchKernelEx(&cfg, umma::syrk_pair_kernel<NP, BK>, maps, p));
+  DF_LAUNCHED("syrk_pair_kernel");
   return DF_OK;
 }
 
@@ -544,6 +824,9 @@ int umma_prepare() {
   static bool done = false;
   if (!done) {
     const int lim = 220 * 1024 + 1024;
+    DF_CUDA(cudaFuncSetAttribute(umma::syrk_pair_kernel<3, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+    DF_CUDA(cudaFuncSetAttribute(umma::syrk_pair_kernel<4, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+    DF_CUDA(cudaFuncSetAttribute(umma::syrk_pair_kernel<5, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
     DF_CUDA(cudaFuncSetAttribute(umma::split_bf16_gemm_kernel<3, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
     DF_CUDA(cudaFuncSetAttribute(umma::split_bf16_gemm_kernel<4, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
     DF_CUDA(cudaFuncSetAttribute(umma::split_bf16_gemm_kernel<5, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
@@ -662,10 +945,12 @@ int build_K_mixed(const void* B, const BLayout& L, int nao, int naux, const doub
   // twice as many k-blocks are in flight to hide the refills from L2.
   long kdim = (long)naux * ncpad;
   const int ns = syrk_n(NP);
-  const int sbk = knob("syrk_bk") == 16 ? 16 : bk;
+  // knob "syrk_pair": 256 x 128 blocks on CTA pairs (cta_group::2), K boxes of bk
+  const bool pair = knob("syrk_pair") != 0;
+  const int sbk = !pair && knob("syrk_bk") == 16 ? 16 : bk;
   for (int j = 0; j < NP; ++j) {
     DF_TRY(make_map(&maps.a[j], w.Xp[j], kdim, npad, kdim, umma::BM, sbk));
-    DF_TRY(make_map(&maps.b[j], w.Xp[j], kdim, npad, kdim, ns, sbk));
+    DF_TRY(make_map(&maps.b[j], w.Xp[j], kdim, npad, kdim, pair ? umma::BM / 2 : ns, sbk));
   }
   umma::Params q{};
   q.mode = umma::SYRK;
@@ -677,7 +962,13 @@ int build_K_mixed(const void* B, const BLayout& L, int nao, int naux, const doub
   q.Kpart = w.Kpart;
   q.n_lower_tiles = syrk_tiles(npad, NP);
   q.err = w.err;
-  {
+  if (pair) {
+    ProfScope ps("k_syrk_tc", s);
+    dim3 grid((unsigned)(2 * pair_blocks(npad)), (unsigned)nsplit);
+    if (NP == 5) DF_TRY((launch_syrk_pair<5, 32>(maps, q, grid, s)));
+    else if (NP == 4) DF_TRY((launch_syrk_pair<4, 32>(maps, q, grid, s)));
+    else DF_TRY((launch_syrk_pair<3, 64>(maps, q, grid, s)));
+  } else {
     ProfScope ps("k_syrk_tc", s);
     dim3 grid((unsigned)q.n_lower_tiles, (unsigned)nsplit);
     if (sbk == 16) {

@@ -131,3 +131,30 @@ def test_syrk_k_box_16_matches_default(n):
     Ko = oracle.df_k(sysm.B, m.nao, C)
     assert rel(K16, K32.cpu().numpy()) <= 1e-6
     assert rel(K16, Ko) <= 2e-6 and rel(K32, Ko) <= 2e-6
+
+
+@pytest.mark.parametrize("n", [13, 27, 52])
+def test_syrk_cta_pair_matches_default(n):
+    """The exchange SYRK on CTA pairs (knob syrk_pair: cta_group::2, 256 x 128 blocks whose
+    B operand is split between the two CTAs) forms the same plane products into the same four
+    accumulators.  13 centres: one 128-row block, so the peer CTA's rows are all padding; 27:
+    two blocks; 52: three blocks, an odd count.  K must agree with the one-CTA SYRK to FP32-partial
+    rounding and stay within the mixed tolerance of the FP64 oracle."""
+    m = gen.make_molecule(n, gen.molecules.box_for(n), 32)
+    sysm = oscf.build_system(m)
+    rng = np.random.default_rng(n + 1)
+    C = 0.3 * rng.standard_normal((m.nao, max(2, m.nocc)))
+    L = dfscf.metric_chol(m.aux_xyz, m.aux_exp)
+    B = dfscf.build_B(m.ao_xyz, m.ao_exp, m.aux_xyz, m.aux_exp, L, "mixed")
+    old = dfscf.lib().df_tune_get(b"syrk_pair")
+    try:
+        assert dfscf.lib().df_tune_set(b"syrk_pair", 0) == 0
+        _, K1 = dfscf.jk(B, None, C, precision="mixed", want_j=False)
+        assert dfscf.lib().df_tune_set(b"syrk_pair", 1) == 0
+        _, K2 = dfscf.jk(B, None, C, precision="mixed", want_j=False)
+    finally:
+        dfscf.lib().df_tune_set(b"syrk_pair", old)
+    Ko = oracle.df_k(sysm.B, m.nao, C)
+    assert torch.isfinite(K2).all()
+    assert rel(K2, K1.cpu().numpy()) <= 1e-6
+    assert rel(K2, Ko) <= 2e-6 and rel(K1, Ko) <= 2e-6
