@@ -96,6 +96,26 @@ def forward(params, X):
     return h, (pres, acts)
 
 
+def bf16_round(x):
+    """Round to the nearest BF16 value (8 significant bits, ties to even), returned as float64:
+    the top 16 bits of the IEEE single, rounded on the 16 bits dropped.  Finite inputs only."""
+    u = np.ascontiguousarray(np.asarray(x, dtype=np.float32)).view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def forward_bf16(params, X):
+    """BF16 inference: the inputs, every weight matrix and every hidden activation rounded to
+    BF16; products and sums, bias and SiLU exact (FP64); the output layer's result unrounded."""
+    h = bf16_round(X)
+    nl = len(LAYERS)
+    for l in range(nl):
+        W, b = bf16_round(params[2 * l]), np.asarray(params[2 * l + 1], dtype=np.float64)
+        z = h @ W.T + b
+        h = bf16_round(silu(z)) if l < nl - 1 else z
+    return h
+
+
 def loss_and_grad(params, X, Y):
     """MSE loss (mean over N*15 entries) and its gradient w.r.t. every parameter."""
     out, (pres, acts) = forward(params, X)

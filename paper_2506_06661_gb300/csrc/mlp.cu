@@ -12,7 +12,8 @@
 //             are the upper triangle (a <= b, row-major) of a symmetric 5x5 block;
 //   training  mean squared error against the symmetrised converged blocks, Adam, FP32
 //             weights and FP32 arithmetic on CUDA cores;
-//   inference the same network with BF16 weights and activations, FP32 accumulation.
+//   inference the same network with BF16 weights and activations and FP32 accumulation, on
+//             the tensor cores (tcgen05, one CTA per 128 pairs, below).
 // Parameters are one float array: for each layer, W [out][in] then b [out].
 #include <cuda_bf16.h>
 
@@ -21,6 +22,7 @@
 
 #include "common.cuh"
 #include "kernels.cuh"
+#include "tcgen05.cuh"
 
 namespace dfscf {
 namespace mlp {
@@ -183,11 +185,6 @@ __global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ g, 
   p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
 }
 
-__global__ void to_bf16_kernel(const float* __restrict__ x, __nv_bfloat16* __restrict__ y, long n) {
-  long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) y[i] = __float2bfloat16_rn(x[i]);
-}
-
 // ---- features, targets, density ------------------------------------------------------------
 // env[A][k] = 1/8 sum_{C != A, R_AC <= 12} rbf_k(R_AC)
 __global__ void env_kernel(const double* __restrict__ xyz, int natm, float* __restrict__ env) {
@@ -292,9 +289,8 @@ struct Work {
   float* dA;          // gradient w.r.t. the previous activation
   float* grad;        // parameter gradient (NPARAM)
   float* loss;
-  __nv_bfloat16* Wb;  // BF16 copy of the parameters
-  __nv_bfloat16* Hb[NLAYER];
-  __nv_bfloat16* Xb;
+  __nv_bfloat16* Wp;  // BF16 weights of the tensor-core inference, zero-padded per layer
+  int* err;           // bounded wait of the inference kernel gave up
 };
 
 static void layout(int n, Arena* a, Sizer* z, Work* w) {
@@ -303,14 +299,13 @@ static void layout(int n, Arena* a, Sizer* z, Work* w) {
   for (int l = 0; l < NLAYER; ++l) {
     TAKE(float, w->Z[l], (size_t)n * layer_out(l));
     TAKE(float, w->H[l], (size_t)n * layer_out(l));
-    TAKE(__nv_bfloat16, w->Hb[l], (size_t)n * layer_out(l));
   }
   TAKE(float, w->G, (size_t)n * NHID);
   TAKE(float, w->dA, (size_t)n * NHID);
   TAKE(float, w->grad, NPARAM);
   TAKE(float, w->loss, 1);
-  TAKE(__nv_bfloat16, w->Wb, NPARAM);
-  TAKE(__nv_bfloat16, w->Xb, (size_t)n * NIN);
+  TAKE(__nv_bfloat16, w->Wp, (size_t)(2 * NHID * NHID + 128 * NHID + 16 * NHID));
+  TAKE(int, w->err, 1);
 #undef TAKE
 }
 
@@ -329,24 +324,193 @@ static int forward_fp32(const float* P, const float* X, int n, Work& w, cudaStre
   return DF_OK;
 }
 
-// BF16 inference: weights and activations in BF16, FP32 accumulation; output in H[3] (FP32).
-static int forward_bf16(const float* P, const float* X, int n, Work& w, cudaStream_t s) {
-  to_bf16_kernel<<<nb((long)NPARAM), 256, 0, s>>>(P, w.Wb, (long)NPARAM);
-  DF_LAUNCHED("to_bf16_kernel");
-  to_bf16_kernel<<<nb((long)n * NIN), 256, 0, s>>>(X, w.Xb, (long)n * NIN);
-  DF_LAUNCHED("to_bf16_kernel");
-  const __nv_bfloat16* in = w.Xb;
-  for (int l = 0; l < NLAYER; ++l) {
-    int fi = layer_in(l), fo = layer_out(l);
-    DF_TRY((sgemm<false, true, __nv_bfloat16>(n, fo, fi, 1.f, in, fi, w.Wb + w_offset(l), fi, 0.f, w.Z[l], fo, s)));
-    if (l < NLAYER - 1) {
-      bias_act_kernel<__nv_bfloat16><<<nb((long)n * fo), 256, 0, s>>>(w.Z[l], P + b_offset(l), n, fo, 1, w.Hb[l]);
-      in = w.Hb[l];
-    } else {
-      bias_act_kernel<float><<<nb((long)n * fo), 256, 0, s>>>(w.Z[l], P + b_offset(l), n, fo, 0, w.H[l]);
-    }
-    DF_LAUNCHED("bias_act_kernel");
+// ---- BF16 inference on the tensor cores (tcgen05) ---------------------------------------------
+// One CTA runs the whole network for 128 pair rows: the activations of a layer stay in shared
+// memory as the A operand of the next (BF16, K-major, 128-byte swizzle: row r's 16-byte unit u of
+// a 64-element K chunk sits at unit u ^ (r mod 8)), each layer's BF16 weights [out][in] arrive by
+// TMA as the B operand, and one thread issues M = 128, N = 256 (16 for the output layer), K = 16
+// MMAs into an FP32 accumulator in TMEM; the four warps read it back row by row, add the bias
+// and apply SiLU in FP32, and store the BF16 activation (or the FP32 output).  Layer 0's K is
+// padded from 65 to 128 and the output layer's N from 15 to 16 with zeros.
+namespace tc {
+
+constexpr int THREADS = 128;
+constexpr int KPAD0 = 128, NOUTP = 16;
+__host__ __device__ constexpr int kpad(int l) { return l == 0 ? KPAD0 : NHID; }
+__host__ __device__ constexpr int npad(int l) { return l == NLAYER - 1 ? NOUTP : NHID; }
+__host__ __device__ constexpr size_t wp_offset(int l) {
+  size_t o = 0;
+  for (int k = 0; k < l; ++k) o += (size_t)kpad(k) * npad(k);
+  return o;
+}
+constexpr size_t WP_COUNT = wp_offset(NLAYER);
+static_assert(WP_COUNT == 2 * NHID * NHID + 128 * NHID + 16 * NHID, "workspace of the packed weights");
+constexpr uint32_t A_CHUNK = 128 * 64 * 2;       // 128 rows x 64 bf16
+constexpr uint32_t A_BYTES = 4 * A_CHUNK;        // K up to 256
+constexpr uint32_t W_BYTES = NHID * NHID * 2;    // largest layer
+constexpr size_t SMEM = A_BYTES + W_BYTES + 1024;
+
+struct Maps {
+  CUtensorMap w[NLAYER];
+};
+
+// BF16 copies of the weights, zero-padded to [npad(l)][kpad(l)].
+__global__ void pack_weights_kernel(const float* __restrict__ P, __nv_bfloat16* __restrict__ Wp) {
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (long)WP_COUNT) return;
+  int l = 0;
+  while (l + 1 < NLAYER && (size_t)i >= wp_offset(l + 1)) ++l;
+  const long j = i - (long)wp_offset(l);
+  const int o = (int)(j / kpad(l)), k = (int)(j % kpad(l));
+  const float v = (o < layer_out(l) && k < layer_in(l)) ? P[w_offset(l) + (size_t)o * layer_in(l) + k] : 0.f;
+  Wp[i] = __float2bfloat16_rn(v);
+}
+
+// Store 8 consecutive BF16 values of row r, K elements k0 .. k0 + 7 (k0 a multiple of 8), into
+// the swizzled A operand.
+__device__ __forceinline__ void store_a8(uint8_t* A, int r, int k0, const float* v) {
+  __align__(16) __nv_bfloat16 h[8];
+#pragma unroll
+  for (int e = 0; e < 8; ++e) h[e] = __float2bfloat16_rn(v[e]);
+  const int c = k0 >> 6, u = (k0 & 63) >> 3;
+  *reinterpret_cast<uint4*>(A + (size_t)c * A_CHUNK + (size_t)r * 128 + (size_t)((u ^ (r & 7)) << 4)) =
+      *reinterpret_cast<const uint4*>(h);
+}
+
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__global__ void __launch_bounds__(THREADS, 1) mlp_forward_kernel(const __grid_constant__ Maps maps,
+                                                                 const float* __restrict__ X, int n,
+                                                                 const float* __restrict__ P, float* __restrict__ out,
+                                                                 int* __restrict__ err) {
+  using namespace umma;
+  extern __shared__ uint8_t dyn_smem[];
+  __shared__ uint64_t wbar, mbar;
+  __shared__ uint32_t tmem_base;
+  __shared__ int abort_flag;
+  uint32_t base = smem_u32(dyn_smem);
+  uint8_t* A = dyn_smem + ((1024u - (base & 1023u)) & 1023u);
+  uint8_t* W = A + A_BYTES;
+  const int r = threadIdx.x, warp = r >> 5;
+  const long g = (long)blockIdx.x * 128 + r;
+  if (r == 0) {
+    mbar_init(&wbar, 1);
+    mbar_init(&mbar, 1);
+    abort_flag = 0;
+    mbar_fence_init();
   }
+  if (warp == 0) {
+    tmem_alloc(&tmem_base, NHID);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base;
+  auto load_weights = [&](int l) {
+    mbar_arrive_expect_tx(&wbar, (uint32_t)(kpad(l) * npad(l) * 2));
+    for (int c = 0; c < kpad(l) / 64; ++c) tma_load_2d(W + (size_t)c * npad(l) * 128, &maps.w[l], &wbar, c * 64, 0);
+  };
+  if (r == 0) load_weights(0);
+  // layer 0's A operand: the features of this CTA's rows (zero past n and past 65)
+  for (int k0 = 0; k0 < KPAD0; k0 += 8) {
+    float v[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) v[e] = (g < n && k0 + e < NIN) ? X[g * NIN + k0 + e] : 0.f;
+    store_a8(A, r, k0, v);
+  }
+  fence_async_smem();
+  __syncthreads();
+  int loads = 1;
+  bool ok = true;
+  for (int l = 0; l < NLAYER && ok; ++l) {
+    const uint32_t ph = (uint32_t)l & 1u;
+    if (r == 0) {
+      if (!mbar_wait(&wbar, ph, &abort_flag)) {
+        abort_flag = 1;
+      } else {
+        tc_fence_after();
+        const uint32_t idesc = idesc_bf16(128, npad(l));
+        const uint32_t sa = smem_u32(A), sw = smem_u32(W);
+        for (int c = 0; c < kpad(l) / 64; ++c)
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk) {
+            const uint64_t off = (uint64_t)(kk * 32) >> 4;
+            umma_bf16(tmem, desc_sw<64>(sa + c * A_CHUNK) + off, desc_sw<64>(sw + (uint32_t)(c * npad(l) * 128)) + off,
+                      idesc, (c > 0 || kk > 0) ? 1u : 0u);
+          }
+        umma_commit(&mbar);
+      }
+    }
+    __syncthreads();
+    if (!abort_flag && !mbar_wait(&mbar, ph, &abort_flag)) abort_flag = 1;
+    tc_fence_after();
+    __syncthreads();  // every thread has seen the MMAs complete (or the abort): W and A may be overwritten
+    if (abort_flag) {  // the same shared value for every thread after the barrier
+      ok = false;
+      break;
+    }
+    if (r == 0 && l + 1 < NLAYER) {
+      load_weights(l + 1);
+      loads++;
+    }
+    const float* bias = P + b_offset(l);
+    for (int c0 = 0; c0 < npad(l); c0 += 16) {
+      uint32_t v[16];
+      tmem_ld_x16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+      tmem_wait_ld();
+      float h[16];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const int col = c0 + j;
+        const float z = __uint_as_float(v[j]) + (col < layer_out(l) ? bias[col] : 0.f);
+        h[j] = l + 1 < NLAYER ? z / (1.f + __expf(-z)) : z;
+      }
+      if (l + 1 < NLAYER) {
+        store_a8(A, r, c0, h);
+        store_a8(A, r, c0 + 8, h + 8);
+      } else if (g < n) {
+#pragma unroll
+        for (int j = 0; j < NOUT; ++j) out[g * NOUT + j] = h[j];
+      }
+    }
+    tc_fence_before();
+    fence_async_smem();
+    __syncthreads();
+  }
+  if (!ok) {  // no result: NaN rows, the flag, and the weights still in flight
+    if (g < n)
+      for (int j = 0; j < NOUT; ++j) out[g * NOUT + j] = __int_as_float(0x7fc00000);
+    if (r == 0) {
+      atomicExch(err, 1);
+      mbar_wait(&wbar, (uint32_t)(loads - 1) & 1u, nullptr);  // completes the last armed phase
+    }
+  }
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    tmem_dealloc(tmem, NHID);
+  }
+}
+
+}  // namespace tc
+
+// BF16 inference on the tensor cores: output in H[3] (FP32, n x 15).
+static int forward_bf16(const float* P, const float* X, int n, Work& w, cudaStream_t s) {
+  tc::pack_weights_kernel<<<nb((long)tc::WP_COUNT), 256, 0, s>>>(P, w.Wp);
+  DF_LAUNCHED("pack_weights_kernel");
+  tc::Maps maps;
+  for (int l = 0; l < NLAYER; ++l)
+    DF_TRY(make_map(&maps.w[l], w.Wp + tc::wp_offset(l), tc::kpad(l), tc::npad(l), tc::kpad(l), tc::npad(l), 64));
+  static bool attr = false;
+  if (!attr) {
+    DF_CUDA(cudaFuncSetAttribute(tc::mlp_forward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc::SMEM));
+    attr = true;
+  }
+  DF_CUDA(cudaMemsetAsync(w.err, 0, sizeof(int), s));
+  tc::mlp_forward_kernel<<<(unsigned)((n + 127) / 128), tc::THREADS, tc::SMEM, s>>>(maps, X, n, P, w.H[NLAYER - 1],
+                                                                                  w.err);
+  DF_LAUNCHED("mlp_forward_kernel");
   return DF_OK;
 }
 

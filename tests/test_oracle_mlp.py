@@ -131,3 +131,24 @@ def test_trace_normalisation_restores_electron_count(c0_system, c0_scf):
     # a density with non-positive trace is returned unchanged (the gate rejects it)
     neg = -0.5 * Dt
     assert np.array_equal(mlp.normalise_trace(neg, ne), neg)
+
+
+def test_bf16_round_pins():
+    """The oracle's BF16 rounding: representable values are kept, halfway cases go to the
+    even significand, the relative error is at most 2^-8 (8 significant bits), and it agrees with torch's CPU
+    float32 -> bfloat16 cast (round to nearest even)."""
+    import torch
+    from oracle import mlp as om
+    keep = np.array([0.0, 1.0, -2.5, 0.5 + 2.0 ** -8, 3.0 * 2.0 ** -100, 65280.0])
+    assert np.array_equal(om.bf16_round(keep), keep)
+    one = 1.0
+    assert om.bf16_round(one + 2.0 ** -8) == one                        # tie, even neighbour is 1
+    assert om.bf16_round(one + 3 * 2.0 ** -8) == one + 2.0 ** -6         # tie, even neighbour above
+    assert om.bf16_round(one + 2.0 ** -8 + 2.0 ** -20) == one + 2.0 ** -7
+    assert om.bf16_round(-(one + 2.0 ** -8 + 2.0 ** -20)) == -(one + 2.0 ** -7)
+    x = np.random.default_rng(5).standard_normal(20000) * np.exp(np.random.default_rng(6).uniform(-20, 20, 20000))
+    x = x.astype(np.float32).astype(np.float64)
+    r = om.bf16_round(x)
+    assert np.max(np.abs(r - x) / np.abs(x)) <= 2.0 ** -8
+    t = torch.tensor(x, dtype=torch.float32).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(r, t)
