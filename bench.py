@@ -146,14 +146,73 @@ def cpu_cores():
         return os.cpu_count() or 1
 
 
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def oracle_threads(n: int) -> None:
+    """Thread count of the oracle library's OpenMP loops."""
+    import ctypes
+    import oracle
+    f = oracle.lib().omp_set_num_threads
+    f.argtypes = [ctypes.c_int]
+    f(int(n))
+
+
+def cpu_b_build_sample(mol):
+    """Oracle B build on the host: the full metric and its Cholesky factor, then the
+    3-centre rows of orbitals 0 and 1 (2 nao columns of the pair index) whitened by forward
+    substitution; the column part scaled to npair columns.  Returns (seconds estimate, text)."""
+    import oracle
+    t0 = time.perf_counter()
+    L = oracle.cholesky(oracle.int2c(mol.aux_xyz, mol.aux_exp))
+    t1 = time.perf_counter()
+    R = oracle.int3c_rows(mol.ao_xyz, mol.ao_exp, mol.aux_xyz, mol.aux_exp, [0, 1])
+    oracle.whiten(L, R.reshape(R.shape[0], -1))
+    t2 = time.perf_counter()
+    ncol = R.shape[1] * R.shape[2]
+    npair = mol.nao * (mol.nao + 1) // 2
+    est = (t1 - t0) + (t2 - t1) * npair / ncol
+    return est, (f"metric + Cholesky {t1 - t0:.1f} s, then {ncol} of {npair} pair columns integrated and whitened "
+                 f"in {t2 - t1:.1f} s, scaled to all columns")
+
+
 def cpu_baseline_obj(mol, wl_name):
     cores = cpu_cores()
     rows = min(mol.naux, 12 * cores)
     t = cpu_oracle_sample(mol, rows)
     per_build = t * mol.naux / rows
-    return {"value": 1.0 / per_build, "unit": "builds/s", "cores": cores, "kind": "oracle",
-            "sample": f"oracle DF-J + DF-K over the first {rows} of {mol.naux} auxiliary rows of the {wl_name} "
-                      f"workload ({t:.1f} s), scaled linearly in naux to one full Fock build"}
+    out = {"value": 1.0 / per_build, "unit": "builds/s", "cores": cores, "kind": "oracle",
+           "sample": f"oracle DF-J + DF-K over the first {rows} of {mol.naux} auxiliary rows of the {wl_name} "
+                     f"workload ({t:.1f} s), scaled linearly in naux to one full Fock build",
+           "cpu_model": cpu_model()}
+    # one core: the same loops with one OpenMP thread on a smaller slice
+    rows1 = min(mol.naux, 6)
+    oracle_threads(1)
+    try:
+        t1 = cpu_oracle_sample(mol, rows1)
+    finally:
+        oracle_threads(cores)
+    out["one_core"] = {"value": rows1 / (t1 * mol.naux), "unit": "builds/s",
+                       "sample": f"{rows1} auxiliary rows on one thread ({t1:.1f} s), scaled to one full build"}
+    est, text = cpu_b_build_sample(mol)
+    out["b_build"] = {"seconds_estimate": est, "cores": cores, "sample": text}
+    return out
 
 
 def run_reference(args):
@@ -378,9 +437,13 @@ def run_ours(args):
         nht = (-(-ncpad // ntc) + 15) // 16 * 16
         # tensor-core flops issued (padded tiles) and the algorithmic count of the same products
         tc_ht = products * 2.0 * naux * npad * npad * (nht * ntc)
-        syrk_n = 128                                          # 128 x 128 lower tiles (4 accumulators)
-        wide = syrk_n // 128
-        syrk_tiles = sum((mt + wide) // wide for mt in range(npad // 128))
+        syrk_n = 128                                          # 128 x 128 tiles (4 accumulators)
+        nblk = npad // 128
+        if int(dfscf.lib().df_tune_get(b"syrk_pair")):
+            # CTA pairs: 256 x 128 blocks up to each double row's diagonal, two tiles each
+            syrk_tiles = 2 * sum(min(2 * mp + 2, nblk) for mp in range((nblk + 1) // 2))
+        else:
+            syrk_tiles = nblk * (nblk + 1) // 2                # lower 128 x 128 tiles
         tc_syrk = products * 2.0 * (naux * ncpad) * (128 * syrk_n) * syrk_tiles
         rlm = {}
         for name, fl, alg in (("k_halftransform_tc", tc_ht, products * ht_flops),

@@ -603,7 +603,7 @@ struct ScfWork {
   double *Fbar, *Call, *Call2, *Fmo, *Lv, *cg_g, *cg_h, *cg_x, *cg_r, *cg_z, *cg_p, *cg_Ap, *Lf, *Lfp, *Lfm, *dD,
       *dJ, *dK1, *dK2, *cg_s, *kk, *kVrow, *ksig, *Pc, *Ps, *Pd, *ktmp, *KPdK;
   int* k_status;
-  double* dav;  // Davidson subspace of the stability analysis: V, H V [kDavidsonMax][nvir * nocc], dots
+  double* dav;  // Davidson subspace of the stability analysis: V, H V [kDavidsonMax][nvir * nocc], G, Q, scalars
   void* eig_aux;  // p vector and grid barrier of the multi-SM eigensolver
   ScfStatus* st;
   DiisState* diis;
@@ -694,7 +694,7 @@ static void scf_layout(int nao, int naux, int nocc, int precision, Arena* a, Siz
     TAKE(double, w->ktmp, vo);
     TAKE(double, w->KPdK, nn);
     TAKE(int, w->k_status, 1);
-    TAKE(double, w->dav, (size_t)2 * kDavidsonMax * vo + (size_t)kDavidsonMax * kDavidsonMax + 8);
+    TAKE(double, w->dav, (size_t)2 * kDavidsonMax * vo + (size_t)2 * kDavidsonMax * kDavidsonMax + 8);
   }
   TAKE(ScfStatus, w->st, 1);
   TAKE(DiisState, w->diis, 1);
@@ -742,10 +742,11 @@ static int diagonalize_fock(const double* Fm, int nao, int nmo, int nocc, ScfWor
 // ---- one molecule's SCF state machine ----------------------------------------------------------
 // Host state of the stability analysis (Davidson; see dav_begin / dav_advance).
 struct DavState {
-  enum Stage { OFF, RITZ, CHECK, NORM } stage = OFF;
+  enum Stage { OFF, RITZ } stage = OFF;
   int m = 0, have = 0, row0 = 0, products = 0, kmax = 0, max_products = 0;
+  bool added = false;  // the newest vector came from a correction (its norm is checked)
   double theta = NAN, mode_scale = 0.0;
-  std::vector<double> Hs, y;
+  std::vector<double> Hs, Qs, y;
 };
 
 struct ScfMol {
@@ -1362,9 +1363,12 @@ static int davidson_store(ScfMol& M, double* w, double* V, int m, long nvo, doub
 }
 
 // Device layout of the Davidson workspace W.dav: V, H V, the Rayleigh-Ritz entries G (row j
-// holds V_i . H V_j, i <= j) and scalars (|r|^2, |t|^2, sign dot, two start indices, scratch).
+// holds V_i . H V_j, i <= j), the Gram entries Q of H V (row j holds H V_i . H V_j) and scalars
+// (|t|^2 of the newest vector, sign dot, two start indices, scratch).  With orthonormal V and a
+// unit y, the residual of the Ritz pair (theta, V y) has |r|^2 = y^T Q y - theta^2, so the host
+// judges convergence from the read-back of G and Q alone: one round trip per iteration.
 struct DavPtrs {
-  double *V, *AV, *G, *misc;
+  double *V, *AV, *G, *Q, *misc;
 };
 static DavPtrs dav_ptrs(ScfMol& M) {
   const long nvo = (long)(M.nmo - M.nocc) * M.nocc;
@@ -1372,13 +1376,15 @@ static DavPtrs dav_ptrs(ScfMol& M) {
   p.V = M.W.dav;
   p.AV = p.V + (size_t)kDavidsonMax * nvo;
   p.G = p.AV + (size_t)kDavidsonMax * nvo;
-  p.misc = p.G + (size_t)kDavidsonMax * kDavidsonMax;
+  p.Q = p.G + (size_t)kDavidsonMax * kDavidsonMax;
+  p.misc = p.Q + (size_t)kDavidsonMax * kDavidsonMax;
   return p;
 }
-constexpr int kDavHost = kDavidsonMax * kDavidsonMax + 8;  // pinned doubles per molecule
+constexpr int kDavHost = 2 * kDavidsonMax * kDavidsonMax + 8;  // pinned doubles per molecule: G, Q, scalars
+constexpr double kDavTol = 1e-5;                                // residual of the converged Ritz pair
 
-// Products H V_j for the vectors without one, their Rayleigh-Ritz entries, and an
-// asynchronous read-back of the new rows of G.
+// Products H V_j for the vectors without one, their entries of G and Q, and an asynchronous
+// read-back of the new rows with the squared norm of the newest vector.
 static int dav_products(ScfMol& M) {
   DavState& d = M.dav;
   const long nvo = (long)(M.nmo - M.nocc) * M.nocc;
@@ -1391,10 +1397,17 @@ static int dav_products(ScfMol& M) {
       dot_kernel<<<1, 1024, 0, M.s>>>(p.V + (size_t)i * nvo, p.AV + (size_t)d.have * nvo, nvo,
                                       p.G + (size_t)d.have * kDavidsonMax + i);
       DF_LAUNCHED("dot_kernel");
+      dot_kernel<<<1, 1024, 0, M.s>>>(p.AV + (size_t)i * nvo, p.AV + (size_t)d.have * nvo, nvo,
+                                      p.Q + (size_t)d.have * kDavidsonMax + i);
+      DF_LAUNCHED("dot_kernel");
     }
   }
-  DF_CUDA(cudaMemcpyAsync(M.h_dav + (size_t)d.row0 * kDavidsonMax, p.G + (size_t)d.row0 * kDavidsonMax,
-                          sizeof(double) * kDavidsonMax * (d.have - d.row0), cudaMemcpyDeviceToHost, M.s));
+  const size_t rows = (size_t)kDavidsonMax * (d.have - d.row0), at = (size_t)d.row0 * kDavidsonMax;
+  DF_CUDA(cudaMemcpyAsync(M.h_dav + at, p.G + at, sizeof(double) * rows, cudaMemcpyDeviceToHost, M.s));
+  DF_CUDA(cudaMemcpyAsync(M.h_dav + kDavidsonMax * kDavidsonMax + at, p.Q + at, sizeof(double) * rows,
+                          cudaMemcpyDeviceToHost, M.s));
+  DF_CUDA(cudaMemcpyAsync(M.h_dav + 2 * kDavidsonMax * kDavidsonMax, p.misc + 1, sizeof(double),
+                          cudaMemcpyDeviceToHost, M.s));
   d.stage = DavState::RITZ;
   return DF_OK;
 }
@@ -1425,6 +1438,7 @@ static int dav_begin(ScfMol& M, double mode_scale) {
   d.max_products = std::max(2, knob("stability_steps"));
   d.mode_scale = mode_scale;
   d.Hs.assign((size_t)kDavidsonMax * kDavidsonMax, 0.0);
+  d.Qs.assign((size_t)kDavidsonMax * kDavidsonMax, 0.0);
   DavPtrs p = dav_ptrs(M);
   // start block: the unit vectors of the two smallest eps_a - eps_i, then the SplitMix
   // direction orthonormalised against them
@@ -1448,6 +1462,7 @@ static int dav_begin(ScfMol& M, double mode_scale) {
     DF_TRY(davidson_store(M, W.cg_Ap, p.V, 2, nvo, p.misc + 1, p.misc + 5));
     d.m = 3;
   }
+  d.added = false;  // start vectors are checked by construction
   return dav_products(M);
 }
 
@@ -1464,11 +1479,28 @@ static int dav_advance(ScfMol& M, bool* finished) {
   double* r = W.cg_r;
   double* wv = W.cg_Ap;
   *finished = false;
+  if (d.stage == DavState::OFF) {
+    *finished = true;
+    return DF_OK;
+  }
+  const double* hG = M.h_dav;
+  const double* hQ = M.h_dav + kDavidsonMax * kDavidsonMax;
+  const double n2 = M.h_dav[2 * kDavidsonMax * kDavidsonMax];
+  // Ritz vector x = V y of the current (theta, y)
+  auto ritz_vector = [&]() -> int {
+    DF_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * nvo, s));
+    for (int i = 0; i < d.m; ++i) {
+      axpy_kernel<<<blocks_for(nvo), 256, 0, s>>>(x, p.V + (size_t)i * nvo, nvo, d.y[i]);
+      DF_LAUNCHED("axpy_kernel");
+    }
+    return DF_OK;
+  };
   auto finish = [&]() -> int {
     M.res.hess_min = d.theta;
     d.stage = DavState::OFF;
     *finished = true;
     if (d.mode_scale > 0.0) {  // x is a unit vector (orthonormal V, unit y)
+      DF_TRY(ritz_vector());
       dav_dot_splitmix_kernel<<<1, 1024, 0, s>>>(x, nvo, p.misc + 2);
       DF_LAUNCHED("dav_dot_splitmix_kernel");
       dav_scale_signed_kernel<<<blocks_for(nvo), 256, 0, s>>>(x, nvo, d.mode_scale, p.misc + 2);
@@ -1476,66 +1508,52 @@ static int dav_advance(ScfMol& M, bool* finished) {
     }
     return DF_OK;
   };
-  switch (d.stage) {
-    case DavState::OFF:
-      *finished = true;
-      return DF_OK;
-    case DavState::RITZ: {
-      for (int j = d.row0; j < d.have; ++j)
-        for (int i = 0; i <= j; ++i)
-          d.Hs[(size_t)i * kDavidsonMax + j] = d.Hs[(size_t)j * kDavidsonMax + i] =
-              M.h_dav[(size_t)j * kDavidsonMax + i];
-      std::vector<double> T((size_t)d.m * d.m);
-      for (int i = 0; i < d.m; ++i)
-        for (int j = 0; j < d.m; ++j) T[(size_t)i * d.m + j] = d.Hs[(size_t)i * kDavidsonMax + j];
-      d.theta = sym_lowest(T, d.m, d.y);
-      // Ritz vector x = V y and residual r = H x - theta x = AV y - theta x
-      DF_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * nvo, s));
-      DF_CUDA(cudaMemsetAsync(r, 0, sizeof(double) * nvo, s));
-      for (int i = 0; i < d.m; ++i) {
-        axpy_kernel<<<blocks_for(nvo), 256, 0, s>>>(x, p.V + (size_t)i * nvo, nvo, d.y[i]);
-        DF_LAUNCHED("axpy_kernel");
-        axpy_kernel<<<blocks_for(nvo), 256, 0, s>>>(r, p.AV + (size_t)i * nvo, nvo, d.y[i]);
-        DF_LAUNCHED("axpy_kernel");
-      }
-      axpy_kernel<<<blocks_for(nvo), 256, 0, s>>>(r, x, nvo, -d.theta);
-      DF_LAUNCHED("axpy_kernel");
-      dot_kernel<<<1, 1024, 0, s>>>(r, r, nvo, p.misc + 0);
-      DF_LAUNCHED("dot_kernel");
-      DF_CUDA(cudaMemcpyAsync(M.h_dav + kDavidsonMax * kDavidsonMax, p.misc, sizeof(double), cudaMemcpyDeviceToHost,
-                              s));
-      d.stage = DavState::CHECK;
-      return DF_OK;
-    }
-    case DavState::CHECK: {
-      const double rn = sqrt(std::max(0.0, M.h_dav[kDavidsonMax * kDavidsonMax]));
-      if (M.opt.verbose) printf("stability: %d products, theta %.10f, |r| %.3e\n", d.products, d.theta, rn);
-      if (rn < 1e-6 * std::max(1.0, fabs(d.theta)) || d.products >= d.max_products || d.m == nvo) return finish();
-      if (d.m == d.kmax) {  // collapse the subspace onto the Ritz vector and its product
-        DF_CUDA(cudaMemcpyAsync(p.V, x, sizeof(double) * nvo, cudaMemcpyDeviceToDevice, s));
-        DF_CUDA(cudaMemcpyAsync(wv, r, sizeof(double) * nvo, cudaMemcpyDeviceToDevice, s));
-        axpy_kernel<<<blocks_for(nvo), 256, 0, s>>>(wv, x, nvo, d.theta);  // H x = r + theta x
-        DF_LAUNCHED("axpy_kernel");
-        DF_CUDA(cudaMemcpyAsync(p.AV, wv, sizeof(double) * nvo, cudaMemcpyDeviceToDevice, s));
-        d.Hs[0] = d.theta;
-        d.m = d.have = 1;
-      }
-      davidson_precond_kernel<<<blocks_for(nvo), 256, 0, s>>>(W.Fmo, nmo, nocc, r, d.theta, wv);
-      DF_LAUNCHED("davidson_precond_kernel");
-      DF_TRY(davidson_store(M, wv, p.V, d.m, nvo, p.misc + 1, p.misc + 5));
-      DF_CUDA(cudaMemcpyAsync(M.h_dav + kDavidsonMax * kDavidsonMax + 1, p.misc + 1, sizeof(double),
-                              cudaMemcpyDeviceToHost, s));
-      d.stage = DavState::NORM;
-      return DF_OK;
-    }
-    case DavState::NORM: {
-      const double n2 = M.h_dav[kDavidsonMax * kDavidsonMax + 1];
-      if (!(n2 > 1e-24)) return finish();  // the correction lies in the subspace
-      d.m++;
-      return dav_products(M);
-    }
+  if (d.added && !(n2 > 1e-24)) {
+    // the last correction lay in the subspace: drop it and keep the previous Ritz pair
+    d.m--;
+    d.have--;
+    return finish();
   }
-  return DF_OK;
+  for (int j = d.row0; j < d.have; ++j)
+    for (int i = 0; i <= j; ++i) {
+      d.Hs[(size_t)i * kDavidsonMax + j] = d.Hs[(size_t)j * kDavidsonMax + i] = hG[(size_t)j * kDavidsonMax + i];
+      d.Qs[(size_t)i * kDavidsonMax + j] = d.Qs[(size_t)j * kDavidsonMax + i] = hQ[(size_t)j * kDavidsonMax + i];
+    }
+  std::vector<double> T((size_t)d.m * d.m);
+  for (int i = 0; i < d.m; ++i)
+    for (int j = 0; j < d.m; ++j) T[(size_t)i * d.m + j] = d.Hs[(size_t)i * kDavidsonMax + j];
+  d.theta = sym_lowest(T, d.m, d.y);
+  double yQy = 0.0;
+  for (int i = 0; i < d.m; ++i)
+    for (int j = 0; j < d.m; ++j) yQy += d.y[i] * d.Qs[(size_t)i * kDavidsonMax + j] * d.y[j];
+  const double rn = sqrt(std::max(0.0, yQy - d.theta * d.theta));
+  if (M.opt.verbose) printf("stability: %d products, theta %.10f, |r| %.3e\n", d.products, d.theta, rn);
+  if (rn < kDavTol * std::max(1.0, fabs(d.theta)) || d.products >= d.max_products || d.m == nvo) return finish();
+  // x = V y and r = H x - theta x = AV y - theta x
+  DF_TRY(ritz_vector());
+  DF_CUDA(cudaMemsetAsync(r, 0, sizeof(double) * nvo, s));
+  for (int i = 0; i < d.m; ++i) {
+    axpy_kernel<<<blocks_for(nvo), 256, 0, s>>>(r, p.AV + (size_t)i * nvo, nvo, d.y[i]);
+    DF_LAUNCHED("axpy_kernel");
+  }
+  if (d.m == d.kmax) {  // collapse the subspace onto the Ritz vector and its product
+    DF_CUDA(cudaMemcpyAsync(p.V, x, sizeof(double) * nvo, cudaMemcpyDeviceToDevice, s));
+    DF_CUDA(cudaMemcpyAsync(p.AV, r, sizeof(double) * nvo, cudaMemcpyDeviceToDevice, s));  // H x
+    std::fill(d.Hs.begin(), d.Hs.end(), 0.0);
+    std::fill(d.Qs.begin(), d.Qs.end(), 0.0);
+    d.Hs[0] = d.theta;
+    d.Qs[0] = yQy;
+    d.y.assign(1, 1.0);  // the Ritz vector in the collapsed basis
+    d.m = d.have = 1;
+  }
+  axpy_kernel<<<blocks_for(nvo), 256, 0, s>>>(r, x, nvo, -d.theta);
+  DF_LAUNCHED("axpy_kernel");
+  davidson_precond_kernel<<<blocks_for(nvo), 256, 0, s>>>(W.Fmo, nmo, nocc, r, d.theta, wv);
+  DF_LAUNCHED("davidson_precond_kernel");
+  DF_TRY(davidson_store(M, wv, p.V, d.m, nvo, p.misc + 1, p.misc + 5));
+  d.m++;
+  d.added = true;
+  return dav_products(M);
 }
 
 // The whole analysis for one molecule, waiting on its stream between the host steps.

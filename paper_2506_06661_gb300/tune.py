@@ -31,7 +31,8 @@ CACHE = os.environ.get("DFSCF_TUNE_CACHE", os.path.join(os.path.dirname(os.path.
 CANDIDATES = {
     "fp64": {"fp64_ht_cols": [16, 32], "fp64_syrk_split": [0, 4, 9, 18, 36], "jpass2_rows": [128, 256, 512],
              "jpass1_rows": [1, 2]},
-    "mixed": {"ht_n": [0, 64, 128], "syrk_bk": [32, 16], "umma_max_stages": [2, 4, 8], "syrk_split": [0, 16, 44, 88, 176],
+    "mixed": {"ht_n": [0, 64, 128], "syrk_pair": [1, 0], "syrk_bk": [32, 16], "umma_max_stages": [2, 4, 8],
+              "syrk_split": [0, 16, 44, 88, 176],
               "jpass2_rows": [128, 256, 512], "jpass1_rows": [1, 2]},
 }
 

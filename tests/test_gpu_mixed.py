@@ -121,13 +121,16 @@ def test_syrk_k_box_16_matches_default(n):
     L = dfscf.metric_chol(m.aux_xyz, m.aux_exp)
     B = dfscf.build_B(m.ao_xyz, m.ao_exp, m.aux_xyz, m.aux_exp, L, "mixed")
     old = dfscf.lib().df_tune_get(b"syrk_bk")
+    old_pair = dfscf.lib().df_tune_get(b"syrk_pair")
     try:
+        assert dfscf.lib().df_tune_set(b"syrk_pair", 0) == 0   # the K box applies to the one-CTA SYRK
         assert dfscf.lib().df_tune_set(b"syrk_bk", 32) == 0
         _, K32 = dfscf.jk(B, None, C, precision="mixed", want_j=False)
         assert dfscf.lib().df_tune_set(b"syrk_bk", 16) == 0
         _, K16 = dfscf.jk(B, None, C, precision="mixed", want_j=False)
     finally:
         dfscf.lib().df_tune_set(b"syrk_bk", old)
+        dfscf.lib().df_tune_set(b"syrk_pair", old_pair)
     Ko = oracle.df_k(sysm.B, m.nao, C)
     assert rel(K16, K32.cpu().numpy()) <= 1e-6
     assert rel(K16, Ko) <= 2e-6 and rel(K32, Ko) <= 2e-6
