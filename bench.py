@@ -635,29 +635,35 @@ def run_scenario_guess(args):
     import torch
     import gen
     from paper_2506_06661_gb300 import guess
-    t0 = time.perf_counter()
-    train = gen.batch_molecules(args.ntrain, 10, 40, 2)
-    # mixed precision ends with FP64 iterations, so the densities are FP64-converged
+    from paper_2506_06661_gb300 import tune
     slots = args.slots if args.slots > 0 else 32
-    res, Ds = guess.converged_densities(train, slots=slots, precision="mixed")
-    ok = [i for i, r in enumerate(res) if r.converged]
-    t_data = time.perf_counter() - t0
-    X, Y, M = guess.build_dataset([train[i] for i in ok], [Ds[i] for i in ok])
-    del Ds
-    model = guess.GuessModel.create(seed=2)
-    t0 = time.perf_counter()
-    hist = guess.train(model, X, Y, M, epochs=args.epochs, batch=4096, lr=1e-3, seed=2)
-    torch.cuda.synchronize()
-    t_train = time.perf_counter() - t0
-    if args.save_model:
-        model.save(args.save_model)
+    if args.load_model:
+        # a model trained by an earlier run of this scenario (same recipe): evaluation only
+        model = guess.GuessModel.load(args.load_model)
+        train, ok, t_data, t_train, hist, nsamp = [], [], 0.0, 0.0, [None, None], 0
+    else:
+        t0 = time.perf_counter()
+        train = gen.batch_molecules(args.ntrain, 10, 40, 2)
+        # mixed precision ends with FP64 iterations, so the densities are FP64-converged
+        res, Ds = guess.converged_densities(train, slots=slots, precision="mixed")
+        ok = [i for i, r in enumerate(res) if r.converged]
+        t_data = time.perf_counter() - t0
+        X, Y, M = guess.build_dataset([train[i] for i in ok], [Ds[i] for i in ok])
+        nsamp = int(M.sum().item())
+        del Ds
+        model = guess.GuessModel.create(seed=2)
+        t0 = time.perf_counter()
+        hist = guess.train(model, X, Y, M, epochs=args.epochs, batch=4096, lr=1e-3, seed=2)
+        torch.cuda.synchronize()
+        t_train = time.perf_counter() - t0
+        if args.save_model:
+            model.save(args.save_model)
     test = gen.batch_molecules(args.neval, 40, 120, 3)
     ev = guess.evaluate(model, test, slots=slots, precision="mixed")
     core_run = ev.pop("_core_run")
     for key in ("energy_core", "energy_learned", "iterations_core", "iterations_learned"):
         ev.pop(key, None)
     # the learned start's first exchange with coarser cuts of dm0's natural occupations
-    from paper_2506_06661_gb300 import tune
     cuts = {}
     for cut in [int(c) for c in args.dm0_cuts.split(",") if c]:
         old = tune.get_knob("dm0_eig_cut")
@@ -667,8 +673,20 @@ def run_scenario_guess(args):
         cuts[f"1e-{cut}"] = {k: e2[k] for k in ("mean_iter_core", "mean_iter_learned", "same_state", "both_converged",
                                                 "wall_s_core", "wall_s_learned", "guess_used")}
     ev["dm0_cuts"] = cuts
+    # wider gates on the idempotency error of the predicted dm0 (default 1.0)
+    gates = {}
+    for gmax in [float(g) for g in args.guess_idem.split(",") if g]:
+        old = tune.get_knob("guess_idem_max")
+        tune.set_knob("guess_idem_max", int(round(100 * gmax)))
+        e2 = guess.evaluate(model, test, slots=slots, precision="mixed", core_run=core_run)
+        tune.set_knob("guess_idem_max", old)
+        gates[f"{gmax:g}"] = {k: e2[k] for k in ("mean_iter_core", "mean_iter_learned", "same_state", "both_converged",
+                                                 "wall_s_core", "wall_s_learned", "wall_s_predict", "guess_used",
+                                                 "guess_rejected")}
+    ev["idem_gates"] = gates
     out = {"scenario": "guess", "train_molecules": len(train), "train_converged": len(ok),
-           "train_samples": int(M.sum().item()), "data_seconds": t_data, "train_seconds": t_train,
+           "model": args.load_model or "trained in this run",
+           "train_samples": nsamp, "data_seconds": t_data, "train_seconds": t_train,
            "epochs": args.epochs, "mse_first_last": [hist[0], hist[-1]], "eval_molecules": len(test),
            "eval_centres": "40-120 (uniform, seed 3)", "eval": ev}
     print(json.dumps(out), flush=True)
@@ -758,6 +776,9 @@ def main():
     ap.add_argument("--neval", type=int, default=512)
     ap.add_argument("--epochs", type=int, default=20)
     ap.add_argument("--save-model", default="")
+    ap.add_argument("--load-model", default="", help="guess scenario: evaluate this saved model instead of training")
+    ap.add_argument("--guess-idem", default="",
+                    help="guess scenario: also evaluate these gates on the idempotency error of dm0 (e.g. 2,5)")
     ap.add_argument("--indices", default="2,6,156,214,246", help="states scenario: batch molecules to probe")
     ap.add_argument("--probes", type=int, default=4, help="states scenario: perturbed restarts per state")
     ap.add_argument("--angle", type=float, default=0.05, help="states scenario: rotation size (rad)")

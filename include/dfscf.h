@@ -194,8 +194,8 @@ int df_eigh_lowest(double* A, int n, int k, double* w, double* Z, void* work, si
  * dm0 (device [nao][nao], may be NULL): initial density; it need not be idempotent nor
  * have the right electron count (paper, Section "Initial Guess for Mean-field Methods").
  * If dm0 fails the checks |tr(dm0 S) - nelec| / nelec < 0.05 and
- * ||Dx Dx - 2 Dx||_F / ||Dx||_F < 1 with Dx = X^T S dm0 S X (dm0 in the orthonormal basis
- * of X) the core-Hamiltonian guess is used instead.  An accepted dm0 with
+ * ||Dx Dx - 2 Dx||_F / ||Dx||_F < g with Dx = X^T S dm0 S X (dm0 in the orthonormal basis
+ * of X; g = knob "guess_idem_max" / 100, default 1) the core-Hamiltonian guess is used instead.  An accepted dm0 with
  * ||Dx Dx - 2 Dx||_F / ||Dx||_F < 1e-6 (a determinant) starts from its occupied orbitals,
  * which span the nocc leading eigenvectors of Dx; any other accepted dm0 runs a first
  * iteration whose exchange uses the eigen-decomposition of dm0 (scf_run_batch advances the
@@ -226,6 +226,9 @@ typedef struct {
   double switch_tol;  /* mixed -> FP64 switch on |dE|           (3e-8)          */
   double switch_err;  /* mixed -> FP64 switch on max|e|         (3e-5)          */
   int verbose;        /* print one line per iteration to stdout (0)             */
+  const float* guess_params; /* device parameters of the learned-guess network
+                                (guess_mlp_create); with dm0 NULL the starting density
+                                is predicted from the geometry (NULL: core guess)   */
 } scf_opts;
 
 typedef struct {
@@ -438,13 +441,15 @@ int df_j_noalloc(const void* B, int nao, int naux, const double* D, double* J, c
  * "mixed_incremental" (0 or 1), "soscf" (0 or 1) and "soscf_cg" (1..64) shape the SCF as
  * described at scf_run; "stability" (0, 1 or 2) finds the lowest eigenvalue of
  * the orbital Hessian of every converged solution by Davidson's method with the
- * eps_a - eps_i preconditioner, to a residual below 1e-6 or at most "stability_steps"
+ * eps_a - eps_i preconditioner, to a residual below 1e-5 or at most "stability_steps"
  * (2..400, default 60) Hessian products (scf_result.hess_min; the products use the SCF's
  * precision, one J and two exchange builds each); with 2, a solution whose
  * hess_min is below -1e-4 (a saddle point) is turned by 0.3 rad along the Ritz vector of that
  * eigenvalue and the SCF goes on from there in FP64 (Newton steps when "soscf" is on) with a
  * fresh max_cycle budget, at most three times (scf_result.stability_restarts); "dm0_eig_cut" (1..16, default 12) drops natural occupations of a
- * non-idempotent dm0 below 10^-cut of the largest from its first exchange.  Two more knobs bound the multi-SM eigensolver's grid barriers:
+ * non-idempotent dm0 below 10^-cut of the largest from its first exchange; "guess_idem_max"
+ * (1..1000, default 100) is the largest idempotency error of an accepted dm0, in hundredths.
+ * Two more knobs bound the multi-SM eigensolver's grid barriers:
  * "eig_barrier_polls" (256..2^30 polls before a wait gives up with DF_ERR_TIMEOUT; default 2^22, about a second) and "eig_barrier_extra"
  * (0 or 1; 1 makes every barrier wait for one arrival that never comes, so that a test can
  * watch the bounded wait run out; leave it 0).  Host-side process-wide state: change

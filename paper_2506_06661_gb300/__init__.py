@@ -49,7 +49,7 @@ class ScfOpts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("diis_space", ctypes.c_int), ("max_cycle", ctypes.c_int),
                 ("n_fp64_final", ctypes.c_int), ("conv_tol", ctypes.c_double), ("conv_err", ctypes.c_double),
                 ("lindep", ctypes.c_double), ("switch_tol", ctypes.c_double), ("switch_err", ctypes.c_double),
-                ("verbose", ctypes.c_int)]
+                ("verbose", ctypes.c_int), ("guess_params", ctypes.c_void_p)]
 
 
 class ScfResultC(ctypes.Structure):
@@ -364,6 +364,10 @@ def default_opts(**kw) -> ScfOpts:
     for k, v in kw.items():
         if k == "precision":
             v = _PREC[v]
+        elif k == "guess_params" and isinstance(v, torch.Tensor):
+            # the learned guess's parameters (float32, on the device); the caller keeps them alive
+            assert v.dtype == torch.float32 and v.is_cuda and v.is_contiguous()
+            v = v.data_ptr()
         setattr(o, k, v)
     return o
 

@@ -34,6 +34,9 @@ size_t eigh_lowest_scratch_doubles(int n, int k);
 size_t eigh_coop_aux_bytes(int n);
 size_t eigh_full_scratch_doubles(int n);
 int eigh_full_rows(double* A, int n, double* w, double* ZT, double* scratch, int* status, cudaStream_t s, void* aux);
+// S^p over the eigenvalues of S above lindep, from its eigenvector rows ZT and eigenvalues (lowdin.cu).
+int lowdin_power(const double* ZT, const double* s_eig, int n, double lindep, double power, double* scratch,
+                 double* out, cudaStream_t s);
 int eigh_lowest_rows(double* A, int n, int k, double* w, double* ZT, double* scratch, int* status, cudaStream_t s,
                      void* aux);
 int transpose(const double* in, int rows, int cols, double* out, cudaStream_t s);

@@ -21,6 +21,16 @@ __global__ void scaled_rows_kernel(const double* __restrict__ ZT, const double* 
 
 static unsigned nblk(long n) { return (unsigned)((n + 255) / 256); }
 
+// S^p = ZT^T diag(s^p) ZT over the eigenvalues above lindep, from eigenvector rows ZT and
+// eigenvalues s of S (scratch: n x n).
+int lowdin_power(const double* ZT, const double* s_eig, int n, double lindep, double power, double* scratch,
+                 double* out, cudaStream_t s) {
+  const long nn = (long)n * n;
+  scaled_rows_kernel<<<nblk(nn), 256, 0, s>>>(ZT, s_eig, n, lindep, power, scratch);
+  DF_LAUNCHED("scaled_rows_kernel");
+  return dgemm(true, false, n, n, n, 1.0, ZT, n, 0, scratch, n, 0, 0.0, out, n, 0, 1, s, 0, 0);
+}
+
 }  // namespace dfscf
 
 using namespace dfscf;

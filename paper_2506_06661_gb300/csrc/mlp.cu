@@ -309,6 +309,16 @@ static void layout(int n, Arena* a, Sizer* z, Work* w) {
 #undef TAKE
 }
 
+// Inference only (forward_bf16): the output H[3], the packed BF16 weights and the error flag.
+static void layout_infer(int n, Arena* a, Sizer* z, Work* w) {
+#define TAKE(T, ptr, count) \
+  if (a) ptr = a->take<T>(count); else z->take<T>(count);
+  TAKE(float, w->H[NLAYER - 1], (size_t)n * NOUT);
+  TAKE(__nv_bfloat16, w->Wp, (size_t)(2 * NHID * NHID + 128 * NHID + 16 * NHID));
+  TAKE(int, w->err, 1);
+#undef TAKE
+}
+
 static unsigned nb(long n, int t = 256) { return (unsigned)((n + t - 1) / t); }
 
 // FP32 forward: H[3] = network(X).
@@ -635,7 +645,9 @@ extern "C" size_t guess_density_work_bytes(int natm) {
   z.take<double>((size_t)NBF * natm * NBF * natm);
   z.take<double>((size_t)NBF * natm * NBF * natm);
   z.take<double>(1);
-  return z.used + guess_mlp_work_bytes((int)np);
+  Work w;
+  layout_infer((int)np, nullptr, &z, &w);
+  return z.used;
 }
 
 extern "C" int guess_density(const float* params, const double* xyz, int natm, int nelec, const double* Sinvhalf,
@@ -661,7 +673,7 @@ extern "C" int guess_density(const float* params, const double* xyz, int natm, i
   DF_LAUNCHED("pair_feature_kernel");
   Arena b(mw, rest);
   Work w;
-  layout((int)np, &b, nullptr, &w);
+  layout_infer((int)np, &b, nullptr, &w);
   DF_REQUIRE(!b.overflow, DF_ERR_NOMEM, "guess_density: workspace too small");
   DF_TRY(forward_bf16(params, feat, (int)np, w, s));
   // orthonormal-basis density from the predicted blocks, then D0 = S^-1/2 Dt S^-1/2

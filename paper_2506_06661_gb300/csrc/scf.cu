@@ -604,6 +604,8 @@ struct ScfWork {
       *dJ, *dK1, *dK2, *cg_s, *kk, *kVrow, *ksig, *Pc, *Ps, *Pd, *ktmp, *KPdK;
   int* k_status;
   double* dav;  // Davidson subspace of the stability analysis: V, H V [kDavidsonMax][nvir * nocc], G, Q, scalars
+  char* guess_ws;      // learned-guess prediction (guess_density), 5 basis functions per centre
+  size_t guess_bytes;
   void* eig_aux;  // p vector and grid barrier of the multi-SM eigensolver
   ScfStatus* st;
   DiisState* diis;
@@ -616,6 +618,10 @@ static void scf_layout(int nao, int naux, int nocc, int precision, Arena* a, Siz
 #define TAKE(T, ptr, count) \
   if (a) ptr = a->take<T>(count); else z->take<T>(count);
   TAKE(double, w->L, (size_t)naux * naux);
+  // learned starting density from the geometry (scf_opts.guess_params), 5 functions per centre
+  w->guess_bytes = nao % 5 == 0 ? guess_density_work_bytes(nao / 5) : 0;
+  w->guess_ws = nullptr;
+  if (w->guess_bytes) TAKE(char, w->guess_ws, w->guess_bytes);
   TAKE(double, w->pair_tab, 5 * (size_t)npair_of(nao));
   TAKE(double, w->S, nn);
   TAKE(double, w->h, nn);
@@ -921,6 +927,15 @@ static int setup_orthogonalize(ScfMol& M) {
   M.res.nmo = nmo;
   canonical_x_kernel<<<blocks_for((long)nao * nmo), 256, 0, s>>>(W.ZT, W.eps, nao, nmo, W.X);
   DF_LAUNCHED("canonical_x_kernel");
+  if (!M.dm0 && M.opt.guess_params && W.guess_bytes && 5 * M.mol.natm == nao) {
+    // learned starting density: S^-1/2 from the eigen-decomposition of S above (the same
+    // eigenvalues as X), the network's Loewdin-basis blocks, dm0 = S^-1/2 Dt S^-1/2 in W.J;
+    // then the same checks as a caller's dm0
+    DF_TRY(lowdin_power(W.ZT, W.eps, nao, M.opt.lindep, -0.5, W.T1, W.K, s));
+    DF_TRY(guess_density(M.opt.guess_params, M.mol.xyz, M.mol.natm, M.mol.nelec, W.K, W.J, W.guess_ws,
+                         W.guess_bytes, s));
+    M.dm0 = W.J;
+  }
   if (!M.dm0) return finish_guess(M, false, false);
   // dm0 in the orthonormal basis X: Dx = X^T S dm0 S X; then the checks on Dx and Dx Dx
   DF_TRY(dgemm(false, false, nao, nao, nao, 1.0, W.S, nao, 0, M.dm0, nao, 0, 0.0, W.T1, nao, 0, 1, s, 0, 0));
@@ -937,12 +952,12 @@ static int setup_orthogonalize(ScfMol& M) {
 }
 
 // After GUESS_CHECK completed: accept dm0 when its electron count is within 5% and its
-// idempotency error in the orthonormal basis, ||Dx Dx - 2 Dx|| / ||Dx||, is below 1; else
-// fall back to the core guess.
+// idempotency error in the orthonormal basis, ||Dx Dx - 2 Dx|| / ||Dx||, is below
+// knob "guess_idem_max" / 100 (default 1); else fall back to the core guess.
 static int setup_guess(ScfMol& M) {
   const ScfStatus& h = *M.hst;
   int ne = M.mol.nelec;
-  bool use = std::isfinite(h.trDS) && fabs(h.trDS - ne) / ne < 0.05 && h.idem < 1.0;
+  bool use = std::isfinite(h.trDS) && fabs(h.trDS - ne) / ne < 0.05 && h.idem < knob("guess_idem_max") / 100.0;
   M.res.guess = use ? 1 : 2;
   // an idempotent dm0 (the learned guess is one): start from its orbitals
   return finish_guess(M, use, use && h.idem < 1e-6);
@@ -2025,6 +2040,7 @@ extern "C" void scf_default_opts(scf_opts* o) {
   o->switch_tol = 3e-8;
   o->switch_err = 3e-5;
   o->verbose = 0;
+  o->guess_params = nullptr;
 }
 
 extern "C" size_t scf_work_bytes(int nao, int naux, int nocc, int precision) {

@@ -221,11 +221,14 @@ def converged_densities(mols, slots: int = 32, precision: str = "fp64", chunk: i
 
 
 def evaluate(model: GuessModel, mols, slots: int = 32, precision: str = "mixed", want_D: bool = False,
-             core_run=None):
+             core_run=None, in_library: bool = True):
     """Batched SCF from the core guess and from the learned guess on the same molecules.
     With want_D the converged densities of both runs are returned too (keys D_core,
     D_learned), and per-molecule energies and iterations always are.  core_run = (batch
-    result, seconds) of an earlier core-guess run on the same molecules skips that run."""
+    result, seconds) of an earlier core-guess run on the same molecules skips that run.
+    in_library: the batched SCF predicts each starting density itself (scf_opts.guess_params,
+    from the overlap eigen-decomposition it computes anyway); else dm0 comes from
+    predict_density, one molecule after another, before the batch."""
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     if core_run is None:
@@ -236,11 +239,16 @@ def evaluate(model: GuessModel, mols, slots: int = 32, precision: str = "mixed",
         out_core, t_core = core_run
     core = out_core.results
     t0 = time.perf_counter()
-    dm0 = [predict_density(model, m) for m in mols]
-    torch.cuda.synchronize()
-    t_predict = time.perf_counter() - t0
-    out_learned = scf_run_batch(mols, slots=slots, precision=precision, dm0s=dm0, raise_on_noconv=False,
-                                want_D=want_D)
+    if in_library:
+        t_predict = 0.0
+        out_learned = scf_run_batch(mols, slots=slots, precision=precision, guess_params=model.params,
+                                    raise_on_noconv=False, want_D=want_D)
+    else:
+        dm0 = [predict_density(model, m) for m in mols]
+        torch.cuda.synchronize()
+        t_predict = time.perf_counter() - t0
+        out_learned = scf_run_batch(mols, slots=slots, precision=precision, dm0s=dm0, raise_on_noconv=False,
+                                    want_D=want_D)
     learned = out_learned.results
     torch.cuda.synchronize()
     t_learned = time.perf_counter() - t0

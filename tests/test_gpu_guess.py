@@ -167,6 +167,15 @@ def test_trained_guess_reduces_iterations():
     # the network's blocks scaled to the electron count pass the validity gate
     assert ev["guess_used"] >= (3 * len(test_mols)) // 4
     assert ev["mean_iter_learned"] < ev["mean_iter_core"]
+    # the library's own prediction (scf_opts.guess_params, Loewdin factors from the SCF's
+    # eigen-decomposition of S) and the caller's dm0 from predict_density start the same SCF:
+    # the same gate decisions, iteration counts within one, energies within 1e-8 Eh
+    ext = guess.evaluate(model, test_mols, slots=12, precision="fp64", in_library=False,
+                         core_run=ev["_core_run"])
+    assert ext["guess_used"] == ev["guess_used"]
+    for a, b, ea, eb in zip(ev["iterations_learned"], ext["iterations_learned"], ev["energy_learned"],
+                            ext["energy_learned"]):
+        assert abs(a - b) <= 1 and abs(ea - eb) <= 1e-8, (a, b, ea, eb)
 
 
 def test_model_blob_roundtrip_and_rejections(tmp_path):
