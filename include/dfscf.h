@@ -426,9 +426,9 @@ int df_j_noalloc(const void* B, int nao, int naux, const double* D, double* J, c
 /* ---- tuning knobs ------------------------------------------------------------------------
  * Launch parameters chosen by the autotuner (paper_2506_06661_gb300/tune.py): "umma_max_stages"
  * (2..8, the largest shared-memory ring depth of the tensor-core GEMM; as many stages as fit
- * up to that), "syrk_pair" (1, the default: the exchange SYRK as 256 x 128 blocks on CTA
- * pairs, tcgen05 cta_group::2, each CTA staging its own A rows and half of B; 0: one CTA per
- * 128 x 128 tile), "syrk_bk" (one-CTA SYRK only: 32, or 16 for K boxes of 16 elements, so that
+ * up to that), "syrk_pair" (0, the default: one CTA per 128 x 128 tile of the exchange
+ * SYRK; 1: 256 x 128 blocks on CTA pairs, tcgen05 cta_group::2, each CTA staging its own A rows
+ * and half of B), "syrk_bk" (one-CTA SYRK only: 32, or 16 for K boxes of 16 elements, so that
  * twice as many narrower stages are in flight), "syrk_split" and "fp64_syrk_split"
  * (K-dimension splits of the exchange SYRK, 0 = built-in heuristic), "jpass2_rows" (32..512,
  * auxiliary rows per CTA slice of J's second pass), "eig_ctas" (CTAs of the multi-SM

@@ -128,7 +128,7 @@ static Knob g_knobs[] = {
     {"umma_max_stages", 8, 2, 8},    // largest shared-memory ring depth of the tcgen05 GEMM (as many as fit)
     {"syrk_bk", 32, 16, 32},         // K box of the tcgen05 exchange SYRK: 32, or 16 for a deeper ring
     {"syrk_split", 0, 0, 4096},      // K-dimension splits of the tcgen05 exchange SYRK
-    {"syrk_pair", 1, 0, 1},          // exchange SYRK on CTA pairs (cta_group::2, 256 x 128 blocks); 0: one CTA per 128 x 128 tile
+    {"syrk_pair", 0, 0, 1},          // exchange SYRK on CTA pairs (cta_group::2, 256 x 128 blocks); 0: one CTA per 128 x 128 tile
     {"fp64_syrk_split", 0, 0, 4096}, // K-dimension splits of the FP64 exchange SYRK
     {"jpass2_rows", 256, 32, 512},   // auxiliary rows per CTA slice of J's second pass
     {"j_fp64_fma", 0, 0, 1},         // J passes: 0 double-float products on FP32 units, 1 FP64 FMAs

@@ -603,7 +603,7 @@ struct ScfWork {
   double *Fbar, *Call, *Call2, *Fmo, *Lv, *cg_g, *cg_h, *cg_x, *cg_r, *cg_z, *cg_p, *cg_Ap, *Lf, *Lfp, *Lfm, *dD,
       *dJ, *dK1, *dK2, *cg_s, *kk, *kVrow, *ksig, *Pc, *Ps, *Pd, *ktmp, *KPdK;
   int* k_status;
-  double* dav;  // Davidson subspace of the stability analysis: V, H V [kDavidsonMax][nvir * nocc], G, Q, scalars
+  double* dav;  // Davidson subspace of the stability analysis: V, H V [kDavidsonMax][nvir * nocc], G, scalars
   char* guess_ws;      // learned-guess prediction (guess_density), 5 basis functions per centre
   size_t guess_bytes;
   void* eig_aux;  // p vector and grid barrier of the multi-SM eigensolver
@@ -700,7 +700,7 @@ static void scf_layout(int nao, int naux, int nocc, int precision, Arena* a, Siz
     TAKE(double, w->ktmp, vo);
     TAKE(double, w->KPdK, nn);
     TAKE(int, w->k_status, 1);
-    TAKE(double, w->dav, (size_t)2 * kDavidsonMax * vo + (size_t)2 * kDavidsonMax * kDavidsonMax + 8);
+    TAKE(double, w->dav, (size_t)2 * kDavidsonMax * vo + (size_t)kDavidsonMax * kDavidsonMax + 8);
   }
   TAKE(ScfStatus, w->st, 1);
   TAKE(DiisState, w->diis, 1);
@@ -750,9 +750,10 @@ static int diagonalize_fock(const double* Fm, int nao, int nmo, int nocc, ScfWor
 struct DavState {
   enum Stage { OFF, RITZ } stage = OFF;
   int m = 0, have = 0, row0 = 0, products = 0, kmax = 0, max_products = 0;
-  bool added = false;  // the newest vector came from a correction (its norm is checked)
+  bool added = false;    // the newest vector came from a correction (its norm is checked)
+  bool have_rr = false;  // the read-back carries the residual of the previous Ritz pair
   double theta = NAN, mode_scale = 0.0;
-  std::vector<double> Hs, Qs, y;
+  std::vector<double> Hs, y;
 };
 
 struct ScfMol {
@@ -1378,12 +1379,14 @@ static int davidson_store(ScfMol& M, double* w, double* V, int m, long nvo, doub
 }
 
 // Device layout of the Davidson workspace W.dav: V, H V, the Rayleigh-Ritz entries G (row j
-// holds V_i . H V_j, i <= j), the Gram entries Q of H V (row j holds H V_i . H V_j) and scalars
-// (|t|^2 of the newest vector, sign dot, two start indices, scratch).  With orthonormal V and a
-// unit y, the residual of the Ritz pair (theta, V y) has |r|^2 = y^T Q y - theta^2, so the host
-// judges convergence from the read-back of G and Q alone: one round trip per iteration.
+// holds V_i . H V_j, i <= j) and scalars (|r|^2 of the last Ritz pair, |t|^2 of the newest
+// vector, sign dot, two start indices, scratch).  One host round trip per iteration: the step
+// that forms the residual r of a Ritz pair also forms the next correction and its product, and
+// the read-back of their entries carries |r|^2, so convergence is judged one iteration late (an
+// extra product at the end; forming |r|^2 from the Gram matrix of H V instead would cancel
+// catastrophically when |H| is large).
 struct DavPtrs {
-  double *V, *AV, *G, *Q, *misc;
+  double *V, *AV, *G, *misc;
 };
 static DavPtrs dav_ptrs(ScfMol& M) {
   const long nvo = (long)(M.nmo - M.nocc) * M.nocc;
@@ -1391,11 +1394,10 @@ static DavPtrs dav_ptrs(ScfMol& M) {
   p.V = M.W.dav;
   p.AV = p.V + (size_t)kDavidsonMax * nvo;
   p.G = p.AV + (size_t)kDavidsonMax * nvo;
-  p.Q = p.G + (size_t)kDavidsonMax * kDavidsonMax;
-  p.misc = p.Q + (size_t)kDavidsonMax * kDavidsonMax;
+  p.misc = p.G + (size_t)kDavidsonMax * kDavidsonMax;
   return p;
 }
-constexpr int kDavHost = 2 * kDavidsonMax * kDavidsonMax + 8;  // pinned doubles per molecule: G, Q, scalars
+constexpr int kDavHost = kDavidsonMax * kDavidsonMax + 8;  // pinned doubles per molecule: G, scalars
 constexpr double kDavTol = 1e-5;                                // residual of the converged Ritz pair
 
 // Products H V_j for the vectors without one, their entries of G and Q, and an asynchronous
@@ -1412,17 +1414,12 @@ static int dav_products(ScfMol& M) {
       dot_kernel<<<1, 1024, 0, M.s>>>(p.V + (size_t)i * nvo, p.AV + (size_t)d.have * nvo, nvo,
                                       p.G + (size_t)d.have * kDavidsonMax + i);
       DF_LAUNCHED("dot_kernel");
-      dot_kernel<<<1, 1024, 0, M.s>>>(p.AV + (size_t)i * nvo, p.AV + (size_t)d.have * nvo, nvo,
-                                      p.Q + (size_t)d.have * kDavidsonMax + i);
-      DF_LAUNCHED("dot_kernel");
     }
   }
   const size_t rows = (size_t)kDavidsonMax * (d.have - d.row0), at = (size_t)d.row0 * kDavidsonMax;
   DF_CUDA(cudaMemcpyAsync(M.h_dav + at, p.G + at, sizeof(double) * rows, cudaMemcpyDeviceToHost, M.s));
-  DF_CUDA(cudaMemcpyAsync(M.h_dav + kDavidsonMax * kDavidsonMax + at, p.Q + at, sizeof(double) * rows,
-                          cudaMemcpyDeviceToHost, M.s));
-  DF_CUDA(cudaMemcpyAsync(M.h_dav + 2 * kDavidsonMax * kDavidsonMax, p.misc + 1, sizeof(double),
-                          cudaMemcpyDeviceToHost, M.s));
+  DF_CUDA(cudaMemcpyAsync(M.h_dav + kDavidsonMax * kDavidsonMax, p.misc, 2 * sizeof(double), cudaMemcpyDeviceToHost,
+                          M.s));
   d.stage = DavState::RITZ;
   return DF_OK;
 }
@@ -1453,7 +1450,6 @@ static int dav_begin(ScfMol& M, double mode_scale) {
   d.max_products = std::max(2, knob("stability_steps"));
   d.mode_scale = mode_scale;
   d.Hs.assign((size_t)kDavidsonMax * kDavidsonMax, 0.0);
-  d.Qs.assign((size_t)kDavidsonMax * kDavidsonMax, 0.0);
   DavPtrs p = dav_ptrs(M);
   // start block: the unit vectors of the two smallest eps_a - eps_i, then the SplitMix
   // direction orthonormalised against them
@@ -1478,6 +1474,7 @@ static int dav_begin(ScfMol& M, double mode_scale) {
     d.m = 3;
   }
   d.added = false;  // start vectors are checked by construction
+  d.have_rr = false;
   return dav_products(M);
 }
 
@@ -1499,8 +1496,8 @@ static int dav_advance(ScfMol& M, bool* finished) {
     return DF_OK;
   }
   const double* hG = M.h_dav;
-  const double* hQ = M.h_dav + kDavidsonMax * kDavidsonMax;
-  const double n2 = M.h_dav[2 * kDavidsonMax * kDavidsonMax];
+  const double rr_prev = M.h_dav[kDavidsonMax * kDavidsonMax];      // |r|^2 of the previous Ritz pair
+  const double n2 = M.h_dav[kDavidsonMax * kDavidsonMax + 1];       // |t|^2 of the newest vector
   // Ritz vector x = V y of the current (theta, y)
   auto ritz_vector = [&]() -> int {
     DF_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * nvo, s));
@@ -1529,22 +1526,22 @@ static int dav_advance(ScfMol& M, bool* finished) {
     d.have--;
     return finish();
   }
+  const double theta_prev = d.theta;
   for (int j = d.row0; j < d.have; ++j)
-    for (int i = 0; i <= j; ++i) {
+    for (int i = 0; i <= j; ++i)
       d.Hs[(size_t)i * kDavidsonMax + j] = d.Hs[(size_t)j * kDavidsonMax + i] = hG[(size_t)j * kDavidsonMax + i];
-      d.Qs[(size_t)i * kDavidsonMax + j] = d.Qs[(size_t)j * kDavidsonMax + i] = hQ[(size_t)j * kDavidsonMax + i];
-    }
   std::vector<double> T((size_t)d.m * d.m);
   for (int i = 0; i < d.m; ++i)
     for (int j = 0; j < d.m; ++j) T[(size_t)i * d.m + j] = d.Hs[(size_t)i * kDavidsonMax + j];
   d.theta = sym_lowest(T, d.m, d.y);
-  double yQy = 0.0;
-  for (int i = 0; i < d.m; ++i)
-    for (int j = 0; j < d.m; ++j) yQy += d.y[i] * d.Qs[(size_t)i * kDavidsonMax + j] * d.y[j];
-  const double rn = sqrt(std::max(0.0, yQy - d.theta * d.theta));
-  if (M.opt.verbose) printf("stability: %d products, theta %.10f, |r| %.3e\n", d.products, d.theta, rn);
-  if (rn < kDavTol * std::max(1.0, fabs(d.theta)) || d.products >= d.max_products || d.m == nvo) return finish();
-  // x = V y and r = H x - theta x = AV y - theta x
+  if (M.opt.verbose)
+    printf("stability: %d products, theta %.10f, previous |r| %.3e\n", d.products, d.theta,
+           d.have_rr ? sqrt(std::max(0.0, rr_prev)) : -1.0);
+  // converged when the previous pair's residual was below the tolerance (this pair is at
+  // least as good: Rayleigh-Ritz on a larger subspace)
+  if (d.have_rr && sqrt(std::max(0.0, rr_prev)) < kDavTol * std::max(1.0, fabs(theta_prev))) return finish();
+  if (d.products >= d.max_products || d.m == nvo) return finish();
+  // x = V y, r = AV y - theta x and |r|^2 (read back with the next entries)
   DF_TRY(ritz_vector());
   DF_CUDA(cudaMemsetAsync(r, 0, sizeof(double) * nvo, s));
   for (int i = 0; i < d.m; ++i) {
@@ -1555,14 +1552,15 @@ static int dav_advance(ScfMol& M, bool* finished) {
     DF_CUDA(cudaMemcpyAsync(p.V, x, sizeof(double) * nvo, cudaMemcpyDeviceToDevice, s));
     DF_CUDA(cudaMemcpyAsync(p.AV, r, sizeof(double) * nvo, cudaMemcpyDeviceToDevice, s));  // H x
     std::fill(d.Hs.begin(), d.Hs.end(), 0.0);
-    std::fill(d.Qs.begin(), d.Qs.end(), 0.0);
     d.Hs[0] = d.theta;
-    d.Qs[0] = yQy;
     d.y.assign(1, 1.0);  // the Ritz vector in the collapsed basis
     d.m = d.have = 1;
   }
   axpy_kernel<<<blocks_for(nvo), 256, 0, s>>>(r, x, nvo, -d.theta);
   DF_LAUNCHED("axpy_kernel");
+  dot_kernel<<<1, 1024, 0, s>>>(r, r, nvo, p.misc + 0);
+  DF_LAUNCHED("dot_kernel");
+  d.have_rr = true;
   davidson_precond_kernel<<<blocks_for(nvo), 256, 0, s>>>(W.Fmo, nmo, nocc, r, d.theta, wv);
   DF_LAUNCHED("davidson_precond_kernel");
   DF_TRY(davidson_store(M, wv, p.V, d.m, nvo, p.misc + 1, p.misc + 5));

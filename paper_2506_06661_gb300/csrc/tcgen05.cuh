@@ -39,12 +39,24 @@ __device__ __forceinline__ uint32_t mbar_try_wait(uint64_t* bar, uint32_t parity
       : "memory");
   return ok;
 }
-// Bounded wait: false if the phase did not complete within WAIT_LIMIT polls or another
-// role already gave up (abort_flag may be null: no early exit).
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+constexpr uint64_t WAIT_NS = 2000000000ull;  // a wait gives up after 2 s of wall-clock time
+
+// Bounded wait: false if the phase did not complete within WAIT_NS (or WAIT_LIMIT polls) or
+// another role already gave up (abort_flag may be null: no early exit).
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
-  for (uint32_t i = 0; i < WAIT_LIMIT; ++i) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = globaltimer_ns();
+  for (uint32_t i = 1; i < WAIT_LIMIT; ++i) {
     if (mbar_try_wait(bar, parity)) return true;
-    if ((i & 255u) == 255u && abort_flag && *abort_flag) return false;
+    if ((i & 255u) == 0u) {
+      if (abort_flag && *abort_flag) return false;
+      if (globaltimer_ns() - t0 > WAIT_NS) return false;
+    }
   }
   return false;
 }

@@ -108,6 +108,8 @@ __global__ void __launch_bounds__(THREADS, 1) split_bf16_gemm_kernel(const __gri
     kb0 = split * p.kb_per_split;
     nkb = min(p.kb_per_split, p.num_kb - kb0);
   }
+  // a wait of this build already gave up (flag set by another CTA): no work, no waits
+  if (*(volatile const int*)p.err) nkb = 0;
   // 1024-byte aligned ring of stages: [A planes | B planes]
   uint32_t base = smem_u32(dyn_smem);
   uint32_t pad = (1024u - (base & 1023u)) & 1023u;
@@ -328,7 +330,9 @@ __global__ void __launch_bounds__(THREADS, 1) syrk_pair_kernel(const __grid_cons
   const int bcol = col0 + (int)rank * (BM / 2);   // this CTA's half of the B rows
   const int split = blockIdx.y;
   const int kb0 = split * p.kb_per_split;
-  const int nkb = min(p.kb_per_split, p.num_kb - kb0);
+  // a wait of this build already gave up (flag set by another CTA): no work; a peer that
+  // read the flag before it was set gives up on its own waits after WAIT_NS
+  const int nkb = *(volatile const int*)p.err ? 0 : min(p.kb_per_split, p.num_kb - kb0);
 
   uint32_t base = smem_u32(dyn_smem);
   uint32_t pad = (1024u - (base & 1023u)) & 1023u;
