@@ -195,7 +195,7 @@ int df_eigh_lowest(double* A, int n, int k, double* w, double* Z, void* work, si
  * have the right electron count (paper, Section "Initial Guess for Mean-field Methods").
  * If dm0 fails the checks |tr(dm0 S) - nelec| / nelec < 0.05 and
  * ||Dx Dx - 2 Dx||_F / ||Dx||_F < g with Dx = X^T S dm0 S X (dm0 in the orthonormal basis
- * of X; g = knob "guess_idem_max" / 100, default 1) the core-Hamiltonian guess is used instead.  An accepted dm0 with
+ * of X; g = knob "guess_idem_max" / 100, default 2) the core-Hamiltonian guess is used instead.  An accepted dm0 with
  * ||Dx Dx - 2 Dx||_F / ||Dx||_F < 1e-6 (a determinant) starts from its occupied orbitals,
  * which span the nocc leading eigenvectors of Dx; any other accepted dm0 runs a first
  * iteration whose exchange uses the eigen-decomposition of dm0 (scf_run_batch advances the
@@ -448,7 +448,7 @@ int df_j_noalloc(const void* B, int nao, int naux, const double* D, double* J, c
  * eigenvalue and the SCF goes on from there in FP64 (Newton steps when "soscf" is on) with a
  * fresh max_cycle budget, at most three times (scf_result.stability_restarts); "dm0_eig_cut" (1..16, default 12) drops natural occupations of a
  * non-idempotent dm0 below 10^-cut of the largest from its first exchange; "guess_idem_max"
- * (1..1000, default 100) is the largest idempotency error of an accepted dm0, in hundredths.
+ * (1..1000, default 200) is the largest idempotency error of an accepted dm0, in hundredths.
  * Two more knobs bound the multi-SM eigensolver's grid barriers:
  * "eig_barrier_polls" (256..2^30 polls before a wait gives up with DF_ERR_TIMEOUT; default 2^22, about a second) and "eig_barrier_extra"
  * (0 or 1; 1 makes every barrier wait for one arrival that never comes, so that a test can

@@ -135,7 +135,7 @@ static Knob g_knobs[] = {
     {"jpass1_rows", 1, 1, 8},        // auxiliary rows per CTA of J's first pass (1, 2, 4 or 8)
     {"fp64_ht_cols", 0, 0, 32},      // FP64 half-transform tile columns: 0 auto, 16 or 32
     {"dm0_eig_cut", 12, 1, 16},      // first exchange of a fractional dm0: occupations below 10^-cut dropped
-    {"guess_idem_max", 100, 1, 1000},// largest idempotency error of an accepted dm0, in hundredths
+    {"guess_idem_max", 200, 1, 1000},// largest idempotency error of an accepted dm0, in hundredths
     {"ht_n", 0, 0, 256},             // tcgen05 half-transform tile columns: 0 widest that fits, else a cap
     {"eig_ctas", 0, 0, 4096},        // CTAs of the multi-SM eigensolver (0 auto, 1 single CTA)
     {"mixed_planes", 5, 3, 5},       // BF16 planes per operand of the mixed exchange (3, 4, 5: 6, 10, 15 products)

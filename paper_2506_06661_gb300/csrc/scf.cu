@@ -954,7 +954,7 @@ static int setup_orthogonalize(ScfMol& M) {
 
 // After GUESS_CHECK completed: accept dm0 when its electron count is within 5% and its
 // idempotency error in the orthonormal basis, ||Dx Dx - 2 Dx|| / ||Dx||, is below
-// knob "guess_idem_max" / 100 (default 1); else fall back to the core guess.
+// knob "guess_idem_max" / 100 (default 2); else fall back to the core guess.
 static int setup_guess(ScfMol& M) {
   const ScfStatus& h = *M.hst;
   int ne = M.mol.nelec;
