@@ -492,6 +492,21 @@ def run_ours(args):
                  "mean_iterations": float(np.mean([r.iterations for r in res])),
                  "mean_fp64_iterations": float(np.mean([r.fp64_iterations for r in res])),
                  "max_in_flight": args.batch_slots, "knobs": batch_knobs or "library defaults"}
+        # the same batch with the stability analysis of every solution and the escape from
+        # saddle points (knob stability = 2), so that every molecule ends in a minimum
+        tune.set_knob("stability", 2)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res2 = dfscf.scf_run_batch(devs, slots=args.batch_slots, precision="mixed", raise_on_noconv=False).results
+        torch.cuda.synchronize()
+        dt2 = time.perf_counter() - t0
+        tune.set_knob("stability", 0)
+        hm = np.array([r.hess_min for r in res2], dtype=float)
+        batch["with_saddle_escape"] = {
+            "seconds": dt2, "molecules_per_s": len(mols) / dt2, "converged": int(sum(r.converged for r in res2)),
+            "saddle_escapes": int(sum(r.stability_restarts for r in res2)),
+            "min_hess_min": float(np.nanmin(hm)) if np.isfinite(hm).any() else None,
+            "negative_hess_min": int(np.sum(hm < 0))}
         del devs
 
     line = {"metric": METRIC, "value": value, "unit": "builds/s", "n_gpus": ws, "steps": args.steps,
