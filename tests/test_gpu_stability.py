@@ -19,11 +19,10 @@ the GPU must end there, stationary under the oracle's Fock build.
 """
 import numpy as np
 import pytest
-from scipy.linalg import expm
 
 import gen
-import oracle
 from oracle import scf as oscf
+from stability_fd import escape, fd_hessian, fd_hessian_eigenvalues, h10_ring
 
 pytestmark = pytest.mark.gpu
 dfscf = pytest.importorskip("paper_2506_06661_gb300")
@@ -38,37 +37,6 @@ def _with_knobs(fn, **knobs):
     finally:
         for k, v in old.items():
             dfscf.lib().df_tune_set(k.encode(), v)
-
-
-def fock(sysm, D):
-    return sysm.h + oracle.df_j(sysm.B, sysm.nao, D) - 0.5 * oracle.df_k_dm(sysm.B, sysm.nao, D)
-
-
-def fd_hessian_eigenvalues(sysm, D):
-    X = oscf.canonical_orthogonalization(sysm.S)
-    nocc = sysm.nocc
-    _, Cp = np.linalg.eigh(X.T @ fock(sysm, D) @ X)
-    nmo = Cp.shape[1]
-    nvir = nmo - nocc
-
-    def grad(kappa):                       # 4 F_vo of the orbitals X C' exp(A(kappa))
-        A = np.zeros((nmo, nmo))
-        A[nocc:, :nocc] = kappa
-        A[:nocc, nocc:] = -kappa.T
-        C = X @ Cp @ expm(A)
-        Co = C[:, :nocc]
-        F = fock(sysm, 2 * Co @ Co.T)
-        return 4 * (C[:, nocc:].T @ F @ Co)
-
-    h = 1e-4
-    n = nvir * nocc
-    H = np.zeros((n, n))
-    for q in range(n):
-        e = np.zeros(n)
-        e[q] = h
-        H[:, q] = ((grad(e.reshape(nvir, nocc)) - grad(-e.reshape(nvir, nocc))) / (2 * h)).ravel()
-    assert np.abs(H - H.T).max() <= 1e-6 * np.abs(H).max()
-    return np.linalg.eigvalsh(0.5 * (H + H.T))
 
 
 def test_hess_min_matches_finite_difference_hessian():
@@ -105,15 +73,6 @@ def test_stability_off_by_default(c0):
     assert np.isnan(r.hess_min)
 
 
-def h10_ring(d=4.5):
-    """Ten centres on a regular ring with neighbours d bohr apart (centred at (10, 10, 10))."""
-    n = 10
-    R = d / (2 * np.sin(np.pi / n))
-    ang = 2 * np.pi * np.arange(n) / n
-    xyz = np.stack([R * np.cos(ang), R * np.sin(ang), np.zeros(n)], 1) + 10.0
-    return gen.molecules.molecule_from_geometry(xyz)
-
-
 @pytest.fixture(scope="module")
 def ring_states():
     """The stretched ring's symmetric RHF solution (reached by DIIS from the core guess) is a
@@ -124,36 +83,10 @@ def ring_states():
     sysm = oscf.build_system(mol)
     sad = oscf.rhf(sysm)
     assert sad.converged
-    lam_sad = fd_hessian_eigenvalues(sysm, sad.D)
+    H, XC = fd_hessian(sysm, sad.D)
+    lam_sad = np.linalg.eigvalsh(H)
     assert lam_sad[0] < -0.05          # 4 x (-0.0243)
-    X = oscf.canonical_orthogonalization(sysm.S)
-    _, Cp = np.linalg.eigh(X.T @ fock(sysm, sad.D) @ X)
-    nocc, nmo = sysm.nocc, Cp.shape[1]
-    # the negative mode, from the same finite differences
-    h = 1e-4
-    nvir = nmo - nocc
-
-    def grad(kappa):
-        A = np.zeros((nmo, nmo))
-        A[nocc:, :nocc] = kappa
-        A[:nocc, nocc:] = -kappa.T
-        C = X @ Cp @ expm(A)
-        Co = C[:, :nocc]
-        return 4 * (C[:, nocc:].T @ fock(sysm, 2 * Co @ Co.T) @ Co)
-
-    n = nvir * nocc
-    H = np.zeros((n, n))
-    for q in range(n):
-        e = np.zeros(n)
-        e[q] = h
-        H[:, q] = ((grad(e.reshape(nvir, nocc)) - grad(-e.reshape(nvir, nocc))) / (2 * h)).ravel()
-    w, V = np.linalg.eigh(0.5 * (H + H.T))
-    u = 0.3 * V[:, 0].reshape(nvir, nocc)
-    A = np.zeros((nmo, nmo))
-    A[nocc:, :nocc] = u
-    A[:nocc, nocc:] = -u.T
-    Co = (X @ Cp @ expm(A))[:, :nocc]
-    low = oscf.rhf(sysm, dm0=2 * Co @ Co.T)
+    low = escape(sysm, sad.D, H, XC)
     assert low.converged and low.energy < sad.energy - 1e-3
     lam_low = fd_hessian_eigenvalues(sysm, low.D)
     assert lam_low[0] > 0
