@@ -410,6 +410,7 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_forward_kernel(const __grid_co
     mbar_fence_init();
   }
   if (warp == 0) {
+    __syncwarp();  // lane 0 initialised the barriers above: the allocation is warp-collective
     tmem_alloc(&tmem_base, NHID);
     tmem_relinquish();
   }
