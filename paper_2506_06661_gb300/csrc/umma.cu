@@ -210,6 +210,7 @@ __global__ void __launch_bounds__(THREADS, 1) split_bf16_gemm_kernel(const __gri
     const int q = warp & 3;  // TMEM lane quarter this warp may access
     const int r = q * 32 + lane;
     bool ok = (nkb > 0) && mbar_wait(&accum_bar, 0, &abort_flag);
+    ok = __all_sync(0xffffffffu, ok);  // the TMEM loads below are warp-collective
     if (!ok && nkb > 0) abort_flag = 1;
     tc_fence_after();
     if (ok) {
@@ -430,6 +431,7 @@ __global__ void __launch_bounds__(THREADS, 1) syrk_pair_kernel(const __grid_cons
     const int q = warp & 3;
     const int r = q * 32 + lane;
     bool ok = (nkb > 0) && mbar_wait(&accum_bar, 0, &abort_flag);
+    ok = __all_sync(0xffffffffu, ok);  // the TMEM loads below are warp-collective
     if (!ok && nkb > 0) abort_flag = 1;
     tc_fence_after();
     const int grow = row0 + r;
