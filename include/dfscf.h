@@ -195,11 +195,16 @@ int df_eigh_lowest(double* A, int n, int k, double* w, double* Z, void* work, si
  * have the right electron count (paper, Section "Initial Guess for Mean-field Methods").
  * If dm0 fails the checks |tr(dm0 S) - nelec| / nelec < 0.05 and
  * ||Dx Dx - 2 Dx||_F / ||Dx||_F < g with Dx = X^T S dm0 S X (dm0 in the orthonormal basis
- * of X; g = knob "guess_idem_max" / 100, default 2) the core-Hamiltonian guess is used instead.  An accepted dm0 with
+ * of X; g = knob "guess_idem_max" / 100, default 2) the core-Hamiltonian guess is used
+ * instead.  An accepted dm0 with
  * ||Dx Dx - 2 Dx||_F / ||Dx||_F < 1e-6 (a determinant) starts from its occupied orbitals,
  * which span the nocc leading eigenvectors of Dx; any other accepted dm0 runs a first
  * iteration whose exchange uses the eigen-decomposition of dm0 (scf_run_batch advances the
- * other molecules while that decomposition runs).
+ * other molecules while that decomposition runs).  With dm0 NULL and opt->guess_params set
+ * (the learned guess's parameters, guess_mlp_create layout) the SCF predicts dm0 itself during
+ * set-up (guess_density with S^-1/2 from the overlap eigen-decomposition it computes for X;
+ * molecules whose nao is not 5 natm use the core guess), then applies the same checks;
+ * res.guess reports 1 (used) or 2 (rejected).
  * Outputs (device, may be NULL): D_out [nao][nao], C_out [nao][nocc], mo_energy [nocc+1].
  * res is HOST memory.  The host loop reads one small status block per iteration.       */
 typedef struct {
