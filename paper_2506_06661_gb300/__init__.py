@@ -178,7 +178,8 @@ def _stream():
 def _ptr(t):
     if t is None:
         return None
-    assert t.is_cuda and t.is_contiguous(), "tensors passed to the library must be contiguous CUDA tensors"
+    if not (t.is_cuda and t.is_contiguous()):
+        raise TypeError("tensors passed to the library must be contiguous CUDA tensors")
     return ctypes.c_void_p(t.data_ptr())
 
 
@@ -366,7 +367,8 @@ def default_opts(**kw) -> ScfOpts:
             v = _PREC[v]
         elif k == "guess_params" and isinstance(v, torch.Tensor):
             # the learned guess's parameters (float32, on the device); the caller keeps them alive
-            assert v.dtype == torch.float32 and v.is_cuda and v.is_contiguous()
+            if not (v.dtype == torch.float32 and v.is_cuda and v.is_contiguous()):
+                raise TypeError("guess_params must be a contiguous float32 CUDA tensor")
             v = v.data_ptr()
         setattr(o, k, v)
     return o

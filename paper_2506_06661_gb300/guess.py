@@ -39,7 +39,8 @@ def init_params(seed: int = 0) -> np.ndarray:
         parts.append(rng.uniform(-bound, bound, size=(fan_out, fan_in)).ravel())
         parts.append(np.zeros(fan_out))
     flat = np.concatenate(parts)
-    assert flat.size == param_count()
+    if flat.size != param_count():
+        raise RuntimeError(f"initial parameters: {flat.size} values, the library expects {param_count()}")
     return flat
 
 
