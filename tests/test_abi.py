@@ -4,6 +4,8 @@ import ctypes
 import os
 import re
 
+import pytest
+
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
@@ -101,3 +103,15 @@ def test_header_is_plain_c_and_links():
            "-L", os.path.dirname(lib_path), "-l:" + os.path.basename(lib_path), "-o", os.devnull]
     r = subprocess.run(cmd, input=prog, capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
+
+
+def test_host_tensors_are_refused_before_reaching_the_library():
+    """The binding hands only contiguous CUDA tensors to the C ABI: a host tensor (or a
+    non-contiguous one) raises TypeError instead of passing a host pointer to device code."""
+    import torch
+    import paper_2506_06661_gb300 as dfscf
+    with pytest.raises(TypeError):
+        dfscf._ptr(torch.zeros(4, dtype=torch.float64))
+    with pytest.raises(TypeError):
+        dfscf.default_opts(guess_params=torch.zeros(4, dtype=torch.float32))
+    assert dfscf._ptr(None) is None
